@@ -1,0 +1,117 @@
+"""Seeded synthetic inputs for the collapsing-water-column pressure Poisson problems.
+
+This module only draws random numbers and evaluates the problem geometry; it
+contains none of the AMG arithmetic, so both the CUDA path and the CPU oracle
+take their inputs from here.
+
+The paper's measurements (Sec. 4) use matrices from a two-fluid dam-break
+simulation that are not available; these fields stand in for them: a water
+column (density 1000) in air (density 1) that collapses over T time steps, so
+the matrix values change every step while the sparsity pattern stays fixed,
+which is the situation the partial-reuse strategy targets (Sec. 3).
+
+Geometry: unit square / cube, N cells per side, cell centre (i + 1/2)/N, cell
+index x + N*y (+ N^2*z).  Water occupies {x < a(t), y < h(t)} in 2D and
+{x < a(t), z < h(t)} in 3D with a(t) = 0.25 + 0.5 t/T, h(t) = 0.125/a(t),
+t = k for k = 0..T-1 (strict inequalities: a centre on the line is air).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+RHO_WATER = 1000.0
+RHO_AIR = 1.0
+
+
+@dataclass(frozen=True)
+class Workload:
+    """One of the synthetic problem configurations."""
+
+    name: str
+    dim: int
+    N: int
+    T: int
+    precision: str  # "fp64" or "mixed"
+
+    @property
+    def n(self) -> int:
+        return self.N ** self.dim
+
+    @property
+    def nnz(self) -> int:
+        N = self.N
+        if self.dim == 2:
+            return N * N + 4 * (N - 1) * N
+        return N ** 3 + 6 * (N - 1) * N * N
+
+
+WORKLOADS = {
+    "2d32": Workload("2d32", 2, 32, 10, "fp64"),
+    "3d64": Workload("3d64", 3, 64, 50, "fp64"),
+    "3d128": Workload("3d128", 3, 128, 100, "mixed"),
+    "3d192": Workload("3d192", 3, 192, 100, "mixed"),
+    "3d64grad": Workload("3d64grad", 3, 64, 1, "fp64"),
+}
+
+
+def water_mask(dim: int, N: int, k: int, T: int) -> np.ndarray:
+    """Boolean mask of water cells at time step k of T (flattened, x fastest)."""
+    c = (np.arange(N, dtype=np.float64) + 0.5) / N
+    a = 0.25 + 0.5 * k / T
+    h = 0.125 / a
+    inx = c < a
+    iny = c < h
+    if dim == 2:
+        m = iny[:, None] & inx[None, :]  # [y, x]
+    else:
+        m = iny[:, None, None] & np.ones(N, dtype=bool)[None, :, None] & inx[None, None, :]  # [z, y, x]
+    return m.reshape(-1)
+
+
+def density(dim: int, N: int, k: int, T: int) -> np.ndarray:
+    """Per-cell density rho at step k: 1000 in the water column, 1 elsewhere."""
+    return np.where(water_mask(dim, N, k, T), RHO_WATER, RHO_AIR).astype(np.float64)
+
+
+def rhs(n: int, seed: int = 0) -> np.ndarray:
+    """Right-hand side f ~ U[-1, 1], the same vector at every step."""
+    return np.random.default_rng(seed).uniform(-1.0, 1.0, n)
+
+
+def noisy_log_density(dim: int, N: int, seed: int = 1, sigma: float = 0.1) -> np.ndarray:
+    """theta = log rho(t=0) + N(0, sigma^2): the differentiable-solve input."""
+    theta0 = np.log(density(dim, N, 0, 1))
+    return theta0 + np.random.default_rng(seed).normal(0.0, sigma, theta0.size)
+
+
+def target_log_density(theta: np.ndarray, seed: int = 2, sigma: float = 0.1) -> np.ndarray:
+    """Perturbed field whose solution serves as u_target."""
+    return theta + np.random.default_rng(seed).normal(0.0, sigma, theta.size)
+
+
+def fd_cells(n: int, count: int = 32, seed: int = 3) -> np.ndarray:
+    """Distinct cell indices for the finite-difference gradient check."""
+    return np.sort(np.random.default_rng(seed).choice(n, size=count, replace=False)).astype(np.int64)
+
+
+def random_spd_like(n: int, density_: float, seed: int) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """A random symmetric, diagonally dominant sparse matrix in sorted CSR form
+    (an irregular pattern for the edge-case tests)."""
+    rng = np.random.default_rng(seed)
+    upper = (rng.random((n, n)) < density_)
+    upper = np.triu(upper, 1)
+    w = -rng.uniform(0.01, 1.0, (n, n)) * upper
+    M = w + w.T
+    d = -M.sum(axis=1) + rng.uniform(0.0, 0.5, n) + 1e-3
+    M[np.arange(n), np.arange(n)] = d
+    ptr = [0]
+    col = []
+    val = []
+    for i in range(n):
+        nz = np.nonzero(M[i])[0]
+        col.extend(nz.tolist())
+        val.extend(M[i, nz].tolist())
+        ptr.append(len(col))
+    return np.asarray(ptr, np.int32), np.asarray(col, np.int32), np.asarray(val, np.float64)

@@ -1,0 +1,512 @@
+"""Pins of the CPU oracle against facts the paper and the mathematics fix.
+
+None of these tests compares the oracle with itself: each checks a closed form,
+a textbook identity, a brute-force recomputation through dense linear algebra,
+or an invariant that a plausible bug (dropped term, wrong sign, transposed
+operand, wrong order) would break.
+"""
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2108_02054_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- assembly
+def test_assembly_matches_hand_derived_2x2():
+    rows = {}
+    rho = None
+    for line in open(os.path.join(GOLDEN, "assembly_2x2.txt")):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        if line.startswith("rho"):
+            rho = np.array([float(x) for x in line.split()[1:]])
+            continue
+        r, rest = line.split(":", 1)
+        ent = {}
+        for tok in rest.split():
+            c, fr = tok.split(":")
+            ent[int(c)] = float(Fraction(fr))
+        rows[int(r)] = ent
+    ptr, col, val = O.poisson_assemble(2, 2, rho)
+    for i in range(4):
+        cols = col[ptr[i]:ptr[i + 1]].tolist()
+        assert cols == sorted(rows[i].keys())
+        for p in range(ptr[i], ptr[i + 1]):
+            assert val[p] == pytest.approx(rows[i][col[p]], rel=1e-15)
+
+
+@pytest.mark.parametrize("dim,N", [(2, 7), (3, 5)])
+def test_assembly_invariants(dim, N):
+    rho = I.density(dim, N, 1, 4)
+    ptr, col, val = O.poisson_assemble(dim, N, rho)
+    A = O.CSR(ptr, col, val, N ** dim).dense()
+    assert np.array_equal(A, A.T)                     # symmetric, bitwise
+    rs = A.sum(axis=1)
+    top = np.zeros(N ** dim, bool)
+    idx = np.arange(N ** dim)
+    top[(idx // N ** (dim - 1)) == N - 1] = True
+    assert np.allclose(rs[~top], 0.0, atol=1e-13)     # Neumann rows: zero row sum
+    assert np.allclose(rs[top], 2.0 / rho[top], rtol=1e-13)  # ghost-cell Dirichlet
+    assert np.all(np.linalg.eigvalsh(A) > 0)          # SPD with the Dirichlet face
+    # interface faces carry the harmonic mean 2/(1000+1)
+    off = -A[np.triu_indices_from(A, 1)]
+    assert np.any(np.isclose(off, 2.0 / 1001.0, rtol=1e-15))
+    assert set(np.round(off[off != 0], 12)) <= {round(2 / 1001, 12), 1.0, 0.001}
+    # pure Neumann variant is singular with the constants as null space
+    p2, c2, v2 = O.poisson_assemble(dim, N, rho, dirichlet_top=False)
+    A0 = O.CSR(p2, c2, v2, N ** dim).dense()
+    assert np.allclose(A0 @ np.ones(N ** dim), 0.0, atol=1e-13)
+
+
+def test_nnz_formula_matches_workloads():
+    for w in I.WORKLOADS.values():
+        assert O.lib().orc_poisson_nnz(w.dim, w.N) == w.nnz
+    assert I.WORKLOADS["3d192"].nnz == 49_324_032
+    assert I.WORKLOADS["3d128"].nnz == 14_581_760
+
+
+# ---------------------------------------------------------------- strength / aggregation
+def _strong_graph(level):
+    A = level.A
+    adj = [set() for _ in range(A.nrows)]
+    for i in range(A.nrows):
+        for p in range(A.ptr[i], A.ptr[i + 1]):
+            if level.strong[p]:
+                adj[i].add(int(A.col[p]))
+    return adj
+
+
+def _dist_le2(adj, i):
+    s = set(adj[i])
+    for j in adj[i]:
+        s |= adj[j]
+    s.discard(i)
+    return s
+
+
+def _luby_rounds(adj, pri, active):
+    """Parallel form: a node becomes a root iff it carries the largest priority
+    among undecided nodes within distance 2; repeated until none is undecided."""
+    und = set(active)
+    roots = set()
+    while und:
+        new = {v for v in und if all(pri[v] > pri[w] for w in _dist_le2(adj, v) if w in und)}
+        assert new, "no progress"
+        roots |= new
+        for r in new:
+            und.discard(r)
+            und -= _dist_le2(adj, r)
+    return roots
+
+
+@pytest.mark.parametrize("case", ["2d", "3d", "random"])
+def test_aggregation_is_the_distance2_mis_and_partitions(case):
+    if case == "2d":
+        rho = I.density(2, 12, 2, 5)
+        ptr, col, val = O.poisson_assemble(2, 12, rho)
+    elif case == "3d":
+        rho = I.density(3, 6, 0, 5)
+        ptr, col, val = O.poisson_assemble(3, 6, rho)
+    else:
+        ptr, col, val = I.random_spd_like(90, 0.06, seed=5)
+    H = O.Hierarchy(ptr, col, val, O.Params(coarse_enough=8, max_levels=2))
+    lv = H.level(0)
+    adj = _strong_graph(lv)
+    n = lv.A.nrows
+    # strength relation is symmetric
+    for i in range(n):
+        for j in adj[i]:
+            assert i in adj[j]
+    active = [i for i in range(n) if adj[i]]
+    isolated = [i for i in range(n) if not adj[i]]
+    assert all(lv.agg[i] == -1 for i in isolated)
+    pri = {i: O.priority(i) for i in range(n)}
+    assert len(set(pri.values())) == n                # bijective priorities
+    # roots recovered as the aggregate representatives: the node of each
+    # aggregate that is adjacent to (or is) every phase-1 member
+    roots = _luby_rounds(adj, pri, active)
+    assert len(roots) == lv.nagg
+    # independence at distance 2 and maximality
+    for r in roots:
+        assert not (_dist_le2(adj, r) & roots)
+    for v in active:
+        assert v in roots or (_dist_le2(adj, v) & roots)
+    # aggregate ids follow ascending root index; phase 1 = root + strong neighbours
+    rs = sorted(roots)
+    for a, r in enumerate(rs):
+        assert lv.agg[r] == a
+        for j in adj[r]:
+            assert lv.agg[j] == a
+    # phase 2: the rest joins the phase-1 aggregate of its strongest neighbour
+    phase1 = {}
+    for a, r in enumerate(rs):
+        phase1[r] = a
+        for j in adj[r]:
+            phase1[j] = a
+    A = lv.A
+    for v in active:
+        if v in phase1:
+            continue
+        best = None
+        for p in range(A.ptr[v], A.ptr[v + 1]):
+            j = int(A.col[p])
+            if j in adj[v] and j in phase1:
+                key = (abs(A.val[p]), pri[rs[phase1[j]]])
+                if best is None or key > best[0]:
+                    best = (key, phase1[j])
+        assert best is not None and lv.agg[v] == best[1]
+    # every non-isolated node in exactly one aggregate, every aggregate non-empty
+    assert np.all(lv.agg[active] >= 0)
+    assert set(lv.agg[active].tolist()) == set(range(lv.nagg))
+
+
+# ---------------------------------------------------------------- prolongation
+def _dense_P_from_definition(lv, omega):
+    A = lv.A.dense()
+    n = A.shape[0]
+    S = np.zeros_like(A, dtype=bool)
+    for i in range(n):
+        for p in range(lv.A.ptr[i], lv.A.ptr[i + 1]):
+            S[i, lv.A.col[p]] = bool(lv.strong[p])
+    AF = np.where(S, A, 0.0)
+    weak = (A != 0) & ~S
+    np.fill_diagonal(weak, False)
+    dF = np.diag(A) + np.where(weak, A, 0.0).sum(axis=1)
+    np.fill_diagonal(AF, dF)
+    Pt = np.zeros((n, lv.nagg))
+    for i in range(n):
+        if lv.agg[i] >= 0:
+            Pt[i, lv.agg[i]] = 1.0
+    return (np.eye(n) - omega * (AF / dF[:, None])) @ Pt, AF, A
+
+
+@pytest.mark.parametrize("dim,N,dirichlet", [(2, 10, False), (3, 5, False), (2, 12, True), (3, 6, True)])
+def test_smoothed_P_matches_dense_definition(dim, N, dirichlet):
+    rho = I.density(dim, N, 1, 3)
+    ptr, col, val = O.poisson_assemble(dim, N, rho, dirichlet_top=dirichlet)
+    H = O.Hierarchy(ptr, col, val, O.Params(coarse_enough=8, max_levels=2), allow_singular=not dirichlet)
+    lv = H.level(0)
+    Pd, AF, A = _dense_P_from_definition(lv, 2.0 / 3.0)
+    P = lv.P.dense()
+    assert np.allclose(P, Pd, atol=1e-14)
+    # filtering preserves row sums
+    assert np.allclose(AF.sum(1), A.sum(1), atol=1e-13)
+    # R is the explicit transpose with sorted rows
+    assert np.array_equal(lv.R.dense(), P.T)
+    for I_ in range(lv.R.nrows):
+        c = lv.R.col[lv.R.ptr[I_]:lv.R.ptr[I_ + 1]]
+        assert np.all(np.diff(c) > 0)
+    if not dirichlet:
+        # constants are interpolated exactly: P 1 = 1 (pure Neumann, no isolated nodes)
+        assert np.all(lv.agg >= 0)
+        assert np.allclose(P @ np.ones(lv.nagg), 1.0, atol=1e-14)
+
+
+def test_plain_aggregation_P_is_tentative():
+    rho = I.density(2, 10, 0, 3)
+    ptr, col, val = O.poisson_assemble(2, 10, rho)
+    H = O.Hierarchy(ptr, col, val, O.Params(coarse_enough=8, max_levels=2, smoothed=0))
+    lv = H.level(0)
+    P = lv.P.dense()
+    assert set(np.unique(P)) <= {0.0, 1.0}
+    assert np.all(P.sum(1)[lv.agg >= 0] == 1.0)
+
+
+# ---------------------------------------------------------------- Galerkin product
+@pytest.mark.parametrize("dim,N,dirichlet", [(2, 16, True), (3, 8, True), (2, 16, False), (3, 8, False)])
+def test_galerkin_matches_dense_brute_force(dim, N, dirichlet):
+    rho = I.density(dim, N, 2, 5)
+    ptr, col, val = O.poisson_assemble(dim, N, rho, dirichlet_top=dirichlet)
+    H = O.Hierarchy(ptr, col, val, O.Params(coarse_enough=4), allow_singular=not dirichlet)
+    assert H.nlevels >= 3
+    checked_levels = []
+    zero_rowsum = not dirichlet  # A 1 = 0 holds on the fine level of the pure-Neumann operator
+    for l in range(H.nlevels - 1):
+        lv, nx = H.level(l), H.level(l + 1)
+        A, P = lv.A.dense(), lv.P.dense()
+        Ac_ref = P.T @ A @ P
+        bound = np.abs(P).T @ np.abs(A) @ np.abs(P)
+        Ac = nx.A.dense()
+        assert np.all(np.abs(Ac - Ac_ref) <= 1e-12 * bound + 1e-300)
+        # structural pattern: every reachable (I,J) and nothing else (plus diagonal)
+        Sp = np.zeros_like(P)
+        for i in range(lv.P.nrows):
+            Sp[i, lv.P.col[lv.P.ptr[i]:lv.P.ptr[i + 1]]] = 1.0
+        Sa = (A != 0) | np.eye(A.shape[0], dtype=bool)
+        patt = (Sp.T @ Sa.astype(float) @ Sp) > 0
+        np.fill_diagonal(patt, True)
+        got = np.zeros_like(patt)
+        for I_ in range(nx.A.nrows):
+            got[I_, nx.A.col[nx.A.ptr[I_]:nx.A.ptr[I_ + 1]]] = True
+        assert np.array_equal(got, patt)
+        # symmetry to rounding; positive definite with the Dirichlet face
+        assert np.all(np.abs(Ac - Ac.T) <= 1e-12 * bound + 1e-300)
+        if dirichlet:
+            assert np.all(np.linalg.eigvalsh(0.5 * (Ac + Ac.T)) > 0)
+        else:
+            # P 1 = 1 wherever every node is aggregated, so A_c 1 = P^T A P 1 = P^T A 1 = 0
+            zero_rowsum = zero_rowsum and bool(np.all(lv.agg >= 0))
+            if zero_rowsum:
+                assert np.all(np.abs(Ac @ np.ones(Ac.shape[0])) <= 1e-12 * bound.sum(1))
+            checked_levels.append((l, zero_rowsum))
+    if not dirichlet:
+        assert checked_levels[0] == (0, True)
+
+
+def test_partial_rebuild_on_unchanged_values_reproduces_full_setup_bitwise():
+    rho = I.density(3, 12, 3, 10)
+    ptr, col, val = O.poisson_assemble(3, 12, rho)
+    H = O.Hierarchy(ptr, col, val, O.Params(coarse_enough=30))
+    ref = [H.level(l) for l in range(H.nlevels)]
+    lu_ref = H.lu()
+    other = O.poisson_assemble(3, 12, I.density(3, 12, 7, 10))[2]
+    assert H.rebuild(other) == 0
+    assert H.rebuild(val) == 0
+    for l in range(H.nlevels):
+        got = H.level(l)
+        assert np.array_equal(got.A.val, ref[l].A.val)
+        assert np.array_equal(got.m, ref[l].m)
+    lu, piv = H.lu()
+    assert np.array_equal(lu, lu_ref[0]) and np.array_equal(piv, lu_ref[1])
+
+
+def test_partial_rebuild_equals_galerkin_of_new_values():
+    N = 8
+    ptr, col, v0 = O.poisson_assemble(3, N, I.density(3, N, 0, 4))
+    _, _, v1 = O.poisson_assemble(3, N, I.density(3, N, 3, 4))
+    H = O.Hierarchy(ptr, col, v0, O.Params(coarse_enough=4))
+    Ps = [H.level(l).P.dense() for l in range(H.nlevels - 1)]
+    H.rebuild(v1)
+    A = O.CSR(ptr, col, v1, N ** 3).dense()
+    for l in range(H.nlevels - 1):
+        P = Ps[l]
+        assert np.array_equal(H.level(l).P.dense(), P)   # transfer operators kept
+        ref = P.T @ A @ P
+        bound = np.abs(P).T @ np.abs(A) @ np.abs(P)
+        A = H.level(l + 1).A.dense()
+        assert np.all(np.abs(A - ref) <= 1e-12 * bound + 1e-300)
+
+
+# ---------------------------------------------------------------- smoother
+@pytest.mark.parametrize("smoother", [0, 1])
+def test_smoother_closed_forms(smoother):
+    rho = I.density(2, 16, 1, 3)
+    ptr, col, val = O.poisson_assemble(2, 16, rho)
+    H = O.Hierarchy(ptr, col, val, O.Params(coarse_enough=20, smoother=smoother))
+    for l in range(H.nlevels - 1):
+        lv = H.level(l)
+        A = lv.A.dense()
+        if smoother == 0:
+            # m_i solves min_m |e_i - m a_i|_2 (row i of I - M A), via least squares
+            for i in range(0, A.shape[0], max(1, A.shape[0] // 17)):
+                m, *_ = np.linalg.lstsq(A[i][:, None], np.eye(A.shape[0])[i], rcond=None)
+                assert lv.m[i] == pytest.approx(m[0], rel=1e-12)
+            # and the Frobenius norm of I - M A is not decreased by perturbing M
+            M = np.diag(lv.m)
+            base = np.linalg.norm(np.eye(A.shape[0]) - M @ A)
+            for s in (1e-3, -1e-3):
+                assert np.linalg.norm(np.eye(A.shape[0]) - (M * (1 + s)) @ A) >= base
+        else:
+            assert np.allclose(lv.m * np.diag(A), 0.72, rtol=1e-15)
+
+
+# ---------------------------------------------------------------- coarse solver
+def test_dense_lu_against_numpy_and_pivot_rule():
+    rng = np.random.default_rng(7)
+    A = rng.normal(size=(40, 40))
+    lu, piv, st = O.dense_lu(A)
+    assert st == 0
+    b = rng.normal(size=40)
+    x = O.dense_lu_solve(lu, piv, b)
+    assert np.allclose(x, np.linalg.solve(A, b), rtol=1e-10, atol=1e-12)
+    # P A = L U
+    L = np.tril(lu, -1) + np.eye(40)
+    U = np.triu(lu)
+    PA = A.copy()
+    for k, p in enumerate(piv):
+        PA[[k, p]] = PA[[p, k]]
+    assert np.allclose(L @ U, PA, atol=1e-12)
+    # ties: the first largest-magnitude entry wins
+    T = np.array([[1.0, 2.0], [-1.0, 3.0]])
+    _, pv, _ = O.dense_lu(T)
+    assert pv[0] == 0
+    T2 = np.array([[1.0, 2.0], [-2.0, 3.0], [2.0, 1.0]])[:2]
+    _, pv2, _ = O.dense_lu(T2)
+    assert pv2[0] == 1
+    # singular matrix reports its status
+    _, _, st = O.dense_lu(np.zeros((3, 3)))
+    assert st == O.ERR_SINGULAR
+
+
+# ---------------------------------------------------------------- V-cycle
+def _tridiag(n):
+    ptr = [0]
+    col, val = [], []
+    for i in range(n):
+        for j, v in ((i - 1, -1.0), (i, 2.0), (i + 1, -1.0)):
+            if 0 <= j < n:
+                col.append(j)
+                val.append(v)
+        ptr.append(len(col))
+    return np.array(ptr, np.int32), np.array(col, np.int32), np.array(val)
+
+
+def test_two_grid_error_operator_1d_poisson():
+    """Alg. 2 with two levels equals the textbook two-grid error propagation
+    E = S (I - P A_c^-1 R A) S, S = I - M A; its spectral radius stays below one
+    and does not grow with n (mesh-independent convergence)."""
+    rhos = []
+    for n in (63, 127, 255):
+        ptr, col, val = _tridiag(n)
+        H = O.Hierarchy(ptr, col, val, O.Params(coarse_enough=1, max_levels=2))
+        assert H.nlevels == 2
+        lv = H.level(0)
+        A = lv.A.dense()
+        P = lv.P.dense()
+        M = np.diag(lv.m)
+        S = np.eye(n) - M @ A
+        Ac = P.T @ A @ P
+        E_ref = S @ (np.eye(n) - P @ np.linalg.solve(Ac, P.T @ A)) @ S
+        B = np.column_stack([H.vcycle(e) for e in np.eye(n)])
+        E = np.eye(n) - B @ A
+        assert np.allclose(E, E_ref, atol=1e-11)
+        rhos.append(max(abs(np.linalg.eigvals(E))))
+    assert max(rhos) < 0.85
+    assert max(rhos) - min(rhos) < 0.1
+
+
+def test_vcycle_preconditioner_is_symmetric():
+    rho = I.density(3, 10, 2, 5)
+    ptr, col, val = O.poisson_assemble(3, 10, rho)
+    H = O.Hierarchy(ptr, col, val, O.Params(coarse_enough=20))
+    rng = np.random.default_rng(11)
+    x, y = rng.normal(size=H.n), rng.normal(size=H.n)
+    a, b = x @ H.vcycle(y), H.vcycle(x) @ y
+    assert a == pytest.approx(b, rel=1e-11)
+    assert x @ H.vcycle(x) > 0
+
+
+# ---------------------------------------------------------------- PCG
+@pytest.mark.parametrize("dim,N", [(2, 20), (3, 9)])
+def test_pcg_against_direct_solve(dim, N):
+    rho = I.density(dim, N, 1, 4)
+    ptr, col, val = O.poisson_assemble(dim, N, rho)
+    H = O.Hierarchy(ptr, col, val, O.Params(coarse_enough=16))
+    f = I.rhs(N ** dim)
+    u, it, rr, st = H.pcg(f, tol=1e-10)
+    assert st == O.OK and 0 < it <= N ** dim
+    A = O.CSR(ptr, col, val, N ** dim).dense()
+    ue = np.linalg.solve(A, f)
+    assert np.linalg.norm(u - ue) / np.linalg.norm(ue) < 1e-6
+    assert np.linalg.norm(f - A @ u) / np.linalg.norm(f) <= 1e-10
+    assert rr <= 1e-10
+
+
+def test_pcg_edge_cases():
+    ptr, col, val = O.poisson_assemble(2, 8, I.density(2, 8, 0, 2))
+    H = O.Hierarchy(ptr, col, val)           # 64 unknowns <= coarse_enough: one level
+    assert H.nlevels == 1
+    f = I.rhs(64)
+    u, it, rr, st = H.pcg(f)
+    assert st == O.OK and it == 1            # exact preconditioner
+    u, it, rr, st = H.pcg(np.zeros(64))
+    assert st == O.OK and it == 0 and np.all(u == 0)
+    H2 = O.Hierarchy(*O.poisson_assemble(3, 8, I.density(3, 8, 0, 2)), O.Params(coarse_enough=8))
+    u, it, rr, st = H2.pcg(I.rhs(512), tol=1e-14, maxiter=1)
+    assert st == O.NOT_CONVERGED and it == 1
+
+
+def test_setup_rejects_bad_patterns():
+    ptr, col, val = O.poisson_assemble(2, 4, np.ones(16))
+    bad = col.copy()
+    bad[1], bad[2] = bad[2], bad[1]          # unsorted row
+    with pytest.raises(ValueError):
+        O.Hierarchy(ptr, bad, val)
+
+
+# ---------------------------------------------------------------- modes
+def test_modes_on_a_short_time_series():
+    dim, N, T = 2, 24, 6
+    ptr, col, _ = O.poisson_assemble(dim, N, I.density(dim, N, 0, T))
+    vals = [O.poisson_assemble(dim, N, I.density(dim, N, k, T))[2] for k in range(T)]
+    f = I.rhs(N * N)
+    prm = O.Params(coarse_enough=20)
+    full = O.run_time_steps(ptr, col, vals, f, O.MODE_FULL_REBUILD, prm)
+    part = O.run_time_steps(ptr, col, vals, f, O.MODE_PARTIAL, prm)
+    reuse = O.run_time_steps(ptr, col, vals, f, O.MODE_FULL_REUSE, prm)
+    assert all(r.status == O.OK for r in full + part)
+    assert all(r.rebuilt for r in full)
+    # Alg. 3: full reuse rebuilds exactly after a step that missed the limit
+    for k in range(1, T):
+        prev = reuse[k - 1]
+        assert reuse[k].rebuilt == (prev.status != O.OK or prev.iters > 100)
+        if reuse[k].rebuilt:
+            assert reuse[k].status == O.OK
+    assert [r.rebuilt for r in part] == [True] + [False] * (T - 1)
+    assert full[0].iters == part[0].iters == reuse[0].iters
+    # full reuse with unchanged values reproduces the same solve
+    same = O.run_time_steps(ptr, col, [vals[0]] * 3, f, O.MODE_FULL_REUSE, prm)
+    assert len({r.iters for r in same}) == 1
+    # a rebuilt step solves exactly like the no-reuse strategy on that step
+    for k in range(T):
+        if reuse[k].rebuilt:
+            assert reuse[k].iters == full[k].iters
+    # partial reuse converges every step (Sec. 4: iterations stay close to no reuse)
+    assert max(r.iters for r in part) <= 2 * max(r.iters for r in full)
+
+
+def test_speedup_convention_reproduces_table2():
+    """Sec. 4, Table 2: speedup % = (T_noreuse / T_strategy - 1) * 100 for both
+    the total (setup + solve) and the setup column."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "table2_speedups.txt")) if l.strip() and l[0] != "#"]
+    base = {}
+    for w, b, s, su, so, tot, sp in rows:
+        if s == "none":
+            base[(w, b)] = (float(su), float(so))
+    checked = 0
+    for w, b, s, su, so, tot, sp in rows:
+        if s == "none":
+            continue
+        bs, bo = base[(w, b)]
+        total = (bs + bo) / (float(su) + float(so)) - 1
+        setup = bs / float(su) - 1
+        assert round(100 * total) == pytest.approx(int(tot), abs=1)
+        assert round(100 * setup) == pytest.approx(int(sp), abs=1)
+        checked += 1
+    assert checked == 8
+
+
+# ---------------------------------------------------------------- adjoint
+def test_adjoint_gradient_against_central_differences():
+    dim, N = 2, 9
+    n = N * N
+    theta = np.log(I.density(dim, N, 0, 1)) + np.random.default_rng(1).normal(0, 0.1, n)
+    f = I.rhs(n)
+    ut = np.random.default_rng(4).normal(size=n)
+
+    def solve(th):
+        p, c, v = O.poisson_assemble(dim, N, np.exp(th))
+        return np.linalg.solve(O.CSR(p, c, v, n).dense(), f)
+
+    def loss(th):
+        return 0.5 * np.sum((solve(th) - ut) ** 2)
+
+    u = solve(theta)
+    p, c, v = O.poisson_assemble(dim, N, np.exp(theta))
+    lam = np.linalg.solve(O.CSR(p, c, v, n).dense().T, u - ut)
+    g = O.poisson_grad_theta(dim, N, np.exp(theta), u, lam)
+    L0 = loss(theta)
+    for h in (1e-4, 1e-6):
+        # central differences carry O(h^2) truncation and ~eps |L| / h roundoff
+        for cell in [0, 5, 17, 40, 72, 80]:
+            e = np.zeros(n)
+            e[cell] = h
+            fd = (loss(theta + e) - loss(theta - e)) / (2 * h)
+            assert g[cell] == pytest.approx(fd, rel=1e-6, abs=10 * np.finfo(float).eps * abs(L0) / h)
