@@ -1,0 +1,160 @@
+/*
+ * amgpr.h -- C ABI of the partial-reuse AMG library (libamgpr.so).
+ *
+ * Method: D. E. Demidov, "Partial reuse AMG setup cost amortization strategy
+ * for the solution of non-steady state problems" (arXiv 2108.02054).
+ * Alg. 1 (AMG setup), Alg. 2 (V-cycle), Alg. 3 (full reuse), Alg. 4 (partial
+ * reuse), Sec. 2 (Krylov solver with one V-cycle as the preconditioner),
+ * Sec. 5 (reuse of the Galerkin product's pattern).
+ *
+ * Conventions for every entry point:
+ *  - Matrices are CSR with int32 row pointers / column indices, columns sorted
+ *    ascending within each row, the diagonal stored in every row.
+ *  - Pointers named d_* are DEVICE pointers (current CUDA device), h_* are
+ *    HOST pointers.  The caller owns every pointer it passes; the library only
+ *    reads or writes it during the call (work is ordered on the context's
+ *    stream; calls that return data synchronise that stream before returning
+ *    unless stated otherwise).
+ *  - Every function returns an amg_status and never aborts the process.  On
+ *    an error, amg_last_error() describes it.  A CUDA error maps to
+ *    AMG_ERR_CUDA; device-side checks report through a status word, never by
+ *    trapping.
+ *  - The library allocates its own device memory (cudaMalloc) for the
+ *    hierarchy and work vectors; amg_destroy frees it.
+ */
+#ifndef AMGPR_H
+#define AMGPR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct amg_ctx amg_ctx;
+
+typedef enum {
+    AMG_OK = 0,
+    AMG_NOT_CONVERGED = 1,     /* solve hit maxiter; u and info are filled in */
+    AMG_ERR_ARG = -1,          /* null pointer, bad size, bad parameter */
+    AMG_ERR_STATE = -2,        /* e.g. partial rebuild before a full setup */
+    AMG_ERR_PATTERN = -3,      /* unsorted / out-of-range columns, missing diagonal */
+    AMG_ERR_BREAKDOWN = -4,    /* CG breakdown: p'Ap <= 0 or non-finite */
+    AMG_ERR_NONFINITE = -5,    /* NaN / Inf in the matrix values */
+    AMG_ERR_CUDA = -6,         /* a CUDA runtime error */
+    AMG_ERR_OOM = -7,          /* device allocation failed */
+    AMG_ERR_SINGULAR = -8,     /* zero pivot in the coarsest LU */
+    AMG_ERR_CAPACITY = -9      /* a row exceeds a fixed kernel capacity */
+} amg_status;
+
+enum { AMG_SMOOTHER_SPAI0 = 0, AMG_SMOOTHER_JACOBI = 1 };
+enum { AMG_PREC_FP64 = 0, AMG_PREC_MIXED = 1 };
+enum { AMG_MODE_PARTIAL = 0, AMG_MODE_FULL_REBUILD = 1, AMG_MODE_FULL_REUSE = 2 };
+
+typedef struct {
+    double theta;          /* strength threshold on the finest level (0.08) */
+    double omega;          /* prolongation smoothing weight (2/3) */
+    double jacobi_omega;   /* damped Jacobi weight when smoother = JACOBI (0.72) */
+    int32_t smoother;      /* AMG_SMOOTHER_* (SPAI0) */
+    int32_t npre, npost;   /* smoothing sweeps before / after the coarse correction (1, 1) */
+    int32_t coarse_enough; /* stop coarsening at or below this many rows (256) */
+    int32_t max_levels;    /* at most this many levels (20) */
+    int32_t theta_halving; /* 1: theta halves on every coarser level (1) */
+    int32_t smoothed;      /* 1: smoothed aggregation, 0: plain aggregation (1) */
+    int32_t precision;     /* AMG_PREC_* (FP64) */
+    int32_t mode;          /* AMG_MODE_* used by amg_step (PARTIAL) */
+    int32_t reuse_iter_limit; /* full reuse: rebuild after a solve that needed more (100) */
+    int32_t maxiter;       /* CG iteration cap (100) */
+} amg_params;
+
+typedef struct {
+    int32_t iters;         /* CG iterations of the last solve */
+    int32_t rebuilt;       /* 1 if the last amg_step ran a full setup */
+    int32_t nlevels;       /* levels of the current hierarchy */
+    int32_t status;        /* status of the last solve */
+    double rel_resid;      /* true relative residual |f - A u| / |f| of the last solve */
+} amg_info;
+
+/* Default parameters (values in the comments above). */
+amg_status amg_default_params(amg_params *prm);
+
+/* Create a context bound to the current CUDA device and to `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *ctx is owned by the
+ * caller and released with amg_destroy. */
+amg_status amg_create(amg_ctx **ctx, const amg_params *prm, void *cuda_stream);
+void amg_destroy(amg_ctx *ctx);
+const char *amg_last_error(const amg_ctx *ctx);
+
+/* Alg. 1: full setup from A (n rows, nnz entries; device CSR).  Copies the
+ * pattern and values; builds strength, aggregates, tentative and smoothed P,
+ * R = P^T, the Galerkin patterns with their gather metadata, every A_{l+1},
+ * the smoothers and the coarsest LU.  Replaces any previous hierarchy. */
+amg_status amg_full_setup(amg_ctx *ctx, int32_t n, int32_t nnz, const int32_t *d_ptr,
+                          const int32_t *d_col, const double *d_val);
+
+/* Alg. 4 body: new values d_val (nnz doubles) on the pattern given to the
+ * last full setup; keeps P and R, recomputes every A_{l+1} = R A_l P over
+ * the cached coarse patterns (Sec. 5), the smoothers and the coarsest LU.
+ * AMG_ERR_STATE without a prior full setup. */
+amg_status amg_partial_rebuild(amg_ctx *ctx, const double *d_val);
+
+/* One time step's setup under the context's mode (Alg. 3 / Alg. 4 / no
+ * reuse): PARTIAL -> partial rebuild (full setup on the first call),
+ * FULL_REBUILD -> full setup, FULL_REUSE -> keep the whole hierarchy unless
+ * the previous solve needed more than reuse_iter_limit iterations or did not
+ * converge.  The new values always become the system matrix of the next
+ * amg_solve.  For the first call, d_ptr/d_col give the pattern (they are
+ * ignored afterwards and may then be NULL). */
+amg_status amg_step(amg_ctx *ctx, int32_t n, int32_t nnz, const int32_t *d_ptr,
+                    const int32_t *d_col, const double *d_val, amg_info *info);
+
+/* Solve A u = f with CG preconditioned by one V-cycle per iteration (Sec. 2,
+ * Alg. 2), u_0 = 0, to |f - A u| / |f| <= tol or params.maxiter iterations.
+ * A is the system matrix of the last setup / step.  d_f, d_u: n doubles.
+ * Returns AMG_OK, AMG_NOT_CONVERGED or an error; info may be NULL. */
+amg_status amg_solve(amg_ctx *ctx, const double *d_f, double *d_u, double tol, amg_info *info);
+
+/* Apply one V-cycle z = B r from a zero initial guess (Alg. 2). */
+amg_status amg_apply_vcycle(amg_ctx *ctx, const double *d_r, double *d_z);
+
+/* End to end with host buffers: copies h_val (nnz doubles) and h_f (n doubles)
+ * to the device, runs amg_step and amg_solve, copies u back to h_u (n
+ * doubles) and synchronises.  The pattern must already be known (a previous
+ * amg_full_setup or amg_step). */
+amg_status amg_step_solve_host(amg_ctx *ctx, const double *h_val, const double *h_f, double *h_u,
+                               double tol, amg_info *info);
+
+/* Hierarchy inspection (for parity tests). */
+amg_status amg_num_levels(const amg_ctx *ctx, int32_t *nlevels);
+/* sizes[0..5] = n, nnz(A), nnz(P), nnz(R), nnz(A*P), number of aggregates */
+amg_status amg_level_sizes(const amg_ctx *ctx, int32_t level, int64_t *sizes);
+/* which: 0 = A_l, 1 = P_l, 2 = R_l; copies into caller device buffers sized
+ * from amg_level_sizes (d_val gets FP64 values; any pointer may be NULL). */
+amg_status amg_export_csr(amg_ctx *ctx, int32_t level, int32_t which, int32_t *d_ptr,
+                          int32_t *d_col, double *d_val);
+/* aggregate per row (-1 isolated), strong flag per entry of A_l, smoother
+ * diagonal (FP64); any pointer may be NULL. */
+amg_status amg_export_level_vec(amg_ctx *ctx, int32_t level, int32_t *d_agg, uint8_t *d_strong,
+                                double *d_m);
+/* Coarsest LU factors (n_L x n_L row-major, FP64) and pivots. */
+amg_status amg_export_coarse_lu(amg_ctx *ctx, double *d_lu, int32_t *d_piv);
+
+/* Synthetic pressure-Poisson workload: -div((1/rho) grad p) on an N^dim cell
+ * grid (dim 2 or 3), harmonic face coefficients 2/(rho_i + rho_j), Dirichlet
+ * p = 0 on the top face through a ghost cell (A_ii += 2/rho_i) when
+ * dirichlet_top != 0, Neumann elsewhere.  It stands in for the dam-break
+ * matrices of Sec. 4.  Pattern: n = N^dim rows, nnz from amg_poisson_nnz. */
+int64_t amg_poisson_nnz(int32_t dim, int32_t N);
+amg_status amg_poisson_pattern(int32_t dim, int32_t N, int32_t *d_ptr, int32_t *d_col, void *cuda_stream);
+amg_status amg_poisson_values(int32_t dim, int32_t N, int32_t dirichlet_top, const double *d_rho,
+                              const int32_t *d_ptr, double *d_val, void *cuda_stream);
+/* Adjoint chain rule for theta = log rho: given u (A u = f) and lam
+ * (A lam = dL/du), grad = dL/dtheta per cell (n doubles). */
+amg_status amg_poisson_grad_theta(int32_t dim, int32_t N, int32_t dirichlet_top, const double *d_rho,
+                                  const double *d_u, const double *d_lam, double *d_grad,
+                                  void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AMGPR_H */

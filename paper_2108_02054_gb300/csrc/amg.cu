@@ -1,0 +1,850 @@
+// amg.cu -- context, hierarchy orchestration and the C ABI of libamgpr.so.
+//
+// Method: partial-reuse AMG setup amortisation (arXiv 2108.02054).
+//   amg_full_setup       Alg. 1 (all GPU kernels; host only sequences them and
+//                        reads back the sizes it must allocate)
+//   amg_partial_rebuild  Alg. 4 body: numeric Galerkin products over the cached
+//                        patterns (Sec. 5), smoothers, coarsest LU
+//   amg_step             Alg. 3 / Alg. 4 / no-reuse time-step dispatch
+//   amg_solve            CG with one V-cycle (Alg. 2) per iteration; the
+//                        iteration's control state lives on the device
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace amgpr;
+
+struct amg_ctx {
+    amg_params prm{};
+    cudaStream_t s = nullptr;
+    cudaMemPool_t pool = nullptr;
+    std::vector<void *> hier;     // hierarchy allocations (replaced by every full setup)
+    std::vector<void *> persist;  // context-lifetime allocations
+    std::string err;
+    // fine pattern (persistent)
+    int32_t n = 0, nnz = 0;
+    int32_t *fine_ptr = nullptr, *fine_col = nullptr;
+    // hierarchy
+    int nlev = 0;
+    Level lev[kMaxLevels];
+    int32_t nL = 0;
+    double *lu = nullptr, *inv = nullptr;
+    int32_t *piv = nullptr;
+    bool have_setup = false;
+    // system matrix of the solve (aliases level 0 except under full reuse)
+    double *A_sys = nullptr;
+    double *A_sys_own = nullptr;
+    // CG
+    double *cg_r = nullptr, *cg_z = nullptr, *cg_p = nullptr, *cg_q = nullptr, *cg_t = nullptr;
+    double *partial = nullptr, *partial2 = nullptr;
+    CgState *cg = nullptr;
+    CgState *h_cg = nullptr;  // pinned
+    int *d_st = nullptr;
+    int *h_st = nullptr;      // pinned
+    // host-buffer staging
+    double *stage_val = nullptr, *stage_f = nullptr, *stage_u = nullptr;
+    // time-step bookkeeping
+    int last_iters = 0;
+    int last_status = AMG_OK;
+    int last_rebuilt = 0;
+};
+
+namespace {
+
+amg_status set_err(amg_ctx *c, amg_status st, const std::string &msg) {
+    if (c) c->err = msg;
+    return st;
+}
+
+#define CK(call)                                                                            \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return set_err(ctx, e_ == cudaErrorMemoryAllocation ? AMG_ERR_OOM : AMG_ERR_CUDA, \
+                           std::string(#call) + ": " + cudaGetErrorString(e_));             \
+    } while (0)
+
+#define TRY(expr)                              \
+    do {                                       \
+        amg_status t_ = (expr);                \
+        if (t_ != AMG_OK) return t_;           \
+    } while (0)
+
+template <class T>
+amg_status alloc(amg_ctx *ctx, T **p, size_t count, bool persistent = false) {
+    void *q = nullptr;
+    size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMallocFromPoolAsync(&q, bytes, ctx->pool, ctx->s);
+    if (e != cudaSuccess)
+        return set_err(ctx, e == cudaErrorMemoryAllocation ? AMG_ERR_OOM : AMG_ERR_CUDA,
+                       std::string("device allocation of ") + std::to_string(bytes) + " bytes: " +
+                           cudaGetErrorString(e));
+    (persistent ? ctx->persist : ctx->hier).push_back(q);
+    *p = (T *)q;
+    return AMG_OK;
+}
+
+void free_hierarchy(amg_ctx *ctx) {
+    for (void *p : ctx->hier) cudaFreeAsync(p, ctx->s);
+    ctx->hier.clear();
+    for (int l = 0; l < kMaxLevels; ++l) ctx->lev[l] = Level{};
+    ctx->nlev = 0;
+    ctx->have_setup = false;
+    ctx->lu = ctx->inv = nullptr;
+    ctx->piv = nullptr;
+}
+
+// read the device status word (synchronises the stream) and map it
+amg_status check_device(amg_ctx *ctx, const char *where) {
+    CK(cudaMemcpyAsync(ctx->h_st, ctx->d_st, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    CK(cudaGetLastError());
+    int st = *ctx->h_st;
+    if (st == 0) return AMG_OK;
+    std::string w(where);
+    if (st & DEV_ERR_PATTERN)
+        return set_err(ctx, AMG_ERR_PATTERN, w + ": unsorted or out-of-range columns, or a missing diagonal");
+    if (st & DEV_ERR_NONFINITE) return set_err(ctx, AMG_ERR_NONFINITE, w + ": non-finite matrix values");
+    if (st & DEV_ERR_SINGULAR) return set_err(ctx, AMG_ERR_SINGULAR, w + ": zero pivot in the coarsest LU");
+    if (st & DEV_ERR_CAPACITY)
+        return set_err(ctx, AMG_ERR_CAPACITY, w + ": a row of a Galerkin product exceeds the kernel capacity");
+    if (st & DEV_ERR_OVERFLOW) return set_err(ctx, AMG_ERR_CAPACITY, w + ": an index count exceeds int32");
+    return set_err(ctx, AMG_ERR_STATE, w + ": inconsistent hierarchy state");
+}
+
+amg_status reset_status(amg_ctx *ctx) {
+    CK(cudaMemsetAsync(ctx->d_st, 0, sizeof(int), ctx->s));
+    return AMG_OK;
+}
+
+template <class T>
+amg_status read_scalar(amg_ctx *ctx, const T *d, T *h) {
+    CK(cudaMemcpyAsync(h, d, sizeof(T), cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    return AMG_OK;
+}
+
+amg_status scan(amg_ctx *ctx, const int32_t *in, int32_t *out, int64_t n) {
+    int64_t *tmp = nullptr;
+    TRY(alloc(ctx, &tmp, (size_t)scan_tmp_elems(n)));
+    scan_counts(in, out, n, ctx->d_st, tmp, ctx->s);
+    return AMG_OK;
+}
+
+bool mixed(const amg_ctx *ctx) { return ctx->prm.precision == AMG_PREC_MIXED; }
+
+amg_status alloc_level_vectors(amg_ctx *ctx, Level &L) {
+    if (mixed(ctx)) {
+        TRY(alloc(ctx, &L.vf.u, L.n));
+        TRY(alloc(ctx, &L.vf.f, L.n));
+        TRY(alloc(ctx, &L.vf.r, L.n));
+        TRY(alloc(ctx, &L.vf.t, L.n));
+        TRY(alloc(ctx, &L.mf, L.n));
+        TRY(alloc(ctx, &L.A_valf, L.nnz));
+    } else {
+        TRY(alloc(ctx, &L.vd.u, L.n));
+        TRY(alloc(ctx, &L.vd.f, L.n));
+        TRY(alloc(ctx, &L.vd.r, L.n));
+        TRY(alloc(ctx, &L.vd.t, L.n));
+        TRY(alloc(ctx, &L.m, L.n));
+    }
+    return AMG_OK;
+}
+
+// symbolic C = X*Y (pattern only), allocating C's arrays
+amg_status symbolic_product(amg_ctx *ctx, int32_t nrows, int32_t ncols, const int32_t *X_ptr, const int32_t *X_col,
+                            const int32_t *Y_ptr, const int32_t *Y_col, int add_diag, int32_t **C_ptr,
+                            int32_t **C_col, int32_t *C_nnz) {
+    int32_t *len = nullptr;
+    TRY(alloc(ctx, &len, (size_t)nrows));
+    TRY(alloc(ctx, C_ptr, (size_t)nrows + 1));
+    launch_spgemm_symbolic(nrows, ncols, X_ptr, X_col, Y_ptr, Y_col, add_diag, len, nullptr, nullptr, ctx->d_st,
+                           ctx->s);
+    TRY(scan(ctx, len, *C_ptr, nrows));
+    TRY(check_device(ctx, "symbolic product"));
+    TRY(read_scalar(ctx, *C_ptr + nrows, C_nnz));
+    TRY(alloc(ctx, C_col, (size_t)*C_nnz));
+    launch_spgemm_symbolic(nrows, ncols, X_ptr, X_col, Y_ptr, Y_col, add_diag, len, *C_ptr, *C_col, ctx->d_st,
+                           ctx->s);
+    return AMG_OK;
+}
+
+amg_status max_row(amg_ctx *ctx, int32_t n, const int32_t *ptr, int32_t *out) {
+    int *d = nullptr;
+    TRY(alloc(ctx, &d, 1));
+    CK(cudaMemsetAsync(d, 0, sizeof(int), ctx->s));
+    launch_row_maxlen(n, ptr, d, ctx->s);
+    int h = 0;
+    TRY(read_scalar(ctx, d, &h));
+    *out = h;
+    return AMG_OK;
+}
+
+// the coarsest direct solver: dense LU (FP64) and its explicit inverse
+amg_status coarse_factor(amg_ctx *ctx) {
+    Level &C = ctx->lev[ctx->nlev - 1];
+    const bool mx = mixed(ctx);
+    launch_csr_to_dense(C.n, C.A_ptr, C.A_col, mx ? nullptr : C.A_val, mx ? C.A_valf : nullptr, ctx->lu, ctx->s);
+    launch_dense_lu(C.n, ctx->lu, ctx->piv, ctx->d_st, ctx->s);
+    launch_lu_inverse(C.n, ctx->lu, ctx->piv, ctx->inv, ctx->s);
+    return AMG_OK;
+}
+
+// numeric part shared by the full setup and the partial rebuild (Alg. 4 body)
+amg_status numeric_rebuild(amg_ctx *ctx, const double *d_val, bool galerkin) {
+    const amg_params &p = ctx->prm;
+    Level &F = ctx->lev[0];
+    const bool mx = mixed(ctx);
+    launch_ingest_fine(F.n, F.A_ptr, d_val, F.dia, p.smoother, p.jacobi_omega, d_val == F.A_val ? nullptr : F.A_val,
+                       mx ? F.A_valf : nullptr, mx ? nullptr : F.m, mx ? F.mf : nullptr, ctx->d_st, ctx->s);
+    for (int l = 0; l + 1 < ctx->nlev; ++l) {
+        Level &L = ctx->lev[l];
+        Level &C = ctx->lev[l + 1];
+        if (galerkin) {
+            if (mx) {
+                launch_ap_numeric_f32(L, L.A_valf, ctx->s);
+                launch_rap_numeric_f32(L, C.A_ptr, C.A_valf, ctx->s);
+            } else {
+                launch_ap_numeric_f64(L, L.A_val, ctx->s);
+                launch_rap_numeric_f64(L, C.A_ptr, C.A_val, ctx->s);
+            }
+        }
+        if (l + 1 < ctx->nlev - 1) {
+            if (mx) launch_smoother_f32(C.n, C.A_ptr, C.A_valf, C.dia, p.smoother, p.jacobi_omega, C.mf, ctx->s);
+            else launch_smoother_f64(C.n, C.A_ptr, C.A_val, C.dia, p.smoother, p.jacobi_omega, C.m, ctx->s);
+        }
+    }
+    return coarse_factor(ctx);
+}
+
+amg_status full_setup_impl(amg_ctx *ctx, const double *d_val) {
+    const amg_params &p = ctx->prm;
+    free_hierarchy(ctx);
+    TRY(reset_status(ctx));
+    const int32_t n = ctx->n, nnz = ctx->nnz;
+    Level &F = ctx->lev[0];
+    F.n = n;
+    F.nnz = nnz;
+    F.A_ptr = ctx->fine_ptr;
+    F.A_col = ctx->fine_col;
+    TRY(alloc(ctx, &F.A_val, (size_t)nnz));
+    TRY(alloc(ctx, &F.dia, (size_t)n));
+    launch_check_pattern(n, F.A_ptr, F.A_col, F.dia, ctx->d_st, ctx->s);
+    launch_check_finite(nnz, d_val, ctx->d_st, ctx->s);
+    CK(cudaMemcpyAsync(F.A_val, d_val, sizeof(double) * (size_t)nnz, cudaMemcpyDeviceToDevice, ctx->s));
+    TRY(check_device(ctx, "full setup input"));
+    ctx->nlev = 1;
+    double theta = p.theta;
+    for (;;) {
+        Level &L = ctx->lev[ctx->nlev - 1];
+        TRY(alloc_level_vectors(ctx, L));
+        TRY(alloc(ctx, &L.agg, (size_t)L.n));
+        TRY(alloc(ctx, &L.strong, (size_t)L.nnz));
+        CK(cudaMemsetAsync(L.agg, 0xff, sizeof(int32_t) * (size_t)L.n, ctx->s));
+        CK(cudaMemsetAsync(L.strong, 0, (size_t)L.nnz, ctx->s));
+        if (L.n <= p.coarse_enough || ctx->nlev >= p.max_levels || ctx->nlev >= kMaxLevels) break;
+        // strength and aggregation
+        int32_t *deg = nullptr, *root_id = nullptr, *agg1 = nullptr, *root_of = nullptr;
+        int8_t *state = nullptr;
+        int64_t *m1 = nullptr, *scan_tmp = nullptr;
+        uint8_t *r1 = nullptr;
+        int *counter = nullptr;
+        TRY(alloc(ctx, &deg, (size_t)L.n));
+        TRY(alloc(ctx, &root_id, (size_t)L.n + 1));
+        TRY(alloc(ctx, &agg1, (size_t)L.n));
+        TRY(alloc(ctx, &root_of, (size_t)L.n));
+        TRY(alloc(ctx, &state, (size_t)L.n));
+        TRY(alloc(ctx, &m1, (size_t)L.n));
+        TRY(alloc(ctx, &r1, (size_t)L.n));
+        TRY(alloc(ctx, &counter, 1));
+        TRY(alloc(ctx, &scan_tmp, (size_t)scan_tmp_elems(L.n)));
+        launch_strength(L.n, L.A_ptr, L.A_col, L.A_val, L.dia, theta * theta, L.strong, deg, ctx->s);
+        int32_t nagg = run_aggregation(L.n, L.A_ptr, L.A_col, L.A_val, L.strong, deg, L.agg, state, m1, r1, root_id,
+                                       agg1, root_of, counter, ctx->d_st, scan_tmp, ctx->s);
+        if (nagg < 0) {
+            CK(cudaGetLastError());
+            return set_err(ctx, AMG_ERR_CUDA, "aggregation did not complete");
+        }
+        TRY(check_device(ctx, "aggregation"));
+        if (nagg == 0 || nagg >= L.n) {
+            // coarsening stalls: this level becomes the coarsest
+            CK(cudaMemsetAsync(L.agg, 0xff, sizeof(int32_t) * (size_t)L.n, ctx->s));
+            CK(cudaMemsetAsync(L.strong, 0, (size_t)L.nnz, ctx->s));
+            break;
+        }
+        L.nc = nagg;
+        // smoothed prolongation
+        int32_t *plen = nullptr;
+        TRY(alloc(ctx, &plen, (size_t)L.n));
+        TRY(alloc(ctx, &L.P_ptr, (size_t)L.n + 1));
+        launch_p_count(L.n, L.A_ptr, L.A_col, L.strong, L.agg, p.smoothed, plen, ctx->s);
+        TRY(scan(ctx, plen, L.P_ptr, L.n));
+        TRY(read_scalar(ctx, L.P_ptr + L.n, &L.nnzP));
+        TRY(alloc(ctx, &L.P_col, (size_t)L.nnzP));
+        TRY(alloc(ctx, &L.P_val, (size_t)L.nnzP));
+        launch_p_fill(L.n, L.A_ptr, L.A_col, L.A_val, L.strong, L.dia, L.agg, p.omega, p.smoothed, L.P_ptr, L.P_col,
+                      L.P_val, ctx->s);
+        // R = P^T
+        int32_t *cnt = nullptr, *cursor = nullptr;
+        TRY(alloc(ctx, &cnt, (size_t)nagg));
+        TRY(alloc(ctx, &cursor, (size_t)nagg));
+        CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)nagg, ctx->s));
+        CK(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * (size_t)nagg, ctx->s));
+        launch_count_cols(L.nnzP, L.P_col, cnt, ctx->s);
+        TRY(alloc(ctx, &L.R_ptr, (size_t)nagg + 1));
+        TRY(scan(ctx, cnt, L.R_ptr, nagg));
+        L.nnzR = L.nnzP;
+        TRY(alloc(ctx, &L.R_col, (size_t)L.nnzR));
+        TRY(alloc(ctx, &L.R_val, (size_t)L.nnzR));
+        launch_transpose_scatter(L.n, L.P_ptr, L.P_col, L.P_val, L.R_ptr, cursor, L.R_col, L.R_val, ctx->s);
+        launch_sort_rows(nagg, L.R_ptr, L.R_col, L.R_val, ctx->s);
+        // symbolic Galerkin product: AP = A*P, A_c = R*AP (+ diagonal)
+        TRY(symbolic_product(ctx, L.n, nagg, L.A_ptr, L.A_col, L.P_ptr, L.P_col, 0, &L.AP_ptr, &L.AP_col,
+                             &L.nnzAP));
+        TRY(alloc(ctx, &L.AP_val, (size_t)L.nnzAP));
+        Level &C = ctx->lev[ctx->nlev];
+        C.n = nagg;
+        TRY(symbolic_product(ctx, nagg, nagg, L.R_ptr, L.R_col, L.AP_ptr, L.AP_col, 1, &C.A_ptr, &C.A_col, &C.nnz));
+        TRY(alloc(ctx, &C.A_val, (size_t)C.nnz));
+        TRY(alloc(ctx, &C.dia, (size_t)C.n));
+        launch_check_pattern(C.n, C.A_ptr, C.A_col, C.dia, ctx->d_st, ctx->s);
+        TRY(max_row(ctx, L.n, L.AP_ptr, &L.max_ap_row));
+        TRY(max_row(ctx, C.n, C.A_ptr, &L.max_ac_row));
+        if (L.max_ap_row > 65535 || L.max_ac_row > 65535)
+            return set_err(ctx, AMG_ERR_CAPACITY, "Galerkin row longer than 65535 entries");
+        // gather metadata: slot of every term of the two numeric stages
+        int32_t *tc = nullptr;
+        TRY(alloc(ctx, &tc, (size_t)std::max(L.n, nagg)));
+        TRY(alloc(ctx, &L.t1ptr, (size_t)L.n + 1));
+        launch_t1_count(L.n, L.A_ptr, L.A_col, L.P_ptr, tc, ctx->s);
+        TRY(scan(ctx, tc, L.t1ptr, L.n));
+        int32_t nt1 = 0, nt2 = 0;
+        TRY(check_device(ctx, "term count"));
+        TRY(read_scalar(ctx, L.t1ptr + L.n, &nt1));
+        L.nt1 = nt1;
+        TRY(alloc(ctx, &L.slot1, (size_t)nt1));
+        launch_t1_fill(L.n, L.A_ptr, L.A_col, L.P_ptr, L.P_col, L.AP_ptr, L.AP_col, L.t1ptr, L.slot1, ctx->d_st,
+                       ctx->s);
+        TRY(alloc(ctx, &L.t2ptr, (size_t)nagg + 1));
+        launch_t2_count(nagg, L.R_ptr, L.R_col, L.AP_ptr, tc, ctx->s);
+        TRY(scan(ctx, tc, L.t2ptr, nagg));
+        TRY(check_device(ctx, "term count"));
+        TRY(read_scalar(ctx, L.t2ptr + nagg, &nt2));
+        L.nt2 = nt2;
+        TRY(alloc(ctx, &L.slot2, (size_t)nt2));
+        launch_t2_fill(nagg, L.R_ptr, L.R_col, L.AP_ptr, L.AP_col, C.A_ptr, C.A_col, L.t2ptr, L.slot2, ctx->d_st,
+                       ctx->s);
+        // numeric values of the next level now: its strength test needs them
+        launch_ap_numeric_f64(L, L.A_val, ctx->s);
+        launch_rap_numeric_f64(L, C.A_ptr, C.A_val, ctx->s);
+        TRY(check_device(ctx, "Galerkin product"));
+        if (mixed(ctx)) {
+            TRY(alloc(ctx, &L.P_valf, (size_t)L.nnzP));
+            TRY(alloc(ctx, &L.R_valf, (size_t)L.nnzR));
+            TRY(alloc(ctx, &L.AP_valf, (size_t)L.nnzAP));
+            launch_cast_f32(L.nnzP, L.P_val, L.P_valf, ctx->s);
+            launch_cast_f32(L.nnzR, L.R_val, L.R_valf, ctx->s);
+        }
+        ctx->nlev++;
+        if (p.theta_halving) theta = theta * 0.5;
+    }
+    // coarsest solver storage
+    Level &C = ctx->lev[ctx->nlev - 1];
+    ctx->nL = C.n;
+    if ((int64_t)C.n * C.n > (int64_t)1 << 28)
+        return set_err(ctx, AMG_ERR_CAPACITY, "coarsest level too large for a dense LU");
+    TRY(alloc(ctx, &ctx->lu, (size_t)C.n * C.n));
+    TRY(alloc(ctx, &ctx->inv, (size_t)C.n * C.n));
+    TRY(alloc(ctx, &ctx->piv, (size_t)C.n));
+    if (mixed(ctx))
+        for (int l = 1; l < ctx->nlev; ++l) launch_cast_f32(ctx->lev[l].nnz, ctx->lev[l].A_val, ctx->lev[l].A_valf, ctx->s);
+    TRY(numeric_rebuild(ctx, ctx->lev[0].A_val, false));
+    TRY(check_device(ctx, "full setup"));
+    ctx->have_setup = true;
+    return AMG_OK;
+}
+
+amg_status ensure_persistent(amg_ctx *ctx, int32_t n, int32_t nnz) {
+    if (ctx->fine_ptr && ctx->n == n && ctx->nnz == nnz) return AMG_OK;
+    for (void *q : ctx->persist) cudaFreeAsync(q, ctx->s);
+    ctx->persist.clear();
+    ctx->n = n;
+    ctx->nnz = nnz;
+    TRY(alloc(ctx, &ctx->fine_ptr, (size_t)n + 1, true));
+    TRY(alloc(ctx, &ctx->fine_col, (size_t)nnz, true));
+    TRY(alloc(ctx, &ctx->cg_r, (size_t)n, true));
+    TRY(alloc(ctx, &ctx->cg_z, (size_t)n, true));
+    TRY(alloc(ctx, &ctx->cg_p, (size_t)n, true));
+    TRY(alloc(ctx, &ctx->cg_q, (size_t)n, true));
+    TRY(alloc(ctx, &ctx->cg_t, (size_t)n, true));
+    TRY(alloc(ctx, &ctx->partial, (size_t)cg_blocks(n), true));
+    TRY(alloc(ctx, &ctx->partial2, (size_t)cg_blocks(n), true));
+    TRY(alloc(ctx, &ctx->cg, 1, true));
+    TRY(alloc(ctx, &ctx->stage_val, (size_t)nnz, true));
+    TRY(alloc(ctx, &ctx->stage_f, (size_t)n, true));
+    TRY(alloc(ctx, &ctx->stage_u, (size_t)n, true));
+    ctx->A_sys_own = nullptr;
+    if (ctx->prm.mode == AMG_MODE_FULL_REUSE) TRY(alloc(ctx, &ctx->A_sys_own, (size_t)nnz, true));
+    return AMG_OK;
+}
+
+amg_status set_pattern(amg_ctx *ctx, int32_t n, int32_t nnz, const int32_t *d_ptr, const int32_t *d_col) {
+    if (n <= 0 || nnz < n || !d_ptr || !d_col) return set_err(ctx, AMG_ERR_ARG, "bad matrix size or null pattern");
+    TRY(ensure_persistent(ctx, n, nnz));
+    if (d_ptr == ctx->fine_ptr && d_col == ctx->fine_col) return AMG_OK;
+    CK(cudaMemcpyAsync(ctx->fine_ptr, d_ptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToDevice, ctx->s));
+    CK(cudaMemcpyAsync(ctx->fine_col, d_col, sizeof(int32_t) * (size_t)nnz, cudaMemcpyDeviceToDevice, ctx->s));
+    return AMG_OK;
+}
+
+void update_sys(amg_ctx *ctx) {
+    ctx->A_sys = ctx->A_sys_own ? ctx->A_sys_own : ctx->lev[0].A_val;
+}
+
+// ---------------------------------------------------------------- V-cycle
+template <class V>
+struct Vops;
+template <>
+struct Vops<double> {
+    static VecSet<double> &vec(Level &L) { return L.vd; }
+    static const double *A(const Level &L) { return L.A_val; }
+    static const double *m(const Level &L) { return L.m; }
+    static const double *P(const Level &L) { return L.P_val; }
+    static const double *R(const Level &L) { return L.R_val; }
+};
+template <>
+struct Vops<float> {
+    static VecSet<float> &vec(Level &L) { return L.vf; }
+    static const float *A(const Level &L) { return L.A_valf; }
+    static const float *m(const Level &L) { return L.mf; }
+    static const float *P(const Level &L) { return L.P_valf; }
+    static const float *R(const Level &L) { return L.R_valf; }
+};
+
+// pre-smoothing from a zero guess and the residual on level l (input f of type TF);
+// returns the level's current iterate pointer
+template <class V, class TF>
+V *down_level(amg_ctx *ctx, int l, const TF *f, const int *skip) {
+    Level &L = ctx->lev[l];
+    VecSet<V> &v = Vops<V>::vec(L);
+    const V *A = Vops<V>::A(L), *m = Vops<V>::m(L);
+    const int npre = ctx->prm.npre;
+    V *u = v.u, *t = v.t;
+    if (npre <= 0) {
+        cudaMemsetAsync(u, 0, sizeof(V) * (size_t)L.n, ctx->s);
+        launch_copy_cast<TF, V>(L.n, f, v.r, skip, ctx->s);
+        return u;
+    }
+    launch_smooth0_residual<V, TF>(L, A, m, f, u, v.r, skip, ctx->s);
+    if (npre > 1) {
+        for (int k = 1; k < npre; ++k) {
+            launch_smooth_sweep<V, TF, V>(L, A, m, f, u, t, skip, ctx->s);
+            std::swap(u, t);
+        }
+        launch_residual<V, TF>(L, A, f, u, v.r, skip, ctx->s);
+    }
+    return u;
+}
+
+// post-smoothing on level l; the last sweep writes `out` (type TO) when given
+template <class V, class TF, class TO>
+void up_level(amg_ctx *ctx, int l, const TF *f, V *u, TO *out, const int *skip) {
+    Level &L = ctx->lev[l];
+    VecSet<V> &v = Vops<V>::vec(L);
+    const V *A = Vops<V>::A(L), *m = Vops<V>::m(L);
+    V *t = (u == v.u) ? v.t : v.u;
+    const int npost = ctx->prm.npost;
+    for (int k = 0; k < npost; ++k) {
+        if (k == npost - 1 && out) {
+            launch_smooth_sweep<V, TF, TO>(L, A, m, f, u, out, skip, ctx->s);
+            return;
+        }
+        launch_smooth_sweep<V, TF, V>(L, A, m, f, u, t, skip, ctx->s);
+        std::swap(u, t);
+    }
+    if (out) launch_copy_cast<V, TO>(L.n, u, out, skip, ctx->s);
+}
+
+template <class V>
+void enqueue_vcycle(amg_ctx *ctx, const double *r, double *z, const int *skip) {
+    const int nl = ctx->nlev;
+    if (nl == 1) {
+        launch_coarse_solve<V, double, double>(ctx->lev[0].n, ctx->inv, r, z, skip, ctx->s);
+        return;
+    }
+    V *cur[kMaxLevels];
+    cur[0] = down_level<V, double>(ctx, 0, r, skip);
+    launch_restrict<V>(ctx->lev[0], Vops<V>::R(ctx->lev[0]), Vops<V>::vec(ctx->lev[0]).r,
+                       Vops<V>::vec(ctx->lev[1]).f, skip, ctx->s);
+    for (int l = 1; l < nl - 1; ++l) {
+        Level &L = ctx->lev[l];
+        cur[l] = down_level<V, V>(ctx, l, Vops<V>::vec(L).f, skip);
+        launch_restrict<V>(L, Vops<V>::R(L), Vops<V>::vec(L).r, Vops<V>::vec(ctx->lev[l + 1]).f, skip, ctx->s);
+    }
+    Level &Cst = ctx->lev[nl - 1];
+    launch_coarse_solve<V, V, V>(Cst.n, ctx->inv, Vops<V>::vec(Cst).f, Vops<V>::vec(Cst).u, skip, ctx->s);
+    cur[nl - 1] = Vops<V>::vec(Cst).u;
+    for (int l = nl - 2; l >= 1; --l) {
+        Level &L = ctx->lev[l];
+        launch_prolong<V>(L, Vops<V>::P(L), cur[l + 1], cur[l], skip, ctx->s);
+        // the post-smoothed iterate stays in this level's buffers
+        V *u = cur[l];
+        VecSet<V> &v = Vops<V>::vec(L);
+        V *t = (u == v.u) ? v.t : v.u;
+        for (int k = 0; k < ctx->prm.npost; ++k) {
+            launch_smooth_sweep<V, V, V>(L, Vops<V>::A(L), Vops<V>::m(L), v.f, u, t, skip, ctx->s);
+            std::swap(u, t);
+        }
+        cur[l] = u;
+    }
+    Level &F = ctx->lev[0];
+    launch_prolong<V>(F, Vops<V>::P(F), cur[1], cur[0], skip, ctx->s);
+    up_level<V, double, double>(ctx, 0, r, cur[0], z, skip);
+}
+
+void vcycle(amg_ctx *ctx, const double *r, double *z, const int *skip) {
+    if (mixed(ctx)) enqueue_vcycle<float>(ctx, r, z, skip);
+    else enqueue_vcycle<double>(ctx, r, z, skip);
+}
+
+// ---------------------------------------------------------------- CG
+amg_status solve_impl(amg_ctx *ctx, const double *f, double *u, double tol, amg_info *info) {
+    const int32_t n = ctx->n;
+    const int nblk = cg_blocks(n);
+    const int maxiter = ctx->prm.maxiter;
+    const bool flex = mixed(ctx);
+    CgState *cg = ctx->cg;
+    const int *done = &cg->done;
+    const double *A = ctx->A_sys;
+    const int32_t *ptr = ctx->fine_ptr, *col = ctx->fine_col;
+    double *r = ctx->cg_r, *z = ctx->cg_z, *p = ctx->cg_p, *q = ctx->cg_q, *t = ctx->cg_t;
+    launch_cg_init(n, f, u, r, ctx->partial, ctx->s);
+    launch_cg_start(nblk, ctx->partial, cg, tol, maxiter, ctx->s);
+    vcycle(ctx, r, z, done);
+    launch_dot(n, r, z, ctx->partial, done, ctx->s);
+    launch_cg_set_rz_p(n, nblk, ctx->partial, z, p, cg, ctx->s);
+    for (int it = 1; it <= maxiter; ++it) {
+        launch_spmv_dot(n, ptr, col, A, p, q, ctx->partial, done, ctx->s);
+        launch_cg_alpha(nblk, ctx->partial, cg, ctx->s);
+        launch_cg_update_ur(n, cg, p, q, u, r, ctx->partial, ctx->s);
+        launch_cg_check(nblk, ctx->partial, cg, ctx->s);
+        launch_true_residual(n, ptr, col, A, f, u, t, ctx->partial, cg, 0, ctx->s);
+        launch_true_check(nblk, ctx->partial, cg, ctx->s);
+        launch_replace_r(n, cg, t, r, ctx->s);
+        if (flex) launch_dot(n, r, z, ctx->partial2, done, ctx->s);
+        vcycle(ctx, r, z, done);
+        launch_dot(n, r, z, ctx->partial, done, ctx->s);
+        if (flex) launch_cg_beta_flexible(nblk, ctx->partial, ctx->partial2, cg, ctx->s);
+        else launch_cg_beta(nblk, ctx->partial, cg, ctx->s);
+        launch_cg_update_p(n, cg, z, p, ctx->s);
+        CK(cudaMemcpyAsync(ctx->h_cg, cg, sizeof(CgState), cudaMemcpyDeviceToHost, ctx->s));
+        CK(cudaStreamSynchronize(ctx->s));
+        if (ctx->h_cg->done) break;
+    }
+    // the true relative residual of the returned iterate
+    launch_true_residual(n, ptr, col, A, f, u, t, ctx->partial, cg, 1, ctx->s);
+    launch_cg_final_norm(nblk, ctx->partial, cg, ctx->s);
+    CK(cudaMemcpyAsync(ctx->h_cg, cg, sizeof(CgState), cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    CK(cudaGetLastError());
+    const CgState &h = *ctx->h_cg;
+    amg_status st = (amg_status)h.status;
+    if (!h.done && st == AMG_OK) st = AMG_NOT_CONVERGED;
+    ctx->last_iters = h.iter;
+    ctx->last_status = st;
+    if (info) {
+        info->iters = h.iter;
+        info->rel_resid = h.tres;
+        info->status = st;
+        info->rebuilt = ctx->last_rebuilt;
+        info->nlevels = ctx->nlev;
+    }
+    if (st == AMG_ERR_BREAKDOWN) set_err(ctx, st, "CG breakdown: p'Ap <= 0 or not finite");
+    else if (st == AMG_NOT_CONVERGED) set_err(ctx, st, "CG reached maxiter");
+    return st;
+}
+
+}  // namespace
+
+// ======================================================================= C ABI
+extern "C" {
+
+amg_status amg_default_params(amg_params *prm) {
+    if (!prm) return AMG_ERR_ARG;
+    prm->theta = 0.08;
+    prm->omega = 2.0 / 3.0;
+    prm->jacobi_omega = 0.72;
+    prm->smoother = AMG_SMOOTHER_SPAI0;
+    prm->npre = 1;
+    prm->npost = 1;
+    prm->coarse_enough = 256;
+    prm->max_levels = 20;
+    prm->theta_halving = 1;
+    prm->smoothed = 1;
+    prm->precision = AMG_PREC_FP64;
+    prm->mode = AMG_MODE_PARTIAL;
+    prm->reuse_iter_limit = 100;
+    prm->maxiter = 100;
+    return AMG_OK;
+}
+
+amg_status amg_create(amg_ctx **out, const amg_params *prm, void *cuda_stream) {
+    if (!out) return AMG_ERR_ARG;
+    *out = nullptr;
+    amg_params p;
+    if (prm) p = *prm;
+    else amg_default_params(&p);
+    if (p.npre < 0 || p.npost < 0 || p.max_levels < 1 || p.coarse_enough < 1 || p.maxiter < 0 ||
+        (p.smoother != AMG_SMOOTHER_SPAI0 && p.smoother != AMG_SMOOTHER_JACOBI) ||
+        (p.precision != AMG_PREC_FP64 && p.precision != AMG_PREC_MIXED) || p.mode < 0 || p.mode > 2 ||
+        !(p.theta >= 0.0) || !std::isfinite(p.omega))
+        return AMG_ERR_ARG;
+    amg_ctx *ctx = new amg_ctx();
+    ctx->prm = p;
+    ctx->s = (cudaStream_t)cuda_stream;
+    int dev = 0;
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    if (cudaGetDevice(&dev) != cudaSuccess) { delete ctx; return AMG_ERR_CUDA; }
+    props.location.id = dev;
+    if (cudaMemPoolCreate(&ctx->pool, &props) != cudaSuccess) { delete ctx; return AMG_ERR_CUDA; }
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    if (cudaMallocHost(&ctx->h_cg, sizeof(CgState)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_st, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&ctx->d_st, sizeof(int)) != cudaSuccess) {
+        amg_destroy(ctx);
+        return AMG_ERR_CUDA;
+    }
+    *out = ctx;
+    return AMG_OK;
+}
+
+void amg_destroy(amg_ctx *ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->s);
+    for (void *p : ctx->hier) cudaFreeAsync(p, ctx->s);
+    for (void *p : ctx->persist) cudaFreeAsync(p, ctx->s);
+    cudaStreamSynchronize(ctx->s);
+    if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+    if (ctx->h_cg) cudaFreeHost(ctx->h_cg);
+    if (ctx->h_st) cudaFreeHost(ctx->h_st);
+    if (ctx->d_st) cudaFree(ctx->d_st);
+    delete ctx;
+}
+
+const char *amg_last_error(const amg_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+amg_status amg_full_setup(amg_ctx *ctx, int32_t n, int32_t nnz, const int32_t *d_ptr, const int32_t *d_col,
+                          const double *d_val) {
+    if (!ctx) return AMG_ERR_ARG;
+    if (!d_val) return set_err(ctx, AMG_ERR_ARG, "null values");
+    TRY(set_pattern(ctx, n, nnz, d_ptr, d_col));
+    amg_status st = full_setup_impl(ctx, d_val);
+    if (st != AMG_OK) {
+        free_hierarchy(ctx);
+        return st;
+    }
+    if (ctx->A_sys_own)
+        CK(cudaMemcpyAsync(ctx->A_sys_own, d_val, sizeof(double) * (size_t)nnz, cudaMemcpyDeviceToDevice, ctx->s));
+    update_sys(ctx);
+    ctx->last_rebuilt = 1;
+    return AMG_OK;
+}
+
+amg_status amg_partial_rebuild(amg_ctx *ctx, const double *d_val) {
+    if (!ctx) return AMG_ERR_ARG;
+    if (!ctx->have_setup) return set_err(ctx, AMG_ERR_STATE, "partial rebuild before a full setup");
+    if (!d_val) return set_err(ctx, AMG_ERR_ARG, "null values");
+    TRY(reset_status(ctx));
+    TRY(numeric_rebuild(ctx, d_val, true));
+    if (ctx->A_sys_own)
+        CK(cudaMemcpyAsync(ctx->A_sys_own, d_val, sizeof(double) * (size_t)ctx->nnz, cudaMemcpyDeviceToDevice,
+                           ctx->s));
+    TRY(check_device(ctx, "partial rebuild"));
+    update_sys(ctx);
+    ctx->last_rebuilt = 0;
+    return AMG_OK;
+}
+
+amg_status amg_step(amg_ctx *ctx, int32_t n, int32_t nnz, const int32_t *d_ptr, const int32_t *d_col,
+                    const double *d_val, amg_info *info) {
+    if (!ctx) return AMG_ERR_ARG;
+    if (!d_val) return set_err(ctx, AMG_ERR_ARG, "null values");
+    if (ctx->have_setup && (n != ctx->n || nnz != ctx->nnz))
+        return set_err(ctx, AMG_ERR_ARG, "size differs from the pattern of the first step");
+    amg_status st = AMG_OK;
+    const int mode = ctx->prm.mode;
+    if (!ctx->have_setup) {
+        st = amg_full_setup(ctx, n, nnz, d_ptr, d_col, d_val);
+    } else if (mode == AMG_MODE_PARTIAL) {
+        st = amg_partial_rebuild(ctx, d_val);
+    } else if (mode == AMG_MODE_FULL_REBUILD) {
+        st = full_setup_impl(ctx, d_val);
+        if (st == AMG_OK) { update_sys(ctx); ctx->last_rebuilt = 1; }
+        else free_hierarchy(ctx);
+    } else {
+        bool rebuild = ctx->last_status != AMG_OK || ctx->last_iters > ctx->prm.reuse_iter_limit;
+        if (rebuild) {
+            st = full_setup_impl(ctx, d_val);
+            if (st != AMG_OK) free_hierarchy(ctx);
+        }
+        if (st == AMG_OK) {
+            CK(cudaMemcpyAsync(ctx->A_sys_own, d_val, sizeof(double) * (size_t)ctx->nnz, cudaMemcpyDeviceToDevice,
+                               ctx->s));
+            update_sys(ctx);
+            ctx->last_rebuilt = rebuild ? 1 : 0;
+        }
+    }
+    if (info) {
+        info->rebuilt = ctx->last_rebuilt;
+        info->nlevels = ctx->nlev;
+    }
+    return st;
+}
+
+amg_status amg_solve(amg_ctx *ctx, const double *d_f, double *d_u, double tol, amg_info *info) {
+    if (!ctx) return AMG_ERR_ARG;
+    if (!ctx->have_setup) return set_err(ctx, AMG_ERR_STATE, "solve before a setup");
+    if (!d_f || !d_u || !(tol >= 0.0)) return set_err(ctx, AMG_ERR_ARG, "null vector or bad tolerance");
+    return solve_impl(ctx, d_f, d_u, tol, info);
+}
+
+amg_status amg_apply_vcycle(amg_ctx *ctx, const double *d_r, double *d_z) {
+    if (!ctx) return AMG_ERR_ARG;
+    if (!ctx->have_setup) return set_err(ctx, AMG_ERR_STATE, "V-cycle before a setup");
+    if (!d_r || !d_z) return set_err(ctx, AMG_ERR_ARG, "null vector");
+    vcycle(ctx, d_r, d_z, nullptr);
+    CK(cudaStreamSynchronize(ctx->s));
+    CK(cudaGetLastError());
+    return AMG_OK;
+}
+
+amg_status amg_step_solve_host(amg_ctx *ctx, const double *h_val, const double *h_f, double *h_u, double tol,
+                               amg_info *info) {
+    if (!ctx) return AMG_ERR_ARG;
+    if (!ctx->fine_ptr) return set_err(ctx, AMG_ERR_STATE, "no pattern: call amg_full_setup or amg_step first");
+    if (!h_val || !h_f || !h_u) return set_err(ctx, AMG_ERR_ARG, "null host buffer");
+    CK(cudaMemcpyAsync(ctx->stage_val, h_val, sizeof(double) * (size_t)ctx->nnz, cudaMemcpyHostToDevice, ctx->s));
+    CK(cudaMemcpyAsync(ctx->stage_f, h_f, sizeof(double) * (size_t)ctx->n, cudaMemcpyHostToDevice, ctx->s));
+    amg_status st = amg_step(ctx, ctx->n, ctx->nnz, ctx->fine_ptr, ctx->fine_col, ctx->stage_val, info);
+    if (st != AMG_OK) return st;
+    st = amg_solve(ctx, ctx->stage_f, ctx->stage_u, tol, info);
+    if (st != AMG_OK && st != AMG_NOT_CONVERGED) return st;
+    CK(cudaMemcpyAsync(h_u, ctx->stage_u, sizeof(double) * (size_t)ctx->n, cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    return st;
+}
+
+amg_status amg_num_levels(const amg_ctx *ctx, int32_t *nlevels) {
+    if (!ctx || !nlevels) return AMG_ERR_ARG;
+    *nlevels = ctx->nlev;
+    return AMG_OK;
+}
+
+amg_status amg_level_sizes(const amg_ctx *ctx, int32_t level, int64_t *sizes) {
+    if (!ctx || !sizes || level < 0 || level >= ctx->nlev) return AMG_ERR_ARG;
+    const Level &L = ctx->lev[level];
+    sizes[0] = L.n;
+    sizes[1] = L.nnz;
+    sizes[2] = L.nnzP;
+    sizes[3] = L.nnzR;
+    sizes[4] = L.nnzAP;
+    sizes[5] = L.nc;
+    return AMG_OK;
+}
+
+amg_status amg_export_csr(amg_ctx *ctx, int32_t level, int32_t which, int32_t *d_ptr, int32_t *d_col,
+                          double *d_val) {
+    if (!ctx || level < 0 || level >= ctx->nlev || which < 0 || which > 2) return AMG_ERR_ARG;
+    Level &L = ctx->lev[level];
+    int32_t nrows = which == 0 ? L.n : which == 1 ? L.n : L.nc;
+    int32_t nnz = which == 0 ? L.nnz : which == 1 ? L.nnzP : L.nnzR;
+    const int32_t *ptr = which == 0 ? L.A_ptr : which == 1 ? L.P_ptr : L.R_ptr;
+    const int32_t *col = which == 0 ? L.A_col : which == 1 ? L.P_col : L.R_col;
+    const double *val = which == 0 ? L.A_val : which == 1 ? L.P_val : L.R_val;
+    const float *valf = which == 0 ? L.A_valf : which == 1 ? L.P_valf : L.R_valf;
+    if (!ptr) return set_err(ctx, AMG_ERR_STATE, "no such operator on this level");
+    if (d_ptr) CK(cudaMemcpyAsync(d_ptr, ptr, sizeof(int32_t) * ((size_t)nrows + 1), cudaMemcpyDeviceToDevice, ctx->s));
+    if (d_col) CK(cudaMemcpyAsync(d_col, col, sizeof(int32_t) * (size_t)nnz, cudaMemcpyDeviceToDevice, ctx->s));
+    if (d_val) {
+        if (mixed(ctx) && valf) launch_copy_cast<float, double>(nnz, valf, d_val, nullptr, ctx->s);
+        else CK(cudaMemcpyAsync(d_val, val, sizeof(double) * (size_t)nnz, cudaMemcpyDeviceToDevice, ctx->s));
+    }
+    CK(cudaStreamSynchronize(ctx->s));
+    return AMG_OK;
+}
+
+amg_status amg_export_level_vec(amg_ctx *ctx, int32_t level, int32_t *d_agg, uint8_t *d_strong, double *d_m) {
+    if (!ctx || level < 0 || level >= ctx->nlev) return AMG_ERR_ARG;
+    Level &L = ctx->lev[level];
+    if (d_agg) CK(cudaMemcpyAsync(d_agg, L.agg, sizeof(int32_t) * (size_t)L.n, cudaMemcpyDeviceToDevice, ctx->s));
+    if (d_strong) CK(cudaMemcpyAsync(d_strong, L.strong, (size_t)L.nnz, cudaMemcpyDeviceToDevice, ctx->s));
+    if (d_m) {
+        if (mixed(ctx)) launch_copy_cast<float, double>(L.n, L.mf, d_m, nullptr, ctx->s);
+        else CK(cudaMemcpyAsync(d_m, L.m, sizeof(double) * (size_t)L.n, cudaMemcpyDeviceToDevice, ctx->s));
+    }
+    CK(cudaStreamSynchronize(ctx->s));
+    return AMG_OK;
+}
+
+amg_status amg_export_coarse_lu(amg_ctx *ctx, double *d_lu, int32_t *d_piv) {
+    if (!ctx || !ctx->have_setup) return AMG_ERR_ARG;
+    size_t nn = (size_t)ctx->nL * (size_t)ctx->nL;
+    if (d_lu) CK(cudaMemcpyAsync(d_lu, ctx->lu, sizeof(double) * nn, cudaMemcpyDeviceToDevice, ctx->s));
+    if (d_piv) CK(cudaMemcpyAsync(d_piv, ctx->piv, sizeof(int32_t) * (size_t)ctx->nL, cudaMemcpyDeviceToDevice, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    return AMG_OK;
+}
+
+int64_t amg_poisson_nnz(int32_t dim, int32_t N) {
+    if ((dim != 2 && dim != 3) || N < 1) return -1;
+    int64_t n1 = N, nf = N - 1;
+    return dim == 2 ? n1 * n1 + 4 * nf * n1 : n1 * n1 * n1 + 6 * nf * n1 * n1;
+}
+
+amg_status amg_poisson_pattern(int32_t dim, int32_t N, int32_t *d_ptr, int32_t *d_col, void *cuda_stream) {
+    if ((dim != 2 && dim != 3) || N < 1 || !d_ptr || !d_col) return AMG_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int64_t n = dim == 2 ? (int64_t)N * N : (int64_t)N * N * N;
+    if (amg_poisson_nnz(dim, N) > INT32_MAX) return AMG_ERR_ARG;
+    int32_t *len = nullptr;
+    int64_t *tmp = nullptr;
+    int *st = nullptr;
+    if (cudaMallocAsync(&len, sizeof(int32_t) * (size_t)n, s) != cudaSuccess) return AMG_ERR_OOM;
+    if (cudaMallocAsync(&tmp, sizeof(int64_t) * (size_t)scan_tmp_elems(n), s) != cudaSuccess) return AMG_ERR_OOM;
+    if (cudaMallocAsync(&st, sizeof(int), s) != cudaSuccess) return AMG_ERR_OOM;
+    cudaMemsetAsync(st, 0, sizeof(int), s);
+    launch_poisson_rowlen(dim, N, len, s);
+    scan_counts(len, d_ptr, n, st, tmp, s);
+    launch_poisson_cols(dim, N, d_ptr, d_col, s);
+    cudaFreeAsync(len, s);
+    cudaFreeAsync(tmp, s);
+    cudaFreeAsync(st, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return AMG_ERR_CUDA;
+    return AMG_OK;
+}
+
+amg_status amg_poisson_values(int32_t dim, int32_t N, int32_t dirichlet_top, const double *d_rho,
+                              const int32_t *d_ptr, double *d_val, void *cuda_stream) {
+    if ((dim != 2 && dim != 3) || N < 1 || !d_rho || !d_ptr || !d_val) return AMG_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    launch_poisson_vals(dim, N, dirichlet_top, d_rho, d_ptr, d_val, s);
+    if (cudaGetLastError() != cudaSuccess) return AMG_ERR_CUDA;
+    return AMG_OK;
+}
+
+amg_status amg_poisson_grad_theta(int32_t dim, int32_t N, int32_t dirichlet_top, const double *d_rho,
+                                  const double *d_u, const double *d_lam, double *d_grad, void *cuda_stream) {
+    if ((dim != 2 && dim != 3) || N < 1 || !d_rho || !d_u || !d_lam || !d_grad) return AMG_ERR_ARG;
+    launch_poisson_grad(dim, N, dirichlet_top, d_rho, d_u, d_lam, d_grad, (cudaStream_t)cuda_stream);
+    if (cudaGetLastError() != cudaSuccess) return AMG_ERR_CUDA;
+    return AMG_OK;
+}
+
+}  // extern "C"

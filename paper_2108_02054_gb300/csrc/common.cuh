@@ -1,0 +1,189 @@
+// common.cuh -- internal declarations shared by the CUDA translation units of
+// libamgpr.so (partial-reuse smoothed-aggregation AMG, arXiv 2108.02054).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/amgpr.h"
+
+namespace amgpr {
+
+// Bits of the device status word that kernels set with atomicOr instead of
+// trapping; the host turns them into an amg_status.
+enum : int {
+    DEV_ERR_PATTERN = 1,
+    DEV_ERR_CAPACITY = 2,
+    DEV_ERR_NONFINITE = 4,
+    DEV_ERR_STATE = 8,
+    DEV_ERR_SINGULAR = 16,
+    DEV_ERR_OVERFLOW = 32,
+};
+
+constexpr int kMaxLevels = 32;
+// symbolic product: per-warp open-addressing hash of at most this many keys
+constexpr int kHashCap = 4096;
+constexpr int kMaxRowUnique = kHashCap / 2;
+
+// Device-resident state of the CG iteration; every CG kernel reads and writes
+// it so that the loop needs no host round trip between its kernels.
+struct CgState {
+    double rz, pq, alpha, beta, rr, nf, res, tres, tol;
+    int iter, maxiter, done, status, replacements, need_true, copy_r, pad;
+};
+
+template <class V>
+struct VecSet {
+    V *u = nullptr, *f = nullptr, *r = nullptr, *t = nullptr;
+};
+
+struct Level {
+    int32_t n = 0, nnz = 0;
+    int32_t *A_ptr = nullptr, *A_col = nullptr, *dia = nullptr;
+    double *A_val = nullptr;   // FP64 values (level 0: the hierarchy's copy of the fine matrix)
+    float *A_valf = nullptr;   // FP32 values (mixed precision)
+    // transfer operators (absent on the coarsest level)
+    int32_t nc = 0, nnzP = 0, nnzR = 0, nnzAP = 0;
+    int32_t *P_ptr = nullptr, *P_col = nullptr;
+    double *P_val = nullptr;
+    float *P_valf = nullptr;
+    int32_t *R_ptr = nullptr, *R_col = nullptr;
+    double *R_val = nullptr;
+    float *R_valf = nullptr;
+    int32_t *AP_ptr = nullptr, *AP_col = nullptr;
+    double *AP_val = nullptr;
+    float *AP_valf = nullptr;
+    // gather metadata of the numeric Galerkin product (resolved once at setup)
+    int64_t nt1 = 0, nt2 = 0;
+    int32_t *t1ptr = nullptr, *t2ptr = nullptr;
+    uint16_t *slot1 = nullptr, *slot2 = nullptr;
+    int32_t max_ap_row = 0, max_ac_row = 0;
+    // aggregation (kept for inspection)
+    int32_t *agg = nullptr;
+    uint8_t *strong = nullptr;
+    // smoother
+    double *m = nullptr;
+    float *mf = nullptr;
+    // V-cycle vectors
+    VecSet<double> vd;
+    VecSet<float> vf;
+};
+
+// ------------------------------------------------------------------ launchers
+// (all enqueue on `s`; `st` is the device status word)
+void scan_counts(const int32_t *in, int32_t *out, int64_t n, int *st, int64_t *tmp, cudaStream_t s);
+int64_t scan_tmp_elems(int64_t n);
+
+void launch_poisson_rowlen(int dim, int N, int32_t *len, cudaStream_t s);
+void launch_poisson_cols(int dim, int N, const int32_t *ptr, int32_t *col, cudaStream_t s);
+void launch_poisson_vals(int dim, int N, int top, const double *rho, const int32_t *ptr, double *val,
+                         cudaStream_t s);
+void launch_poisson_grad(int dim, int N, int top, const double *rho, const double *u, const double *lam,
+                         double *grad, cudaStream_t s);
+
+void launch_check_pattern(int32_t n, const int32_t *ptr, const int32_t *col, int32_t *dia, int *st,
+                          cudaStream_t s);
+void launch_check_finite(int64_t nnz, const double *val, int *st, cudaStream_t s);
+void launch_strength(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const int32_t *dia,
+                     double eps2, uint8_t *strong, int32_t *deg, cudaStream_t s);
+// aggregation; returns the number of aggregates (host sync inside), or -1 on error
+int32_t run_aggregation(int32_t n, const int32_t *ptr, const int32_t *col, const double *val,
+                        const uint8_t *strong, const int32_t *deg, int32_t *agg, int8_t *state, int64_t *m1,
+                        uint8_t *r1, int32_t *root_id, int32_t *agg1, int32_t *root_of, int *counter, int *st,
+                        int64_t *scan_tmp, cudaStream_t s);
+void launch_p_count(int32_t n, const int32_t *ptr, const int32_t *col, const uint8_t *strong, const int32_t *agg,
+                    int smoothed, int32_t *plen, cudaStream_t s);
+void launch_p_fill(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const uint8_t *strong,
+                   const int32_t *dia, const int32_t *agg, double omega, int smoothed, const int32_t *P_ptr,
+                   int32_t *P_col, double *P_val, cudaStream_t s);
+void launch_count_cols(int64_t nnz, const int32_t *col, int32_t *cnt, cudaStream_t s);
+void launch_transpose_scatter(int32_t n, const int32_t *P_ptr, const int32_t *P_col, const double *P_val,
+                              const int32_t *R_ptr, int32_t *cursor, int32_t *R_col, double *R_val, cudaStream_t s);
+void launch_sort_rows(int32_t nrows, const int32_t *ptr, int32_t *col, double *val, cudaStream_t s);
+// symbolic C = X*Y pattern: pass 1 (C_ptr == nullptr) writes row lengths into len,
+// pass 2 writes sorted columns into C_col at C_ptr
+void launch_spgemm_symbolic(int32_t nrows, int32_t ncols, const int32_t *X_ptr, const int32_t *X_col,
+                            const int32_t *Y_ptr, const int32_t *Y_col, int add_diag, int32_t *len,
+                            const int32_t *C_ptr, int32_t *C_col, int *st, cudaStream_t s);
+void launch_t1_count(int32_t n, const int32_t *A_ptr, const int32_t *A_col, const int32_t *P_ptr, int32_t *cnt,
+                     cudaStream_t s);
+void launch_t1_fill(int32_t n, const int32_t *A_ptr, const int32_t *A_col, const int32_t *P_ptr,
+                    const int32_t *P_col, const int32_t *AP_ptr, const int32_t *AP_col, const int32_t *t1ptr,
+                    uint16_t *slot1, int *st, cudaStream_t s);
+void launch_t2_count(int32_t nc, const int32_t *R_ptr, const int32_t *R_col, const int32_t *AP_ptr, int32_t *cnt,
+                     cudaStream_t s);
+void launch_t2_fill(int32_t nc, const int32_t *R_ptr, const int32_t *R_col, const int32_t *AP_ptr,
+                    const int32_t *AP_col, const int32_t *Ac_ptr, const int32_t *Ac_col, const int32_t *t2ptr,
+                    uint16_t *slot2, int *st, cudaStream_t s);
+void launch_row_maxlen(int32_t n, const int32_t *ptr, int *out, cudaStream_t s);
+
+// numeric Galerkin product, FP64 (bit-exact accumulation order)
+void launch_ap_numeric_f64(const Level &L, const double *A_val, cudaStream_t s);
+void launch_rap_numeric_f64(const Level &L, const int32_t *Ac_ptr, double *Ac_val, cudaStream_t s);
+// numeric Galerkin product, FP32 values with compensated accumulation
+void launch_ap_numeric_f32(const Level &L, const float *A_valf, cudaStream_t s);
+void launch_rap_numeric_f32(const Level &L, const int32_t *Ac_ptr, float *Ac_valf, cudaStream_t s);
+
+// smoother diagonal; optional fused copy / cast of the values read
+void launch_smoother_f64(int32_t n, const int32_t *ptr, const double *val, const int32_t *dia, int type, double wj,
+                         double *m, cudaStream_t s);
+void launch_smoother_f32(int32_t n, const int32_t *ptr, const float *val, const int32_t *dia, int type, double wj,
+                         float *m, cudaStream_t s);
+// level-0 ingest: copy new values to the hierarchy (and the FP32 copy), check them, build the smoother
+void launch_ingest_fine(int32_t n, const int32_t *ptr, const double *val_in, const int32_t *dia, int type,
+                        double wj, double *val_out, float *valf_out, double *m, float *mf, int *st,
+                        cudaStream_t s);
+void launch_cast_f32(int64_t n, const double *in, float *out, cudaStream_t s);
+
+// coarsest level: dense LU and explicit inverse
+void launch_csr_to_dense(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const float *valf,
+                         double *dense, cudaStream_t s);
+void launch_dense_lu(int32_t n, double *a, int32_t *piv, int *st, cudaStream_t s);
+void launch_lu_inverse(int32_t n, const double *lu, const int32_t *piv, double *inv, cudaStream_t s);
+
+// V-cycle pieces; `skip` (may be null) makes the kernel return at once when *skip != 0
+template <class V, class TF>
+void launch_smooth0_residual(const Level &L, const V *val, const V *m, const TF *f, V *u, V *r, const int *skip,
+                             cudaStream_t s);
+template <class V, class TF, class TO>
+void launch_smooth_sweep(const Level &L, const V *val, const V *m, const TF *f, const V *u_in, TO *u_out,
+                         const int *skip, cudaStream_t s);
+template <class V, class TF>
+void launch_residual(const Level &L, const V *val, const TF *f, const V *u, V *r, const int *skip, cudaStream_t s);
+template <class V>
+void launch_restrict(const Level &L, const V *Rval, const V *r, V *fc, const int *skip, cudaStream_t s);
+template <class V>
+void launch_prolong(const Level &L, const V *Pval, const V *uc, V *u, const int *skip, cudaStream_t s);
+template <class V, class TF, class TO>
+void launch_coarse_solve(int32_t n, const double *inv, const TF *f, TO *u, const int *skip, cudaStream_t s);
+template <class TI, class TO>
+void launch_copy_cast(int64_t n, const TI *in, TO *out, const int *skip, cudaStream_t s);
+
+// CG (FP64)
+int cg_blocks(int64_t n);
+void launch_cg_init(int32_t n, const double *f, double *u, double *r, double *partial, cudaStream_t s);
+void launch_cg_start(int nblk, const double *partial, CgState *cg, double tol, int maxiter, cudaStream_t s);
+void launch_dot(int32_t n, const double *x, const double *y, double *partial, const int *skip, cudaStream_t s);
+void launch_cg_set_rz_p(int32_t n, int nblk, const double *partial, const double *z, double *p, CgState *cg,
+                        cudaStream_t s);
+void launch_spmv_dot(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *p,
+                     double *q, double *partial, const int *skip, cudaStream_t s);
+void launch_cg_alpha(int nblk, const double *partial, CgState *cg, cudaStream_t s);
+void launch_cg_update_ur(int32_t n, const CgState *cg, const double *p, const double *q, double *u, double *r,
+                         double *partial, cudaStream_t s);
+void launch_cg_check(int nblk, const double *partial, CgState *cg, cudaStream_t s);
+void launch_true_residual(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *f,
+                          const double *u, double *t, double *partial, const CgState *cg, int force,
+                          cudaStream_t s);
+void launch_true_check(int nblk, const double *partial, CgState *cg, cudaStream_t s);
+void launch_replace_r(int32_t n, const CgState *cg, const double *t, double *r, cudaStream_t s);
+void launch_cg_beta(int nblk, const double *partial, CgState *cg, cudaStream_t s);
+void launch_cg_beta_flexible(int nblk, const double *partial, const double *partial_old, CgState *cg,
+                             cudaStream_t s);
+void launch_cg_update_p(int32_t n, const CgState *cg, const double *z, double *p, cudaStream_t s);
+void launch_cg_final_norm(int nblk, const double *partial, CgState *cg, cudaStream_t s);
+
+}  // namespace amgpr

@@ -1,0 +1,835 @@
+// solve_kernels.cu -- per-time-step kernels of partial-reuse AMG
+// (arXiv 2108.02054, Alg. 4 body and Alg. 2 inside CG):
+//   * numeric Galerkin product A_{l+1} = R (A_l P) over the cached coarse
+//     pattern (Sec. 5): a gather through slot indices resolved at setup, an
+//     atomic-free segmented reduction; FP64 with one fma per term in the
+//     fixed order (A entries, then P entries; R entries, then A*P entries),
+//     or FP32 values with double-float (compensated) accumulation;
+//   * smoother diagonals (SPAI0 / damped Jacobi), the coarsest dense LU and
+//     its explicit inverse;
+//   * V-cycle pieces and the device-driven CG iteration.
+#include <cfloat>
+
+#include "common.cuh"
+
+namespace amgpr {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int nblocks(int64_t n, int t = kThreads) {
+    int64_t b = (n + t - 1) / t;
+    return (int)(b < 1 ? 1 : b);
+}
+
+__device__ __forceinline__ bool skipped(const int *skip) { return skip != nullptr && *skip != 0; }
+
+// ------------------------------------------------------------------ Galerkin, FP64
+constexpr int kApThreads = 128;
+constexpr int kApSlots = 32;
+constexpr int kRapWarps = 4;
+constexpr int kRapSlots = 1024;
+
+// stage 1: AP[i, :] = sum over k in row i of A (column order), over the
+// entries of row k of P (column order), of fma(a_ik, P_kJ, acc)
+__global__ void __launch_bounds__(kApThreads)
+k_ap_numeric_f64(int32_t n, const int32_t *__restrict__ A_ptr, const int32_t *__restrict__ A_col,
+                 const double *__restrict__ A_val, const int32_t *__restrict__ P_ptr,
+                 const double *__restrict__ P_val, const int32_t *__restrict__ AP_ptr,
+                 const int32_t *__restrict__ t1ptr, const uint16_t *__restrict__ slot1,
+                 double *__restrict__ AP_val) {
+    __shared__ double acc[kApSlots * kApThreads];
+    const int32_t i = blockIdx.x * kApThreads + threadIdx.x;
+    if (i >= n) return;
+    const int32_t b = AP_ptr[i], L = AP_ptr[i + 1] - b;
+    int64_t t = t1ptr[i];
+    double *a;
+    int stride;
+    if (L <= kApSlots) { a = acc + threadIdx.x; stride = kApThreads; }
+    else { a = AP_val + b; stride = 1; }
+    for (int s = 0; s < L; ++s) a[s * stride] = 0.0;
+    for (int32_t p = A_ptr[i]; p < A_ptr[i + 1]; ++p) {
+        const int32_t k = A_col[p];
+        const double x = A_val[p];
+        for (int32_t q = P_ptr[k]; q < P_ptr[k + 1]; ++q) {
+            const int s = slot1[t++];
+            a[s * stride] = fma(x, P_val[q], a[s * stride]);
+        }
+    }
+    if (L <= kApSlots)
+        for (int s = 0; s < L; ++s) AP_val[b + s] = a[s * stride];
+}
+
+// stage 2: one warp per coarse row I: over R entries (I,i) in column order, the
+// lanes take the entries of row i of AP (distinct slots), fma(R_Ii, AP_iJ, acc)
+__global__ void __launch_bounds__(kRapWarps * 32)
+k_rap_numeric_f64(int32_t nc, const int32_t *__restrict__ R_ptr, const int32_t *__restrict__ R_col,
+                  const double *__restrict__ R_val, const int32_t *__restrict__ AP_ptr,
+                  const double *__restrict__ AP_val, const int32_t *__restrict__ Ac_ptr,
+                  const int32_t *__restrict__ t2ptr, const uint16_t *__restrict__ slot2,
+                  double *__restrict__ Ac_val) {
+    __shared__ double acc[kRapWarps][kRapSlots];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int32_t I = blockIdx.x * kRapWarps + w;
+    if (I >= nc) return;
+    const int32_t b = Ac_ptr[I], L = Ac_ptr[I + 1] - b;
+    double *a = L <= kRapSlots ? acc[w] : Ac_val + b;
+    for (int s = lane; s < L; s += 32) a[s] = 0.0;
+    __syncwarp();
+    int64_t t = t2ptr[I];
+    for (int32_t r = R_ptr[I]; r < R_ptr[I + 1]; ++r) {
+        const int32_t i = R_col[r];
+        const double x = R_val[r];
+        const int32_t e0 = AP_ptr[i], le = AP_ptr[i + 1] - e0;
+        for (int32_t e = lane; e < le; e += 32) {
+            const int s = slot2[t + e];
+            a[s] = fma(x, AP_val[e0 + e], a[s]);
+        }
+        t += le;
+        __syncwarp();
+    }
+    if (L <= kRapSlots)
+        for (int s = lane; s < L; s += 32) Ac_val[b + s] = a[s];
+}
+
+// ------------------------------------------------------------------ Galerkin, FP32 compensated
+// double-float accumulation: (hi, lo) += x*y with the product error from fmaf
+// and the addition error from a two-sum (error-free transformations)
+__device__ __forceinline__ void df_acc(float &hi, float &lo, float x, float y) {
+    const float p = x * y;
+    const float pe = fmaf(x, y, -p);
+    const float s = hi + p;
+    const float bp = s - hi;
+    const float se = (hi - (s - bp)) + (p - bp);
+    hi = s;
+    lo = lo + (se + pe);
+}
+
+__global__ void __launch_bounds__(kApThreads)
+k_ap_numeric_f32(int32_t n, const int32_t *__restrict__ A_ptr, const int32_t *__restrict__ A_col,
+                 const float *__restrict__ A_val, const int32_t *__restrict__ P_ptr,
+                 const float *__restrict__ P_val, const int32_t *__restrict__ AP_ptr,
+                 const int32_t *__restrict__ t1ptr, const uint16_t *__restrict__ slot1,
+                 float *__restrict__ AP_val) {
+    __shared__ float acc_hi[kApSlots * kApThreads];
+    __shared__ float acc_lo[kApSlots * kApThreads];
+    const int32_t i = blockIdx.x * kApThreads + threadIdx.x;
+    if (i >= n) return;
+    const int32_t b = AP_ptr[i], L = AP_ptr[i + 1] - b;
+    int64_t t = t1ptr[i];
+    if (L <= kApSlots) {
+        float *hi = acc_hi + threadIdx.x, *lo = acc_lo + threadIdx.x;
+        for (int s = 0; s < L; ++s) { hi[s * kApThreads] = 0.f; lo[s * kApThreads] = 0.f; }
+        for (int32_t p = A_ptr[i]; p < A_ptr[i + 1]; ++p) {
+            const int32_t k = A_col[p];
+            const float x = A_val[p];
+            for (int32_t q = P_ptr[k]; q < P_ptr[k + 1]; ++q) {
+                const int s = slot1[t++] * kApThreads;
+                df_acc(hi[s], lo[s], x, P_val[q]);
+            }
+        }
+        for (int s = 0; s < L; ++s) AP_val[b + s] = hi[s * kApThreads] + lo[s * kApThreads];
+    } else {
+        // long rows (coarse levels only): plain FP32 accumulation in place
+        for (int s = 0; s < L; ++s) AP_val[b + s] = 0.f;
+        for (int32_t p = A_ptr[i]; p < A_ptr[i + 1]; ++p) {
+            const int32_t k = A_col[p];
+            const float x = A_val[p];
+            for (int32_t q = P_ptr[k]; q < P_ptr[k + 1]; ++q) {
+                const int s = slot1[t++];
+                AP_val[b + s] = fmaf(x, P_val[q], AP_val[b + s]);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kRapWarps * 32)
+k_rap_numeric_f32(int32_t nc, const int32_t *__restrict__ R_ptr, const int32_t *__restrict__ R_col,
+                  const float *__restrict__ R_val, const int32_t *__restrict__ AP_ptr,
+                  const float *__restrict__ AP_val, const int32_t *__restrict__ Ac_ptr,
+                  const int32_t *__restrict__ t2ptr, const uint16_t *__restrict__ slot2,
+                  float *__restrict__ Ac_val) {
+    __shared__ float acc_hi[kRapWarps][kRapSlots];
+    __shared__ float acc_lo[kRapWarps][kRapSlots];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int32_t I = blockIdx.x * kRapWarps + w;
+    if (I >= nc) return;
+    const int32_t b = Ac_ptr[I], L = Ac_ptr[I + 1] - b;
+    int64_t t = t2ptr[I];
+    if (L <= kRapSlots) {
+        float *hi = acc_hi[w], *lo = acc_lo[w];
+        for (int s = lane; s < L; s += 32) { hi[s] = 0.f; lo[s] = 0.f; }
+        __syncwarp();
+        for (int32_t r = R_ptr[I]; r < R_ptr[I + 1]; ++r) {
+            const int32_t i = R_col[r];
+            const float x = R_val[r];
+            const int32_t e0 = AP_ptr[i], le = AP_ptr[i + 1] - e0;
+            for (int32_t e = lane; e < le; e += 32) {
+                const int s = slot2[t + e];
+                df_acc(hi[s], lo[s], x, AP_val[e0 + e]);
+            }
+            t += le;
+            __syncwarp();
+        }
+        for (int s = lane; s < L; s += 32) Ac_val[b + s] = hi[s] + lo[s];
+    } else {
+        for (int s = lane; s < L; s += 32) Ac_val[b + s] = 0.f;
+        __syncwarp();
+        for (int32_t r = R_ptr[I]; r < R_ptr[I + 1]; ++r) {
+            const int32_t i = R_col[r];
+            const float x = R_val[r];
+            const int32_t e0 = AP_ptr[i], le = AP_ptr[i + 1] - e0;
+            for (int32_t e = lane; e < le; e += 32) {
+                const int s = slot2[t + e];
+                Ac_val[b + s] = fmaf(x, AP_val[e0 + e], Ac_val[b + s]);
+            }
+            t += le;
+            __syncwarp();
+        }
+    }
+}
+
+// ------------------------------------------------------------------ smoothers
+// SPAI0: m_i = a_ii / sum_j a_ij^2 (fma, column order), 0 for a zero sum;
+// damped Jacobi: m_i = w / a_ii.
+template <class V>
+__global__ void k_smoother(int32_t n, const int32_t *__restrict__ ptr, const V *__restrict__ val,
+                           const int32_t *__restrict__ dia, int type, V wj, V *__restrict__ m) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const V aii = val[dia[i]];
+    if (type == AMG_SMOOTHER_SPAI0) {
+        V s = 0;
+        for (int32_t p = ptr[i]; p < ptr[i + 1]; ++p) s = fma(val[p], val[p], s);
+        m[i] = s != V(0) ? aii / s : V(0);
+    } else {
+        m[i] = aii != V(0) ? wj / aii : V(0);
+    }
+}
+
+// fine level: copy the new values into the hierarchy (optionally an FP32
+// copy as well), flag non-finite entries and build the smoother in one pass
+__global__ void k_ingest_fine(int32_t n, const int32_t *__restrict__ ptr, const double *__restrict__ in,
+                              const int32_t *__restrict__ dia, int type, double wj, double *__restrict__ out,
+                              float *__restrict__ outf, double *__restrict__ m, float *__restrict__ mf, int *st) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    bool finite = true;
+    for (int32_t p = ptr[i]; p < ptr[i + 1]; ++p) {
+        const double v = in[p];
+        finite = finite && isfinite(v);
+        s = fma(v, v, s);
+        if (out) out[p] = v;
+        if (outf) outf[p] = (float)v;
+    }
+    if (!finite) atomicOr(st, DEV_ERR_NONFINITE);
+    const double aii = in[dia[i]];
+    double mi;
+    if (type == AMG_SMOOTHER_SPAI0) mi = s != 0.0 ? aii / s : 0.0;
+    else mi = aii != 0.0 ? wj / aii : 0.0;
+    if (m) m[i] = mi;
+    if (mf) mf[i] = (float)mi;
+}
+
+__global__ void k_cast_f32(int64_t n, const double *__restrict__ in, float *__restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (float)in[i];
+}
+
+// ------------------------------------------------------------------ coarsest level
+__global__ void k_csr_to_dense(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                               const double *__restrict__ val, const float *__restrict__ valf,
+                               double *__restrict__ dense) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int32_t p = ptr[i]; p < ptr[i + 1]; ++p)
+        dense[(int64_t)i * n + col[p]] = val ? val[p] : (double)valf[p];
+}
+
+struct ValIdx {
+    double v;
+    int i;
+};
+__device__ __forceinline__ ValIdx better(ValIdx a, ValIdx b) {
+    // larger magnitude wins; equal magnitudes: the lower row index
+    if (b.v > a.v || (b.v == a.v && b.i < a.i)) return b;
+    return a;
+}
+
+// LU with partial pivoting (first entry of largest magnitude), in place,
+// row-major; l = a_rk / a_kk, a_rc = fma(-l, a_kc, a_rc)
+__global__ void __launch_bounds__(1024) k_dense_lu(int32_t n, double *__restrict__ a, int32_t *__restrict__ piv,
+                                                   int *st) {
+    __shared__ ValIdx wbest[32];
+    __shared__ int s_p, s_sing;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int32_t k = 0; k < n; ++k) {
+        ValIdx best{-1.0, n};
+        for (int32_t r = k + tid; r < n; r += blockDim.x) best = better(best, ValIdx{fabs(a[(int64_t)r * n + k]), r});
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ValIdx other{__shfl_xor_sync(0xffffffffu, best.v, o), __shfl_xor_sync(0xffffffffu, best.i, o)};
+            best = better(best, other);
+        }
+        if (lane == 0) wbest[warp] = best;
+        __syncthreads();
+        if (tid == 0) {
+            ValIdx b = wbest[0];
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) b = better(b, wbest[w]);
+            s_p = b.i;
+            s_sing = !(b.v > 0.0);
+            piv[k] = b.i;
+        }
+        __syncthreads();
+        if (s_sing) {
+            if (tid == 0) atomicOr(st, DEV_ERR_SINGULAR);
+            return;
+        }
+        const int32_t p = s_p;
+        if (p != k)
+            for (int32_t c = tid; c < n; c += blockDim.x) {
+                double t = a[(int64_t)k * n + c];
+                a[(int64_t)k * n + c] = a[(int64_t)p * n + c];
+                a[(int64_t)p * n + c] = t;
+            }
+        __syncthreads();
+        const double akk = a[(int64_t)k * n + k];
+        for (int32_t r = k + 1 + tid; r < n; r += blockDim.x) a[(int64_t)r * n + k] = a[(int64_t)r * n + k] / akk;
+        __syncthreads();
+        const int32_t m = n - k - 1;
+        for (int64_t idx = tid; idx < (int64_t)m * m; idx += blockDim.x) {
+            const int32_t r = k + 1 + (int32_t)(idx / m), c = k + 1 + (int32_t)(idx % m);
+            a[(int64_t)r * n + c] = fma(-a[(int64_t)r * n + k], a[(int64_t)k * n + c], a[(int64_t)r * n + c]);
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// explicit inverse from the LU factors: one warp per column j of A^-1
+__global__ void k_lu_inverse(int32_t n, const double *__restrict__ lu, const int32_t *__restrict__ piv,
+                             double *__restrict__ inv) {
+    const int lane = threadIdx.x & 31;
+    const int32_t j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (j >= n) return;
+    double *x = inv + j;  // column j, stride n
+    for (int32_t r = lane; r < n; r += 32) x[(int64_t)r * n] = (r == j) ? 1.0 : 0.0;
+    __syncwarp();
+    if (lane == 0)
+        for (int32_t k = 0; k < n; ++k) {
+            const int32_t p = piv[k];
+            if (p != k) {
+                double t = x[(int64_t)k * n];
+                x[(int64_t)k * n] = x[(int64_t)p * n];
+                x[(int64_t)p * n] = t;
+            }
+        }
+    __syncwarp();
+    for (int32_t r = 1; r < n; ++r) {
+        double s = 0.0;
+        for (int32_t c = lane; c < r; c += 32) s = fma(lu[(int64_t)r * n + c], x[(int64_t)c * n], s);
+        s = warp_sum(s);
+        if (lane == 0) x[(int64_t)r * n] -= s;
+        __syncwarp();
+    }
+    for (int32_t r = n - 1; r >= 0; --r) {
+        double s = 0.0;
+        for (int32_t c = r + 1 + lane; c < n; c += 32) s = fma(lu[(int64_t)r * n + c], x[(int64_t)c * n], s);
+        s = warp_sum(s);
+        if (lane == 0) x[(int64_t)r * n] = (x[(int64_t)r * n] - s) / lu[(int64_t)r * n + r];
+        __syncwarp();
+    }
+}
+
+// u = A_L^-1 f, one warp per row
+template <class TF, class TO>
+__global__ void k_coarse_solve(int32_t n, const double *__restrict__ inv, const TF *__restrict__ f,
+                               TO *__restrict__ u, const int *skip) {
+    if (skipped(skip)) return;
+    const int lane = threadIdx.x & 31;
+    const int32_t r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (r >= n) return;
+    double s = 0.0;
+    for (int32_t c = lane; c < n; c += 32) s = fma(inv[(int64_t)r * n + c], (double)f[c], s);
+    s = warp_sum(s);
+    if (lane == 0) u[r] = (TO)s;
+}
+
+// ------------------------------------------------------------------ V-cycle pieces
+// zero-guess pre-smoothing fused with the residual: u = m o f, r = f - A u
+template <class V, class TF>
+__global__ void k_smooth0_residual(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                                   const V *__restrict__ val, const V *__restrict__ m, const TF *__restrict__ f,
+                                   V *__restrict__ u, V *__restrict__ r, const int *skip) {
+    if (skipped(skip)) return;
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    V s = 0;
+    for (int32_t p = ptr[i]; p < ptr[i + 1]; ++p) {
+        const int32_t j = col[p];
+        s = fma(val[p], m[j] * (V)f[j], s);
+    }
+    const V fi = (V)f[i];
+    u[i] = m[i] * fi;
+    r[i] = fi - s;
+}
+
+// u_out = u_in + m o (f - A u_in)
+template <class V, class TF, class TO>
+__global__ void k_smooth_sweep(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                               const V *__restrict__ val, const V *__restrict__ m, const TF *__restrict__ f,
+                               const V *__restrict__ u_in, TO *__restrict__ u_out, const int *skip) {
+    if (skipped(skip)) return;
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    V s = 0;
+    for (int32_t p = ptr[i]; p < ptr[i + 1]; ++p) s = fma(val[p], u_in[col[p]], s);
+    u_out[i] = (TO)fma(m[i], (V)f[i] - s, u_in[i]);
+}
+
+template <class V, class TF>
+__global__ void k_residual(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                           const V *__restrict__ val, const TF *__restrict__ f, const V *__restrict__ u,
+                           V *__restrict__ r, const int *skip) {
+    if (skipped(skip)) return;
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    V s = 0;
+    for (int32_t p = ptr[i]; p < ptr[i + 1]; ++p) s = fma(val[p], u[col[p]], s);
+    r[i] = (V)f[i] - s;
+}
+
+// f_c = R r (R = P^T stored explicitly, rows sorted): a gather, no atomics
+template <class V>
+__global__ void k_restrict(int32_t nc, const int32_t *__restrict__ R_ptr, const int32_t *__restrict__ R_col,
+                           const V *__restrict__ R_val, const V *__restrict__ r, V *__restrict__ fc,
+                           const int *skip) {
+    if (skipped(skip)) return;
+    const int32_t I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nc) return;
+    V s = 0;
+    for (int32_t p = R_ptr[I]; p < R_ptr[I + 1]; ++p) s = fma(R_val[p], r[R_col[p]], s);
+    fc[I] = s;
+}
+
+// u += P u_c
+template <class V>
+__global__ void k_prolong(int32_t n, const int32_t *__restrict__ P_ptr, const int32_t *__restrict__ P_col,
+                          const V *__restrict__ P_val, const V *__restrict__ uc, V *__restrict__ u,
+                          const int *skip) {
+    if (skipped(skip)) return;
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    V s = u[i];
+    for (int32_t p = P_ptr[i]; p < P_ptr[i + 1]; ++p) s = fma(P_val[p], uc[P_col[p]], s);
+    u[i] = s;
+}
+
+template <class TI, class TO>
+__global__ void k_copy_cast(int64_t n, const TI *__restrict__ in, TO *__restrict__ out, const int *skip) {
+    if (skipped(skip)) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (TO)in[i];
+}
+
+// ------------------------------------------------------------------ CG (FP64)
+constexpr int kCgThreads = 256;
+constexpr int kCgMaxBlocks = 152 * 8;
+
+// deterministic block sum (fixed lane / warp order)
+__device__ double block_sum(double v) {
+    __shared__ double ws[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) ws[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (w == 0) {
+        t = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0.0;
+        t = warp_sum(t);
+    }
+    __syncthreads();
+    return t;  // valid in thread 0
+}
+
+// one block: sum of the per-block partials in index order
+__device__ double sum_partials(const double *__restrict__ partial, int nblk) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += partial[b];
+    return block_sum(s);
+}
+
+__global__ void k_cg_init(int32_t n, const double *__restrict__ f, double *__restrict__ u, double *__restrict__ r,
+                          double *__restrict__ partial) {
+    double s = 0.0;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double fi = f[i];
+        u[i] = 0.0;
+        r[i] = fi;
+        s = fma(fi, fi, s);
+    }
+    s = block_sum(s);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void k_cg_start(int nblk, const double *__restrict__ partial, CgState *cg, double tol, int maxiter) {
+    double ff = sum_partials(partial, nblk);
+    if (threadIdx.x == 0) {
+        CgState c{};
+        c.nf = sqrt(ff);
+        c.tol = tol;
+        c.maxiter = maxiter;
+        c.done = (c.nf == 0.0) || maxiter <= 0;
+        c.status = (maxiter <= 0 && c.nf != 0.0) ? AMG_NOT_CONVERGED : AMG_OK;
+        *cg = c;
+    }
+}
+
+__global__ void k_dot(int32_t n, const double *__restrict__ x, const double *__restrict__ y,
+                      double *__restrict__ partial, const int *skip) {
+    if (skipped(skip)) return;
+    double s = 0.0;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) s = fma(x[i], y[i], s);
+    s = block_sum(s);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// after the first preconditioner application: rz = r.z, p = z
+__global__ void k_cg_set_rz_p(int32_t n, int nblk, const double *__restrict__ partial, const double *__restrict__ z,
+                              double *__restrict__ p, CgState *cg) {
+    if (cg->done) return;
+    if (blockIdx.x == 0) {
+        double rz = sum_partials(partial, nblk);
+        if (threadIdx.x == 0) cg->rz = rz;
+    }
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = z[i];
+}
+
+__global__ void k_spmv_dot(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                           const double *__restrict__ val, const double *__restrict__ p, double *__restrict__ q,
+                           double *__restrict__ partial, const int *skip) {
+    if (skipped(skip)) return;
+    double d = 0.0;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int32_t e = ptr[i]; e < ptr[i + 1]; ++e) s = fma(val[e], p[col[e]], s);
+        q[i] = s;
+        d = fma(p[i], s, d);
+    }
+    d = block_sum(d);
+    if (threadIdx.x == 0) partial[blockIdx.x] = d;
+}
+
+__global__ void k_cg_alpha(int nblk, const double *__restrict__ partial, CgState *cg) {
+    if (cg->done) return;
+    double pq = sum_partials(partial, nblk);
+    if (threadIdx.x == 0) {
+        cg->pq = pq;
+        if (!(pq > 0.0) || !isfinite(pq)) {
+            cg->iter += 1;
+            cg->status = AMG_ERR_BREAKDOWN;
+            cg->done = 1;
+        } else {
+            cg->alpha = cg->rz / pq;
+        }
+    }
+}
+
+__global__ void k_cg_update_ur(int32_t n, const CgState *cg, const double *__restrict__ p,
+                               const double *__restrict__ q, double *__restrict__ u, double *__restrict__ r,
+                               double *__restrict__ partial) {
+    if (cg->done) return;
+    const double alpha = cg->alpha;
+    double s = 0.0;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        u[i] = fma(alpha, p[i], u[i]);
+        const double ri = fma(-alpha, q[i], r[i]);
+        r[i] = ri;
+        s = fma(ri, ri, s);
+    }
+    s = block_sum(s);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void k_cg_check(int nblk, const double *__restrict__ partial, CgState *cg) {
+    if (cg->done) return;
+    double rr = sum_partials(partial, nblk);
+    if (threadIdx.x == 0) {
+        cg->iter += 1;
+        cg->rr = rr;
+        cg->res = sqrt(rr) / cg->nf;
+        cg->need_true = cg->res <= cg->tol;
+        if (!cg->need_true && cg->iter >= cg->maxiter) {
+            cg->done = 1;
+            cg->status = AMG_NOT_CONVERGED;
+        }
+    }
+}
+
+// t = f - A u (the true residual), when the recurrence reports convergence
+// (or unconditionally with force)
+__global__ void k_true_residual(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                                const double *__restrict__ val, const double *__restrict__ f,
+                                const double *__restrict__ u, double *__restrict__ t, double *__restrict__ partial,
+                                const CgState *cg, int force) {
+    if (!force && (cg->done || !cg->need_true)) return;
+    double d = 0.0;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int32_t e = ptr[i]; e < ptr[i + 1]; ++e) s = fma(val[e], u[col[e]], s);
+        const double ti = f[i] - s;
+        t[i] = ti;
+        d = fma(ti, ti, d);
+    }
+    d = block_sum(d);
+    if (threadIdx.x == 0) partial[blockIdx.x] = d;
+}
+
+// convergence needs the true residual too; otherwise replace r by it (twice at most)
+__global__ void k_true_check(int nblk, const double *__restrict__ partial, CgState *cg) {
+    if (cg->done || !cg->need_true) return;
+    double tt = sum_partials(partial, nblk);
+    if (threadIdx.x == 0) {
+        cg->tres = sqrt(tt) / cg->nf;
+        if (cg->tres <= cg->tol) {
+            cg->done = 1;
+            cg->status = AMG_OK;
+        } else if (cg->replacements >= 2 || cg->iter >= cg->maxiter) {
+            cg->done = 1;
+            cg->status = AMG_NOT_CONVERGED;
+        } else {
+            cg->replacements += 1;
+            cg->copy_r = 1;
+        }
+    }
+}
+
+__global__ void k_replace_r(int32_t n, const CgState *cg, const double *__restrict__ t, double *__restrict__ r) {
+    if (cg->done || !cg->copy_r) return;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) r[i] = t[i];
+}
+
+// beta = (r.z)_new / (r.z)_old (flexible variant: minus r_new.z_old, kept in pq)
+__global__ void k_cg_beta(int nblk, const double *__restrict__ partial, CgState *cg) {
+    if (cg->done) return;
+    double rz = sum_partials(partial, nblk);
+    if (threadIdx.x == 0) {
+        cg->beta = rz / cg->rz;
+        cg->rz = rz;
+        cg->copy_r = 0;
+        cg->need_true = 0;
+    }
+}
+
+__global__ void k_cg_beta_flexible(int nblk, const double *__restrict__ partial,
+                                   const double *__restrict__ partial_old, CgState *cg) {
+    if (cg->done) return;
+    double rz = sum_partials(partial, nblk);
+    double rzo = sum_partials(partial_old, nblk);
+    if (threadIdx.x == 0) {
+        cg->beta = (rz - rzo) / cg->rz;
+        cg->rz = rz;
+        cg->copy_r = 0;
+        cg->need_true = 0;
+    }
+}
+
+__global__ void k_cg_update_p(int32_t n, const CgState *cg, const double *__restrict__ z, double *__restrict__ p) {
+    if (cg->done) return;
+    const double beta = cg->beta;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        p[i] = fma(beta, p[i], z[i]);
+}
+
+__global__ void k_cg_final_norm(int nblk, const double *__restrict__ partial, CgState *cg) {
+    double tt = sum_partials(partial, nblk);
+    if (threadIdx.x == 0) cg->tres = cg->nf > 0.0 ? sqrt(tt) / cg->nf : 0.0;
+}
+
+}  // namespace
+
+// ======================================================================= launchers
+void launch_ap_numeric_f64(const Level &L, const double *A_val, cudaStream_t s) {
+    k_ap_numeric_f64<<<nblocks(L.n, kApThreads), kApThreads, 0, s>>>(L.n, L.A_ptr, L.A_col, A_val, L.P_ptr, L.P_val,
+                                                                     L.AP_ptr, L.t1ptr, L.slot1, L.AP_val);
+}
+void launch_rap_numeric_f64(const Level &L, const int32_t *Ac_ptr, double *Ac_val, cudaStream_t s) {
+    unsigned g = (unsigned)((L.nc + kRapWarps - 1) / kRapWarps);
+    k_rap_numeric_f64<<<g, kRapWarps * 32, 0, s>>>(L.nc, L.R_ptr, L.R_col, L.R_val, L.AP_ptr, L.AP_val, Ac_ptr,
+                                                   L.t2ptr, L.slot2, Ac_val);
+}
+void launch_ap_numeric_f32(const Level &L, const float *A_valf, cudaStream_t s) {
+    k_ap_numeric_f32<<<nblocks(L.n, kApThreads), kApThreads, 0, s>>>(L.n, L.A_ptr, L.A_col, A_valf, L.P_ptr,
+                                                                     L.P_valf, L.AP_ptr, L.t1ptr, L.slot1, L.AP_valf);
+}
+void launch_rap_numeric_f32(const Level &L, const int32_t *Ac_ptr, float *Ac_valf, cudaStream_t s) {
+    unsigned g = (unsigned)((L.nc + kRapWarps - 1) / kRapWarps);
+    k_rap_numeric_f32<<<g, kRapWarps * 32, 0, s>>>(L.nc, L.R_ptr, L.R_col, L.R_valf, L.AP_ptr, L.AP_valf, Ac_ptr,
+                                                   L.t2ptr, L.slot2, Ac_valf);
+}
+
+void launch_smoother_f64(int32_t n, const int32_t *ptr, const double *val, const int32_t *dia, int type, double wj,
+                         double *m, cudaStream_t s) {
+    k_smoother<double><<<nblocks(n), kThreads, 0, s>>>(n, ptr, val, dia, type, wj, m);
+}
+void launch_smoother_f32(int32_t n, const int32_t *ptr, const float *val, const int32_t *dia, int type, double wj,
+                         float *m, cudaStream_t s) {
+    k_smoother<float><<<nblocks(n), kThreads, 0, s>>>(n, ptr, val, dia, type, (float)wj, m);
+}
+void launch_ingest_fine(int32_t n, const int32_t *ptr, const double *val_in, const int32_t *dia, int type,
+                        double wj, double *val_out, float *valf_out, double *m, float *mf, int *st,
+                        cudaStream_t s) {
+    k_ingest_fine<<<nblocks(n), kThreads, 0, s>>>(n, ptr, val_in, dia, type, wj, val_out, valf_out, m, mf, st);
+}
+void launch_cast_f32(int64_t n, const double *in, float *out, cudaStream_t s) {
+    int64_t b = nblocks(n);
+    k_cast_f32<<<(unsigned)(b > 8192 ? 8192 : b), kThreads, 0, s>>>(n, in, out);
+}
+
+void launch_csr_to_dense(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const float *valf,
+                         double *dense, cudaStream_t s) {
+    cudaMemsetAsync(dense, 0, sizeof(double) * (size_t)n * (size_t)n, s);
+    k_csr_to_dense<<<nblocks(n), kThreads, 0, s>>>(n, ptr, col, val, valf, dense);
+}
+void launch_dense_lu(int32_t n, double *a, int32_t *piv, int *st, cudaStream_t s) {
+    k_dense_lu<<<1, 1024, 0, s>>>(n, a, piv, st);
+}
+void launch_lu_inverse(int32_t n, const double *lu, const int32_t *piv, double *inv, cudaStream_t s) {
+    k_lu_inverse<<<nblocks((int64_t)n * 32, 128), 128, 0, s>>>(n, lu, piv, inv);
+}
+
+template <class V, class TF>
+void launch_smooth0_residual(const Level &L, const V *val, const V *m, const TF *f, V *u, V *r, const int *skip,
+                             cudaStream_t s) {
+    k_smooth0_residual<V, TF><<<nblocks(L.n), kThreads, 0, s>>>(L.n, L.A_ptr, L.A_col, val, m, f, u, r, skip);
+}
+template <class V, class TF, class TO>
+void launch_smooth_sweep(const Level &L, const V *val, const V *m, const TF *f, const V *u_in, TO *u_out,
+                         const int *skip, cudaStream_t s) {
+    k_smooth_sweep<V, TF, TO><<<nblocks(L.n), kThreads, 0, s>>>(L.n, L.A_ptr, L.A_col, val, m, f, u_in, u_out, skip);
+}
+template <class V, class TF>
+void launch_residual(const Level &L, const V *val, const TF *f, const V *u, V *r, const int *skip, cudaStream_t s) {
+    k_residual<V, TF><<<nblocks(L.n), kThreads, 0, s>>>(L.n, L.A_ptr, L.A_col, val, f, u, r, skip);
+}
+template <class V>
+void launch_restrict(const Level &L, const V *Rval, const V *r, V *fc, const int *skip, cudaStream_t s) {
+    k_restrict<V><<<nblocks(L.nc), kThreads, 0, s>>>(L.nc, L.R_ptr, L.R_col, Rval, r, fc, skip);
+}
+template <class V>
+void launch_prolong(const Level &L, const V *Pval, const V *uc, V *u, const int *skip, cudaStream_t s) {
+    k_prolong<V><<<nblocks(L.n), kThreads, 0, s>>>(L.n, L.P_ptr, L.P_col, Pval, uc, u, skip);
+}
+template <class V, class TF, class TO>
+void launch_coarse_solve(int32_t n, const double *inv, const TF *f, TO *u, const int *skip, cudaStream_t s) {
+    k_coarse_solve<TF, TO><<<nblocks((int64_t)n * 32, 128), 128, 0, s>>>(n, inv, f, u, skip);
+}
+template <class TI, class TO>
+void launch_copy_cast(int64_t n, const TI *in, TO *out, const int *skip, cudaStream_t s) {
+    int64_t b = nblocks(n);
+    k_copy_cast<TI, TO><<<(unsigned)(b > 8192 ? 8192 : b), kThreads, 0, s>>>(n, in, out, skip);
+}
+
+#define INST_V(V, TF, TO)                                                                                           \
+    template void launch_smooth_sweep<V, TF, TO>(const Level &, const V *, const V *, const TF *, const V *, TO *, \
+                                                 const int *, cudaStream_t);
+INST_V(double, double, double)
+INST_V(float, float, float)
+INST_V(float, double, double)
+INST_V(float, double, float)
+INST_V(float, float, double)
+#undef INST_V
+template void launch_smooth0_residual<double, double>(const Level &, const double *, const double *, const double *,
+                                                      double *, double *, const int *, cudaStream_t);
+template void launch_smooth0_residual<float, float>(const Level &, const float *, const float *, const float *,
+                                                    float *, float *, const int *, cudaStream_t);
+template void launch_smooth0_residual<float, double>(const Level &, const float *, const float *, const double *,
+                                                     float *, float *, const int *, cudaStream_t);
+template void launch_residual<double, double>(const Level &, const double *, const double *, const double *, double *,
+                                              const int *, cudaStream_t);
+template void launch_residual<float, float>(const Level &, const float *, const float *, const float *, float *,
+                                            const int *, cudaStream_t);
+template void launch_residual<float, double>(const Level &, const float *, const double *, const float *, float *,
+                                             const int *, cudaStream_t);
+template void launch_restrict<double>(const Level &, const double *, const double *, double *, const int *,
+                                      cudaStream_t);
+template void launch_restrict<float>(const Level &, const float *, const float *, float *, const int *, cudaStream_t);
+template void launch_prolong<double>(const Level &, const double *, const double *, double *, const int *,
+                                     cudaStream_t);
+template void launch_prolong<float>(const Level &, const float *, const float *, float *, const int *, cudaStream_t);
+template void launch_coarse_solve<double, double, double>(int32_t, const double *, const double *, double *,
+                                                          const int *, cudaStream_t);
+template void launch_coarse_solve<float, float, float>(int32_t, const double *, const float *, float *, const int *,
+                                                       cudaStream_t);
+template void launch_coarse_solve<float, double, double>(int32_t, const double *, const double *, double *,
+                                                         const int *, cudaStream_t);
+template void launch_copy_cast<float, float>(int64_t, const float *, float *, const int *, cudaStream_t);
+template void launch_copy_cast<double, double>(int64_t, const double *, double *, const int *, cudaStream_t);
+template void launch_copy_cast<double, float>(int64_t, const double *, float *, const int *, cudaStream_t);
+template void launch_copy_cast<float, double>(int64_t, const float *, double *, const int *, cudaStream_t);
+
+int cg_blocks(int64_t n) {
+    int64_t b = (n + kCgThreads - 1) / kCgThreads;
+    if (b > kCgMaxBlocks) b = kCgMaxBlocks;
+    return (int)(b < 1 ? 1 : b);
+}
+void launch_cg_init(int32_t n, const double *f, double *u, double *r, double *partial, cudaStream_t s) {
+    k_cg_init<<<cg_blocks(n), kCgThreads, 0, s>>>(n, f, u, r, partial);
+}
+void launch_cg_start(int nblk, const double *partial, CgState *cg, double tol, int maxiter, cudaStream_t s) {
+    k_cg_start<<<1, 1024, 0, s>>>(nblk, partial, cg, tol, maxiter);
+}
+void launch_dot(int32_t n, const double *x, const double *y, double *partial, const int *skip, cudaStream_t s) {
+    k_dot<<<cg_blocks(n), kCgThreads, 0, s>>>(n, x, y, partial, skip);
+}
+void launch_cg_set_rz_p(int32_t n, int nblk, const double *partial, const double *z, double *p, CgState *cg,
+                        cudaStream_t s) {
+    k_cg_set_rz_p<<<cg_blocks(n), kCgThreads, 0, s>>>(n, nblk, partial, z, p, cg);
+}
+void launch_spmv_dot(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *p,
+                     double *q, double *partial, const int *skip, cudaStream_t s) {
+    k_spmv_dot<<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, col, val, p, q, partial, skip);
+}
+void launch_cg_alpha(int nblk, const double *partial, CgState *cg, cudaStream_t s) {
+    k_cg_alpha<<<1, 1024, 0, s>>>(nblk, partial, cg);
+}
+void launch_cg_update_ur(int32_t n, const CgState *cg, const double *p, const double *q, double *u, double *r,
+                         double *partial, cudaStream_t s) {
+    k_cg_update_ur<<<cg_blocks(n), kCgThreads, 0, s>>>(n, cg, p, q, u, r, partial);
+}
+void launch_cg_check(int nblk, const double *partial, CgState *cg, cudaStream_t s) {
+    k_cg_check<<<1, 1024, 0, s>>>(nblk, partial, cg);
+}
+void launch_true_residual(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *f,
+                          const double *u, double *t, double *partial, const CgState *cg, int force,
+                          cudaStream_t s) {
+    k_true_residual<<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, col, val, f, u, t, partial, cg, force);
+}
+void launch_true_check(int nblk, const double *partial, CgState *cg, cudaStream_t s) {
+    k_true_check<<<1, 1024, 0, s>>>(nblk, partial, cg);
+}
+void launch_replace_r(int32_t n, const CgState *cg, const double *t, double *r, cudaStream_t s) {
+    k_replace_r<<<cg_blocks(n), kCgThreads, 0, s>>>(n, cg, t, r);
+}
+void launch_cg_beta(int nblk, const double *partial, CgState *cg, cudaStream_t s) {
+    k_cg_beta<<<1, 1024, 0, s>>>(nblk, partial, cg);
+}
+void launch_cg_beta_flexible(int nblk, const double *partial, const double *partial_old, CgState *cg,
+                             cudaStream_t s) {
+    k_cg_beta_flexible<<<1, 1024, 0, s>>>(nblk, partial, partial_old, cg);
+}
+void launch_cg_update_p(int32_t n, const CgState *cg, const double *z, double *p, cudaStream_t s) {
+    k_cg_update_p<<<cg_blocks(n), kCgThreads, 0, s>>>(n, cg, z, p);
+}
+void launch_cg_final_norm(int nblk, const double *partial, CgState *cg, cudaStream_t s) {
+    k_cg_final_norm<<<1, 1024, 0, s>>>(nblk, partial, cg);
+}
+
+}  // namespace amgpr

@@ -1,0 +1,300 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
+same seeded inputs.
+
+Bar: structure (strength flags, aggregates, P/R/A_c patterns, pivots) bit-exact;
+FP64 values within 1e-12 of the oracle relative to the absolute-sum bound
+(|P|^T |A| |P|) and, by construction of the summation order, bit-exact;
+solutions to the same 1e-8 relative residual with iteration counts within one.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle as O
+from paper_2108_02054_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from paper_2108_02054_gb300 import amg as B
+
+
+def gpu_problem(dim, N, k, T, dirichlet=True):
+    rho = I.density(dim, N, k, T)
+    ptr, col = B.poisson_pattern(dim, N)
+    val = B.poisson_values(dim, N, torch.tensor(rho, device="cuda"), ptr, dirichlet_top=dirichlet)
+    return ptr, col, val
+
+
+def oracle_problem(dim, N, k, T, dirichlet=True):
+    return O.poisson_assemble(dim, N, I.density(dim, N, k, T), dirichlet_top=dirichlet)
+
+
+def _sp(ptr, col, val, ncols):
+    return sp.csr_matrix((val, col, ptr), shape=(len(ptr) - 1, ncols))
+
+
+def compare_hierarchy(G, H, values_bitwise=True, check_values=True):
+    assert G.nlevels == H.nlevels
+    for l in range(H.nlevels):
+        g = G.export_level(l)
+        o = H.level(l)
+        assert g["n"] == o.A.nrows
+        gp, gc, gv = g["A"]
+        assert np.array_equal(gp, o.A.ptr) and np.array_equal(gc, o.A.col), f"A pattern level {l}"
+        assert np.array_equal(g["agg"], o.agg), f"aggregates level {l}"
+        assert np.array_equal(g["strong"], o.strong), f"strength level {l}"
+        if check_values:
+            if l > 0:
+                lo = H.level(l - 1)
+                Pa = abs(_sp(lo.P.ptr, lo.P.col, lo.P.val, lo.nagg))
+                Aa = abs(_sp(lo.A.ptr, lo.A.col, lo.A.val, lo.A.nrows))
+                bound = (Pa.T @ Aa @ Pa).tocsr()
+                bound.sort_indices()
+                bd = np.asarray(bound[np.repeat(np.arange(o.A.nrows), np.diff(o.A.ptr)), o.A.col]).ravel()
+                assert np.all(np.abs(gv - o.A.val) <= 1e-12 * bd + 1e-300), f"A values level {l}"
+            if values_bitwise:
+                assert np.array_equal(gv, o.A.val), f"A values bitwise level {l}"
+            if l < H.nlevels - 1:
+                assert np.allclose(g["m"], o.m, rtol=1e-13, atol=0), f"smoother level {l}"
+        if l < H.nlevels - 1:
+            assert g["nagg"] == o.nagg
+            for name, ref in (("P", o.P), ("R", o.R)):
+                p_, c_, v_ = g[name]
+                assert np.array_equal(p_, ref.ptr) and np.array_equal(c_, ref.col), f"{name} pattern level {l}"
+                if check_values:
+                    assert np.array_equal(v_, ref.val), f"{name} values level {l}"
+            assert g["nnzAP"] == int(H.sizes(l)[4])
+
+
+# ------------------------------------------------------------------ assembly
+@pytest.mark.parametrize("dim,N,dirichlet", [(2, 32, True), (3, 17, True), (3, 64, True), (2, 9, False)])
+def test_assembly_bitwise(dim, N, dirichlet):
+    ptr, col, val = gpu_problem(dim, N, 3, 10, dirichlet)
+    optr, ocol, oval = oracle_problem(dim, N, 3, 10, dirichlet)
+    assert np.array_equal(ptr.cpu().numpy(), optr)
+    assert np.array_equal(col.cpu().numpy(), ocol)
+    assert np.array_equal(val.cpu().numpy(), oval)
+
+
+# ------------------------------------------------------------------ full setup
+@pytest.mark.parametrize("dim,N,ce", [(2, 32, 256), (3, 24, 64), (3, 33, 256), (3, 64, 256)])
+def test_full_setup_matches_oracle(dim, N, ce):
+    ptr, col, val = gpu_problem(dim, N, 2, 10)
+    G = B.AMG(coarse_enough=ce)
+    G.full_setup(ptr, col, val)
+    H = O.Hierarchy(*oracle_problem(dim, N, 2, 10), O.Params(coarse_enough=ce))
+    assert G.nlevels >= 2
+    compare_hierarchy(G, H)
+    lu, piv = G.coarse_lu()
+    olu, opiv = H.lu()
+    assert np.array_equal(piv, opiv)
+    assert np.allclose(lu, olu, rtol=1e-12, atol=1e-14 * np.abs(olu).max())
+
+
+@pytest.mark.parametrize("variant", ["jacobi", "plain", "const_theta", "npre2"])
+def test_full_setup_variants(variant):
+    kw, okw = {}, {}
+    if variant == "jacobi":
+        kw = okw = {"smoother": 1}
+    elif variant == "plain":
+        kw = okw = {"smoothed": 0}
+    elif variant == "const_theta":
+        kw = okw = {"theta_halving": 0}
+    else:
+        kw = okw = {"npre": 2, "npost": 2}
+    ptr, col, val = gpu_problem(3, 20, 4, 10)
+    G = B.AMG(coarse_enough=40, **kw)
+    G.full_setup(ptr, col, val)
+    H = O.Hierarchy(*oracle_problem(3, 20, 4, 10), O.Params(coarse_enough=40, **okw))
+    compare_hierarchy(G, H)
+    f = I.rhs(20 ** 3)
+    u, info = G.solve(torch.tensor(f, device="cuda"), 1e-8)
+    uo, it, rr, st = H.pcg(f, 1e-8)
+    assert info.status == 0 and st == 0
+    assert abs(info.iters - it) <= 1
+
+
+def test_irregular_random_matrix():
+    ptr, col, val = I.random_spd_like(700, 0.01, seed=9)
+    G = B.AMG(coarse_enough=30)
+    G.full_setup(*(torch.tensor(a, device="cuda") for a in (ptr, col, val)))
+    H = O.Hierarchy(ptr, col, val, O.Params(coarse_enough=30))
+    compare_hierarchy(G, H)
+
+
+# ------------------------------------------------------------------ partial rebuild (Alg. 4)
+@pytest.mark.parametrize("dim,N,T", [(2, 32, 10), (3, 40, 20)])
+def test_partial_rebuild_matches_oracle(dim, N, T):
+    ptr, col, v0 = gpu_problem(dim, N, 0, T)
+    G = B.AMG()
+    G.full_setup(ptr, col, v0)
+    H = O.Hierarchy(*oracle_problem(dim, N, 0, T))
+    for k in (1, T // 2, T - 1):
+        _, _, vk = gpu_problem(dim, N, k, T)
+        G.partial_rebuild(vk)
+        assert H.rebuild(oracle_problem(dim, N, k, T)[2]) == 0
+        compare_hierarchy(G, H)
+        lu, piv = G.coarse_lu()
+        olu, opiv = H.lu()
+        assert np.array_equal(piv, opiv)
+
+
+def test_partial_rebuild_on_unchanged_values_equals_full_setup_bitwise():
+    ptr, col, v0 = gpu_problem(3, 32, 3, 10)
+    _, _, v1 = gpu_problem(3, 32, 8, 10)
+    G = B.AMG()
+    G.full_setup(ptr, col, v0)
+    ref = [G.export_level(l) for l in range(G.nlevels)]
+    G.partial_rebuild(v1)
+    G.partial_rebuild(v0)
+    for l in range(G.nlevels):
+        g = G.export_level(l)
+        assert np.array_equal(g["A"][2], ref[l]["A"][2])
+        assert np.array_equal(g["m"], ref[l]["m"])
+
+
+# ------------------------------------------------------------------ V-cycle and solve
+@pytest.mark.parametrize("dim,N", [(2, 32), (3, 48)])
+def test_vcycle_matches_oracle(dim, N):
+    ptr, col, v = gpu_problem(dim, N, 1, 5)
+    G = B.AMG()
+    G.full_setup(ptr, col, v)
+    H = O.Hierarchy(*oracle_problem(dim, N, 1, 5))
+    r = np.random.default_rng(5).normal(size=N ** dim)
+    z = G.vcycle(torch.tensor(r, device="cuda")).cpu().numpy()
+    zo = H.vcycle(r)
+    assert np.linalg.norm(z - zo) <= 1e-10 * np.linalg.norm(zo)
+
+
+@pytest.mark.parametrize("dim,N,T", [(2, 32, 10), (3, 64, 50)])
+def test_solve_matches_oracle(dim, N, T):
+    ptr, col, v = gpu_problem(dim, N, T // 2, T)
+    G = B.AMG()
+    G.full_setup(ptr, col, v)
+    H = O.Hierarchy(*oracle_problem(dim, N, T // 2, T))
+    f = I.rhs(N ** dim)
+    u, info = G.solve(torch.tensor(f, device="cuda"), 1e-8)
+    uo, it, rr, st = H.pcg(f, 1e-8)
+    assert info.status == B.AMG_OK and st == O.OK
+    assert abs(info.iters - it) <= 1
+    assert info.rel_resid <= 1e-8
+    un = u.cpu().numpy()
+    A = _sp(*oracle_problem(dim, N, T // 2, T), N ** dim)
+    assert np.linalg.norm(f - A @ un) / np.linalg.norm(f) <= 1e-8
+    assert np.linalg.norm(un - uo) <= 1e-5 * np.linalg.norm(uo)
+
+
+def test_single_level_and_zero_rhs():
+    ptr, col, v = gpu_problem(2, 8, 0, 2)
+    G = B.AMG()
+    G.full_setup(ptr, col, v)
+    assert G.nlevels == 1
+    f = torch.tensor(I.rhs(64), device="cuda")
+    u, info = G.solve(f, 1e-10)
+    assert info.status == 0 and info.iters == 1 and info.rel_resid <= 1e-10
+    u, info = G.solve(torch.zeros(64, dtype=torch.float64, device="cuda"))
+    assert info.iters == 0 and torch.all(u == 0)
+
+
+# ------------------------------------------------------------------ time-step modes
+@pytest.mark.parametrize("mode", [B.MODE_PARTIAL, B.MODE_FULL_REBUILD, B.MODE_FULL_REUSE] if torch.cuda.is_available() else [0])
+def test_time_series_modes_match_oracle(mode):
+    dim, N, T = 2, 32, 10
+    ptr, col, _ = gpu_problem(dim, N, 0, T)
+    f = I.rhs(N * N)
+    ft = torch.tensor(f, device="cuda")
+    G = B.AMG(mode=mode)
+    vals = [oracle_problem(dim, N, k, T)[2] for k in range(T)]
+    recs = O.run_time_steps(*oracle_problem(dim, N, 0, T)[:2], vals, f, mode)
+    for k in range(T):
+        _, _, vk = gpu_problem(dim, N, k, T)
+        si = G.step(vk, ptr, col)
+        u, info = G.solve(ft, 1e-8)
+        assert bool(si.rebuilt) == recs[k].rebuilt, k
+        assert info.status == recs[k].status, k
+        assert abs(info.iters - recs[k].iters) <= 1, k
+        if info.status == 0:
+            assert info.rel_resid <= 1e-8
+
+
+def test_host_buffer_entry_point():
+    dim, N = 3, 24
+    ptr, col, v0 = gpu_problem(dim, N, 0, 4)
+    G = B.AMG()
+    G.step(v0, ptr, col)
+    f = I.rhs(N ** 3)
+    hv = np.ascontiguousarray(oracle_problem(dim, N, 2, 4)[2])
+    hu = np.zeros(N ** 3)
+    info = G.step_solve_host(hv, f, hu, 1e-8)
+    H = O.Hierarchy(*oracle_problem(dim, N, 0, 4))
+    H.rebuild(hv)
+    uo, it, rr, st = H.pcg(f, 1e-8)
+    assert info.status == 0 and abs(info.iters - it) <= 1
+    assert np.linalg.norm(hu - uo) <= 1e-5 * np.linalg.norm(uo)
+
+
+# ------------------------------------------------------------------ mixed precision
+@pytest.mark.parametrize("dim,N,T", [(2, 32, 10), (3, 64, 50)])
+def test_mixed_precision_reaches_fp64_tolerance(dim, N, T):
+    ptr, col, v0 = gpu_problem(dim, N, 0, T)
+    G = B.AMG(precision=B.PREC_MIXED)
+    G.full_setup(ptr, col, v0)
+    H = O.Hierarchy(*oracle_problem(dim, N, 0, T))
+    f = I.rhs(N ** dim)
+    ft = torch.tensor(f, device="cuda")
+    for k in (0, T - 1):
+        if k:
+            _, _, vk = gpu_problem(dim, N, k, T)
+            G.partial_rebuild(vk)
+            H.rebuild(oracle_problem(dim, N, k, T)[2])
+        # structure identical to the FP64 oracle; values within FP32 accuracy
+        compare_hierarchy(G, H, values_bitwise=False, check_values=False)
+        for l in range(1, G.nlevels):
+            gv = G.export_level(l)["A"][2]
+            ov = H.level(l).A.val
+            scale = np.abs(ov).max()
+            assert np.max(np.abs(gv - ov)) <= 1e-5 * scale
+        u, info = G.solve(ft, 1e-8)
+        uo, it, rr, st = H.pcg(f, 1e-8)
+        assert info.status == 0 and info.rel_resid <= 1e-8
+        assert info.iters <= it + 3
+        assert np.linalg.norm(u.cpu().numpy() - uo) <= 1e-5 * np.linalg.norm(uo)
+
+
+# ------------------------------------------------------------------ errors (all detected without faults)
+def test_error_statuses():
+    ptr, col, v = gpu_problem(2, 16, 0, 2)
+    G = B.AMG()
+    with pytest.raises(B.AmgError) as e:
+        G.partial_rebuild(v)
+    assert e.value.status == B.AMG_ERR_STATE
+    bad = col.clone()
+    bad[1], bad[2] = col[2], col[1]
+    with pytest.raises(B.AmgError) as e:
+        G.full_setup(ptr, bad, v)
+    assert e.value.status == B.AMG_ERR_PATTERN
+    nan = v.clone()
+    nan[5] = float("nan")
+    with pytest.raises(B.AmgError) as e:
+        G.full_setup(ptr, col, nan)
+    assert e.value.status == B.AMG_ERR_NONFINITE
+    G.full_setup(ptr, col, v)
+    with pytest.raises(B.AmgError) as e:
+        G.partial_rebuild(nan)
+    assert e.value.status == B.AMG_ERR_NONFINITE
+    G.full_setup(ptr, col, v)
+    f = torch.tensor(I.rhs(256), device="cuda")
+    G1 = B.AMG(maxiter=1, coarse_enough=16)
+    G1.full_setup(ptr, col, v)
+    u, info = G1.solve(f, 1e-14)
+    assert info.status == B.AMG_NOT_CONVERGED and info.iters == 1
+    # an indefinite system breaks CG down: reported, not trapped
+    G2 = B.AMG(coarse_enough=16)
+    G2.full_setup(ptr, col, v)
+    neg = -v
+    G2.partial_rebuild(neg)
+    with pytest.raises(B.AmgError) as e:
+        G2.solve(f, 1e-8)
+    assert e.value.status in (B.AMG_ERR_BREAKDOWN,)
