@@ -1,0 +1,390 @@
+#!/usr/bin/env python
+"""Benchmark: seconds per time step (setup + solve) of partial-reuse AMG on one
+GB300, against full rebuild and full reuse on the same steps (arXiv
+2108.02054, Alg. 3 / Alg. 4, Table 2's comparison), plus the per-kernel
+memory roofline of the dominant kernel.
+
+Default workload: the 3D 7-point collapsing-column pressure Poisson on a 64^3
+grid (262,144 unknowns), FP64, 50 time steps, CG to 1e-8 relative residual.
+Inputs (every step's matrix values, the right-hand side) are resident on the
+device before timing; L2 is flushed (256 MB write) between timed steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload 3d64|2d32|3d128|3d192]
+  python bench.py --impl reference ...   (the CPU oracle arm, same metric)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2108_02054_gb300 import inputs as I  # noqa: E402
+
+METRIC = "sec/time step (setup+solve) partial vs full rebuild at 1e-8; RAP/SpMV HBM GB/s"
+UNIT = "s/time step"
+TOL = 1e-8
+FLUSH_BYTES = 256 << 20
+
+DESCR = {
+    "2d32": "2D 5-point collapsing-column pressure Poisson, 32x32 cells (1,024 unknowns), FP64, 10 time steps",
+    "3d64": "3D 7-point collapsing-column pressure Poisson, 64^3 cells (262,144 unknowns), FP64, 50 time steps",
+    "3d128": "3D 7-point collapsing-column pressure Poisson, 128^3 cells (2,097,152 unknowns), FP32 hierarchy / "
+             "FP64 outer CG, 100 time steps",
+    "3d192": "3D 7-point collapsing-column pressure Poisson, 192^3 cells (7,077,888 unknowns), FP32 hierarchy / "
+             "FP64 outer CG, 100 time steps",
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="3d64", choices=sorted(DESCR))
+    ap.add_argument("--compare-steps", type=int, default=10,
+                    help="timed steps of the full-rebuild and full-reuse comparison runs")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6672.5), "measured"
+    return 6800.0, "fallback"
+
+
+def step_indices(w, warmup, steps):
+    """Time-step indices: step 0 is the (untimed) full setup, then warm-up and
+    timed steps walk k = 1, 2, ... cycling through 1..T-1."""
+    span = max(w.T - 1, 1)
+    seq = [1 + (j % span) for j in range(warmup + steps)]
+    return seq[:warmup], seq[warmup:]
+
+
+# --------------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------- our arm
+def level_sizes(G):
+    out = []
+    for l in range(G.nlevels):
+        n, nnz, nnzP, nnzR, nnzAP, nagg = G.level_sizes(l)
+        out.append({"n": n, "nnz": nnz, "nnzP": nnzP, "nnzAP": nnzAP, "nagg": nagg})
+    return out
+
+
+def algorithmic_bytes(slot, lv, s):
+    """Bytes one launch must move at minimum (int32 indices, s-byte values of
+    the hierarchy; CG vectors are FP64).  lv: level sizes list."""
+    L0 = lv[0]
+    n, nnz = L0["n"], L0["nnz"]
+    nc, nnzP = L0["nagg"], L0["nnzP"]
+    nnzc = lv[1]["nnz"] if len(lv) > 1 else 0
+    if slot == "cg_spmv":      # q = A p, p.q: ptr, col, val(f64), p, q
+        return 4 * (n + 1) + 12 * nnz + 16 * n
+    if slot == "smooth0_l0":   # u = m f, r = f - A(m f): ptr, col, val, m, f(f64), u, r
+        return 4 * (n + 1) + nnz * (4 + s) + n * s + 8 * n + 2 * n * s
+    if slot == "sweep_l0":     # z = u + m (f - A u): ptr, col, val, m, f(f64), u, z(f64)
+        return 4 * (n + 1) + nnz * (4 + s) + n * s + 8 * n + n * s + 8 * n
+    if slot == "restrict_l0":  # f_c = R r
+        return 4 * (nc + 1) + nnzP * (4 + s) + n * s + nc * s
+    if slot == "prolong_l0":   # u += P u_c
+        return 4 * (n + 1) + nnzP * (4 + s) + nc * s + 2 * n * s
+    if slot == "ap_l0":        # stage 1 of the Galerkin product: A (ptr, col, val), P (ptr, val)
+        return 4 * (n + 1) + nnz * (4 + s) + 4 * (n + 1) + nnzP * s
+    if slot == "rap_l0":       # stage 2: R (ptr, col, val), A_c values out
+        return 4 * (nc + 1) + nnzP * (4 + s) + nnzc * s
+    if slot == "ingest":       # fine values in (f64), hierarchy copy out, smoother diagonal
+        return 4 * (n + 1) + 8 * nnz + (8 if s == 8 else 12) * nnz + n * s
+    if slot in ("cg_update",):  # u, p, q, r in; u, r out
+        return 8 * n * 6
+    if slot == "cg_p":
+        return 8 * n * 3
+    if slot == "dot":
+        return 8 * n * 2
+    return None
+
+
+def run_mode(B, torch, w, mode, ptr, col, vals, f, warm_idx, timed_idx, flush, profile=False, barrier=None):
+    prec = B.PREC_MIXED if w.precision == "mixed" else B.PREC_FP64
+    G = B.AMG(precision=prec, mode=mode)
+    u = torch.empty_like(f)
+    G.step(vals[0], ptr, col)
+    G.solve(f, TOL, u=u)
+    for k in warm_idx:
+        G.step(vals[k])
+        G.solve(f, TOL, u=u)
+    torch.cuda.synchronize()
+    if barrier:
+        barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in timed_idx]
+    if profile:
+        G.profile(True)
+    l0 = B.kernel_launches()
+    infos = []
+    t0 = time.perf_counter()
+    for (e0, e1, e2), k in zip(ev, timed_idx):
+        flush.zero_()                      # evict L2 between timed steps (outside the events)
+        e0.record()
+        si = G.step(vals[k])
+        e1.record()
+        _, info = G.solve(f, TOL, u=u)
+        e2.record()
+        infos.append((si, info))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    launches = B.kernel_launches() - l0
+    prof = G.profile_read() if profile else None
+    G.profile(False)
+    setup = [a.elapsed_time(b) for a, b, c in ev]
+    solve = [b.elapsed_time(c) for a, b, c in ev]
+    res = {
+        "setup_ms": statistics.mean(setup), "solve_ms": statistics.mean(solve),
+        "step_ms": statistics.mean([a + b for a, b in zip(setup, solve)]),
+        "step_ms_median": statistics.median([a + b for a, b in zip(setup, solve)]),
+        "iters": statistics.mean([i.iters for _, i in infos]),
+        "max_rel_resid": max(i.rel_resid for _, i in infos),
+        "rebuilds": sum(s.rebuilt for s, _ in infos),
+        "all_converged": all(i.status == 0 for _, i in infos),
+        "wall_s": wall, "launches": launches, "levels": level_sizes(G),
+    }
+    return G, res, prof, u
+
+
+def e2e_leg(B, np, G, w, vals_host, f_host, idx):
+    """Same steps through the host-buffer entry point: the H2D copy of the step's
+    values and right-hand side and the D2H copy of u are inside the timing."""
+    import torch
+    hu = torch.empty(w.n, dtype=torch.float64).pin_memory()
+    hf = torch.tensor(f_host).pin_memory()
+    hv = {k: torch.tensor(v).pin_memory() for k, v in vals_host.items()}
+    times = []
+    for k in idx:
+        t0 = time.perf_counter()
+        G.step_solve_host(hv[k].numpy(), hf.numpy(), hu.numpy(), TOL)
+        times.append(time.perf_counter() - t0)
+    return statistics.mean(times), 8 * (w.nnz + w.n), 8 * w.n
+
+
+def oracle_steps(w, idx, budget_s):
+    """The CPU oracle on the same time steps (partial reuse: full setup at step
+    0, untimed; then rebuild + PCG per step), stopping once budget_s is spent."""
+    import oracle as O
+    ptr, col, v0 = O.poisson_assemble(w.dim, w.N, I.density(w.dim, w.N, 0, w.T))
+    H = O.Hierarchy(ptr, col, v0)
+    f = I.rhs(w.n)
+    times, done = [], []
+    t_all = time.perf_counter()
+    for k in idx:
+        v = O.poisson_assemble(w.dim, w.N, I.density(w.dim, w.N, k, w.T))[2]
+        t0 = time.perf_counter()
+        H.rebuild(v)
+        H.pcg(f, TOL, 100, sys_val=v)
+        times.append(time.perf_counter() - t0)
+        done.append(k)
+        if time.perf_counter() - t_all > budget_s:
+            break
+    return statistics.mean(times), done
+
+
+def cores_used():
+    """The oracle is a single-threaded C program: it uses one core."""
+    return 1
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    barrier = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        barrier = lambda: dist.barrier(device_ids=[local])  # noqa: E731
+    from paper_2108_02054_gb300 import amg as B
+
+    w = I.WORKLOADS[args.workload]
+    warm_idx, timed_idx = step_indices(w, args.warmup, args.steps)
+    ptr, col = B.poisson_pattern(w.dim, w.N)
+    needed = sorted(set([0] + warm_idx + timed_idx))
+    vals = {k: B.poisson_values(w.dim, w.N, torch.tensor(I.density(w.dim, w.N, k, w.T), device="cuda"), ptr)
+            for k in needed}
+    f = torch.tensor(I.rhs(w.n), device="cuda")
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    G, part, prof, u = run_mode(B, torch, w, B.MODE_PARTIAL, ptr, col, vals, f, warm_idx, timed_idx, flush,
+                                profile=False, barrier=barrier)
+    clk = clocks.stop()
+    # same steps again with per-kernel event timing (the roofline numbers)
+    _, _, prof, _ = run_mode(B, torch, w, B.MODE_PARTIAL, ptr, col, vals, f, warm_idx, timed_idx, flush,
+                             profile=True)
+    nc = min(args.compare_steps, len(timed_idx))
+    _, full, _, _ = run_mode(B, torch, w, B.MODE_FULL_REBUILD, ptr, col, vals, f, warm_idx, timed_idx[:nc], flush)
+    _, reuse, _, _ = run_mode(B, torch, w, B.MODE_FULL_REUSE, ptr, col, vals, f, warm_idx, timed_idx[:nc], flush)
+
+    step_s = part["step_ms"] / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([step_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_s = float(t.item())
+    value = step_s / world  # replicas: every rank runs its own time series
+
+    # roofline of the dominant kernel
+    s = 4 if w.precision == "mixed" else 8
+    peak, peak_kind = measured_peaks()
+    kernels = {}
+    for name, (ms, cnt) in prof.items():
+        if cnt == 0 or ms <= 0:
+            continue
+        per = ms / cnt
+        by = algorithmic_bytes(name, part["levels"], s)
+        kernels[name] = {"ms_total_per_step": ms / len(timed_idx), "launches_per_step": cnt / len(timed_idx),
+                         "us_per_launch": per * 1e3,
+                         "algorithmic_bytes": by,
+                         "achieved_gbs": (by / (per * 1e-3) / 1e9) if by else None}
+    dom = max((k for k in kernels if kernels[k]["achieved_gbs"]), key=lambda k: kernels[k]["ms_total_per_step"])
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "traffic_bytes.json")
+    if os.path.exists(tp):
+        traffic = json.load(open(tp)).get(f"{args.workload}:{dom}")
+    ach = kernels[dom]["achieved_gbs"]
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(ach / peak, 4), "peak_source": peak_kind, "traffic": traffic,
+                "algorithmic_bytes_per_launch": kernels[dom]["algorithmic_bytes"]}
+
+    # end to end through the host-buffer entry point (rank-local)
+    vals_host = {k: v.cpu().numpy() for k, v in vals.items()}
+    e2e_s, h2d, d2h = e2e_leg(B, np, G, w, vals_host, I.rhs(w.n), timed_idx[:min(len(timed_idx), 10)])
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": len(timed_idx),
+        "warmup": len(warm_idx), "ms_per_step": part["step_ms"], "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if w.precision == "mixed" else "f64",
+        "data": "synthetic (seeded collapsing water column, density ratio 1000:1)",
+        "config": {"workload": f"{args.workload}: {DESCR[args.workload]}", "n": w.n, "nnz": w.nnz, "T": w.T,
+                   "tol": TOL, "mode": "partial reuse", "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "flushed between timed steps (256 MB write, outside the timed events)",
+                   "step_indices": [timed_idx[0], timed_idx[-1]]},
+        "modes": {"partial": _strip(part), "full_rebuild": _strip(full), "full_reuse": _strip(reuse)},
+        "speedup_pct_vs_full_rebuild": {
+            "total": round(100 * (full["step_ms"] / part["step_ms"] - 1), 1),
+            "setup": round(100 * (full["setup_ms"] / part["setup_ms"] - 1), 1)},
+        "roofline": roofline,
+        "kernels": kernels,
+        "e2e": {"value": e2e_s / world, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": part["launches"],
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, done = oracle_steps(w, timed_idx, budget_s=20.0)
+        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores_used(), "kind": "oracle",
+                               "sample": f"{len(done)} time steps ({done[0]}..{done[-1]}) of the same workload, "
+                                         "serial C oracle, FP64, rebuild + PCG per step"}
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier(device_ids=[local])
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def _strip(r):
+    return {k: v for k, v in r.items() if k != "levels"} | {"levels": [l["n"] for l in r["levels"]]}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = I.WORKLOADS[args.workload]
+    warm_idx, timed_idx = step_indices(w, args.warmup, args.steps)
+    v, done = oracle_steps(w, timed_idx, budget_s=120.0)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": len(done),
+        "warmup": 0, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (seeded collapsing water column, density ratio 1000:1)",
+        "config": {"workload": f"{args.workload}: {DESCR[args.workload]}", "n": w.n, "nnz": w.nnz, "T": w.T,
+                   "tol": TOL, "mode": "partial reuse"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores_used(), "kind": "oracle",
+                         "sample": f"{len(done)} time steps ({done[0]}..{done[-1]}), serial C oracle"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -139,6 +139,34 @@ amg_status amg_export_level_vec(amg_ctx *ctx, int32_t level, int32_t *d_agg, uin
 /* Coarsest LU factors (n_L x n_L row-major, FP64) and pivots. */
 amg_status amg_export_coarse_lu(amg_ctx *ctx, double *d_lu, int32_t *d_piv);
 
+/* Instrumentation (no counterpart in the paper; used to report per-kernel
+ * time against the memory roofline).  amg_profile(ctx, 1) records a CUDA
+ * event pair on the context's stream around every launch of the kernels named
+ * by the AMG_PROF_* slots; amg_profile_read synchronises the stream, returns
+ * the summed milliseconds and the number of timed launches of one slot and
+ * clears it.  amg_kernel_launches returns the number of kernels this library
+ * has launched in the process so far (all contexts). */
+enum {
+    AMG_PROF_CG_SPMV = 0,      /* CG: q = A p fused with p.q (fine level, FP64) */
+    AMG_PROF_SMOOTH0_L0 = 1,   /* V-cycle, finest level: zero-guess smoothing + residual */
+    AMG_PROF_SWEEP_L0 = 2,     /* V-cycle, finest level: last post-smoothing sweep */
+    AMG_PROF_RESTRICT_L0 = 3,  /* V-cycle: f_2 = R r on the finest level */
+    AMG_PROF_PROLONG_L0 = 4,   /* V-cycle: u += P u_2 on the finest level */
+    AMG_PROF_AP_L0 = 5,        /* Galerkin stage 1 on the finest level: A P */
+    AMG_PROF_RAP_L0 = 6,       /* Galerkin stage 2 on the finest level: R (A P) */
+    AMG_PROF_INGEST = 7,       /* fine values in: copy / cast / smoother */
+    AMG_PROF_LU = 8,           /* coarsest dense LU */
+    AMG_PROF_INV = 9,          /* coarsest explicit inverse */
+    AMG_PROF_CG_UPDATE = 10,   /* CG: u += alpha p, r -= alpha q, r.r */
+    AMG_PROF_CG_P = 11,        /* CG: p = z + beta p */
+    AMG_PROF_DOT = 12,         /* CG: r.z */
+    AMG_PROF_COARSE = 13,      /* coarsest solve (dense inverse times vector) */
+    AMG_PROF_NSLOTS = 14
+};
+amg_status amg_profile(amg_ctx *ctx, int32_t enable);
+amg_status amg_profile_read(amg_ctx *ctx, int32_t slot, double *total_ms, int64_t *launches);
+int64_t amg_kernel_launches(void);
+
 /* Synthetic pressure-Poisson workload: -div((1/rho) grad p) on an N^dim cell
  * grid (dim 2 or 3), harmonic face coefficients 2/(rho_i + rho_j), Dirichlet
  * p = 0 on the top face through a ghost cell (A_ii += 2/rho_i) when

@@ -33,8 +33,10 @@ EXPORTS = [
     "amg_default_params", "amg_create", "amg_destroy", "amg_last_error", "amg_full_setup", "amg_partial_rebuild",
     "amg_step", "amg_solve", "amg_apply_vcycle", "amg_step_solve_host", "amg_num_levels", "amg_level_sizes",
     "amg_export_csr", "amg_export_level_vec", "amg_export_coarse_lu", "amg_poisson_nnz", "amg_poisson_pattern",
-    "amg_poisson_values", "amg_poisson_grad_theta",
+    "amg_poisson_values", "amg_poisson_grad_theta", "amg_profile", "amg_profile_read", "amg_kernel_launches",
 ]
+PROF_SLOTS = ["cg_spmv", "smooth0_l0", "sweep_l0", "restrict_l0", "prolong_l0", "ap_l0", "rap_l0", "ingest", "lu",
+              "inv", "cg_update", "cg_p", "dot", "coarse"]
 
 
 class amg_params(ctypes.Structure):
@@ -92,6 +94,9 @@ def lib():
                 "amg_poisson_pattern": (_i32, [_i32, _i32, _vp, _vp, _vp]),
                 "amg_poisson_values": (_i32, [_i32, _i32, _i32, _vp, _vp, _vp, _vp]),
                 "amg_poisson_grad_theta": (_i32, [_i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp]),
+                "amg_profile": (_i32, [_vp, _i32]),
+                "amg_profile_read": (_i32, [_vp, _i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
+                "amg_kernel_launches": (ctypes.c_int64, []),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -245,6 +250,19 @@ class AMG:
         out["m"] = m.cpu().numpy()
         return out
 
+    def profile(self, enable: bool = True):
+        self._check(lib().amg_profile(self._h, int(enable)))
+
+    def profile_read(self) -> dict:
+        """{slot name: (total ms, timed launches)} since the last read."""
+        out = {}
+        for k, name in enumerate(PROF_SLOTS):
+            ms = ctypes.c_double()
+            cnt = ctypes.c_int64()
+            self._check(lib().amg_profile_read(self._h, k, ctypes.byref(ms), ctypes.byref(cnt)))
+            out[name] = (ms.value, cnt.value)
+        return out
+
     def coarse_lu(self):
         import torch
         nL = self.level_sizes(self.nlevels - 1)[0]
@@ -255,6 +273,11 @@ class AMG:
 
 
 # ---------------------------------------------------------------- workload assembly
+def kernel_launches() -> int:
+    """Kernels launched by libamgpr.so in this process so far."""
+    return int(lib().amg_kernel_launches())
+
+
 def poisson_nnz(dim: int, N: int) -> int:
     return int(lib().amg_poisson_nnz(dim, N))
 

@@ -9,6 +9,7 @@
 //   amg_solve            CG with one V-cycle (Alg. 2) per iteration; the
 //                        iteration's control state lives on the device
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -17,6 +18,20 @@
 #include "common.cuh"
 
 using namespace amgpr;
+
+namespace amgpr {
+static std::atomic<int64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+int64_t launch_total() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace amgpr
+
+// CUDA-event timing of selected kernels on the context's stream (off unless
+// amg_profile(ctx, 1)); slot numbers are the AMG_PROF_* values of amgpr.h
+struct ProfData {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> rec[AMG_PROF_NSLOTS];
+};
 
 struct amg_ctx {
     amg_params prm{};
@@ -47,6 +62,7 @@ struct amg_ctx {
     int *h_st = nullptr;      // pinned
     // host-buffer staging
     double *stage_val = nullptr, *stage_f = nullptr, *stage_u = nullptr;
+    ProfData prof;
     // time-step bookkeeping
     int last_iters = 0;
     int last_status = AMG_OK;
@@ -59,6 +75,35 @@ amg_status set_err(amg_ctx *c, amg_status st, const std::string &msg) {
     if (c) c->err = msg;
     return st;
 }
+
+cudaEvent_t prof_event(amg_ctx *c) {
+    if (c->prof.pool.empty()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        return e;
+    }
+    cudaEvent_t e = c->prof.pool.back();
+    c->prof.pool.pop_back();
+    return e;
+}
+
+struct ProfScope {
+    amg_ctx *c;
+    int slot;
+    cudaEvent_t b = nullptr;
+    ProfScope(amg_ctx *c_, int slot_, bool active = true) : c(c_), slot(slot_) {
+        if (c->prof.on && active) {
+            b = prof_event(c);
+            cudaEventRecord(b, c->s);
+        }
+    }
+    ~ProfScope() {
+        if (!b) return;
+        cudaEvent_t e = prof_event(c);
+        cudaEventRecord(e, c->s);
+        c->prof.rec[slot].push_back({b, e});
+    }
+};
 
 #define CK(call)                                                                            \
     do {                                                                                    \
@@ -189,8 +234,8 @@ amg_status coarse_factor(amg_ctx *ctx) {
     Level &C = ctx->lev[ctx->nlev - 1];
     const bool mx = mixed(ctx);
     launch_csr_to_dense(C.n, C.A_ptr, C.A_col, mx ? nullptr : C.A_val, mx ? C.A_valf : nullptr, ctx->lu, ctx->s);
-    launch_dense_lu(C.n, ctx->lu, ctx->piv, ctx->d_st, ctx->s);
-    launch_lu_inverse(C.n, ctx->lu, ctx->piv, ctx->inv, ctx->s);
+    { ProfScope ps_(ctx, AMG_PROF_LU, true); launch_dense_lu(C.n, ctx->lu, ctx->piv, ctx->d_st, ctx->s); }
+    { ProfScope ps_(ctx, AMG_PROF_INV, true); launch_lu_inverse(C.n, ctx->lu, ctx->piv, ctx->inv, ctx->s); }
     return AMG_OK;
 }
 
@@ -199,18 +244,22 @@ amg_status numeric_rebuild(amg_ctx *ctx, const double *d_val, bool galerkin) {
     const amg_params &p = ctx->prm;
     Level &F = ctx->lev[0];
     const bool mx = mixed(ctx);
-    launch_ingest_fine(F.n, F.A_ptr, d_val, F.dia, p.smoother, p.jacobi_omega, d_val == F.A_val ? nullptr : F.A_val,
-                       mx ? F.A_valf : nullptr, mx ? nullptr : F.m, mx ? F.mf : nullptr, ctx->d_st, ctx->s);
+    {
+        ProfScope ps_(ctx, AMG_PROF_INGEST);
+        launch_ingest_fine(F.n, F.A_ptr, d_val, F.dia, p.smoother, p.jacobi_omega,
+                           d_val == F.A_val ? nullptr : F.A_val, mx ? F.A_valf : nullptr, mx ? nullptr : F.m,
+                           mx ? F.mf : nullptr, ctx->d_st, ctx->s);
+    }
     for (int l = 0; l + 1 < ctx->nlev; ++l) {
         Level &L = ctx->lev[l];
         Level &C = ctx->lev[l + 1];
         if (galerkin) {
             if (mx) {
-                launch_ap_numeric_f32(L, L.A_valf, ctx->s);
-                launch_rap_numeric_f32(L, C.A_ptr, C.A_valf, ctx->s);
+                { ProfScope ps_(ctx, AMG_PROF_AP_L0, l == 0); launch_ap_numeric_f32(L, L.A_valf, ctx->s); }
+                { ProfScope ps_(ctx, AMG_PROF_RAP_L0, l == 0); launch_rap_numeric_f32(L, C.A_ptr, C.A_valf, ctx->s); }
             } else {
-                launch_ap_numeric_f64(L, L.A_val, ctx->s);
-                launch_rap_numeric_f64(L, C.A_ptr, C.A_val, ctx->s);
+                { ProfScope ps_(ctx, AMG_PROF_AP_L0, l == 0); launch_ap_numeric_f64(L, L.A_val, ctx->s); }
+                { ProfScope ps_(ctx, AMG_PROF_RAP_L0, l == 0); launch_rap_numeric_f64(L, C.A_ptr, C.A_val, ctx->s); }
             }
         }
         if (l + 1 < ctx->nlev - 1) {
@@ -439,7 +488,7 @@ V *down_level(amg_ctx *ctx, int l, const TF *f, const int *skip) {
         launch_copy_cast<TF, V>(L.n, f, v.r, skip, ctx->s);
         return u;
     }
-    launch_smooth0_residual<V, TF>(L, A, m, f, u, v.r, skip, ctx->s);
+    { ProfScope ps_(ctx, AMG_PROF_SMOOTH0_L0, l == 0); launch_smooth0_residual<V, TF>(L, A, m, f, u, v.r, skip, ctx->s); }
     if (npre > 1) {
         for (int k = 1; k < npre; ++k) {
             launch_smooth_sweep<V, TF, V>(L, A, m, f, u, t, skip, ctx->s);
@@ -460,7 +509,7 @@ void up_level(amg_ctx *ctx, int l, const TF *f, V *u, TO *out, const int *skip) 
     const int npost = ctx->prm.npost;
     for (int k = 0; k < npost; ++k) {
         if (k == npost - 1 && out) {
-            launch_smooth_sweep<V, TF, TO>(L, A, m, f, u, out, skip, ctx->s);
+            { ProfScope ps_(ctx, AMG_PROF_SWEEP_L0, l == 0); launch_smooth_sweep<V, TF, TO>(L, A, m, f, u, out, skip, ctx->s); }
             return;
         }
         launch_smooth_sweep<V, TF, V>(L, A, m, f, u, t, skip, ctx->s);
@@ -478,15 +527,18 @@ void enqueue_vcycle(amg_ctx *ctx, const double *r, double *z, const int *skip) {
     }
     V *cur[kMaxLevels];
     cur[0] = down_level<V, double>(ctx, 0, r, skip);
-    launch_restrict<V>(ctx->lev[0], Vops<V>::R(ctx->lev[0]), Vops<V>::vec(ctx->lev[0]).r,
-                       Vops<V>::vec(ctx->lev[1]).f, skip, ctx->s);
+    {
+        ProfScope ps_(ctx, AMG_PROF_RESTRICT_L0);
+        launch_restrict<V>(ctx->lev[0], Vops<V>::R(ctx->lev[0]), Vops<V>::vec(ctx->lev[0]).r,
+                           Vops<V>::vec(ctx->lev[1]).f, skip, ctx->s);
+    }
     for (int l = 1; l < nl - 1; ++l) {
         Level &L = ctx->lev[l];
         cur[l] = down_level<V, V>(ctx, l, Vops<V>::vec(L).f, skip);
         launch_restrict<V>(L, Vops<V>::R(L), Vops<V>::vec(L).r, Vops<V>::vec(ctx->lev[l + 1]).f, skip, ctx->s);
     }
     Level &Cst = ctx->lev[nl - 1];
-    launch_coarse_solve<V, V, V>(Cst.n, ctx->inv, Vops<V>::vec(Cst).f, Vops<V>::vec(Cst).u, skip, ctx->s);
+    { ProfScope ps_(ctx, AMG_PROF_COARSE, true); launch_coarse_solve<V, V, V>(Cst.n, ctx->inv, Vops<V>::vec(Cst).f, Vops<V>::vec(Cst).u, skip, ctx->s); }
     cur[nl - 1] = Vops<V>::vec(Cst).u;
     for (int l = nl - 2; l >= 1; --l) {
         Level &L = ctx->lev[l];
@@ -502,7 +554,7 @@ void enqueue_vcycle(amg_ctx *ctx, const double *r, double *z, const int *skip) {
         cur[l] = u;
     }
     Level &F = ctx->lev[0];
-    launch_prolong<V>(F, Vops<V>::P(F), cur[1], cur[0], skip, ctx->s);
+    { ProfScope ps_(ctx, AMG_PROF_PROLONG_L0, true); launch_prolong<V>(F, Vops<V>::P(F), cur[1], cur[0], skip, ctx->s); }
     up_level<V, double, double>(ctx, 0, r, cur[0], z, skip);
 }
 
@@ -528,19 +580,19 @@ amg_status solve_impl(amg_ctx *ctx, const double *f, double *u, double tol, amg_
     launch_dot(n, r, z, ctx->partial, done, ctx->s);
     launch_cg_set_rz_p(n, nblk, ctx->partial, z, p, cg, ctx->s);
     for (int it = 1; it <= maxiter; ++it) {
-        launch_spmv_dot(n, ptr, col, A, p, q, ctx->partial, done, ctx->s);
+        { ProfScope ps_(ctx, AMG_PROF_CG_SPMV, true); launch_spmv_dot(n, ptr, col, A, p, q, ctx->partial, done, ctx->s); }
         launch_cg_alpha(nblk, ctx->partial, cg, ctx->s);
-        launch_cg_update_ur(n, cg, p, q, u, r, ctx->partial, ctx->s);
+        { ProfScope ps_(ctx, AMG_PROF_CG_UPDATE, true); launch_cg_update_ur(n, cg, p, q, u, r, ctx->partial, ctx->s); }
         launch_cg_check(nblk, ctx->partial, cg, ctx->s);
         launch_true_residual(n, ptr, col, A, f, u, t, ctx->partial, cg, 0, ctx->s);
         launch_true_check(nblk, ctx->partial, cg, ctx->s);
         launch_replace_r(n, cg, t, r, ctx->s);
         if (flex) launch_dot(n, r, z, ctx->partial2, done, ctx->s);
         vcycle(ctx, r, z, done);
-        launch_dot(n, r, z, ctx->partial, done, ctx->s);
+        { ProfScope ps_(ctx, AMG_PROF_DOT, true); launch_dot(n, r, z, ctx->partial, done, ctx->s); }
         if (flex) launch_cg_beta_flexible(nblk, ctx->partial, ctx->partial2, cg, ctx->s);
         else launch_cg_beta(nblk, ctx->partial, cg, ctx->s);
-        launch_cg_update_p(n, cg, z, p, ctx->s);
+        { ProfScope ps_(ctx, AMG_PROF_CG_P, true); launch_cg_update_p(n, cg, z, p, ctx->s); }
         CK(cudaMemcpyAsync(ctx->h_cg, cg, sizeof(CgState), cudaMemcpyDeviceToHost, ctx->s));
         CK(cudaStreamSynchronize(ctx->s));
         if (ctx->h_cg->done) break;
@@ -631,6 +683,9 @@ void amg_destroy(amg_ctx *ctx) {
     for (void *p : ctx->hier) cudaFreeAsync(p, ctx->s);
     for (void *p : ctx->persist) cudaFreeAsync(p, ctx->s);
     cudaStreamSynchronize(ctx->s);
+    for (auto &v : ctx->prof.rec)
+        for (auto &pr : v) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+    for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
     if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     if (ctx->h_cg) cudaFreeHost(ctx->h_cg);
     if (ctx->h_st) cudaFreeHost(ctx->h_st);
@@ -801,6 +856,31 @@ amg_status amg_export_coarse_lu(amg_ctx *ctx, double *d_lu, int32_t *d_piv) {
     CK(cudaStreamSynchronize(ctx->s));
     return AMG_OK;
 }
+
+amg_status amg_profile(amg_ctx *ctx, int32_t enable) {
+    if (!ctx) return AMG_ERR_ARG;
+    ctx->prof.on = enable != 0;
+    return AMG_OK;
+}
+
+amg_status amg_profile_read(amg_ctx *ctx, int32_t slot, double *total_ms, int64_t *launches) {
+    if (!ctx || slot < 0 || slot >= AMG_PROF_NSLOTS || !total_ms || !launches) return AMG_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->s));
+    double ms = 0.0;
+    for (auto &pr : ctx->prof.rec[slot]) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, pr.first, pr.second));
+        ms += t;
+        ctx->prof.pool.push_back(pr.first);
+        ctx->prof.pool.push_back(pr.second);
+    }
+    *total_ms = ms;
+    *launches = (int64_t)ctx->prof.rec[slot].size();
+    ctx->prof.rec[slot].clear();
+    return AMG_OK;
+}
+
+int64_t amg_kernel_launches(void) { return launch_total(); }
 
 int64_t amg_poisson_nnz(int32_t dim, int32_t N) {
     if ((dim != 2 && dim != 3) || N < 1) return -1;

@@ -74,6 +74,9 @@ struct Level {
 
 // ------------------------------------------------------------------ launchers
 // (all enqueue on `s`; `st` is the device status word)
+// every launcher counts its kernel launches (process-wide)
+void count_launch();
+int64_t launch_total();
 void scan_counts(const int32_t *in, int32_t *out, int64_t n, int *st, int64_t *tmp, cudaStream_t s);
 int64_t scan_tmp_elems(int64_t n);
 

@@ -655,40 +655,50 @@ void scan_counts(const int32_t *in, int32_t *out, int64_t n, int *st, int64_t *t
         return;
     }
     int64_t nb = (n + kScanTile - 1) / kScanTile;
+    count_launch();
     k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, tmp);
+    count_launch();
     k_scan_blocks<<<1, kScanThreads, 0, s>>>(tmp, nb);
+    count_launch();
     k_scan_final<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, tmp, nb, st);
 }
 
 void launch_poisson_rowlen(int dim, int N, int32_t *len, cudaStream_t s) {
     int64_t n = dim == 2 ? (int64_t)N * N : (int64_t)N * N * N;
+    count_launch();
     k_poisson_rowlen<<<nblocks(n), kThreads, 0, s>>>(dim, N, n, len);
 }
 void launch_poisson_cols(int dim, int N, const int32_t *ptr, int32_t *col, cudaStream_t s) {
     int64_t n = dim == 2 ? (int64_t)N * N : (int64_t)N * N * N;
+    count_launch();
     k_poisson_cols<<<nblocks(n), kThreads, 0, s>>>(dim, N, n, ptr, col);
 }
 void launch_poisson_vals(int dim, int N, int top, const double *rho, const int32_t *ptr, double *val,
                          cudaStream_t s) {
     int64_t n = dim == 2 ? (int64_t)N * N : (int64_t)N * N * N;
+    count_launch();
     k_poisson_vals<<<nblocks(n), kThreads, 0, s>>>(dim, N, n, top, rho, ptr, val);
 }
 void launch_poisson_grad(int dim, int N, int top, const double *rho, const double *u, const double *lam,
                          double *grad, cudaStream_t s) {
     int64_t n = dim == 2 ? (int64_t)N * N : (int64_t)N * N * N;
+    count_launch();
     k_poisson_grad<<<nblocks(n), kThreads, 0, s>>>(dim, N, n, top, rho, u, lam, grad);
 }
 
 void launch_check_pattern(int32_t n, const int32_t *ptr, const int32_t *col, int32_t *dia, int *st,
                           cudaStream_t s) {
+    count_launch();
     k_check_pattern<<<nblocks(n), kThreads, 0, s>>>(n, ptr, col, dia, st);
 }
 void launch_check_finite(int64_t nnz, const double *val, int *st, cudaStream_t s) {
     int64_t b = nblocks(nnz);
+    count_launch();
     k_check_finite<<<(unsigned)(b > 4096 ? 4096 : b), kThreads, 0, s>>>(nnz, val, st);
 }
 void launch_strength(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const int32_t *dia,
                      double eps2, uint8_t *strong, int32_t *deg, cudaStream_t s) {
+    count_launch();
     k_strength<<<nblocks(n), kThreads, 0, s>>>(n, ptr, col, val, dia, eps2, strong, deg);
 }
 
@@ -697,14 +707,19 @@ int32_t run_aggregation(int32_t n, const int32_t *ptr, const int32_t *col, const
                         uint8_t *r1, int32_t *root_id, int32_t *agg1, int32_t *root_of, int *counter, int *st,
                         int64_t *scan_tmp, cudaStream_t s) {
     const int nb = nblocks(n);
+    count_launch();
     k_mis_init<<<nb, kThreads, 0, s>>>(n, deg, state);
     // every round turns at least the undecided node of largest priority into
     // a root, so at most n rounds; in practice a few dozen
     for (int32_t round = 0; round <= n; ++round) {
+        count_launch();
         k_mis_m1<<<nb, kThreads, 0, s>>>(n, ptr, col, strong, state, m1);
+        count_launch();
         k_mis_select<<<nb, kThreads, 0, s>>>(n, ptr, col, strong, state, m1);
+        count_launch();
         k_mis_r1<<<nb, kThreads, 0, s>>>(n, ptr, col, strong, state, r1);
         cudaMemsetAsync(counter, 0, sizeof(int), s);
+        count_launch();
         k_mis_exclude<<<nb, kThreads, 0, s>>>(n, ptr, col, strong, state, r1, counter);
         int h = -1;
         if (cudaMemcpyAsync(&h, counter, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return -1;
@@ -712,36 +727,44 @@ int32_t run_aggregation(int32_t n, const int32_t *ptr, const int32_t *col, const
         if (h == 0) break;
         if (round == n) return -1;
     }
+    count_launch();
     k_root_flags<<<nb, kThreads, 0, s>>>(n, state, agg);
     scan_counts(agg, root_id, n, st, scan_tmp, s);
     int32_t nagg = 0;
     if (cudaMemcpyAsync(&nagg, root_id + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) return -1;
     if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
+    count_launch();
     k_agg_phase1<<<nb, kThreads, 0, s>>>(n, ptr, col, strong, state, root_id, agg1, root_of);
+    count_launch();
     k_agg_phase2<<<nb, kThreads, 0, s>>>(n, ptr, col, val, strong, state, agg1, root_of, agg, st);
     return nagg;
 }
 
 void launch_p_count(int32_t n, const int32_t *ptr, const int32_t *col, const uint8_t *strong, const int32_t *agg,
                     int smoothed, int32_t *plen, cudaStream_t s) {
+    count_launch();
     k_p_count<<<nblocks(n), kThreads, 0, s>>>(n, ptr, col, strong, agg, smoothed, plen);
 }
 void launch_p_fill(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const uint8_t *strong,
                    const int32_t *dia, const int32_t *agg, double omega, int smoothed, const int32_t *P_ptr,
                    int32_t *P_col, double *P_val, cudaStream_t s) {
+    count_launch();
     k_p_fill<<<nblocks(n), kThreads, 0, s>>>(n, ptr, col, val, strong, dia, agg, omega, smoothed, P_ptr, P_col,
                                              P_val);
 }
 void launch_count_cols(int64_t nnz, const int32_t *col, int32_t *cnt, cudaStream_t s) {
     int64_t b = nblocks(nnz);
+    count_launch();
     k_count_cols<<<(unsigned)(b > 8192 ? 8192 : b), kThreads, 0, s>>>(nnz, col, cnt);
 }
 void launch_transpose_scatter(int32_t n, const int32_t *P_ptr, const int32_t *P_col, const double *P_val,
                               const int32_t *R_ptr, int32_t *cursor, int32_t *R_col, double *R_val,
                               cudaStream_t s) {
+    count_launch();
     k_transpose_scatter<<<nblocks(n), kThreads, 0, s>>>(n, P_ptr, P_col, P_val, R_ptr, cursor, R_col, R_val);
 }
 void launch_sort_rows(int32_t nrows, const int32_t *ptr, int32_t *col, double *val, cudaStream_t s) {
+    count_launch();
     k_sort_rows<<<nblocks(nrows, 128), 128, 0, s>>>(nrows, ptr, col, val);
 }
 
@@ -755,29 +778,35 @@ void launch_spgemm_symbolic(int32_t nrows, int32_t ncols, const int32_t *X_ptr, 
     }
     if (nrows <= 0) return;
     unsigned grid = (unsigned)((nrows + kSymWarps - 1) / kSymWarps);
+    count_launch();
     k_spgemm_symbolic<<<grid, kSymWarps * 32, kSymSmem, s>>>(nrows, ncols, X_ptr, X_col, Y_ptr, Y_col, add_diag,
                                                               len, C_ptr, C_col, st);
 }
 
 void launch_t1_count(int32_t n, const int32_t *A_ptr, const int32_t *A_col, const int32_t *P_ptr, int32_t *cnt,
                      cudaStream_t s) {
+    count_launch();
     k_t1_count<<<nblocks(n), kThreads, 0, s>>>(n, A_ptr, A_col, P_ptr, cnt);
 }
 void launch_t1_fill(int32_t n, const int32_t *A_ptr, const int32_t *A_col, const int32_t *P_ptr,
                     const int32_t *P_col, const int32_t *AP_ptr, const int32_t *AP_col, const int32_t *t1ptr,
                     uint16_t *slot1, int *st, cudaStream_t s) {
+    count_launch();
     k_t1_fill<<<nblocks(n), kThreads, 0, s>>>(n, A_ptr, A_col, P_ptr, P_col, AP_ptr, AP_col, t1ptr, slot1, st);
 }
 void launch_t2_count(int32_t nc, const int32_t *R_ptr, const int32_t *R_col, const int32_t *AP_ptr, int32_t *cnt,
                      cudaStream_t s) {
+    count_launch();
     k_t2_count<<<nblocks(nc), kThreads, 0, s>>>(nc, R_ptr, R_col, AP_ptr, cnt);
 }
 void launch_t2_fill(int32_t nc, const int32_t *R_ptr, const int32_t *R_col, const int32_t *AP_ptr,
                     const int32_t *AP_col, const int32_t *Ac_ptr, const int32_t *Ac_col, const int32_t *t2ptr,
                     uint16_t *slot2, int *st, cudaStream_t s) {
+    count_launch();
     k_t2_fill<<<nblocks(nc, 128), 128, 0, s>>>(nc, R_ptr, R_col, AP_ptr, AP_col, Ac_ptr, Ac_col, t2ptr, slot2, st);
 }
 void launch_row_maxlen(int32_t n, const int32_t *ptr, int *out, cudaStream_t s) {
+    count_launch();
     k_row_maxlen<<<nblocks(n), kThreads, 0, s>>>(n, ptr, out);
 }
 

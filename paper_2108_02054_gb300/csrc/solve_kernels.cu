@@ -657,83 +657,101 @@ __global__ void k_cg_final_norm(int nblk, const double *__restrict__ partial, Cg
 
 // ======================================================================= launchers
 void launch_ap_numeric_f64(const Level &L, const double *A_val, cudaStream_t s) {
+    count_launch();
     k_ap_numeric_f64<<<nblocks(L.n, kApThreads), kApThreads, 0, s>>>(L.n, L.A_ptr, L.A_col, A_val, L.P_ptr, L.P_val,
                                                                      L.AP_ptr, L.t1ptr, L.slot1, L.AP_val);
 }
 void launch_rap_numeric_f64(const Level &L, const int32_t *Ac_ptr, double *Ac_val, cudaStream_t s) {
     unsigned g = (unsigned)((L.nc + kRapWarps - 1) / kRapWarps);
+    count_launch();
     k_rap_numeric_f64<<<g, kRapWarps * 32, 0, s>>>(L.nc, L.R_ptr, L.R_col, L.R_val, L.AP_ptr, L.AP_val, Ac_ptr,
                                                    L.t2ptr, L.slot2, Ac_val);
 }
 void launch_ap_numeric_f32(const Level &L, const float *A_valf, cudaStream_t s) {
+    count_launch();
     k_ap_numeric_f32<<<nblocks(L.n, kApThreads), kApThreads, 0, s>>>(L.n, L.A_ptr, L.A_col, A_valf, L.P_ptr,
                                                                      L.P_valf, L.AP_ptr, L.t1ptr, L.slot1, L.AP_valf);
 }
 void launch_rap_numeric_f32(const Level &L, const int32_t *Ac_ptr, float *Ac_valf, cudaStream_t s) {
     unsigned g = (unsigned)((L.nc + kRapWarps - 1) / kRapWarps);
+    count_launch();
     k_rap_numeric_f32<<<g, kRapWarps * 32, 0, s>>>(L.nc, L.R_ptr, L.R_col, L.R_valf, L.AP_ptr, L.AP_valf, Ac_ptr,
                                                    L.t2ptr, L.slot2, Ac_valf);
 }
 
 void launch_smoother_f64(int32_t n, const int32_t *ptr, const double *val, const int32_t *dia, int type, double wj,
                          double *m, cudaStream_t s) {
+    count_launch();
     k_smoother<double><<<nblocks(n), kThreads, 0, s>>>(n, ptr, val, dia, type, wj, m);
 }
 void launch_smoother_f32(int32_t n, const int32_t *ptr, const float *val, const int32_t *dia, int type, double wj,
                          float *m, cudaStream_t s) {
+    count_launch();
     k_smoother<float><<<nblocks(n), kThreads, 0, s>>>(n, ptr, val, dia, type, (float)wj, m);
 }
 void launch_ingest_fine(int32_t n, const int32_t *ptr, const double *val_in, const int32_t *dia, int type,
                         double wj, double *val_out, float *valf_out, double *m, float *mf, int *st,
                         cudaStream_t s) {
+    count_launch();
     k_ingest_fine<<<nblocks(n), kThreads, 0, s>>>(n, ptr, val_in, dia, type, wj, val_out, valf_out, m, mf, st);
 }
 void launch_cast_f32(int64_t n, const double *in, float *out, cudaStream_t s) {
     int64_t b = nblocks(n);
+    count_launch();
     k_cast_f32<<<(unsigned)(b > 8192 ? 8192 : b), kThreads, 0, s>>>(n, in, out);
 }
 
 void launch_csr_to_dense(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const float *valf,
                          double *dense, cudaStream_t s) {
     cudaMemsetAsync(dense, 0, sizeof(double) * (size_t)n * (size_t)n, s);
+    count_launch();
     k_csr_to_dense<<<nblocks(n), kThreads, 0, s>>>(n, ptr, col, val, valf, dense);
 }
 void launch_dense_lu(int32_t n, double *a, int32_t *piv, int *st, cudaStream_t s) {
+    count_launch();
     k_dense_lu<<<1, 1024, 0, s>>>(n, a, piv, st);
 }
 void launch_lu_inverse(int32_t n, const double *lu, const int32_t *piv, double *inv, cudaStream_t s) {
+    count_launch();
     k_lu_inverse<<<nblocks((int64_t)n * 32, 128), 128, 0, s>>>(n, lu, piv, inv);
 }
 
 template <class V, class TF>
 void launch_smooth0_residual(const Level &L, const V *val, const V *m, const TF *f, V *u, V *r, const int *skip,
                              cudaStream_t s) {
+    count_launch();
     k_smooth0_residual<V, TF><<<nblocks(L.n), kThreads, 0, s>>>(L.n, L.A_ptr, L.A_col, val, m, f, u, r, skip);
 }
 template <class V, class TF, class TO>
 void launch_smooth_sweep(const Level &L, const V *val, const V *m, const TF *f, const V *u_in, TO *u_out,
                          const int *skip, cudaStream_t s) {
+    count_launch();
     k_smooth_sweep<V, TF, TO><<<nblocks(L.n), kThreads, 0, s>>>(L.n, L.A_ptr, L.A_col, val, m, f, u_in, u_out, skip);
 }
 template <class V, class TF>
 void launch_residual(const Level &L, const V *val, const TF *f, const V *u, V *r, const int *skip, cudaStream_t s) {
+    count_launch();
     k_residual<V, TF><<<nblocks(L.n), kThreads, 0, s>>>(L.n, L.A_ptr, L.A_col, val, f, u, r, skip);
 }
 template <class V>
 void launch_restrict(const Level &L, const V *Rval, const V *r, V *fc, const int *skip, cudaStream_t s) {
+    count_launch();
     k_restrict<V><<<nblocks(L.nc), kThreads, 0, s>>>(L.nc, L.R_ptr, L.R_col, Rval, r, fc, skip);
 }
 template <class V>
 void launch_prolong(const Level &L, const V *Pval, const V *uc, V *u, const int *skip, cudaStream_t s) {
+    count_launch();
     k_prolong<V><<<nblocks(L.n), kThreads, 0, s>>>(L.n, L.P_ptr, L.P_col, Pval, uc, u, skip);
 }
 template <class V, class TF, class TO>
 void launch_coarse_solve(int32_t n, const double *inv, const TF *f, TO *u, const int *skip, cudaStream_t s) {
+    count_launch();
     k_coarse_solve<TF, TO><<<nblocks((int64_t)n * 32, 128), 128, 0, s>>>(n, inv, f, u, skip);
 }
 template <class TI, class TO>
 void launch_copy_cast(int64_t n, const TI *in, TO *out, const int *skip, cudaStream_t s) {
     int64_t b = nblocks(n);
+    count_launch();
     k_copy_cast<TI, TO><<<(unsigned)(b > 8192 ? 8192 : b), kThreads, 0, s>>>(n, in, out, skip);
 }
 
@@ -781,54 +799,69 @@ int cg_blocks(int64_t n) {
     return (int)(b < 1 ? 1 : b);
 }
 void launch_cg_init(int32_t n, const double *f, double *u, double *r, double *partial, cudaStream_t s) {
+    count_launch();
     k_cg_init<<<cg_blocks(n), kCgThreads, 0, s>>>(n, f, u, r, partial);
 }
 void launch_cg_start(int nblk, const double *partial, CgState *cg, double tol, int maxiter, cudaStream_t s) {
+    count_launch();
     k_cg_start<<<1, 1024, 0, s>>>(nblk, partial, cg, tol, maxiter);
 }
 void launch_dot(int32_t n, const double *x, const double *y, double *partial, const int *skip, cudaStream_t s) {
+    count_launch();
     k_dot<<<cg_blocks(n), kCgThreads, 0, s>>>(n, x, y, partial, skip);
 }
 void launch_cg_set_rz_p(int32_t n, int nblk, const double *partial, const double *z, double *p, CgState *cg,
                         cudaStream_t s) {
+    count_launch();
     k_cg_set_rz_p<<<cg_blocks(n), kCgThreads, 0, s>>>(n, nblk, partial, z, p, cg);
 }
 void launch_spmv_dot(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *p,
                      double *q, double *partial, const int *skip, cudaStream_t s) {
+    count_launch();
     k_spmv_dot<<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, col, val, p, q, partial, skip);
 }
 void launch_cg_alpha(int nblk, const double *partial, CgState *cg, cudaStream_t s) {
+    count_launch();
     k_cg_alpha<<<1, 1024, 0, s>>>(nblk, partial, cg);
 }
 void launch_cg_update_ur(int32_t n, const CgState *cg, const double *p, const double *q, double *u, double *r,
                          double *partial, cudaStream_t s) {
+    count_launch();
     k_cg_update_ur<<<cg_blocks(n), kCgThreads, 0, s>>>(n, cg, p, q, u, r, partial);
 }
 void launch_cg_check(int nblk, const double *partial, CgState *cg, cudaStream_t s) {
+    count_launch();
     k_cg_check<<<1, 1024, 0, s>>>(nblk, partial, cg);
 }
 void launch_true_residual(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *f,
                           const double *u, double *t, double *partial, const CgState *cg, int force,
                           cudaStream_t s) {
+    count_launch();
     k_true_residual<<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, col, val, f, u, t, partial, cg, force);
 }
 void launch_true_check(int nblk, const double *partial, CgState *cg, cudaStream_t s) {
+    count_launch();
     k_true_check<<<1, 1024, 0, s>>>(nblk, partial, cg);
 }
 void launch_replace_r(int32_t n, const CgState *cg, const double *t, double *r, cudaStream_t s) {
+    count_launch();
     k_replace_r<<<cg_blocks(n), kCgThreads, 0, s>>>(n, cg, t, r);
 }
 void launch_cg_beta(int nblk, const double *partial, CgState *cg, cudaStream_t s) {
+    count_launch();
     k_cg_beta<<<1, 1024, 0, s>>>(nblk, partial, cg);
 }
 void launch_cg_beta_flexible(int nblk, const double *partial, const double *partial_old, CgState *cg,
                              cudaStream_t s) {
+    count_launch();
     k_cg_beta_flexible<<<1, 1024, 0, s>>>(nblk, partial, partial_old, cg);
 }
 void launch_cg_update_p(int32_t n, const CgState *cg, const double *z, double *p, cudaStream_t s) {
+    count_launch();
     k_cg_update_p<<<cg_blocks(n), kCgThreads, 0, s>>>(n, cg, z, p);
 }
 void launch_cg_final_norm(int nblk, const double *partial, CgState *cg, cudaStream_t s) {
+    count_launch();
     k_cg_final_norm<<<1, 1024, 0, s>>>(nblk, partial, cg);
 }
 
