@@ -182,6 +182,30 @@ amg_status amg_poisson_grad_theta(int32_t dim, int32_t N, int32_t dirichlet_top,
                                   const double *d_u, const double *d_lam, double *d_grad,
                                   void *cuda_stream);
 
+/* Allocation-free variant of amg_poisson_pattern (no counterpart in the
+ * paper).  It exists for callers that must not allocate device memory at
+ * the time of the call: a host framework whose caching allocator already
+ * holds nearly all of the GPU's memory, or a latency-critical loop that
+ * forbids allocation once it runs.  Same outputs as amg_poisson_pattern
+ * (d_ptr: n + 1 int32, d_col: amg_poisson_nnz(dim, N) int32, device), written
+ * in order on cuda_stream (asynchronous: the call does not synchronise).
+ * It calls no allocator: the row lengths are scanned in place in d_ptr and
+ * the scan's block sums live in a fixed device array inside the library
+ * (about 128 KiB, held by every device that loads the library until the
+ * process exits).
+ *  - n = N^dim must not exceed AMG_NOALLOC_MAX_CELLS: larger grids return
+ *    AMG_ERR_CAPACITY without launching anything.
+ *  - The first call on a device looks up that array's device address (once
+ *    per device, with that device current); make this first call before any
+ *    stream capture.
+ *  - All calls share the one array and it keeps the last call's contents;
+ *    each call writes every entry it reads, so nothing needs clearing, but
+ *    calls whose work overlaps on the GPU (on different streams, or from
+ *    different threads) race on it: order them on one stream or synchronise. */
+#define AMG_NOALLOC_MAX_CELLS (1LL << 26)
+amg_status amg_poisson_pattern_noalloc(int32_t dim, int32_t N, int32_t *d_ptr, int32_t *d_col,
+                                       void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

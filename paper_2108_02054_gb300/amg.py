@@ -34,6 +34,7 @@ EXPORTS = [
     "amg_step", "amg_solve", "amg_apply_vcycle", "amg_step_solve_host", "amg_num_levels", "amg_level_sizes",
     "amg_export_csr", "amg_export_level_vec", "amg_export_coarse_lu", "amg_poisson_nnz", "amg_poisson_pattern",
     "amg_poisson_values", "amg_poisson_grad_theta", "amg_profile", "amg_profile_read", "amg_kernel_launches",
+    "amg_poisson_pattern_noalloc",
 ]
 PROF_SLOTS = ["cg_spmv", "smooth0_l0", "sweep_l0", "restrict_l0", "prolong_l0", "ap_l0", "rap_l0", "ingest", "lu",
               "inv", "cg_update", "cg_p", "dot", "coarse"]
@@ -97,6 +98,7 @@ def lib():
                 "amg_profile": (_i32, [_vp, _i32]),
                 "amg_profile_read": (_i32, [_vp, _i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
                 "amg_kernel_launches": (ctypes.c_int64, []),
+                "amg_poisson_pattern_noalloc": (_i32, [_i32, _i32, _vp, _vp, _vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
