@@ -180,6 +180,8 @@ def run_mode(B, torch, w, mode, ptr, col, vals, f, warm_idx, timed_idx, flush, p
         G.profile(True)
     l0 = B.kernel_launches()
     infos = []
+    names = {B.MODE_PARTIAL: "partial", B.MODE_FULL_REBUILD: "full_rebuild", B.MODE_FULL_REUSE: "full_reuse"}
+    torch.cuda.nvtx.range_push(names[mode] + ("_profiled" if profile else "_timed"))
     t0 = time.perf_counter()
     for (e0, e1, e2), k in zip(ev, timed_idx):
         flush.zero_()                      # evict L2 between timed steps (outside the events)
@@ -191,6 +193,7 @@ def run_mode(B, torch, w, mode, ptr, col, vals, f, warm_idx, timed_idx, flush, p
         infos.append((si, info))
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
+    torch.cuda.nvtx.range_pop()
     launches = B.kernel_launches() - l0
     prof = G.profile_read() if profile else None
     G.profile(False)

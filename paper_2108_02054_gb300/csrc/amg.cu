@@ -22,6 +22,7 @@ using namespace amgpr;
 namespace amgpr {
 static std::atomic<int64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void add_launches(int64_t d) { g_launches.fetch_add(d, std::memory_order_relaxed); }
 int64_t launch_total() { return g_launches.load(std::memory_order_relaxed); }
 }  // namespace amgpr
 
@@ -63,6 +64,15 @@ struct amg_ctx {
     // host-buffer staging
     double *stage_val = nullptr, *stage_f = nullptr, *stage_u = nullptr;
     ProfData prof;
+    // whole-solve CUDA graph (rebuilt after a full setup or a new tolerance)
+    cudaStream_t s_cap = nullptr, s_cap_main = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    bool use_graph = true;
+    bool graph_valid = false;
+    double graph_tol = -1.0;
+    double *cg_f = nullptr, *cg_u = nullptr;
+    int64_t graph_pro = 0, graph_body = 0, graph_epi = 0;  // kernels per part of the graph
     // time-step bookkeeping
     int last_iters = 0;
     int last_status = AMG_OK;
@@ -141,6 +151,7 @@ void free_hierarchy(amg_ctx *ctx) {
     ctx->have_setup = false;
     ctx->lu = ctx->inv = nullptr;
     ctx->piv = nullptr;
+    ctx->graph_valid = false;
 }
 
 // read the device status word (synchronises the stream) and map it
@@ -430,6 +441,9 @@ amg_status ensure_persistent(amg_ctx *ctx, int32_t n, int32_t nnz) {
     TRY(alloc(ctx, &ctx->cg_p, (size_t)n, true));
     TRY(alloc(ctx, &ctx->cg_q, (size_t)n, true));
     TRY(alloc(ctx, &ctx->cg_t, (size_t)n, true));
+    TRY(alloc(ctx, &ctx->cg_f, (size_t)n, true));
+    TRY(alloc(ctx, &ctx->cg_u, (size_t)n, true));
+    ctx->graph_valid = false;
     TRY(alloc(ctx, &ctx->partial, (size_t)cg_blocks(n), true));
     TRY(alloc(ctx, &ctx->partial2, (size_t)cg_blocks(n), true));
     TRY(alloc(ctx, &ctx->cg, 1, true));
@@ -564,43 +578,133 @@ void vcycle(amg_ctx *ctx, const double *r, double *z, const int *skip) {
 }
 
 // ---------------------------------------------------------------- CG
-amg_status solve_impl(amg_ctx *ctx, const double *f, double *u, double tol, amg_info *info) {
+// CG prologue: u = 0, r = f, z = B r, p = z, rz = r.z (device state in ctx->cg)
+void enqueue_cg_prologue(amg_ctx *ctx, const double *f, double *u, double tol) {
     const int32_t n = ctx->n;
     const int nblk = cg_blocks(n);
-    const int maxiter = ctx->prm.maxiter;
+    CgState *cg = ctx->cg;
+    launch_cg_init(n, f, u, ctx->cg_r, ctx->partial, ctx->s);
+    launch_cg_start(nblk, ctx->partial, cg, tol, ctx->prm.maxiter, ctx->s);
+    vcycle(ctx, ctx->cg_r, ctx->cg_z, &cg->done);
+    launch_dot(n, ctx->cg_r, ctx->cg_z, ctx->partial, &cg->done, ctx->s);
+    launch_cg_set_rz_p(n, nblk, ctx->partial, ctx->cg_z, ctx->cg_p, cg, ctx->s);
+}
+
+// one CG iteration; every kernel returns at once when the state says done
+void enqueue_cg_iteration(amg_ctx *ctx, const double *f, double *u) {
+    const int32_t n = ctx->n;
+    const int nblk = cg_blocks(n);
     const bool flex = mixed(ctx);
     CgState *cg = ctx->cg;
     const int *done = &cg->done;
     const double *A = ctx->A_sys;
     const int32_t *ptr = ctx->fine_ptr, *col = ctx->fine_col;
     double *r = ctx->cg_r, *z = ctx->cg_z, *p = ctx->cg_p, *q = ctx->cg_q, *t = ctx->cg_t;
-    launch_cg_init(n, f, u, r, ctx->partial, ctx->s);
-    launch_cg_start(nblk, ctx->partial, cg, tol, maxiter, ctx->s);
+    { ProfScope ps_(ctx, AMG_PROF_CG_SPMV, true); launch_spmv_dot(n, ptr, col, A, p, q, ctx->partial, done, ctx->s); }
+    launch_cg_alpha(nblk, ctx->partial, cg, ctx->s);
+    { ProfScope ps_(ctx, AMG_PROF_CG_UPDATE, true); launch_cg_update_ur(n, cg, p, q, u, r, ctx->partial, ctx->s); }
+    launch_cg_check(nblk, ctx->partial, cg, ctx->s);
+    launch_true_residual(n, ptr, col, A, f, u, t, ctx->partial, cg, 0, ctx->s);
+    launch_true_check(nblk, ctx->partial, cg, ctx->s);
+    launch_replace_r(n, cg, t, r, ctx->s);
+    if (flex) launch_dot(n, r, z, ctx->partial2, done, ctx->s);
     vcycle(ctx, r, z, done);
-    launch_dot(n, r, z, ctx->partial, done, ctx->s);
-    launch_cg_set_rz_p(n, nblk, ctx->partial, z, p, cg, ctx->s);
-    for (int it = 1; it <= maxiter; ++it) {
-        { ProfScope ps_(ctx, AMG_PROF_CG_SPMV, true); launch_spmv_dot(n, ptr, col, A, p, q, ctx->partial, done, ctx->s); }
-        launch_cg_alpha(nblk, ctx->partial, cg, ctx->s);
-        { ProfScope ps_(ctx, AMG_PROF_CG_UPDATE, true); launch_cg_update_ur(n, cg, p, q, u, r, ctx->partial, ctx->s); }
-        launch_cg_check(nblk, ctx->partial, cg, ctx->s);
-        launch_true_residual(n, ptr, col, A, f, u, t, ctx->partial, cg, 0, ctx->s);
-        launch_true_check(nblk, ctx->partial, cg, ctx->s);
-        launch_replace_r(n, cg, t, r, ctx->s);
-        if (flex) launch_dot(n, r, z, ctx->partial2, done, ctx->s);
-        vcycle(ctx, r, z, done);
-        { ProfScope ps_(ctx, AMG_PROF_DOT, true); launch_dot(n, r, z, ctx->partial, done, ctx->s); }
-        if (flex) launch_cg_beta_flexible(nblk, ctx->partial, ctx->partial2, cg, ctx->s);
-        else launch_cg_beta(nblk, ctx->partial, cg, ctx->s);
-        { ProfScope ps_(ctx, AMG_PROF_CG_P, true); launch_cg_update_p(n, cg, z, p, ctx->s); }
-        CK(cudaMemcpyAsync(ctx->h_cg, cg, sizeof(CgState), cudaMemcpyDeviceToHost, ctx->s));
-        CK(cudaStreamSynchronize(ctx->s));
-        if (ctx->h_cg->done) break;
+    { ProfScope ps_(ctx, AMG_PROF_DOT, true); launch_dot(n, r, z, ctx->partial, done, ctx->s); }
+    if (flex) launch_cg_beta_flexible(nblk, ctx->partial, ctx->partial2, cg, ctx->s);
+    else launch_cg_beta(nblk, ctx->partial, cg, ctx->s);
+    { ProfScope ps_(ctx, AMG_PROF_CG_P, true); launch_cg_update_p(n, cg, z, p, ctx->s); }
+}
+
+// the true relative residual of the returned iterate
+void enqueue_cg_epilogue(amg_ctx *ctx, const double *f, double *u) {
+    const int32_t n = ctx->n;
+    launch_true_residual(n, ctx->fine_ptr, ctx->fine_col, ctx->A_sys, f, u, ctx->cg_t, ctx->partial, ctx->cg, 1,
+                         ctx->s);
+    launch_cg_final_norm(cg_blocks(n), ctx->partial, ctx->cg, ctx->s);
+}
+
+void drop_graph(amg_ctx *ctx) {
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    ctx->graph_exec = nullptr;
+    ctx->graph = nullptr;
+}
+
+// The whole solve as one graph: prologue, a while-conditional node whose body
+// is one CG iteration (plus the loop-control kernel), epilogue.  It works on
+// the context's own f / u buffers, so it stays valid until the hierarchy or
+// the tolerance changes.
+amg_status build_solve_graph(amg_ctx *ctx, double tol) {
+    drop_graph(ctx);
+    // capture on two private streams (the caller's stream may be the legacy
+    // default stream, which cannot be captured); the graph is launched on the
+    // caller's stream
+    CK(cudaStreamSynchronize(ctx->s));
+    cudaStream_t user_s = ctx->s;
+    cudaStream_t main_s = ctx->s_cap_main;
+    const double *f = ctx->cg_f;
+    double *u = ctx->cg_u;
+    CK(cudaStreamBeginCapture(main_s, cudaStreamCaptureModeThreadLocal));
+    ctx->s = main_s;
+    const int64_t c0 = launch_total();
+    enqueue_cg_prologue(ctx, f, u, tol);
+    const int64_t c1 = launch_total();
+    int64_t c2 = c1;
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(main_s, &cs, nullptr, &g, &deps, nullptr, &ndeps);
+    cudaGraphConditionalHandle h;
+    cudaGraphNode_t cond;
+    cudaGraphNodeParams cp = {};
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&cond, g, deps, nullptr, ndeps, &cp);
     }
-    // the true relative residual of the returned iterate
-    launch_true_residual(n, ptr, col, A, f, u, t, ctx->partial, cg, 1, ctx->s);
-    launch_cg_final_norm(nblk, ctx->partial, cg, ctx->s);
-    CK(cudaMemcpyAsync(ctx->h_cg, cg, sizeof(CgState), cudaMemcpyDeviceToHost, ctx->s));
+    if (e == cudaSuccess) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(ctx->s_cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            ctx->s = ctx->s_cap;
+            enqueue_cg_iteration(ctx, f, u);
+            launch_cg_loop_control(ctx->cg, h, ctx->s);
+            c2 = launch_total();
+            ctx->s = main_s;
+            cudaGraph_t tmp = nullptr;
+            e = cudaStreamEndCapture(ctx->s_cap, &tmp);
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(main_s, &cond, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess) enqueue_cg_epilogue(ctx, f, u);
+    const int64_t c3 = launch_total();
+    // captured launches do not run now: count them when the graph executes
+    add_launches(c0 - c3);
+    ctx->graph_pro = c1 - c0;
+    ctx->graph_body = c2 - c1;
+    ctx->graph_epi = c3 - c2;
+    ctx->s = user_s;
+    cudaGraph_t done_graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(main_s, &done_graph);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) {
+        if (done_graph) cudaGraphDestroy(done_graph);
+        cudaGetLastError();
+        return set_err(ctx, AMG_ERR_CUDA, std::string("building the solve graph: ") + cudaGetErrorString(e));
+    }
+    ctx->graph = done_graph;
+    CK(cudaGraphInstantiate(&ctx->graph_exec, ctx->graph, 0));
+    ctx->graph_tol = tol;
+    ctx->graph_valid = true;
+    return AMG_OK;
+}
+
+amg_status finish_solve(amg_ctx *ctx, amg_info *info) {
+    CK(cudaMemcpyAsync(ctx->h_cg, ctx->cg, sizeof(CgState), cudaMemcpyDeviceToHost, ctx->s));
     CK(cudaStreamSynchronize(ctx->s));
     CK(cudaGetLastError());
     const CgState &h = *ctx->h_cg;
@@ -618,6 +722,29 @@ amg_status solve_impl(amg_ctx *ctx, const double *f, double *u, double tol, amg_
     if (st == AMG_ERR_BREAKDOWN) set_err(ctx, st, "CG breakdown: p'Ap <= 0 or not finite");
     else if (st == AMG_NOT_CONVERGED) set_err(ctx, st, "CG reached maxiter");
     return st;
+}
+
+amg_status solve_impl(amg_ctx *ctx, const double *f, double *u, double tol, amg_info *info) {
+    const int32_t n = ctx->n;
+    if (ctx->use_graph && !ctx->prof.on) {
+        if (!ctx->graph_valid || ctx->graph_tol != tol) TRY(build_solve_graph(ctx, tol));
+        CK(cudaMemcpyAsync(ctx->cg_f, f, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, ctx->s));
+        CK(cudaGraphLaunch(ctx->graph_exec, ctx->s));
+        CK(cudaMemcpyAsync(u, ctx->cg_u, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, ctx->s));
+        amg_status st = finish_solve(ctx, info);
+        add_launches(ctx->graph_pro + ctx->graph_epi + ctx->graph_body * (int64_t)ctx->h_cg->pad);
+        return st;
+    }
+    // eager path: the host checks the device state after every iteration
+    enqueue_cg_prologue(ctx, f, u, tol);
+    for (int it = 1; it <= ctx->prm.maxiter; ++it) {
+        enqueue_cg_iteration(ctx, f, u);
+        CK(cudaMemcpyAsync(ctx->h_cg, ctx->cg, sizeof(CgState), cudaMemcpyDeviceToHost, ctx->s));
+        CK(cudaStreamSynchronize(ctx->s));
+        if (ctx->h_cg->done) break;
+    }
+    enqueue_cg_epilogue(ctx, f, u);
+    return finish_solve(ctx, info);
 }
 
 }  // namespace
@@ -667,7 +794,9 @@ amg_status amg_create(amg_ctx **out, const amg_params *prm, void *cuda_stream) {
     if (cudaMemPoolCreate(&ctx->pool, &props) != cudaSuccess) { delete ctx; return AMG_ERR_CUDA; }
     uint64_t thr = UINT64_MAX;
     cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &thr);
-    if (cudaMallocHost(&ctx->h_cg, sizeof(CgState)) != cudaSuccess ||
+    if (cudaStreamCreateWithFlags(&ctx->s_cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->s_cap_main, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_cg, sizeof(CgState)) != cudaSuccess ||
         cudaMallocHost(&ctx->h_st, sizeof(int)) != cudaSuccess ||
         cudaMalloc(&ctx->d_st, sizeof(int)) != cudaSuccess) {
         amg_destroy(ctx);
@@ -683,6 +812,9 @@ void amg_destroy(amg_ctx *ctx) {
     for (void *p : ctx->hier) cudaFreeAsync(p, ctx->s);
     for (void *p : ctx->persist) cudaFreeAsync(p, ctx->s);
     cudaStreamSynchronize(ctx->s);
+    drop_graph(ctx);
+    if (ctx->s_cap) cudaStreamDestroy(ctx->s_cap);
+    if (ctx->s_cap_main) cudaStreamDestroy(ctx->s_cap_main);
     for (auto &v : ctx->prof.rec)
         for (auto &pr : v) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);

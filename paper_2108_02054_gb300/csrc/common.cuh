@@ -32,7 +32,8 @@ constexpr int kMaxRowUnique = kHashCap / 2;
 // it so that the loop needs no host round trip between its kernels.
 struct CgState {
     double rz, pq, alpha, beta, rr, nf, res, tres, tol;
-    int iter, maxiter, done, status, replacements, need_true, copy_r, pad;
+    int iter, maxiter, done, status, replacements, need_true, copy_r;
+    int pad;  // loop bodies executed (graph path)
 };
 
 template <class V>
@@ -76,6 +77,7 @@ struct Level {
 // (all enqueue on `s`; `st` is the device status word)
 // every launcher counts its kernel launches (process-wide)
 void count_launch();
+void add_launches(int64_t d);
 int64_t launch_total();
 void scan_counts(const int32_t *in, int32_t *out, int64_t n, int *st, int64_t *tmp, cudaStream_t s);
 int64_t scan_tmp_elems(int64_t n);
@@ -188,5 +190,6 @@ void launch_cg_beta_flexible(int nblk, const double *partial, const double *part
                              cudaStream_t s);
 void launch_cg_update_p(int32_t n, const CgState *cg, const double *z, double *p, cudaStream_t s);
 void launch_cg_final_norm(int nblk, const double *partial, CgState *cg, cudaStream_t s);
+void launch_cg_loop_control(CgState *cg, cudaGraphConditionalHandle h, cudaStream_t s);
 
 }  // namespace amgpr

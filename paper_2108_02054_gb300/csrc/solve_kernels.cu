@@ -61,38 +61,6 @@ k_ap_numeric_f64(int32_t n, const int32_t *__restrict__ A_ptr, const int32_t *__
         for (int s = 0; s < L; ++s) AP_val[b + s] = a[s * stride];
 }
 
-// stage 2: one warp per coarse row I: over R entries (I,i) in column order, the
-// lanes take the entries of row i of AP (distinct slots), fma(R_Ii, AP_iJ, acc)
-__global__ void __launch_bounds__(kRapWarps * 32)
-k_rap_numeric_f64(int32_t nc, const int32_t *__restrict__ R_ptr, const int32_t *__restrict__ R_col,
-                  const double *__restrict__ R_val, const int32_t *__restrict__ AP_ptr,
-                  const double *__restrict__ AP_val, const int32_t *__restrict__ Ac_ptr,
-                  const int32_t *__restrict__ t2ptr, const uint16_t *__restrict__ slot2,
-                  double *__restrict__ Ac_val) {
-    __shared__ double acc[kRapWarps][kRapSlots];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int32_t I = blockIdx.x * kRapWarps + w;
-    if (I >= nc) return;
-    const int32_t b = Ac_ptr[I], L = Ac_ptr[I + 1] - b;
-    double *a = L <= kRapSlots ? acc[w] : Ac_val + b;
-    for (int s = lane; s < L; s += 32) a[s] = 0.0;
-    __syncwarp();
-    int64_t t = t2ptr[I];
-    for (int32_t r = R_ptr[I]; r < R_ptr[I + 1]; ++r) {
-        const int32_t i = R_col[r];
-        const double x = R_val[r];
-        const int32_t e0 = AP_ptr[i], le = AP_ptr[i + 1] - e0;
-        for (int32_t e = lane; e < le; e += 32) {
-            const int s = slot2[t + e];
-            a[s] = fma(x, AP_val[e0 + e], a[s]);
-        }
-        t += le;
-        __syncwarp();
-    }
-    if (L <= kRapSlots)
-        for (int s = lane; s < L; s += 32) Ac_val[b + s] = a[s];
-}
-
 // ------------------------------------------------------------------ Galerkin, FP32 compensated
 // double-float accumulation: (hi, lo) += x*y with the product error from fmaf
 // and the addition error from a two-sum (error-free transformations)
@@ -144,50 +112,119 @@ k_ap_numeric_f32(int32_t n, const int32_t *__restrict__ A_ptr, const int32_t *__
     }
 }
 
+// Galerkin stage 2, A_c = R (AP): one warp per coarse row I.  The row's terms
+// (R entry r in column order, then the entries of row R_col[r] of AP in
+// column order) are taken 32 at a time, one per lane; a lane finds its R entry
+// by binary search in the staged prefix of AP row lengths.  Lanes whose terms
+// hit the same slot apply them in lane order (rank among __match_any_sync
+// peers), so every slot still accumulates in the sequential term order: the
+// FP64 result is bit-identical to the plain row-by-row product, while the
+// loads of 32 terms overlap.  FP32 accumulates in double-float pairs.
+constexpr int kRapMaxR = 192;
+
+template <class V>
+__device__ __forceinline__ void rap_apply(V *hi, V *lo, bool comp, int s, V x, V y);
+template <>
+__device__ __forceinline__ void rap_apply<double>(double *hi, double *, bool, int s, double x, double y) {
+    hi[s] = fma(x, y, hi[s]);
+}
+template <>
+__device__ __forceinline__ void rap_apply<float>(float *hi, float *lo, bool comp, int s, float x, float y) {
+    if (comp) df_acc(hi[s], lo[s], x, y);
+    else hi[s] = fmaf(x, y, hi[s]);
+}
+
+template <class V>
 __global__ void __launch_bounds__(kRapWarps * 32)
-k_rap_numeric_f32(int32_t nc, const int32_t *__restrict__ R_ptr, const int32_t *__restrict__ R_col,
-                  const float *__restrict__ R_val, const int32_t *__restrict__ AP_ptr,
-                  const float *__restrict__ AP_val, const int32_t *__restrict__ Ac_ptr,
-                  const int32_t *__restrict__ t2ptr, const uint16_t *__restrict__ slot2,
-                  float *__restrict__ Ac_val) {
-    __shared__ float acc_hi[kRapWarps][kRapSlots];
-    __shared__ float acc_lo[kRapWarps][kRapSlots];
+k_rap_terms(int32_t nc, const int32_t *__restrict__ R_ptr, const int32_t *__restrict__ R_col,
+            const V *__restrict__ R_val, const int32_t *__restrict__ AP_ptr, const V *__restrict__ AP_val,
+            const int32_t *__restrict__ Ac_ptr, const int32_t *__restrict__ t2ptr,
+            const uint16_t *__restrict__ slot2, V *__restrict__ Ac_val) {
+    __shared__ V acc_hi[kRapWarps][kRapSlots];
+    __shared__ V acc_lo[kRapWarps][sizeof(V) == 4 ? kRapSlots : 1];
+    __shared__ int32_t s_end[kRapWarps][kRapMaxR];
+    __shared__ int32_t s_e0[kRapWarps][kRapMaxR];
+    __shared__ V s_x[kRapWarps][kRapMaxR];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int32_t I = blockIdx.x * kRapWarps + w;
-    if (I >= nc) return;
+    if (I >= nc) return;  // warp-uniform
+    const int32_t rb = R_ptr[I], nr = R_ptr[I + 1] - rb;
     const int32_t b = Ac_ptr[I], L = Ac_ptr[I + 1] - b;
-    int64_t t = t2ptr[I];
-    if (L <= kRapSlots) {
-        float *hi = acc_hi[w], *lo = acc_lo[w];
-        for (int s = lane; s < L; s += 32) { hi[s] = 0.f; lo[s] = 0.f; }
-        __syncwarp();
-        for (int32_t r = R_ptr[I]; r < R_ptr[I + 1]; ++r) {
+    const bool in_smem = L <= kRapSlots;
+    const bool comp = sizeof(V) == 4 && in_smem;
+    V *hi = in_smem ? acc_hi[w] : Ac_val + b;  // long coarse rows accumulate in place
+    V *lo = acc_lo[w];
+    for (int s = lane; s < L; s += 32) {
+        hi[s] = V(0);
+        if (comp) lo[s] = V(0);
+    }
+    __syncwarp();
+    const int64_t t0 = t2ptr[I];
+    if (nr > kRapMaxR) {
+        // long R row: R entries in order, the lanes over one AP row's distinct slots
+        int64_t t = t0;
+        for (int32_t r = rb; r < rb + nr; ++r) {
             const int32_t i = R_col[r];
-            const float x = R_val[r];
+            const V x = R_val[r];
             const int32_t e0 = AP_ptr[i], le = AP_ptr[i + 1] - e0;
-            for (int32_t e = lane; e < le; e += 32) {
-                const int s = slot2[t + e];
-                df_acc(hi[s], lo[s], x, AP_val[e0 + e]);
-            }
+            for (int32_t e = lane; e < le; e += 32) rap_apply<V>(hi, lo, comp, slot2[t + e], x, AP_val[e0 + e]);
             t += le;
             __syncwarp();
         }
-        for (int s = lane; s < L; s += 32) Ac_val[b + s] = hi[s] + lo[s];
     } else {
-        for (int s = lane; s < L; s += 32) Ac_val[b + s] = 0.f;
-        __syncwarp();
-        for (int32_t r = R_ptr[I]; r < R_ptr[I + 1]; ++r) {
-            const int32_t i = R_col[r];
-            const float x = R_val[r];
-            const int32_t e0 = AP_ptr[i], le = AP_ptr[i + 1] - e0;
-            for (int32_t e = lane; e < le; e += 32) {
-                const int s = slot2[t + e];
-                Ac_val[b + s] = fmaf(x, AP_val[e0 + e], Ac_val[b + s]);
+        int32_t carry = 0;
+        for (int32_t r0 = 0; r0 < nr; r0 += 32) {
+            const int32_t r = r0 + lane;
+            int32_t len = 0;
+            if (r < nr) {
+                const int32_t i = R_col[rb + r];
+                const int32_t e0 = AP_ptr[i];
+                len = AP_ptr[i + 1] - e0;
+                s_e0[w][r] = e0;
+                s_x[w][r] = R_val[rb + r];
             }
-            t += le;
-            __syncwarp();
+            int32_t inc = len;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            if (r < nr) s_end[w][r] = carry + inc;
+            carry += __shfl_sync(0xffffffffu, inc, 31);
+        }
+        __syncwarp();
+        const int32_t nterms = carry;
+        for (int32_t base = 0; base < nterms; base += 32) {
+            const int32_t t = base + lane;
+            const bool valid = t < nterms;
+            int slot = 0;
+            V x = V(0), y = V(0);
+            if (valid) {
+                int32_t lo_r = 0, hi_r = nr - 1;  // first r with s_end[r] > t
+                while (lo_r < hi_r) {
+                    const int32_t mid = (lo_r + hi_r) >> 1;
+                    if (s_end[w][mid] > t) hi_r = mid; else lo_r = mid + 1;
+                }
+                const int32_t start = lo_r ? s_end[w][lo_r - 1] : 0;
+                y = AP_val[s_e0[w][lo_r] + (t - start)];
+                x = s_x[w][lo_r];
+                slot = slot2[t0 + t];
+            }
+            const unsigned active = __ballot_sync(0xffffffffu, valid);
+            int rank = 0;
+            if (valid) {
+                const unsigned peers = __match_any_sync(active, slot);
+                rank = __popc(peers & ((1u << lane) - 1u));
+            }
+            const int maxrank = (int)__reduce_max_sync(0xffffffffu, (unsigned)rank);
+            for (int k = 0; k <= maxrank; ++k) {
+                if (valid && rank == k) rap_apply<V>(hi, lo, comp, slot, x, y);
+                __syncwarp();
+            }
         }
     }
+    if (in_smem)
+        for (int s = lane; s < L; s += 32) Ac_val[b + s] = comp ? V(hi[s] + lo[s]) : hi[s];
 }
 
 // ------------------------------------------------------------------ smoothers
@@ -248,44 +285,65 @@ __global__ void k_csr_to_dense(int32_t n, const int32_t *__restrict__ ptr, const
         dense[(int64_t)i * n + col[p]] = val ? val[p] : (double)valf[p];
 }
 
-struct ValIdx {
-    double v;
+// Pivot candidates compare |a| through its IEEE bit pattern: with the sign
+// bit cleared, the unsigned order of the bits is the order of the magnitudes,
+// so the search needs no FP64 compares (slow on this part's FP64 pipe).  NaN
+// patterns map to 0 and are never chosen.
+struct KeyIdx {
+    unsigned long long k;
     int i;
 };
-__device__ __forceinline__ ValIdx better(ValIdx a, ValIdx b) {
+__device__ __forceinline__ unsigned long long mag_key(double x) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+    return b > 0x7ff0000000000000ull ? 0ull : b;
+}
+__device__ __forceinline__ KeyIdx better(KeyIdx a, KeyIdx b) {
     // larger magnitude wins; equal magnitudes: the lower row index
-    if (b.v > a.v || (b.v == a.v && b.i < a.i)) return b;
+    if (b.k > a.k || (b.k == a.k && b.i < a.i)) return b;
     return a;
 }
 
 // LU with partial pivoting (first entry of largest magnitude), in place,
-// row-major; l = a_rk / a_kk, a_rc = fma(-l, a_kc, a_rc)
-__global__ void __launch_bounds__(1024) k_dense_lu(int32_t n, double *__restrict__ a, int32_t *__restrict__ piv,
+// row-major; l = a_rk / a_kk, a_rc = fma(-l, a_kc, a_rc).  One block; the
+// matrix is staged in shared memory when it fits (kLuSmemN rows), so the n
+// dependent elimination steps run at shared-memory latency.
+constexpr int kLuSmemN = 160;
+__global__ void __launch_bounds__(1024) k_dense_lu(int32_t n, double *__restrict__ g, int32_t *__restrict__ piv,
                                                    int *st) {
-    __shared__ ValIdx wbest[32];
+    extern __shared__ double sm_lu[];
+    __shared__ KeyIdx wbest[32];
     __shared__ int s_p, s_sing;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool staged = n <= kLuSmemN;
+    double *a = staged ? sm_lu : g;
+    const int64_t nn = (int64_t)n * n;
+    if (staged)
+        for (int64_t e = tid; e < nn; e += blockDim.x) a[e] = g[e];
+    __syncthreads();
     for (int32_t k = 0; k < n; ++k) {
-        ValIdx best{-1.0, n};
-        for (int32_t r = k + tid; r < n; r += blockDim.x) best = better(best, ValIdx{fabs(a[(int64_t)r * n + k]), r});
+        KeyIdx best{0ull, n};
+        for (int32_t r = k + tid; r < n; r += blockDim.x) best = better(best, KeyIdx{mag_key(a[(int64_t)r * n + k]), r});
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            ValIdx other{__shfl_xor_sync(0xffffffffu, best.v, o), __shfl_xor_sync(0xffffffffu, best.i, o)};
+            KeyIdx other{__shfl_xor_sync(0xffffffffu, best.k, o), __shfl_xor_sync(0xffffffffu, best.i, o)};
             best = better(best, other);
         }
         if (lane == 0) wbest[warp] = best;
         __syncthreads();
         if (tid == 0) {
-            ValIdx b = wbest[0];
-            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) b = better(b, wbest[w]);
-            s_p = b.i;
-            s_sing = !(b.v > 0.0);
-            piv[k] = b.i;
+            KeyIdx bb = wbest[0];
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) bb = better(bb, wbest[w]);
+            // no usable pivot (zero or NaN column): report singular and leave
+            // identity pivots from here on, so every pivot index stays in range
+            s_sing = bb.k == 0ull || bb.i < k || bb.i >= n;
+            s_p = s_sing ? k : bb.i;
+            piv[k] = s_p;
         }
         __syncthreads();
         if (s_sing) {
             if (tid == 0) atomicOr(st, DEV_ERR_SINGULAR);
-            return;
+            for (int32_t r = k + 1 + tid; r < n; r += blockDim.x) piv[r] = r;
+            break;
         }
         const int32_t p = s_p;
         if (p != k)
@@ -298,13 +356,16 @@ __global__ void __launch_bounds__(1024) k_dense_lu(int32_t n, double *__restrict
         const double akk = a[(int64_t)k * n + k];
         for (int32_t r = k + 1 + tid; r < n; r += blockDim.x) a[(int64_t)r * n + k] = a[(int64_t)r * n + k] / akk;
         __syncthreads();
-        const int32_t m = n - k - 1;
-        for (int64_t idx = tid; idx < (int64_t)m * m; idx += blockDim.x) {
-            const int32_t r = k + 1 + (int32_t)(idx / m), c = k + 1 + (int32_t)(idx % m);
-            a[(int64_t)r * n + c] = fma(-a[(int64_t)r * n + k], a[(int64_t)k * n + c], a[(int64_t)r * n + c]);
+        // rank-1 update of the trailing block: warps over rows, lanes over columns
+        for (int32_t r = k + 1 + warp; r < n; r += (int32_t)(blockDim.x >> 5)) {
+            const double l = a[(int64_t)r * n + k];
+            for (int32_t c = k + 1 + lane; c < n; c += 32)
+                a[(int64_t)r * n + c] = fma(-l, a[(int64_t)k * n + c], a[(int64_t)r * n + c]);
         }
         __syncthreads();
     }
+    if (staged)
+        for (int64_t e = tid; e < nn; e += blockDim.x) g[e] = a[e];
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -313,39 +374,55 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// explicit inverse from the LU factors: one warp per column j of A^-1
-__global__ void k_lu_inverse(int32_t n, const double *__restrict__ lu, const int32_t *__restrict__ piv,
-                             double *__restrict__ inv) {
-    const int lane = threadIdx.x & 31;
-    const int32_t j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (j >= n) return;
-    double *x = inv + j;  // column j, stride n
-    for (int32_t r = lane; r < n; r += 32) x[(int64_t)r * n] = (r == j) ? 1.0 : 0.0;
+// explicit inverse from the LU factors: one warp per column j of A^-1; the
+// factors and each warp's column are staged in shared memory when they fit
+constexpr int kInvWarps = 1;  // one warp per block: the FP64 work spreads over many SMs
+__global__ void __launch_bounds__(kInvWarps * 32)
+k_lu_inverse(int32_t n, const double *__restrict__ lu_g, const int32_t *__restrict__ piv, double *__restrict__ inv) {
+    extern __shared__ double sm_inv[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const bool staged = n <= kLuSmemN;
+    const int64_t nn = (int64_t)n * n;
+    const double *lu = lu_g;
+    if (staged) {
+        for (int64_t e = threadIdx.x; e < nn; e += blockDim.x) sm_inv[e] = lu_g[e];
+        lu = sm_inv;
+    }
+    __syncthreads();
+    const int32_t j = blockIdx.x * kInvWarps + w;
+    if (j >= n) return;  // warp-uniform; no block barrier follows
+    double *x;
+    int64_t xs;
+    if (staged) { x = sm_inv + nn + (int64_t)w * n; xs = 1; }
+    else { x = inv + j; xs = n; }
+    for (int32_t r = lane; r < n; r += 32) x[r * xs] = (r == j) ? 1.0 : 0.0;
     __syncwarp();
     if (lane == 0)
         for (int32_t k = 0; k < n; ++k) {
             const int32_t p = piv[k];
-            if (p != k) {
-                double t = x[(int64_t)k * n];
-                x[(int64_t)k * n] = x[(int64_t)p * n];
-                x[(int64_t)p * n] = t;
+            if (p != k && p >= 0 && p < n) {
+                double t = x[k * xs];
+                x[k * xs] = x[p * xs];
+                x[p * xs] = t;
             }
         }
     __syncwarp();
     for (int32_t r = 1; r < n; ++r) {
         double s = 0.0;
-        for (int32_t c = lane; c < r; c += 32) s = fma(lu[(int64_t)r * n + c], x[(int64_t)c * n], s);
+        for (int32_t c = lane; c < r; c += 32) s = fma(lu[(int64_t)r * n + c], x[c * xs], s);
         s = warp_sum(s);
-        if (lane == 0) x[(int64_t)r * n] -= s;
+        if (lane == 0) x[r * xs] -= s;
         __syncwarp();
     }
     for (int32_t r = n - 1; r >= 0; --r) {
         double s = 0.0;
-        for (int32_t c = r + 1 + lane; c < n; c += 32) s = fma(lu[(int64_t)r * n + c], x[(int64_t)c * n], s);
+        for (int32_t c = r + 1 + lane; c < n; c += 32) s = fma(lu[(int64_t)r * n + c], x[c * xs], s);
         s = warp_sum(s);
-        if (lane == 0) x[(int64_t)r * n] = (x[(int64_t)r * n] - s) / lu[(int64_t)r * n + r];
+        if (lane == 0) x[r * xs] = (x[r * xs] - s) / lu[(int64_t)r * n + r];
         __syncwarp();
     }
+    if (staged)
+        for (int32_t r = lane; r < n; r += 32) inv[(int64_t)r * n + j] = x[r];
 }
 
 // u = A_L^-1 f, one warp per row
@@ -406,17 +483,23 @@ __global__ void k_residual(int32_t n, const int32_t *__restrict__ ptr, const int
     r[i] = (V)f[i] - s;
 }
 
-// f_c = R r (R = P^T stored explicitly, rows sorted): a gather, no atomics
+// f_c = R r (R = P^T stored explicitly, rows sorted): a gather, no atomics;
+// 8 lanes per coarse row, combined by shuffles in a fixed order
+constexpr int kRestrictLanes = 8;
 template <class V>
 __global__ void k_restrict(int32_t nc, const int32_t *__restrict__ R_ptr, const int32_t *__restrict__ R_col,
                            const V *__restrict__ R_val, const V *__restrict__ r, V *__restrict__ fc,
                            const int *skip) {
     if (skipped(skip)) return;
-    const int32_t I = blockIdx.x * blockDim.x + threadIdx.x;
-    if (I >= nc) return;
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t I = (int32_t)(gt / kRestrictLanes);
+    const int sub = (int)(gt % kRestrictLanes);
     V s = 0;
-    for (int32_t p = R_ptr[I]; p < R_ptr[I + 1]; ++p) s = fma(R_val[p], r[R_col[p]], s);
-    fc[I] = s;
+    if (I < nc)
+        for (int32_t p = R_ptr[I] + sub; p < R_ptr[I + 1]; p += kRestrictLanes) s = fma(R_val[p], r[R_col[p]], s);
+#pragma unroll
+    for (int o = kRestrictLanes / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (I < nc && sub == 0) fc[I] = s;
 }
 
 // u += P u_c
@@ -648,6 +731,18 @@ __global__ void k_cg_update_p(int32_t n, const CgState *cg, const double *__rest
         p[i] = fma(beta, p[i], z[i]);
 }
 
+// end of one captured CG iteration: keep looping while the iteration is not
+// done; a hard cap (maxiter + 4 bodies) ends the loop whatever the state says
+__global__ void k_cg_loop_control(CgState *cg, cudaGraphConditionalHandle h) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    cg->pad += 1;  // bodies executed
+    if (!cg->done && cg->pad > cg->maxiter + 4) {
+        cg->done = 1;
+        cg->status = AMG_NOT_CONVERGED;
+    }
+    cudaGraphSetConditional(h, cg->done ? 0u : 1u);
+}
+
 __global__ void k_cg_final_norm(int nblk, const double *__restrict__ partial, CgState *cg) {
     double tt = sum_partials(partial, nblk);
     if (threadIdx.x == 0) cg->tres = cg->nf > 0.0 ? sqrt(tt) / cg->nf : 0.0;
@@ -664,8 +759,8 @@ void launch_ap_numeric_f64(const Level &L, const double *A_val, cudaStream_t s) 
 void launch_rap_numeric_f64(const Level &L, const int32_t *Ac_ptr, double *Ac_val, cudaStream_t s) {
     unsigned g = (unsigned)((L.nc + kRapWarps - 1) / kRapWarps);
     count_launch();
-    k_rap_numeric_f64<<<g, kRapWarps * 32, 0, s>>>(L.nc, L.R_ptr, L.R_col, L.R_val, L.AP_ptr, L.AP_val, Ac_ptr,
-                                                   L.t2ptr, L.slot2, Ac_val);
+    k_rap_terms<double><<<g, kRapWarps * 32, 0, s>>>(L.nc, L.R_ptr, L.R_col, L.R_val, L.AP_ptr, L.AP_val, Ac_ptr,
+                                                     L.t2ptr, L.slot2, Ac_val);
 }
 void launch_ap_numeric_f32(const Level &L, const float *A_valf, cudaStream_t s) {
     count_launch();
@@ -675,8 +770,8 @@ void launch_ap_numeric_f32(const Level &L, const float *A_valf, cudaStream_t s) 
 void launch_rap_numeric_f32(const Level &L, const int32_t *Ac_ptr, float *Ac_valf, cudaStream_t s) {
     unsigned g = (unsigned)((L.nc + kRapWarps - 1) / kRapWarps);
     count_launch();
-    k_rap_numeric_f32<<<g, kRapWarps * 32, 0, s>>>(L.nc, L.R_ptr, L.R_col, L.R_valf, L.AP_ptr, L.AP_valf, Ac_ptr,
-                                                   L.t2ptr, L.slot2, Ac_valf);
+    k_rap_terms<float><<<g, kRapWarps * 32, 0, s>>>(L.nc, L.R_ptr, L.R_col, L.R_valf, L.AP_ptr, L.AP_valf, Ac_ptr,
+                                                    L.t2ptr, L.slot2, Ac_valf);
 }
 
 void launch_smoother_f64(int32_t n, const int32_t *ptr, const double *val, const int32_t *dia, int type, double wj,
@@ -708,12 +803,26 @@ void launch_csr_to_dense(int32_t n, const int32_t *ptr, const int32_t *col, cons
     k_csr_to_dense<<<nblocks(n), kThreads, 0, s>>>(n, ptr, col, val, valf, dense);
 }
 void launch_dense_lu(int32_t n, double *a, int32_t *piv, int *st, cudaStream_t s) {
+    static bool attr = false;
+    const int max_bytes = kLuSmemN * kLuSmemN * (int)sizeof(double);
+    if (!attr) {
+        cudaFuncSetAttribute(k_dense_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        attr = true;
+    }
+    const size_t bytes = n <= kLuSmemN ? (size_t)n * n * sizeof(double) : 0;
     count_launch();
-    k_dense_lu<<<1, 1024, 0, s>>>(n, a, piv, st);
+    k_dense_lu<<<1, 1024, bytes, s>>>(n, a, piv, st);
 }
 void launch_lu_inverse(int32_t n, const double *lu, const int32_t *piv, double *inv, cudaStream_t s) {
+    static bool attr = false;
+    const int max_bytes = (kLuSmemN * kLuSmemN + kInvWarps * kLuSmemN) * (int)sizeof(double);
+    if (!attr) {
+        cudaFuncSetAttribute(k_lu_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        attr = true;
+    }
+    const size_t bytes = n <= kLuSmemN ? ((size_t)n * n + (size_t)kInvWarps * n) * sizeof(double) : 0;
     count_launch();
-    k_lu_inverse<<<nblocks((int64_t)n * 32, 128), 128, 0, s>>>(n, lu, piv, inv);
+    k_lu_inverse<<<(unsigned)((n + kInvWarps - 1) / kInvWarps), kInvWarps * 32, bytes, s>>>(n, lu, piv, inv);
 }
 
 template <class V, class TF>
@@ -736,7 +845,8 @@ void launch_residual(const Level &L, const V *val, const TF *f, const V *u, V *r
 template <class V>
 void launch_restrict(const Level &L, const V *Rval, const V *r, V *fc, const int *skip, cudaStream_t s) {
     count_launch();
-    k_restrict<V><<<nblocks(L.nc), kThreads, 0, s>>>(L.nc, L.R_ptr, L.R_col, Rval, r, fc, skip);
+    k_restrict<V><<<nblocks((int64_t)L.nc * kRestrictLanes), kThreads, 0, s>>>(L.nc, L.R_ptr, L.R_col, Rval, r, fc,
+                                                                                skip);
 }
 template <class V>
 void launch_prolong(const Level &L, const V *Pval, const V *uc, V *u, const int *skip, cudaStream_t s) {
@@ -859,6 +969,10 @@ void launch_cg_beta_flexible(int nblk, const double *partial, const double *part
 void launch_cg_update_p(int32_t n, const CgState *cg, const double *z, double *p, cudaStream_t s) {
     count_launch();
     k_cg_update_p<<<cg_blocks(n), kCgThreads, 0, s>>>(n, cg, z, p);
+}
+void launch_cg_loop_control(CgState *cg, cudaGraphConditionalHandle h, cudaStream_t s) {
+    count_launch();
+    k_cg_loop_control<<<1, 32, 0, s>>>(cg, h);
 }
 void launch_cg_final_norm(int nblk, const double *partial, CgState *cg, cudaStream_t s) {
     count_launch();

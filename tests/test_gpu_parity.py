@@ -298,3 +298,23 @@ def test_error_statuses():
     with pytest.raises(B.AmgError) as e:
         G2.solve(f, 1e-8)
     assert e.value.status in (B.AMG_ERR_BREAKDOWN,)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_graph_solve_equals_eager_solve(precision):
+    """The whole-solve CUDA graph (while-conditional loop) runs exactly the
+    kernels of the host-driven loop: identical iterates and counts."""
+    ptr, col, v = gpu_problem(3, 40, 5, 10)
+    G = B.AMG(precision=precision)
+    G.full_setup(ptr, col, v)
+    f = torch.tensor(I.rhs(40 ** 3), device="cuda")
+    u1, i1 = G.solve(f, 1e-8)
+    u2, i2 = G.solve(f, 1e-8)           # graph reused
+    G.profile(True)                     # per-kernel timing forces the eager loop
+    u3, i3 = G.solve(f, 1e-8)
+    G.profile(False)
+    G.profile_read()
+    assert i1.iters == i2.iters == i3.iters and i1.status == i3.status == 0
+    assert torch.equal(u1, u2) and torch.equal(u1, u3)
+    u4, i4 = G.solve(f, 1e-11)          # a new tolerance rebuilds the graph
+    assert i4.iters > i1.iters and i4.rel_resid <= 1e-11
