@@ -69,6 +69,7 @@ struct amg_ctx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     bool use_graph = true;
+    bool use_gather = true;  // partial rebuilds apply the Galerkin product as gather operators
     bool graph_valid = false;
     double graph_tol = -1.0;
     double *cg_f = nullptr, *cg_u = nullptr;
@@ -250,6 +251,42 @@ amg_status coarse_factor(amg_ctx *ctx) {
     return AMG_OK;
 }
 
+// Build, for level l, the two fixed gather operators of the numeric Galerkin
+// product (AP = N a, A_c = M AP) from the slot metadata of the setup.  Done
+// once per hierarchy, at the first partial rebuild (full rebuilds never pay it).
+amg_status build_gather(amg_ctx *ctx, int l) {
+    Level &L = ctx->lev[l];
+    Level &C = ctx->lev[l + 1];
+    const bool mx = mixed(ctx);
+    const int64_t nt1 = L.nt1, nt2 = L.nt2;
+    const int64_t tmax = std::max(nt1, nt2);
+    int32_t *perm = nullptr, *idx_tmp = nullptr;
+    double *w_tmp = nullptr;
+    TRY(alloc(ctx, &perm, (size_t)tmax));
+    TRY(alloc(ctx, &idx_tmp, (size_t)tmax));
+    TRY(alloc(ctx, &w_tmp, (size_t)tmax));
+    // stage 1: one output per entry of AP
+    TRY(alloc(ctx, &L.g1_ptr, (size_t)L.nnzAP + 1));
+    TRY(alloc(ctx, &L.g1_idx, (size_t)nt1));
+    if (mx) TRY(alloc(ctx, &L.g1_wf, (size_t)nt1));
+    else TRY(alloc(ctx, &L.g1_w, (size_t)nt1));
+    launch_group_terms(L.n, L.t1ptr, L.slot1, L.AP_ptr, L.g1_ptr, perm, ctx->d_st, ctx->s);
+    CK(cudaMemcpyAsync(L.g1_ptr + L.nnzAP, L.t1ptr + L.n, sizeof(int32_t), cudaMemcpyDeviceToDevice, ctx->s));
+    launch_stage1_terms(L.n, L.A_ptr, L.A_col, L.P_ptr, L.P_val, L.t1ptr, idx_tmp, w_tmp, ctx->s);
+    launch_permute_terms(nt1, perm, idx_tmp, w_tmp, L.g1_idx, mx ? nullptr : L.g1_w, mx ? L.g1_wf : nullptr, ctx->s);
+    // stage 2: one output per entry of A_c
+    TRY(alloc(ctx, &L.g2_ptr, (size_t)C.nnz + 1));
+    TRY(alloc(ctx, &L.g2_idx, (size_t)nt2));
+    if (mx) TRY(alloc(ctx, &L.g2_wf, (size_t)nt2));
+    else TRY(alloc(ctx, &L.g2_w, (size_t)nt2));
+    launch_group_terms(L.nc, L.t2ptr, L.slot2, C.A_ptr, L.g2_ptr, perm, ctx->d_st, ctx->s);
+    CK(cudaMemcpyAsync(L.g2_ptr + C.nnz, L.t2ptr + L.nc, sizeof(int32_t), cudaMemcpyDeviceToDevice, ctx->s));
+    launch_stage2_terms(L.nc, L.R_ptr, L.R_col, L.R_val, L.AP_ptr, L.t2ptr, idx_tmp, w_tmp, ctx->s);
+    launch_permute_terms(nt2, perm, idx_tmp, w_tmp, L.g2_idx, mx ? nullptr : L.g2_w, mx ? L.g2_wf : nullptr, ctx->s);
+    L.gather_ready = true;
+    return AMG_OK;
+}
+
 // numeric part shared by the full setup and the partial rebuild (Alg. 4 body)
 amg_status numeric_rebuild(amg_ctx *ctx, const double *d_val, bool galerkin) {
     const amg_params &p = ctx->prm;
@@ -264,7 +301,15 @@ amg_status numeric_rebuild(amg_ctx *ctx, const double *d_val, bool galerkin) {
     for (int l = 0; l + 1 < ctx->nlev; ++l) {
         Level &L = ctx->lev[l];
         Level &C = ctx->lev[l + 1];
-        if (galerkin) {
+        if (galerkin && L.gather_ready) {
+            if (mx) {
+                { ProfScope ps_(ctx, AMG_PROF_AP_L0, l == 0); launch_gather_apply<float>(L.nnzAP, L.g1_ptr, L.g1_idx, L.g1_wf, L.A_valf, L.AP_valf, ctx->s); }
+                { ProfScope ps_(ctx, AMG_PROF_RAP_L0, l == 0); launch_gather_apply<float>(C.nnz, L.g2_ptr, L.g2_idx, L.g2_wf, L.AP_valf, C.A_valf, ctx->s); }
+            } else {
+                { ProfScope ps_(ctx, AMG_PROF_AP_L0, l == 0); launch_gather_apply<double>(L.nnzAP, L.g1_ptr, L.g1_idx, L.g1_w, L.A_val, L.AP_val, ctx->s); }
+                { ProfScope ps_(ctx, AMG_PROF_RAP_L0, l == 0); launch_gather_apply<double>(C.nnz, L.g2_ptr, L.g2_idx, L.g2_w, L.AP_val, C.A_val, ctx->s); }
+            }
+        } else if (galerkin) {
             if (mx) {
                 { ProfScope ps_(ctx, AMG_PROF_AP_L0, l == 0); launch_ap_numeric_f32(L, L.A_valf, ctx->s); }
                 { ProfScope ps_(ctx, AMG_PROF_RAP_L0, l == 0); launch_rap_numeric_f32(L, C.A_ptr, C.A_valf, ctx->s); }
@@ -849,6 +894,9 @@ amg_status amg_partial_rebuild(amg_ctx *ctx, const double *d_val) {
     if (!ctx->have_setup) return set_err(ctx, AMG_ERR_STATE, "partial rebuild before a full setup");
     if (!d_val) return set_err(ctx, AMG_ERR_ARG, "null values");
     TRY(reset_status(ctx));
+    if (ctx->use_gather)
+        for (int l = 0; l + 1 < ctx->nlev; ++l)
+            if (!ctx->lev[l].gather_ready) TRY(build_gather(ctx, l));
     TRY(numeric_rebuild(ctx, d_val, true));
     if (ctx->A_sys_own)
         CK(cudaMemcpyAsync(ctx->A_sys_own, d_val, sizeof(double) * (size_t)ctx->nnz, cudaMemcpyDeviceToDevice,

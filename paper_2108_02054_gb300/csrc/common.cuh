@@ -62,6 +62,11 @@ struct Level {
     int32_t *t1ptr = nullptr, *t2ptr = nullptr;
     uint16_t *slot1 = nullptr, *slot2 = nullptr;
     int32_t max_ap_row = 0, max_ac_row = 0;
+    // the same products as fixed gather operators, built at the first partial rebuild
+    bool gather_ready = false;
+    int32_t *g1_ptr = nullptr, *g1_idx = nullptr, *g2_ptr = nullptr, *g2_idx = nullptr;
+    double *g1_w = nullptr, *g2_w = nullptr;
+    float *g1_wf = nullptr, *g2_wf = nullptr;
     // aggregation (kept for inspection)
     int32_t *agg = nullptr;
     uint8_t *strong = nullptr;
@@ -124,6 +129,18 @@ void launch_t2_fill(int32_t nc, const int32_t *R_ptr, const int32_t *R_col, cons
                     const int32_t *AP_col, const int32_t *Ac_ptr, const int32_t *Ac_col, const int32_t *t2ptr,
                     uint16_t *slot2, int *st, cudaStream_t s);
 void launch_row_maxlen(int32_t n, const int32_t *ptr, int *out, cudaStream_t s);
+// gather operators of the numeric Galerkin product (AP = N a, A_c = M AP)
+void launch_group_terms(int32_t nrows, const int32_t *tptr, const uint16_t *slot, const int32_t *out_ptr,
+                        int32_t *eptr, int32_t *perm, int *st, cudaStream_t s);
+void launch_stage1_terms(int32_t n, const int32_t *A_ptr, const int32_t *A_col, const int32_t *P_ptr,
+                         const double *P_val, const int32_t *t1ptr, int32_t *idx, double *wgt, cudaStream_t s);
+void launch_stage2_terms(int32_t nc, const int32_t *R_ptr, const int32_t *R_col, const double *R_val,
+                         const int32_t *AP_ptr, const int32_t *t2ptr, int32_t *idx, double *wgt, cudaStream_t s);
+void launch_permute_terms(int64_t nt, const int32_t *perm, const int32_t *idx_in, const double *w_in,
+                          int32_t *idx_out, double *w_out, float *wf_out, cudaStream_t s);
+template <class V>
+void launch_gather_apply(int64_t nout, const int32_t *eptr, const int32_t *idx, const V *w, const V *x, V *y,
+                         cudaStream_t s);
 
 // numeric Galerkin product, FP64 (bit-exact accumulation order)
 void launch_ap_numeric_f64(const Level &L, const double *A_val, cudaStream_t s);

@@ -636,6 +636,120 @@ __global__ void k_t2_fill(int32_t nc, const int32_t *__restrict__ R_ptr, const i
     }
 }
 
+// ------------------------------------------------------------------ gather operators
+// With P and R fixed, the numeric Galerkin product is linear in the values:
+// AP = N a and A_c = M AP, with fixed sparse N (coefficients P_kJ) and M
+// (coefficients R_Ii).  These kernels build N and M from the slot metadata:
+// each output entry's terms are grouped, keeping their sequential order.
+
+constexpr int kGroupWarps = 4;
+constexpr int kGroupSlots = 2048;
+
+// One warp per output row: a stable counting sort of the row's terms by slot.
+// eptr[out_ptr[row] + s] = first sorted position of slot s; perm[pos] = term.
+__global__ void __launch_bounds__(kGroupWarps * 32)
+k_group_terms(int32_t nrows, const int32_t *__restrict__ tptr, const uint16_t *__restrict__ slot,
+              const int32_t *__restrict__ out_ptr, int32_t *__restrict__ eptr, int32_t *__restrict__ perm,
+              int *st) {
+    __shared__ int32_t cnt[kGroupWarps][kGroupSlots];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int32_t row = blockIdx.x * kGroupWarps + w;
+    if (row >= nrows) return;  // warp-uniform
+    const int32_t t0 = tptr[row], t1 = tptr[row + 1];
+    const int32_t ob = out_ptr[row], L = out_ptr[row + 1] - ob;
+    if (L > kGroupSlots) {
+        if (lane == 0) atomicOr(st, DEV_ERR_CAPACITY);
+        return;
+    }
+    int32_t *c = cnt[w];
+    for (int s = lane; s < L; s += 32) c[s] = 0;
+    __syncwarp();
+    for (int32_t t = t0 + lane; t < t1; t += 32) atomicAdd(&c[slot[t]], 1);
+    __syncwarp();
+    int32_t carry = 0;
+    for (int32_t s0 = 0; s0 < L; s0 += 32) {
+        const int32_t s = s0 + lane;
+        const int32_t v = s < L ? c[s] : 0;
+        int32_t inc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (s < L) {
+            const int32_t start = carry + inc - v;
+            c[s] = start;
+            eptr[ob + s] = t0 + start;
+        }
+        carry += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    __syncwarp();
+    for (int32_t base = t0; base < t1; base += 32) {
+        const int32_t t = base + lane;
+        const bool valid = t < t1;
+        const unsigned active = __ballot_sync(0xffffffffu, valid);
+        if (valid) {
+            const int sl = slot[t];
+            const unsigned peers = __match_any_sync(active, sl);
+            const int rank = __popc(peers & ((1u << lane) - 1u));
+            perm[t0 + c[sl] + rank] = t;
+            __syncwarp(active);
+            if (rank == 0) c[sl] += __popc(peers);
+        }
+        __syncwarp();
+    }
+}
+
+// term attributes in the sequential order, stage 1: A entry and P value
+__global__ void k_stage1_terms(int32_t n, const int32_t *__restrict__ A_ptr, const int32_t *__restrict__ A_col,
+                               const int32_t *__restrict__ P_ptr, const double *__restrict__ P_val,
+                               const int32_t *__restrict__ t1ptr, int32_t *__restrict__ idx,
+                               double *__restrict__ wgt) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t t = t1ptr[i];
+    for (int32_t p = A_ptr[i]; p < A_ptr[i + 1]; ++p) {
+        const int32_t k = A_col[p];
+        for (int32_t q = P_ptr[k]; q < P_ptr[k + 1]; ++q) {
+            idx[t] = p;
+            wgt[t] = P_val[q];
+            ++t;
+        }
+    }
+}
+
+// stage 2: AP entry and R value
+__global__ void k_stage2_terms(int32_t nc, const int32_t *__restrict__ R_ptr, const int32_t *__restrict__ R_col,
+                               const double *__restrict__ R_val, const int32_t *__restrict__ AP_ptr,
+                               const int32_t *__restrict__ t2ptr, int32_t *__restrict__ idx,
+                               double *__restrict__ wgt) {
+    const int32_t I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nc) return;
+    int64_t t = t2ptr[I];
+    for (int32_t r = R_ptr[I]; r < R_ptr[I + 1]; ++r) {
+        const int32_t i = R_col[r];
+        const double x = R_val[r];
+        for (int32_t e = AP_ptr[i]; e < AP_ptr[i + 1]; ++e) {
+            idx[t] = e;
+            wgt[t] = x;
+            ++t;
+        }
+    }
+}
+
+// sorted operator: idx_out[pos] = idx_in[perm[pos]], weights likewise (FP64 or FP32)
+__global__ void k_permute_terms(int64_t nt, const int32_t *__restrict__ perm, const int32_t *__restrict__ idx_in,
+                                const double *__restrict__ w_in, int32_t *__restrict__ idx_out,
+                                double *__restrict__ w_out, float *__restrict__ wf_out) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nt; p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t t = perm[p];
+        idx_out[p] = idx_in[t];
+        const double w = w_in[t];
+        if (w_out) w_out[p] = w;
+        if (wf_out) wf_out[p] = (float)w;
+    }
+}
+
 __global__ void k_row_maxlen(int32_t n, const int32_t *__restrict__ ptr, int *out) {
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     int l = i < n ? ptr[i + 1] - ptr[i] : 0;
@@ -804,6 +918,31 @@ void launch_t2_fill(int32_t nc, const int32_t *R_ptr, const int32_t *R_col, cons
                     uint16_t *slot2, int *st, cudaStream_t s) {
     count_launch();
     k_t2_fill<<<nblocks(nc, 128), 128, 0, s>>>(nc, R_ptr, R_col, AP_ptr, AP_col, Ac_ptr, Ac_col, t2ptr, slot2, st);
+}
+void launch_group_terms(int32_t nrows, const int32_t *tptr, const uint16_t *slot, const int32_t *out_ptr,
+                        int32_t *eptr, int32_t *perm, int *st, cudaStream_t s) {
+    if (nrows <= 0) return;
+    count_launch();
+    k_group_terms<<<(unsigned)((nrows + kGroupWarps - 1) / kGroupWarps), kGroupWarps * 32, 0, s>>>(
+        nrows, tptr, slot, out_ptr, eptr, perm, st);
+}
+void launch_stage1_terms(int32_t n, const int32_t *A_ptr, const int32_t *A_col, const int32_t *P_ptr,
+                         const double *P_val, const int32_t *t1ptr, int32_t *idx, double *wgt, cudaStream_t s) {
+    count_launch();
+    k_stage1_terms<<<nblocks(n), kThreads, 0, s>>>(n, A_ptr, A_col, P_ptr, P_val, t1ptr, idx, wgt);
+}
+void launch_stage2_terms(int32_t nc, const int32_t *R_ptr, const int32_t *R_col, const double *R_val,
+                         const int32_t *AP_ptr, const int32_t *t2ptr, int32_t *idx, double *wgt, cudaStream_t s) {
+    count_launch();
+    k_stage2_terms<<<nblocks(nc, 128), 128, 0, s>>>(nc, R_ptr, R_col, R_val, AP_ptr, t2ptr, idx, wgt);
+}
+void launch_permute_terms(int64_t nt, const int32_t *perm, const int32_t *idx_in, const double *w_in,
+                          int32_t *idx_out, double *w_out, float *wf_out, cudaStream_t s) {
+    if (nt <= 0) return;
+    int64_t b = nblocks(nt);
+    count_launch();
+    k_permute_terms<<<(unsigned)(b > 8192 ? 8192 : b), kThreads, 0, s>>>(nt, perm, idx_in, w_in, idx_out, w_out,
+                                                                         wf_out);
 }
 void launch_row_maxlen(int32_t n, const int32_t *ptr, int *out, cudaStream_t s) {
     count_launch();

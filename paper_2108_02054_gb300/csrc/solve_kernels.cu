@@ -227,6 +227,36 @@ k_rap_terms(int32_t nc, const int32_t *__restrict__ R_ptr, const int32_t *__rest
         for (int s = lane; s < L; s += 32) Ac_val[b + s] = comp ? V(hi[s] + lo[s]) : hi[s];
 }
 
+// ------------------------------------------------------------------ Galerkin as gather operators
+// y[e] = sum over the terms t of entry e, in their sequential order, of
+// w[t] * x[idx[t]]: the two stages of the numeric Galerkin product once P and
+// R are fixed (w = P_kJ with x = a, then w = R_Ii with x = AP).  FP64: one fma
+// per term from 0.0, the same operations as the row-by-row product; FP32:
+// double-float accumulation.
+template <class V>
+__global__ void k_gather_apply(int64_t nout, const int32_t *__restrict__ eptr, const int32_t *__restrict__ idx,
+                               const V *__restrict__ w, const V *__restrict__ x, V *__restrict__ y);
+template <>
+__global__ void k_gather_apply<double>(int64_t nout, const int32_t *__restrict__ eptr,
+                                       const int32_t *__restrict__ idx, const double *__restrict__ w,
+                                       const double *__restrict__ x, double *__restrict__ y) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nout) return;
+    double acc = 0.0;
+    for (int32_t t = eptr[e]; t < eptr[e + 1]; ++t) acc = fma(w[t], x[idx[t]], acc);
+    y[e] = acc;
+}
+template <>
+__global__ void k_gather_apply<float>(int64_t nout, const int32_t *__restrict__ eptr,
+                                      const int32_t *__restrict__ idx, const float *__restrict__ w,
+                                      const float *__restrict__ x, float *__restrict__ y) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nout) return;
+    float hi = 0.f, lo = 0.f;
+    for (int32_t t = eptr[e]; t < eptr[e + 1]; ++t) df_acc(hi, lo, w[t], x[idx[t]]);
+    y[e] = hi + lo;
+}
+
 // ------------------------------------------------------------------ smoothers
 // SPAI0: m_i = a_ii / sum_j a_ij^2 (fma, column order), 0 for a zero sum;
 // damped Jacobi: m_i = w / a_ii.
@@ -773,6 +803,18 @@ void launch_rap_numeric_f32(const Level &L, const int32_t *Ac_ptr, float *Ac_val
     k_rap_terms<float><<<g, kRapWarps * 32, 0, s>>>(L.nc, L.R_ptr, L.R_col, L.R_valf, L.AP_ptr, L.AP_valf, Ac_ptr,
                                                     L.t2ptr, L.slot2, Ac_valf);
 }
+
+template <class V>
+void launch_gather_apply(int64_t nout, const int32_t *eptr, const int32_t *idx, const V *w, const V *x, V *y,
+                         cudaStream_t s) {
+    if (nout <= 0) return;
+    count_launch();
+    k_gather_apply<V><<<nblocks(nout), kThreads, 0, s>>>(nout, eptr, idx, w, x, y);
+}
+template void launch_gather_apply<double>(int64_t, const int32_t *, const int32_t *, const double *, const double *,
+                                          double *, cudaStream_t);
+template void launch_gather_apply<float>(int64_t, const int32_t *, const int32_t *, const float *, const float *,
+                                         float *, cudaStream_t);
 
 void launch_smoother_f64(int32_t n, const int32_t *ptr, const double *val, const int32_t *dia, int type, double wj,
                          double *m, cudaStream_t s) {
