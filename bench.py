@@ -65,6 +65,22 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def measured_traffic(workload, kernel):
+    """DRAM bytes (read + write) per launch of `kernel` from a committed ncu
+    summary line 'roofline-traffic: <workload> <kernel> <bytes>', else None."""
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    for name in sorted(os.listdir(pdir)):
+        if not name.endswith(".md"):
+            continue
+        for line in open(os.path.join(pdir, name)):
+            f = line.split()
+            if len(f) == 4 and f[0] == "roofline-traffic:" and f[1] == workload and f[2] == kernel:
+                return int(f[3])
+    return None
+
+
 def step_indices(w, warmup, steps):
     """Time-step indices: step 0 is the (untimed) full setup, then warm-up and
     timed steps walk k = 1, 2, ... cycling through 1..T-1."""
@@ -312,10 +328,7 @@ def run_ours(args):
                          "algorithmic_bytes": by,
                          "achieved_gbs": (by / (per * 1e-3) / 1e9) if by else None}
     dom = max((k for k in kernels if kernels[k]["achieved_gbs"]), key=lambda k: kernels[k]["ms_total_per_step"])
-    traffic = None
-    tp = os.path.join(ROOT, "profiles", "traffic_bytes.json")
-    if os.path.exists(tp):
-        traffic = json.load(open(tp)).get(f"{args.workload}:{dom}")
+    traffic = measured_traffic(args.workload, dom)
     ach = kernels[dom]["achieved_gbs"]
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(ach / peak, 4), "peak_source": peak_kind, "traffic": traffic,

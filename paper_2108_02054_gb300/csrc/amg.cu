@@ -241,6 +241,18 @@ amg_status max_row(amg_ctx *ctx, int32_t n, const int32_t *ptr, int32_t *out) {
     return AMG_OK;
 }
 
+// Lanes per row for a level's matrix-vector kernels: about eight entries per
+// lane, then more lanes until the level offers enough threads to fill the GPU
+// (short fine-level rows keep one lane and the plain sequential row sum).
+int choose_lpr(int64_t rows, int64_t nnz) {
+    if (rows <= 0) return 1;
+    const double avg = (double)nnz / (double)rows;
+    int p = 1;
+    while (p < 32 && 8.0 * p < avg) p *= 2;
+    while (p < 32 && rows * p < 152LL * 1024) p *= 2;
+    return p;
+}
+
 // the coarsest direct solver: dense LU (FP64) and its explicit inverse
 amg_status coarse_factor(amg_ctx *ctx) {
     Level &C = ctx->lev[ctx->nlev - 1];
@@ -351,6 +363,7 @@ amg_status full_setup_impl(amg_ctx *ctx, const double *d_val) {
         TRY(alloc(ctx, &L.strong, (size_t)L.nnz));
         CK(cudaMemsetAsync(L.agg, 0xff, sizeof(int32_t) * (size_t)L.n, ctx->s));
         CK(cudaMemsetAsync(L.strong, 0, (size_t)L.nnz, ctx->s));
+        L.lpr = choose_lpr(L.n, L.nnz);
         if (L.n <= p.coarse_enough || ctx->nlev >= p.max_levels || ctx->nlev >= kMaxLevels) break;
         // strength and aggregation
         int32_t *deg = nullptr, *root_id = nullptr, *agg1 = nullptr, *root_of = nullptr;
@@ -407,6 +420,7 @@ amg_status full_setup_impl(amg_ctx *ctx, const double *d_val) {
         TRY(alloc(ctx, &L.R_val, (size_t)L.nnzR));
         launch_transpose_scatter(L.n, L.P_ptr, L.P_col, L.P_val, L.R_ptr, cursor, L.R_col, L.R_val, ctx->s);
         launch_sort_rows(nagg, L.R_ptr, L.R_col, L.R_val, ctx->s);
+        L.lpr_r = choose_lpr(nagg, L.nnzR);
         // symbolic Galerkin product: AP = A*P, A_c = R*AP (+ diagonal)
         TRY(symbolic_product(ctx, L.n, nagg, L.A_ptr, L.A_col, L.P_ptr, L.P_col, 0, &L.AP_ptr, &L.AP_col,
                              &L.nnzAP));
@@ -558,6 +572,33 @@ V *down_level(amg_ctx *ctx, int l, const TF *f, const int *skip) {
     return u;
 }
 
+// post-smoothing on the finest level; the last sweep writes z and, when
+// rz_partial is given, the per-block partials of r.z (r = f here)
+template <class V>
+void up_finest(amg_ctx *ctx, const double *f, V *u, double *out, double *rz_partial, const int *skip) {
+    Level &L = ctx->lev[0];
+    VecSet<V> &v = Vops<V>::vec(L);
+    const V *A = Vops<V>::A(L), *m = Vops<V>::m(L);
+    V *t = (u == v.u) ? v.t : v.u;
+    const int npost = ctx->prm.npost;
+    for (int k = 0; k < npost; ++k) {
+        if (k == npost - 1) {
+            if (rz_partial) {
+                ProfScope ps_(ctx, AMG_PROF_SWEEP_L0);
+                launch_smooth_sweep_dot<V>(L, A, m, f, u, out, rz_partial, skip, ctx->s);
+            } else {
+                ProfScope ps_(ctx, AMG_PROF_SWEEP_L0);
+                launch_smooth_sweep<V, double, double>(L, A, m, f, u, out, skip, ctx->s);
+            }
+            return;
+        }
+        launch_smooth_sweep<V, double, V>(L, A, m, f, u, t, skip, ctx->s);
+        std::swap(u, t);
+    }
+    launch_copy_cast<V, double>(L.n, u, out, skip, ctx->s);
+    if (rz_partial) launch_dot(ctx->n, f, out, rz_partial, skip, ctx->s);
+}
+
 // post-smoothing on level l; the last sweep writes `out` (type TO) when given
 template <class V, class TF, class TO>
 void up_level(amg_ctx *ctx, int l, const TF *f, V *u, TO *out, const int *skip) {
@@ -578,10 +619,11 @@ void up_level(amg_ctx *ctx, int l, const TF *f, V *u, TO *out, const int *skip) 
 }
 
 template <class V>
-void enqueue_vcycle(amg_ctx *ctx, const double *r, double *z, const int *skip) {
+void enqueue_vcycle(amg_ctx *ctx, const double *r, double *z, const int *skip, double *rz_partial) {
     const int nl = ctx->nlev;
     if (nl == 1) {
         launch_coarse_solve<V, double, double>(ctx->lev[0].n, ctx->inv, r, z, skip, ctx->s);
+        if (rz_partial) launch_dot(ctx->n, r, z, rz_partial, skip, ctx->s);
         return;
     }
     V *cur[kMaxLevels];
@@ -614,12 +656,13 @@ void enqueue_vcycle(amg_ctx *ctx, const double *r, double *z, const int *skip) {
     }
     Level &F = ctx->lev[0];
     { ProfScope ps_(ctx, AMG_PROF_PROLONG_L0, true); launch_prolong<V>(F, Vops<V>::P(F), cur[1], cur[0], skip, ctx->s); }
-    up_level<V, double, double>(ctx, 0, r, cur[0], z, skip);
+    up_finest<V>(ctx, r, cur[0], z, rz_partial, skip);
 }
 
-void vcycle(amg_ctx *ctx, const double *r, double *z, const int *skip) {
-    if (mixed(ctx)) enqueue_vcycle<float>(ctx, r, z, skip);
-    else enqueue_vcycle<double>(ctx, r, z, skip);
+// z = B r; with rz_partial, also the per-block partials of r.z
+void vcycle(amg_ctx *ctx, const double *r, double *z, const int *skip, double *rz_partial = nullptr) {
+    if (mixed(ctx)) enqueue_vcycle<float>(ctx, r, z, skip, rz_partial);
+    else enqueue_vcycle<double>(ctx, r, z, skip, rz_partial);
 }
 
 // ---------------------------------------------------------------- CG
@@ -630,8 +673,7 @@ void enqueue_cg_prologue(amg_ctx *ctx, const double *f, double *u, double tol) {
     CgState *cg = ctx->cg;
     launch_cg_init(n, f, u, ctx->cg_r, ctx->partial, ctx->s);
     launch_cg_start(nblk, ctx->partial, cg, tol, ctx->prm.maxiter, ctx->s);
-    vcycle(ctx, ctx->cg_r, ctx->cg_z, &cg->done);
-    launch_dot(n, ctx->cg_r, ctx->cg_z, ctx->partial, &cg->done, ctx->s);
+    vcycle(ctx, ctx->cg_r, ctx->cg_z, &cg->done, ctx->partial);
     launch_cg_set_rz_p(n, nblk, ctx->partial, ctx->cg_z, ctx->cg_p, cg, ctx->s);
 }
 
@@ -653,8 +695,7 @@ void enqueue_cg_iteration(amg_ctx *ctx, const double *f, double *u) {
     launch_true_check(nblk, ctx->partial, cg, ctx->s);
     launch_replace_r(n, cg, t, r, ctx->s);
     if (flex) launch_dot(n, r, z, ctx->partial2, done, ctx->s);
-    vcycle(ctx, r, z, done);
-    { ProfScope ps_(ctx, AMG_PROF_DOT, true); launch_dot(n, r, z, ctx->partial, done, ctx->s); }
+    vcycle(ctx, r, z, done, ctx->partial);  // z = B r and the partials of r.z
     if (flex) launch_cg_beta_flexible(nblk, ctx->partial, ctx->partial2, cg, ctx->s);
     else launch_cg_beta(nblk, ctx->partial, cg, ctx->s);
     { ProfScope ps_(ctx, AMG_PROF_CG_P, true); launch_cg_update_p(n, cg, z, p, ctx->s); }

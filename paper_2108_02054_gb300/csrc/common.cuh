@@ -62,6 +62,8 @@ struct Level {
     int32_t *t1ptr = nullptr, *t2ptr = nullptr;
     uint16_t *slot1 = nullptr, *slot2 = nullptr;
     int32_t max_ap_row = 0, max_ac_row = 0;
+    // lanes per row of the matrix-vector pieces on this level (A rows, R rows)
+    int lpr = 1, lpr_r = 8;
     // the same products as fixed gather operators, built at the first partial rebuild
     bool gather_ready = false;
     int32_t *g1_ptr = nullptr, *g1_idx = nullptr, *g2_ptr = nullptr, *g2_idx = nullptr;
@@ -175,6 +177,10 @@ void launch_smooth_sweep(const Level &L, const V *val, const V *m, const TF *f, 
                          const int *skip, cudaStream_t s);
 template <class V, class TF>
 void launch_residual(const Level &L, const V *val, const TF *f, const V *u, V *r, const int *skip, cudaStream_t s);
+// last finest-level post-smoothing sweep fused with the CG product r.z (cg_blocks(n) partials)
+template <class V>
+void launch_smooth_sweep_dot(const Level &L, const V *val, const V *m, const double *f, const V *u_in, double *z,
+                             double *partial, const int *skip, cudaStream_t s);
 template <class V>
 void launch_restrict(const Level &L, const V *Rval, const V *r, V *fc, const int *skip, cudaStream_t s);
 template <class V>

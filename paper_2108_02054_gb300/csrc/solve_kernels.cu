@@ -334,22 +334,84 @@ __device__ __forceinline__ KeyIdx better(KeyIdx a, KeyIdx b) {
 }
 
 // LU with partial pivoting (first entry of largest magnitude), in place,
-// row-major; l = a_rk / a_kk, a_rc = fma(-l, a_kc, a_rc).  One block; the
-// matrix is staged in shared memory when it fits (kLuSmemN rows), so the n
-// dependent elimination steps run at shared-memory latency.
+// row-major; l = a_rk / a_kk, a_rc = fma(-l, a_kc, a_rc); the result (factors
+// and pivots) is that of the textbook row-swapping elimination.
+// Small matrices (n <= kLuSmemN) are factorised in shared memory by one block
+// with a lazy row permutation: rows are not moved during the elimination,
+// perm[i] names the physical row at position i, and the factors are written
+// out in position order at the end.  Larger ones use the global-memory kernel.
 constexpr int kLuSmemN = 160;
-__global__ void __launch_bounds__(1024) k_dense_lu(int32_t n, double *__restrict__ g, int32_t *__restrict__ piv,
+constexpr int kLuThreads = 1024;
+__global__ void __launch_bounds__(kLuThreads) k_dense_lu_smem(int32_t n, double *__restrict__ g,
+                                                              int32_t *__restrict__ piv, int *st) {
+    extern __shared__ double a[];
+    __shared__ KeyIdx wbest[kLuThreads / 32];
+    __shared__ int32_t perm[kLuSmemN];
+    __shared__ int s_sing;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int nw = kLuThreads / 32;
+    const int64_t nn = (int64_t)n * n;
+    for (int64_t e = tid; e < nn; e += kLuThreads) a[e] = g[e];
+    for (int32_t i = tid; i < n; i += kLuThreads) perm[i] = i;
+    __syncthreads();
+    int32_t k = 0;
+    for (; k < n; ++k) {
+        KeyIdx best{0ull, n};
+        for (int32_t i = k + tid; i < n; i += kLuThreads) best = better(best, KeyIdx{mag_key(a[(int64_t)perm[i] * n + k]), i});
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            KeyIdx other{__shfl_xor_sync(0xffffffffu, best.k, o), __shfl_xor_sync(0xffffffffu, best.i, o)};
+            best = better(best, other);
+        }
+        if (lane == 0) wbest[warp] = best;
+        __syncthreads();
+        if (warp == 0) {
+            KeyIdx bb = lane < nw ? wbest[lane] : KeyIdx{0ull, n};
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                KeyIdx other{__shfl_xor_sync(0xffffffffu, bb.k, o), __shfl_xor_sync(0xffffffffu, bb.i, o)};
+                bb = better(bb, other);
+            }
+            if (lane == 0) {
+                // no usable pivot (zero or NaN column): singular, identity pivots from here on
+                const int sing = bb.k == 0ull || bb.i < k || bb.i >= n;
+                const int32_t pos = sing ? k : bb.i;
+                s_sing = sing;
+                piv[k] = pos;
+                const int32_t t = perm[k];
+                perm[k] = perm[pos];
+                perm[pos] = t;
+            }
+        }
+        __syncthreads();
+        if (s_sing) break;
+        const int64_t rk = (int64_t)perm[k] * n;
+        const double akk = a[rk + k];
+        // all multipliers at once (one division latency per step), then the rank-1 update
+        for (int32_t i = k + 1 + tid; i < n; i += kLuThreads) {
+            const int64_t ri = (int64_t)perm[i] * n;
+            a[ri + k] = a[ri + k] / akk;
+        }
+        __syncthreads();
+        for (int32_t i = k + 1 + warp; i < n; i += nw) {
+            const int64_t ri = (int64_t)perm[i] * n;
+            const double l = a[ri + k];
+            for (int32_t c = k + 1 + lane; c < n; c += 32) a[ri + c] = fma(-l, a[rk + c], a[ri + c]);
+        }
+        __syncthreads();
+    }
+    if (k < n) {
+        if (tid == 0) atomicOr(st, DEV_ERR_SINGULAR);
+        for (int32_t r = k + 1 + tid; r < n; r += kLuThreads) piv[r] = r;
+    }
+    for (int64_t e = tid; e < nn; e += kLuThreads) g[e] = a[(int64_t)perm[e / n] * n + e % n];
+}
+
+__global__ void __launch_bounds__(1024) k_dense_lu(int32_t n, double *__restrict__ a, int32_t *__restrict__ piv,
                                                    int *st) {
-    extern __shared__ double sm_lu[];
     __shared__ KeyIdx wbest[32];
     __shared__ int s_p, s_sing;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const bool staged = n <= kLuSmemN;
-    double *a = staged ? sm_lu : g;
-    const int64_t nn = (int64_t)n * n;
-    if (staged)
-        for (int64_t e = tid; e < nn; e += blockDim.x) a[e] = g[e];
-    __syncthreads();
     for (int32_t k = 0; k < n; ++k) {
         KeyIdx best{0ull, n};
         for (int32_t r = k + tid; r < n; r += blockDim.x) best = better(best, KeyIdx{mag_key(a[(int64_t)r * n + k]), r});
@@ -363,8 +425,6 @@ __global__ void __launch_bounds__(1024) k_dense_lu(int32_t n, double *__restrict
         if (tid == 0) {
             KeyIdx bb = wbest[0];
             for (int w = 1; w < (int)(blockDim.x >> 5); ++w) bb = better(bb, wbest[w]);
-            // no usable pivot (zero or NaN column): report singular and leave
-            // identity pivots from here on, so every pivot index stays in range
             s_sing = bb.k == 0ull || bb.i < k || bb.i >= n;
             s_p = s_sing ? k : bb.i;
             piv[k] = s_p;
@@ -386,7 +446,6 @@ __global__ void __launch_bounds__(1024) k_dense_lu(int32_t n, double *__restrict
         const double akk = a[(int64_t)k * n + k];
         for (int32_t r = k + 1 + tid; r < n; r += blockDim.x) a[(int64_t)r * n + k] = a[(int64_t)r * n + k] / akk;
         __syncthreads();
-        // rank-1 update of the trailing block: warps over rows, lanes over columns
         for (int32_t r = k + 1 + warp; r < n; r += (int32_t)(blockDim.x >> 5)) {
             const double l = a[(int64_t)r * n + k];
             for (int32_t c = k + 1 + lane; c < n; c += 32)
@@ -394,8 +453,6 @@ __global__ void __launch_bounds__(1024) k_dense_lu(int32_t n, double *__restrict
         }
         __syncthreads();
     }
-    if (staged)
-        for (int64_t e = tid; e < nn; e += blockDim.x) g[e] = a[e];
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -404,9 +461,10 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// explicit inverse from the LU factors: one warp per column j of A^-1; the
-// factors and each warp's column are staged in shared memory when they fit
-constexpr int kInvWarps = 1;  // one warp per block: the FP64 work spreads over many SMs
+// explicit inverse from the LU factors: one warp per column j of A^-1, in
+// column (axpy) form so that no step needs a reduction; the factors, the
+// pivots and each warp's column are staged in shared memory when they fit
+constexpr int kInvWarps = 4;
 __global__ void __launch_bounds__(kInvWarps * 32)
 k_lu_inverse(int32_t n, const double *__restrict__ lu_g, const int32_t *__restrict__ piv, double *__restrict__ inv) {
     extern __shared__ double sm_inv[];
@@ -414,9 +472,13 @@ k_lu_inverse(int32_t n, const double *__restrict__ lu_g, const int32_t *__restri
     const bool staged = n <= kLuSmemN;
     const int64_t nn = (int64_t)n * n;
     const double *lu = lu_g;
+    const int32_t *pv = piv;
     if (staged) {
         for (int64_t e = threadIdx.x; e < nn; e += blockDim.x) sm_inv[e] = lu_g[e];
+        int32_t *spv = (int32_t *)(sm_inv + nn + (int64_t)kInvWarps * n);
+        for (int32_t e = threadIdx.x; e < n; e += blockDim.x) spv[e] = piv[e];
         lu = sm_inv;
+        pv = spv;
     }
     __syncthreads();
     const int32_t j = blockIdx.x * kInvWarps + w;
@@ -425,30 +487,28 @@ k_lu_inverse(int32_t n, const double *__restrict__ lu_g, const int32_t *__restri
     int64_t xs;
     if (staged) { x = sm_inv + nn + (int64_t)w * n; xs = 1; }
     else { x = inv + j; xs = n; }
-    for (int32_t r = lane; r < n; r += 32) x[r * xs] = (r == j) ? 1.0 : 0.0;
+    // P e_j is the unit vector at the position that the row swaps move j to
+    int32_t pos = j;
+    for (int32_t k = 0; k < n; ++k) {
+        const int32_t p = pv[k];
+        if (p < 0 || p >= n || p == k) continue;
+        if (pos == k) pos = p;
+        else if (pos == p) pos = k;
+    }
+    for (int32_t r = lane; r < n; r += 32) x[r * xs] = (r == pos) ? 1.0 : 0.0;
     __syncwarp();
-    if (lane == 0)
-        for (int32_t k = 0; k < n; ++k) {
-            const int32_t p = piv[k];
-            if (p != k && p >= 0 && p < n) {
-                double t = x[k * xs];
-                x[k * xs] = x[p * xs];
-                x[p * xs] = t;
-            }
-        }
-    __syncwarp();
-    for (int32_t r = 1; r < n; ++r) {
-        double s = 0.0;
-        for (int32_t c = lane; c < r; c += 32) s = fma(lu[(int64_t)r * n + c], x[c * xs], s);
-        s = warp_sum(s);
-        if (lane == 0) x[r * xs] -= s;
+    // L y = P e_j (unit lower triangular); entries before pos stay zero
+    for (int32_t k = pos; k < n - 1; ++k) {
+        const double xk = x[k * xs];
+        for (int32_t r = k + 1 + lane; r < n; r += 32) x[r * xs] = fma(-lu[(int64_t)r * n + k], xk, x[r * xs]);
         __syncwarp();
     }
-    for (int32_t r = n - 1; r >= 0; --r) {
-        double s = 0.0;
-        for (int32_t c = r + 1 + lane; c < n; c += 32) s = fma(lu[(int64_t)r * n + c], x[c * xs], s);
-        s = warp_sum(s);
-        if (lane == 0) x[r * xs] = (x[r * xs] - s) / lu[(int64_t)r * n + r];
+    // U x = y
+    for (int32_t k = n - 1; k >= 0; --k) {
+        if (lane == 0) x[k * xs] = x[k * xs] / lu[(int64_t)k * n + k];
+        __syncwarp();
+        const double xk = x[k * xs];
+        for (int32_t r = lane; r < k; r += 32) x[r * xs] = fma(-lu[(int64_t)r * n + k], xk, x[r * xs]);
         __syncwarp();
     }
     if (staged)
@@ -470,65 +530,114 @@ __global__ void k_coarse_solve(int32_t n, const double *__restrict__ inv, const 
 }
 
 // ------------------------------------------------------------------ V-cycle pieces
+// Every matrix-vector piece takes LPR lanes per row (a power of two <= 32,
+// chosen per level from the row length and count): the lanes stride over the
+// row and combine with xor shuffles.  LPR = 1 is the plain sequential row sum.
+template <int LPR, class V>
+__device__ __forceinline__ V group_sum(V s) {
+#pragma unroll
+    for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
 // zero-guess pre-smoothing fused with the residual: u = m o f, r = f - A u
-template <class V, class TF>
+template <class V, class TF, int LPR>
 __global__ void k_smooth0_residual(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                                    const V *__restrict__ val, const V *__restrict__ m, const TF *__restrict__ f,
                                    V *__restrict__ u, V *__restrict__ r, const int *skip) {
     if (skipped(skip)) return;
-    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t i = (int32_t)(gt / LPR);
+    const int sub = (int)(gt % LPR);
     V s = 0;
-    for (int32_t p = ptr[i]; p < ptr[i + 1]; ++p) {
-        const int32_t j = col[p];
-        s = fma(val[p], m[j] * (V)f[j], s);
+    if (i < n)
+        for (int32_t p = ptr[i] + sub; p < ptr[i + 1]; p += LPR) {
+            const int32_t j = col[p];
+            s = fma(val[p], m[j] * (V)f[j], s);
+        }
+    s = group_sum<LPR>(s);
+    if (i < n && sub == 0) {
+        const V fi = (V)f[i];
+        u[i] = m[i] * fi;
+        r[i] = fi - s;
     }
-    const V fi = (V)f[i];
-    u[i] = m[i] * fi;
-    r[i] = fi - s;
 }
 
 // u_out = u_in + m o (f - A u_in)
-template <class V, class TF, class TO>
+template <class V, class TF, class TO, int LPR>
 __global__ void k_smooth_sweep(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                                const V *__restrict__ val, const V *__restrict__ m, const TF *__restrict__ f,
                                const V *__restrict__ u_in, TO *__restrict__ u_out, const int *skip) {
     if (skipped(skip)) return;
-    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t i = (int32_t)(gt / LPR);
+    const int sub = (int)(gt % LPR);
     V s = 0;
-    for (int32_t p = ptr[i]; p < ptr[i + 1]; ++p) s = fma(val[p], u_in[col[p]], s);
-    u_out[i] = (TO)fma(m[i], (V)f[i] - s, u_in[i]);
+    if (i < n)
+        for (int32_t p = ptr[i] + sub; p < ptr[i + 1]; p += LPR) s = fma(val[p], u_in[col[p]], s);
+    s = group_sum<LPR>(s);
+    if (i < n && sub == 0) u_out[i] = (TO)fma(m[i], (V)f[i] - s, u_in[i]);
 }
 
-template <class V, class TF>
+// the V-cycle's last finest-level sweep fused with the CG product r.z:
+// z = u_in + m o (r - A u_in) and a per-block partial of r.z (block_sum order)
+__device__ double block_sum(double v);
+template <class V, int LPR>
+__global__ void k_smooth_sweep_dot(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                                   const V *__restrict__ val, const V *__restrict__ m, const double *__restrict__ f,
+                                   const V *__restrict__ u_in, double *__restrict__ z, double *__restrict__ partial,
+                                   const int *skip) {
+    if (skipped(skip)) return;
+    const int64_t total = (int64_t)n * LPR;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    double d = 0.0;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < total; base += stride) {
+        const int64_t gt = base + threadIdx.x;
+        const int32_t i = (int32_t)(gt / LPR);
+        const int sub = (int)(gt % LPR);
+        V s = 0;
+        if (gt < total)
+            for (int32_t p = ptr[i] + sub; p < ptr[i + 1]; p += LPR) s = fma(val[p], u_in[col[p]], s);
+        s = group_sum<LPR>(s);
+        if (gt < total && sub == 0) {
+            const double fi = f[i];
+            const double zi = (double)fma(m[i], (V)fi - s, u_in[i]);
+            z[i] = zi;
+            d = fma(fi, zi, d);
+        }
+    }
+    d = block_sum(d);
+    if (threadIdx.x == 0) partial[blockIdx.x] = d;
+}
+
+template <class V, class TF, int LPR>
 __global__ void k_residual(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                            const V *__restrict__ val, const TF *__restrict__ f, const V *__restrict__ u,
                            V *__restrict__ r, const int *skip) {
     if (skipped(skip)) return;
-    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t i = (int32_t)(gt / LPR);
+    const int sub = (int)(gt % LPR);
     V s = 0;
-    for (int32_t p = ptr[i]; p < ptr[i + 1]; ++p) s = fma(val[p], u[col[p]], s);
-    r[i] = (V)f[i] - s;
+    if (i < n)
+        for (int32_t p = ptr[i] + sub; p < ptr[i + 1]; p += LPR) s = fma(val[p], u[col[p]], s);
+    s = group_sum<LPR>(s);
+    if (i < n && sub == 0) r[i] = (V)f[i] - s;
 }
 
-// f_c = R r (R = P^T stored explicitly, rows sorted): a gather, no atomics;
-// 8 lanes per coarse row, combined by shuffles in a fixed order
-constexpr int kRestrictLanes = 8;
-template <class V>
+// f_c = R r (R = P^T stored explicitly, rows sorted): a gather, no atomics
+template <class V, int LPR>
 __global__ void k_restrict(int32_t nc, const int32_t *__restrict__ R_ptr, const int32_t *__restrict__ R_col,
                            const V *__restrict__ R_val, const V *__restrict__ r, V *__restrict__ fc,
                            const int *skip) {
     if (skipped(skip)) return;
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int32_t I = (int32_t)(gt / kRestrictLanes);
-    const int sub = (int)(gt % kRestrictLanes);
+    const int32_t I = (int32_t)(gt / LPR);
+    const int sub = (int)(gt % LPR);
     V s = 0;
     if (I < nc)
-        for (int32_t p = R_ptr[I] + sub; p < R_ptr[I + 1]; p += kRestrictLanes) s = fma(R_val[p], r[R_col[p]], s);
-#pragma unroll
-    for (int o = kRestrictLanes / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        for (int32_t p = R_ptr[I] + sub; p < R_ptr[I + 1]; p += LPR) s = fma(R_val[p], r[R_col[p]], s);
+    s = group_sum<LPR>(s);
     if (I < nc && sub == 0) fc[I] = s;
 }
 
@@ -848,47 +957,78 @@ void launch_dense_lu(int32_t n, double *a, int32_t *piv, int *st, cudaStream_t s
     static bool attr = false;
     const int max_bytes = kLuSmemN * kLuSmemN * (int)sizeof(double);
     if (!attr) {
-        cudaFuncSetAttribute(k_dense_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(k_dense_lu_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         attr = true;
     }
-    const size_t bytes = n <= kLuSmemN ? (size_t)n * n * sizeof(double) : 0;
     count_launch();
-    k_dense_lu<<<1, 1024, bytes, s>>>(n, a, piv, st);
+    if (n <= kLuSmemN)
+        k_dense_lu_smem<<<1, kLuThreads, (size_t)n * n * sizeof(double), s>>>(n, a, piv, st);
+    else
+        k_dense_lu<<<1, 1024, 0, s>>>(n, a, piv, st);
 }
 void launch_lu_inverse(int32_t n, const double *lu, const int32_t *piv, double *inv, cudaStream_t s) {
     static bool attr = false;
-    const int max_bytes = (kLuSmemN * kLuSmemN + kInvWarps * kLuSmemN) * (int)sizeof(double);
+    const int max_bytes = (kLuSmemN * kLuSmemN + kInvWarps * kLuSmemN) * (int)sizeof(double) +
+                          kLuSmemN * (int)sizeof(int32_t);
     if (!attr) {
         cudaFuncSetAttribute(k_lu_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         attr = true;
     }
-    const size_t bytes = n <= kLuSmemN ? ((size_t)n * n + (size_t)kInvWarps * n) * sizeof(double) : 0;
+    const size_t bytes =
+        n <= kLuSmemN ? ((size_t)n * n + (size_t)kInvWarps * n) * sizeof(double) + (size_t)n * sizeof(int32_t) : 0;
     count_launch();
     k_lu_inverse<<<(unsigned)((n + kInvWarps - 1) / kInvWarps), kInvWarps * 32, bytes, s>>>(n, lu, piv, inv);
 }
+
+#define LPR_DISPATCH(lpr, KCALL)                   \
+    switch (lpr) {                                 \
+        case 1: { constexpr int P_ = 1; KCALL; } break;   \
+        case 2: { constexpr int P_ = 2; KCALL; } break;   \
+        case 4: { constexpr int P_ = 4; KCALL; } break;   \
+        case 8: { constexpr int P_ = 8; KCALL; } break;   \
+        case 16: { constexpr int P_ = 16; KCALL; } break; \
+        default: { constexpr int P_ = 32; KCALL; } break; \
+    }
 
 template <class V, class TF>
 void launch_smooth0_residual(const Level &L, const V *val, const V *m, const TF *f, V *u, V *r, const int *skip,
                              cudaStream_t s) {
     count_launch();
-    k_smooth0_residual<V, TF><<<nblocks(L.n), kThreads, 0, s>>>(L.n, L.A_ptr, L.A_col, val, m, f, u, r, skip);
+    const unsigned g = (unsigned)nblocks((int64_t)L.n * L.lpr);
+    LPR_DISPATCH(L.lpr, (k_smooth0_residual<V, TF, P_><<<g, kThreads, 0, s>>>(L.n, L.A_ptr, L.A_col, val, m, f, u,
+                                                                              r, skip)))
 }
 template <class V, class TF, class TO>
 void launch_smooth_sweep(const Level &L, const V *val, const V *m, const TF *f, const V *u_in, TO *u_out,
                          const int *skip, cudaStream_t s) {
     count_launch();
-    k_smooth_sweep<V, TF, TO><<<nblocks(L.n), kThreads, 0, s>>>(L.n, L.A_ptr, L.A_col, val, m, f, u_in, u_out, skip);
+    const unsigned g = (unsigned)nblocks((int64_t)L.n * L.lpr);
+    LPR_DISPATCH(L.lpr, (k_smooth_sweep<V, TF, TO, P_><<<g, kThreads, 0, s>>>(L.n, L.A_ptr, L.A_col, val, m, f,
+                                                                              u_in, u_out, skip)))
 }
+template <class V>
+void launch_smooth_sweep_dot(const Level &L, const V *val, const V *m, const double *f, const V *u_in, double *z,
+                             double *partial, const int *skip, cudaStream_t s) {
+    count_launch();
+    const unsigned g = (unsigned)cg_blocks(L.n);
+    LPR_DISPATCH(L.lpr, (k_smooth_sweep_dot<V, P_><<<g, 256, 0, s>>>(L.n, L.A_ptr, L.A_col, val, m, f, u_in, z,
+                                                                      partial, skip)))
+}
+template void launch_smooth_sweep_dot<double>(const Level &, const double *, const double *, const double *,
+                                              const double *, double *, double *, const int *, cudaStream_t);
+template void launch_smooth_sweep_dot<float>(const Level &, const float *, const float *, const double *,
+                                             const float *, double *, double *, const int *, cudaStream_t);
 template <class V, class TF>
 void launch_residual(const Level &L, const V *val, const TF *f, const V *u, V *r, const int *skip, cudaStream_t s) {
     count_launch();
-    k_residual<V, TF><<<nblocks(L.n), kThreads, 0, s>>>(L.n, L.A_ptr, L.A_col, val, f, u, r, skip);
+    const unsigned g = (unsigned)nblocks((int64_t)L.n * L.lpr);
+    LPR_DISPATCH(L.lpr, (k_residual<V, TF, P_><<<g, kThreads, 0, s>>>(L.n, L.A_ptr, L.A_col, val, f, u, r, skip)))
 }
 template <class V>
 void launch_restrict(const Level &L, const V *Rval, const V *r, V *fc, const int *skip, cudaStream_t s) {
     count_launch();
-    k_restrict<V><<<nblocks((int64_t)L.nc * kRestrictLanes), kThreads, 0, s>>>(L.nc, L.R_ptr, L.R_col, Rval, r, fc,
-                                                                                skip);
+    const unsigned g = (unsigned)nblocks((int64_t)L.nc * L.lpr_r);
+    LPR_DISPATCH(L.lpr_r, (k_restrict<V, P_><<<g, kThreads, 0, s>>>(L.nc, L.R_ptr, L.R_col, Rval, r, fc, skip)))
 }
 template <class V>
 void launch_prolong(const Level &L, const V *Pval, const V *uc, V *u, const int *skip, cudaStream_t s) {
