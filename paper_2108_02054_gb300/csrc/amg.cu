@@ -56,7 +56,10 @@ struct amg_ctx {
     double *A_sys_own = nullptr;
     // CG
     double *cg_r = nullptr, *cg_z = nullptr, *cg_p = nullptr, *cg_q = nullptr, *cg_t = nullptr;
-    double *partial = nullptr, *partial2 = nullptr;
+    // per-block partial sums of the CG reductions, one set per reduction so
+    // that a kernel may read one set while writing another
+    double *partial = nullptr;
+    double *part_pq = nullptr, *part_rr = nullptr, *part_rz = nullptr, *part_rzo = nullptr, *part_tt = nullptr;
     CgState *cg = nullptr;
     CgState *h_cg = nullptr;  // pinned
     int *d_st = nullptr;
@@ -65,7 +68,7 @@ struct amg_ctx {
     double *stage_val = nullptr, *stage_f = nullptr, *stage_u = nullptr;
     ProfData prof;
     // whole-solve CUDA graph (rebuilt after a full setup or a new tolerance)
-    cudaStream_t s_cap = nullptr, s_cap_main = nullptr;
+    cudaStream_t s_cap = nullptr, s_cap_main = nullptr, s_cap_if = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     bool use_graph = true;
@@ -73,7 +76,7 @@ struct amg_ctx {
     bool graph_valid = false;
     double graph_tol = -1.0;
     double *cg_f = nullptr, *cg_u = nullptr;
-    int64_t graph_pro = 0, graph_body = 0, graph_epi = 0;  // kernels per part of the graph
+    int64_t graph_pro = 0, graph_body = 0, graph_epi = 0, graph_branch = 0;  // kernels per part of the graph
     // time-step bookkeeping
     int last_iters = 0;
     int last_status = AMG_OK;
@@ -503,9 +506,18 @@ amg_status ensure_persistent(amg_ctx *ctx, int32_t n, int32_t nnz) {
     TRY(alloc(ctx, &ctx->cg_f, (size_t)n, true));
     TRY(alloc(ctx, &ctx->cg_u, (size_t)n, true));
     ctx->graph_valid = false;
-    TRY(alloc(ctx, &ctx->partial, (size_t)cg_blocks(n), true));
-    TRY(alloc(ctx, &ctx->partial2, (size_t)cg_blocks(n), true));
+    {
+        const size_t nb = (size_t)cg_blocks(n);
+        TRY(alloc(ctx, &ctx->partial, 5 * nb, true));
+        ctx->part_pq = ctx->partial;
+        ctx->part_rr = ctx->partial + nb;
+        ctx->part_rz = ctx->partial + 2 * nb;
+        ctx->part_rzo = ctx->partial + 3 * nb;
+        ctx->part_tt = ctx->partial + 4 * nb;
+    }
     TRY(alloc(ctx, &ctx->cg, 1, true));
+    // the reduction counters inside must start at zero; kernels leave them zero
+    CK(cudaMemsetAsync(ctx->cg, 0, sizeof(CgState), ctx->s));
     TRY(alloc(ctx, &ctx->stage_val, (size_t)nnz, true));
     TRY(alloc(ctx, &ctx->stage_f, (size_t)n, true));
     TRY(alloc(ctx, &ctx->stage_u, (size_t)n, true));
@@ -585,7 +597,7 @@ void up_finest(amg_ctx *ctx, const double *f, V *u, double *out, double *rz_part
         if (k == npost - 1) {
             if (rz_partial) {
                 ProfScope ps_(ctx, AMG_PROF_SWEEP_L0);
-                launch_smooth_sweep_dot<V>(L, A, m, f, u, out, rz_partial, skip, ctx->s);
+                launch_smooth_sweep_dot<V>(L, A, m, f, u, out, rz_partial, ctx->cg, skip, ctx->s);
             } else {
                 ProfScope ps_(ctx, AMG_PROF_SWEEP_L0);
                 launch_smooth_sweep<V, double, double>(L, A, m, f, u, out, skip, ctx->s);
@@ -596,7 +608,7 @@ void up_finest(amg_ctx *ctx, const double *f, V *u, double *out, double *rz_part
         std::swap(u, t);
     }
     launch_copy_cast<V, double>(L.n, u, out, skip, ctx->s);
-    if (rz_partial) launch_dot(ctx->n, f, out, rz_partial, skip, ctx->s);
+    if (rz_partial) launch_dot(ctx->n, f, out, rz_partial, skip, ctx->cg, 1, ctx->s);
 }
 
 // post-smoothing on level l; the last sweep writes `out` (type TO) when given
@@ -623,7 +635,7 @@ void enqueue_vcycle(amg_ctx *ctx, const double *r, double *z, const int *skip, d
     const int nl = ctx->nlev;
     if (nl == 1) {
         launch_coarse_solve<V, double, double>(ctx->lev[0].n, ctx->inv, r, z, skip, ctx->s);
-        if (rz_partial) launch_dot(ctx->n, r, z, rz_partial, skip, ctx->s);
+        if (rz_partial) launch_dot(ctx->n, r, z, rz_partial, skip, ctx->cg, 1, ctx->s);
         return;
     }
     V *cur[kMaxLevels];
@@ -669,44 +681,54 @@ void vcycle(amg_ctx *ctx, const double *r, double *z, const int *skip, double *r
 // CG prologue: u = 0, r = f, z = B r, p = z, rz = r.z (device state in ctx->cg)
 void enqueue_cg_prologue(amg_ctx *ctx, const double *f, double *u, double tol) {
     const int32_t n = ctx->n;
-    const int nblk = cg_blocks(n);
     CgState *cg = ctx->cg;
-    launch_cg_init(n, f, u, ctx->cg_r, ctx->partial, ctx->s);
-    launch_cg_start(nblk, ctx->partial, cg, tol, ctx->prm.maxiter, ctx->s);
-    vcycle(ctx, ctx->cg_r, ctx->cg_z, &cg->done, ctx->partial);
-    launch_cg_set_rz_p(n, nblk, ctx->partial, ctx->cg_z, ctx->cg_p, cg, ctx->s);
+    launch_cg_init(n, f, u, ctx->cg_r, ctx->part_rr, cg, tol, ctx->prm.maxiter, ctx->s);
+    vcycle(ctx, ctx->cg_r, ctx->cg_z, &cg->done, ctx->part_rz);
+    launch_cg_set_rz_p(n, ctx->cg_z, ctx->cg_p, cg, ctx->s);
 }
 
-// one CG iteration; every kernel returns at once when the state says done
-void enqueue_cg_iteration(amg_ctx *ctx, const double *f, double *u) {
+// One CG iteration in three parts; every kernel returns at once when the
+// state says done.  A: q = A p, alpha, u and r, the recurrence residual check.
+void enqueue_cg_iter_a(amg_ctx *ctx, double *u, int use_h, cudaGraphConditionalHandle hb) {
     const int32_t n = ctx->n;
-    const int nblk = cg_blocks(n);
+    CgState *cg = ctx->cg;
+    {
+        ProfScope ps_(ctx, AMG_PROF_CG_SPMV, true);
+        launch_spmv_dot(n, ctx->fine_ptr, ctx->fine_col, ctx->A_sys, ctx->cg_p, ctx->cg_q, ctx->part_pq, cg, ctx->s);
+    }
+    {
+        ProfScope ps_(ctx, AMG_PROF_CG_UPDATE, true);
+        launch_cg_update_ur(n, cg, ctx->cg_p, ctx->cg_q, u, ctx->cg_r, ctx->part_rr, use_h, hb, ctx->s);
+    }
+}
+
+// B: only when the recurrence met the tolerance: the true residual, and r
+// replaced by it if it misses
+void enqueue_cg_iter_b(amg_ctx *ctx, const double *f, double *u) {
+    const int32_t n = ctx->n;
+    CgState *cg = ctx->cg;
+    launch_true_residual(n, ctx->fine_ptr, ctx->fine_col, ctx->A_sys, f, u, ctx->cg_t, ctx->part_tt, cg, 0, ctx->s);
+    launch_replace_r(n, cg, ctx->cg_t, ctx->cg_r, ctx->s);
+}
+
+// C: z = B r with the partials of r.z, beta and p (and the loop condition)
+void enqueue_cg_iter_c(amg_ctx *ctx, int use_h, cudaGraphConditionalHandle h) {
+    const int32_t n = ctx->n;
     const bool flex = mixed(ctx);
     CgState *cg = ctx->cg;
-    const int *done = &cg->done;
-    const double *A = ctx->A_sys;
-    const int32_t *ptr = ctx->fine_ptr, *col = ctx->fine_col;
-    double *r = ctx->cg_r, *z = ctx->cg_z, *p = ctx->cg_p, *q = ctx->cg_q, *t = ctx->cg_t;
-    { ProfScope ps_(ctx, AMG_PROF_CG_SPMV, true); launch_spmv_dot(n, ptr, col, A, p, q, ctx->partial, done, ctx->s); }
-    launch_cg_alpha(nblk, ctx->partial, cg, ctx->s);
-    { ProfScope ps_(ctx, AMG_PROF_CG_UPDATE, true); launch_cg_update_ur(n, cg, p, q, u, r, ctx->partial, ctx->s); }
-    launch_cg_check(nblk, ctx->partial, cg, ctx->s);
-    launch_true_residual(n, ptr, col, A, f, u, t, ctx->partial, cg, 0, ctx->s);
-    launch_true_check(nblk, ctx->partial, cg, ctx->s);
-    launch_replace_r(n, cg, t, r, ctx->s);
-    if (flex) launch_dot(n, r, z, ctx->partial2, done, ctx->s);
-    vcycle(ctx, r, z, done, ctx->partial);  // z = B r and the partials of r.z
-    if (flex) launch_cg_beta_flexible(nblk, ctx->partial, ctx->partial2, cg, ctx->s);
-    else launch_cg_beta(nblk, ctx->partial, cg, ctx->s);
-    { ProfScope ps_(ctx, AMG_PROF_CG_P, true); launch_cg_update_p(n, cg, z, p, ctx->s); }
+    if (flex) launch_dot(n, ctx->cg_r, ctx->cg_z, ctx->part_rzo, &cg->done, cg, 2, ctx->s);
+    vcycle(ctx, ctx->cg_r, ctx->cg_z, &cg->done, ctx->part_rz);
+    {
+        ProfScope ps_(ctx, AMG_PROF_CG_P, true);
+        launch_cg_update_p(n, cg, ctx->cg_z, ctx->cg_p, use_h, h, ctx->s);
+    }
 }
 
 // the true relative residual of the returned iterate
 void enqueue_cg_epilogue(amg_ctx *ctx, const double *f, double *u) {
     const int32_t n = ctx->n;
-    launch_true_residual(n, ctx->fine_ptr, ctx->fine_col, ctx->A_sys, f, u, ctx->cg_t, ctx->partial, ctx->cg, 1,
+    launch_true_residual(n, ctx->fine_ptr, ctx->fine_col, ctx->A_sys, f, u, ctx->cg_t, ctx->part_tt, ctx->cg, 1,
                          ctx->s);
-    launch_cg_final_norm(cg_blocks(n), ctx->partial, ctx->cg, ctx->s);
 }
 
 void drop_graph(amg_ctx *ctx) {
@@ -716,66 +738,115 @@ void drop_graph(amg_ctx *ctx) {
     ctx->graph = nullptr;
 }
 
-// The whole solve as one graph: prologue, a while-conditional node whose body
-// is one CG iteration (plus the loop-control kernel), epilogue.  It works on
-// the context's own f / u buffers, so it stays valid until the hierarchy or
-// the tolerance changes.
-amg_status build_solve_graph(amg_ctx *ctx, double tol) {
-    drop_graph(ctx);
-    // capture on two private streams (the caller's stream may be the legacy
-    // default stream, which cannot be captured); the graph is launched on the
-    // caller's stream
-    CK(cudaStreamSynchronize(ctx->s));
-    cudaStream_t user_s = ctx->s;
-    cudaStream_t main_s = ctx->s_cap_main;
-    const double *f = ctx->cg_f;
-    double *u = ctx->cg_u;
-    CK(cudaStreamBeginCapture(main_s, cudaStreamCaptureModeThreadLocal));
-    ctx->s = main_s;
-    const int64_t c0 = launch_total();
-    enqueue_cg_prologue(ctx, f, u, tol);
-    const int64_t c1 = launch_total();
-    int64_t c2 = c1;
+// add a conditional node after the current capture dependencies of stream s
+// and make it the stream's only dependency; returns its body graph
+cudaError_t add_conditional(cudaStream_t s, cudaGraphConditionalNodeType type, unsigned def,
+                            cudaGraphConditionalHandle *h, cudaGraphNode_t *node, cudaGraph_t *body) {
     cudaStreamCaptureStatus cs;
     cudaGraph_t g = nullptr;
     const cudaGraphNode_t *deps = nullptr;
     size_t ndeps = 0;
-    cudaError_t e = cudaStreamGetCaptureInfo(main_s, &cs, nullptr, &g, &deps, nullptr, &ndeps);
-    cudaGraphConditionalHandle h;
-    cudaGraphNode_t cond;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &ndeps);
+    if (e != cudaSuccess) return e;
+    e = cudaGraphConditionalHandleCreate(h, g, def, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return e;
     cudaGraphNodeParams cp = {};
-    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = *h;
+    cp.conditional.type = type;
+    cp.conditional.size = 1;
+    e = cudaGraphAddNode(node, g, deps, nullptr, ndeps, &cp);
+    if (e != cudaSuccess) return e;
+    *body = cp.conditional.phGraph_out[0];
+    return cudaSuccess;
+}
+
+// The whole solve as one graph: prologue, a WHILE conditional node whose body
+// is one CG iteration (its last kernel sets the loop condition), epilogue.
+// Inside the body, the true-residual branch sits in an IF conditional node
+// that the convergence check opens.  It works on the context's own f / u
+// buffers, so it stays valid until the hierarchy or the tolerance changes.
+// Capture runs on private streams (the caller's stream may be the legacy
+// default stream, which cannot be captured); the graph is launched on the
+// caller's stream.
+amg_status build_solve_graph(amg_ctx *ctx, double tol) {
+    drop_graph(ctx);
+    CK(cudaStreamSynchronize(ctx->s));
+    cudaStream_t user_s = ctx->s;
+    const double *f = ctx->cg_f;
+    double *u = ctx->cg_u;
+    const int64_t c0 = launch_total();
+    int64_t c1 = c0, c2 = c0;
+    CK(cudaStreamBeginCapture(ctx->s_cap_main, cudaStreamCaptureModeThreadLocal));
+    ctx->s = ctx->s_cap_main;
+    enqueue_cg_prologue(ctx, f, u, tol);
+    c1 = launch_total();
+    cudaGraphConditionalHandle h_loop = 0, h_true = 0;
+    cudaGraphNode_t loop_node = nullptr, if_node = nullptr;
+    cudaGraph_t body = nullptr, tbody = nullptr;
+    cudaError_t e = add_conditional(ctx->s_cap_main, cudaGraphCondTypeWhile, 1, &h_loop, &loop_node, &body);
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(ctx->s_cap, body, nullptr, nullptr, 0,
+                                                            cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        cp.type = cudaGraphNodeTypeConditional;
-        cp.conditional.handle = h;
-        cp.conditional.type = cudaGraphCondTypeWhile;
-        cp.conditional.size = 1;
-        e = cudaGraphAddNode(&cond, g, deps, nullptr, ndeps, &cp);
-    }
-    if (e == cudaSuccess) {
-        cudaGraph_t body = cp.conditional.phGraph_out[0];
-        e = cudaStreamBeginCaptureToGraph(ctx->s_cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-            ctx->s = ctx->s_cap;
-            enqueue_cg_iteration(ctx, f, u);
-            launch_cg_loop_control(ctx->cg, h, ctx->s);
-            c2 = launch_total();
-            ctx->s = main_s;
-            cudaGraph_t tmp = nullptr;
-            e = cudaStreamEndCapture(ctx->s_cap, &tmp);
+        ctx->s = ctx->s_cap;
+        const int64_t ca = launch_total();
+        // the IF handle belongs to the body graph; the check kernel sets it
+        cudaError_t eh = cudaGraphConditionalHandleCreate(&h_true, body, 0, cudaGraphCondAssignDefault);
+        if (eh == cudaSuccess) {
+            enqueue_cg_iter_a(ctx, u, 1, h_true);
+            cudaStreamCaptureStatus cs;
+            cudaGraph_t g = nullptr;
+            const cudaGraphNode_t *deps = nullptr;
+            size_t ndeps = 0;
+            eh = cudaStreamGetCaptureInfo(ctx->s_cap, &cs, nullptr, &g, &deps, nullptr, &ndeps);
+            cudaGraphNodeParams cp = {};
+            if (eh == cudaSuccess) {
+                cp.type = cudaGraphNodeTypeConditional;
+                cp.conditional.handle = h_true;
+                cp.conditional.type = cudaGraphCondTypeIf;
+                cp.conditional.size = 1;
+                eh = cudaGraphAddNode(&if_node, g, deps, nullptr, ndeps, &cp);
+            }
+            if (eh == cudaSuccess) {
+                tbody = cp.conditional.phGraph_out[0];
+                eh = cudaStreamBeginCaptureToGraph(ctx->s_cap_if, tbody, nullptr, nullptr, 0,
+                                                   cudaStreamCaptureModeThreadLocal);
+            }
+            if (eh == cudaSuccess) {
+                ctx->s = ctx->s_cap_if;
+                const int64_t cb = launch_total();
+                enqueue_cg_iter_b(ctx, f, u);
+                // the branch runs only in some iterations: counted when it does
+                ctx->graph_branch = launch_total() - cb;
+                ctx->s = ctx->s_cap;
+                cudaGraph_t tmp = nullptr;
+                eh = cudaStreamEndCapture(ctx->s_cap_if, &tmp);
+            }
+            if (eh == cudaSuccess)
+                eh = cudaStreamUpdateCaptureDependencies(ctx->s_cap, &if_node, nullptr, 1,
+                                                         cudaStreamSetCaptureDependencies);
+            if (eh == cudaSuccess) enqueue_cg_iter_c(ctx, 1, h_loop);
         }
+        c2 = launch_total() - ctx->graph_branch;
+        (void)ca;
+        ctx->s = ctx->s_cap_main;
+        cudaGraph_t tmp = nullptr;
+        e = cudaStreamEndCapture(ctx->s_cap, &tmp);
+        if (e == cudaSuccess) e = eh;
     }
-    if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(main_s, &cond, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess)
+        e = cudaStreamUpdateCaptureDependencies(ctx->s_cap_main, &loop_node, nullptr, 1,
+                                                cudaStreamSetCaptureDependencies);
     if (e == cudaSuccess) enqueue_cg_epilogue(ctx, f, u);
     const int64_t c3 = launch_total();
-    // captured launches do not run now: count them when the graph executes
+    // captured launches do not run now: they are counted when the graph runs
     add_launches(c0 - c3);
     ctx->graph_pro = c1 - c0;
-    ctx->graph_body = c2 - c1;
-    ctx->graph_epi = c3 - c2;
+    ctx->graph_body = (c2 - c1);
+    ctx->graph_epi = c3 - c2 - ctx->graph_branch;
     ctx->s = user_s;
     cudaGraph_t done_graph = nullptr;
-    cudaError_t e2 = cudaStreamEndCapture(main_s, &done_graph);
+    cudaError_t e2 = cudaStreamEndCapture(ctx->s_cap_main, &done_graph);
     if (e == cudaSuccess) e = e2;
     if (e != cudaSuccess) {
         if (done_graph) cudaGraphDestroy(done_graph);
@@ -818,13 +889,20 @@ amg_status solve_impl(amg_ctx *ctx, const double *f, double *u, double tol, amg_
         CK(cudaGraphLaunch(ctx->graph_exec, ctx->s));
         CK(cudaMemcpyAsync(u, ctx->cg_u, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, ctx->s));
         amg_status st = finish_solve(ctx, info);
-        add_launches(ctx->graph_pro + ctx->graph_epi + ctx->graph_body * (int64_t)ctx->h_cg->pad);
+        // bodies executed = completed p updates plus the final (returning) pass;
+        // the true-residual branch ran in 1 + replacements bodies when it converged
+        const CgState &hc = *ctx->h_cg;
+        const int64_t bodies = (int64_t)hc.pad + 1;
+        const int64_t branches = (hc.status == AMG_OK && hc.iter > 0) ? 1 + hc.replacements : hc.replacements;
+        add_launches(ctx->graph_pro + ctx->graph_epi + ctx->graph_body * bodies + ctx->graph_branch * branches);
         return st;
     }
     // eager path: the host checks the device state after every iteration
     enqueue_cg_prologue(ctx, f, u, tol);
     for (int it = 1; it <= ctx->prm.maxiter; ++it) {
-        enqueue_cg_iteration(ctx, f, u);
+        enqueue_cg_iter_a(ctx, u, 0, 0);
+        enqueue_cg_iter_b(ctx, f, u);
+        enqueue_cg_iter_c(ctx, 0, 0);
         CK(cudaMemcpyAsync(ctx->h_cg, ctx->cg, sizeof(CgState), cudaMemcpyDeviceToHost, ctx->s));
         CK(cudaStreamSynchronize(ctx->s));
         if (ctx->h_cg->done) break;
@@ -882,6 +960,7 @@ amg_status amg_create(amg_ctx **out, const amg_params *prm, void *cuda_stream) {
     cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &thr);
     if (cudaStreamCreateWithFlags(&ctx->s_cap, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&ctx->s_cap_main, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->s_cap_if, cudaStreamNonBlocking) != cudaSuccess ||
         cudaMallocHost(&ctx->h_cg, sizeof(CgState)) != cudaSuccess ||
         cudaMallocHost(&ctx->h_st, sizeof(int)) != cudaSuccess ||
         cudaMalloc(&ctx->d_st, sizeof(int)) != cudaSuccess) {
@@ -901,6 +980,7 @@ void amg_destroy(amg_ctx *ctx) {
     drop_graph(ctx);
     if (ctx->s_cap) cudaStreamDestroy(ctx->s_cap);
     if (ctx->s_cap_main) cudaStreamDestroy(ctx->s_cap_main);
+    if (ctx->s_cap_if) cudaStreamDestroy(ctx->s_cap_if);
     for (auto &v : ctx->prof.rec)
         for (auto &pr : v) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);

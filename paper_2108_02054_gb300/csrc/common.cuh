@@ -30,8 +30,10 @@ constexpr int kMaxRowUnique = kHashCap / 2;
 
 // Device-resident state of the CG iteration; every CG kernel reads and writes
 // it so that the loop needs no host round trip between its kernels.
+enum { CG_CTR_INIT = 0, CG_CTR_PQ, CG_CTR_RR, CG_CTR_RZ, CG_CTR_RZO, CG_CTR_TT, CG_NCTR = 8 };
 struct CgState {
-    double rz, pq, alpha, beta, rr, nf, res, tres, tol;
+    double rz, rz_next, rzo, pq, alpha, beta, rr, nf, res, tres, tol;
+    unsigned ctr[CG_NCTR];  // arrival counters of the last-block reductions (zero between kernels)
     int iter, maxiter, done, status, replacements, need_true, copy_r;
     int pad;  // loop bodies executed (graph path)
 };
@@ -180,7 +182,7 @@ void launch_residual(const Level &L, const V *val, const TF *f, const V *u, V *r
 // last finest-level post-smoothing sweep fused with the CG product r.z (cg_blocks(n) partials)
 template <class V>
 void launch_smooth_sweep_dot(const Level &L, const V *val, const V *m, const double *f, const V *u_in, double *z,
-                             double *partial, const int *skip, cudaStream_t s);
+                             double *partial, CgState *cg, const int *skip, cudaStream_t s);
 template <class V>
 void launch_restrict(const Level &L, const V *Rval, const V *r, V *fc, const int *skip, cudaStream_t s);
 template <class V>
@@ -190,29 +192,23 @@ void launch_coarse_solve(int32_t n, const double *inv, const TF *f, TO *u, const
 template <class TI, class TO>
 void launch_copy_cast(int64_t n, const TI *in, TO *out, const int *skip, cudaStream_t s);
 
-// CG (FP64)
+// CG (FP64); reductions finish in the last block of the producing kernel
 int cg_blocks(int64_t n);
-void launch_cg_init(int32_t n, const double *f, double *u, double *r, double *partial, cudaStream_t s);
-void launch_cg_start(int nblk, const double *partial, CgState *cg, double tol, int maxiter, cudaStream_t s);
-void launch_dot(int32_t n, const double *x, const double *y, double *partial, const int *skip, cudaStream_t s);
-void launch_cg_set_rz_p(int32_t n, int nblk, const double *partial, const double *z, double *p, CgState *cg,
-                        cudaStream_t s);
+void launch_cg_init(int32_t n, const double *f, double *u, double *r, double *partial, CgState *cg, double tol,
+                    int maxiter, cudaStream_t s);
+// x.y into per-block partials; with cg, the last block stores the total
+// (target 1: the new r.z, target 2: r_new.z_old)
+void launch_dot(int32_t n, const double *x, const double *y, double *partial, const int *skip, CgState *cg, int target,
+                cudaStream_t s);
+void launch_cg_set_rz_p(int32_t n, const double *z, double *p, CgState *cg, cudaStream_t s);
 void launch_spmv_dot(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *p,
-                     double *q, double *partial, const int *skip, cudaStream_t s);
-void launch_cg_alpha(int nblk, const double *partial, CgState *cg, cudaStream_t s);
-void launch_cg_update_ur(int32_t n, const CgState *cg, const double *p, const double *q, double *u, double *r,
-                         double *partial, cudaStream_t s);
-void launch_cg_check(int nblk, const double *partial, CgState *cg, cudaStream_t s);
+                     double *q, double *partial, CgState *cg, cudaStream_t s);
+void launch_cg_update_ur(int32_t n, CgState *cg, const double *p, const double *q, double *u, double *r,
+                         double *partial, int use_h, cudaGraphConditionalHandle hb, cudaStream_t s);
 void launch_true_residual(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *f,
-                          const double *u, double *t, double *partial, const CgState *cg, int force,
-                          cudaStream_t s);
-void launch_true_check(int nblk, const double *partial, CgState *cg, cudaStream_t s);
+                          const double *u, double *t, double *partial, CgState *cg, int force, cudaStream_t s);
 void launch_replace_r(int32_t n, const CgState *cg, const double *t, double *r, cudaStream_t s);
-void launch_cg_beta(int nblk, const double *partial, CgState *cg, cudaStream_t s);
-void launch_cg_beta_flexible(int nblk, const double *partial, const double *partial_old, CgState *cg,
-                             cudaStream_t s);
-void launch_cg_update_p(int32_t n, const CgState *cg, const double *z, double *p, cudaStream_t s);
-void launch_cg_final_norm(int nblk, const double *partial, CgState *cg, cudaStream_t s);
-void launch_cg_loop_control(CgState *cg, cudaGraphConditionalHandle h, cudaStream_t s);
+void launch_cg_update_p(int32_t n, CgState *cg, const double *z, double *p, int use_h, cudaGraphConditionalHandle h,
+                        cudaStream_t s);
 
 }  // namespace amgpr

@@ -582,11 +582,12 @@ __global__ void k_smooth_sweep(int32_t n, const int32_t *__restrict__ ptr, const
 // the V-cycle's last finest-level sweep fused with the CG product r.z:
 // z = u_in + m o (r - A u_in) and a per-block partial of r.z (block_sum order)
 __device__ double block_sum(double v);
+__device__ bool cg_reduce(double d, double *partial, unsigned *counter, double *total);
 template <class V, int LPR>
 __global__ void k_smooth_sweep_dot(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                                    const V *__restrict__ val, const V *__restrict__ m, const double *__restrict__ f,
                                    const V *__restrict__ u_in, double *__restrict__ z, double *__restrict__ partial,
-                                   const int *skip) {
+                                   CgState *cg, const int *skip) {
     if (skipped(skip)) return;
     const int64_t total = (int64_t)n * LPR;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -606,8 +607,9 @@ __global__ void k_smooth_sweep_dot(int32_t n, const int32_t *__restrict__ ptr, c
             d = fma(fi, zi, d);
         }
     }
-    d = block_sum(d);
-    if (threadIdx.x == 0) partial[blockIdx.x] = d;
+    // the last block stores the new r.z in the CG state
+    double rz = 0.0;
+    if (cg_reduce(d, partial, &cg->ctr[CG_CTR_RZ], &rz) && threadIdx.x == 0) cg->rz_next = rz;
 }
 
 template <class V, class TF, int LPR>
@@ -662,6 +664,10 @@ __global__ void k_copy_cast(int64_t n, const TI *__restrict__ in, TO *__restrict
 }
 
 // ------------------------------------------------------------------ CG (FP64)
+// Each reduction writes one partial per block; the block that finishes last
+// (a fenced atomic counter, reset by that block) sums the partials in index
+// order and takes the iteration's scalar step itself, so no separate
+// single-block kernel is needed and the sums stay deterministic.
 constexpr int kCgThreads = 256;
 constexpr int kCgMaxBlocks = 152 * 8;
 
@@ -681,15 +687,42 @@ __device__ double block_sum(double v) {
     return t;  // valid in thread 0
 }
 
-// one block: sum of the per-block partials in index order
-__device__ double sum_partials(const double *__restrict__ partial, int nblk) {
+// true in every thread of the block that is the last of the grid to get here
+__device__ bool cg_last_block(unsigned *counter) {
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned t = atomicAdd(counter, 1u);
+        s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    return s_last != 0;
+}
+
+// the last block's sum of all partials, in index order (valid in thread 0)
+__device__ double cg_sum_partials(const double *partial, int nblk) {
     double s = 0.0;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += partial[b];
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += __ldcg(partial + b);
     return block_sum(s);
 }
 
+// publish this block's partial; the last block returns the total (thread 0)
+__device__ bool cg_reduce(double d, double *partial, unsigned *counter, double *total) {
+    d = block_sum(d);
+    if (threadIdx.x == 0) partial[blockIdx.x] = d;
+    if (!cg_last_block(counter)) return false;
+    const double t = cg_sum_partials(partial, gridDim.x);
+    if (threadIdx.x == 0) {
+        *total = t;
+        *counter = 0u;
+    }
+    return true;
+}
+
+// u = 0, r = f; the last block initialises the iteration state from |f|
 __global__ void k_cg_init(int32_t n, const double *__restrict__ f, double *__restrict__ u, double *__restrict__ r,
-                          double *__restrict__ partial) {
+                          double *__restrict__ partial, CgState *cg, double tol, int maxiter) {
     double s = 0.0;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double fi = f[i];
@@ -697,47 +730,56 @@ __global__ void k_cg_init(int32_t n, const double *__restrict__ f, double *__res
         r[i] = fi;
         s = fma(fi, fi, s);
     }
-    s = block_sum(s);
-    if (threadIdx.x == 0) partial[blockIdx.x] = s;
-}
-
-__global__ void k_cg_start(int nblk, const double *__restrict__ partial, CgState *cg, double tol, int maxiter) {
-    double ff = sum_partials(partial, nblk);
-    if (threadIdx.x == 0) {
-        CgState c{};
-        c.nf = sqrt(ff);
-        c.tol = tol;
-        c.maxiter = maxiter;
-        c.done = (c.nf == 0.0) || maxiter <= 0;
-        c.status = (maxiter <= 0 && c.nf != 0.0) ? AMG_NOT_CONVERGED : AMG_OK;
-        *cg = c;
+    double ff = 0.0;
+    if (cg_reduce(s, partial, &cg->ctr[CG_CTR_INIT], &ff) && threadIdx.x == 0) {
+        cg->nf = sqrt(ff);
+        cg->tol = tol;
+        cg->maxiter = maxiter;
+        cg->done = (cg->nf == 0.0) || maxiter <= 0;
+        cg->status = (maxiter <= 0 && cg->nf != 0.0) ? AMG_NOT_CONVERGED : AMG_OK;
+        cg->iter = 0;
+        cg->replacements = 0;
+        cg->need_true = 0;
+        cg->copy_r = 0;
+        cg->pad = 0;
+        cg->rz = cg->rz_next = cg->rzo = 0.0;
+        cg->alpha = cg->beta = cg->pq = cg->rr = cg->res = cg->tres = 0.0;
     }
 }
 
+// x.y; with a state, the last block stores it (target 1: the new r.z,
+// target 2: r_new.z_old of the flexible variant)
 __global__ void k_dot(int32_t n, const double *__restrict__ x, const double *__restrict__ y,
-                      double *__restrict__ partial, const int *skip) {
+                      double *__restrict__ partial, const int *skip, CgState *cg, int target) {
     if (skipped(skip)) return;
     double s = 0.0;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) s = fma(x[i], y[i], s);
-    s = block_sum(s);
-    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+    if (!cg) {
+        s = block_sum(s);
+        if (threadIdx.x == 0) partial[blockIdx.x] = s;
+        return;
+    }
+    double t = 0.0;
+    if (cg_reduce(s, partial, &cg->ctr[target == 1 ? CG_CTR_RZ : CG_CTR_RZO], &t) && threadIdx.x == 0) {
+        if (target == 1) cg->rz_next = t;
+        else cg->rzo = t;
+    }
 }
 
-// after the first preconditioner application: rz = r.z, p = z
-__global__ void k_cg_set_rz_p(int32_t n, int nblk, const double *__restrict__ partial, const double *__restrict__ z,
-                              double *__restrict__ p, CgState *cg) {
+// after the first preconditioner application: p = z, r.z becomes current
+__global__ void k_cg_set_rz_p(int32_t n, const double *__restrict__ z, double *__restrict__ p, CgState *cg) {
     if (cg->done) return;
-    if (blockIdx.x == 0) {
-        double rz = sum_partials(partial, nblk);
-        if (threadIdx.x == 0) cg->rz = rz;
-    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) cg->rz = cg->rz_next;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = z[i];
 }
 
+// q = A p; the last block forms p.q and alpha = r.z / p.q (breakdown: p.q <= 0)
 __global__ void k_spmv_dot(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                            const double *__restrict__ val, const double *__restrict__ p, double *__restrict__ q,
-                           double *__restrict__ partial, const int *skip) {
-    if (skipped(skip)) return;
+                           double *__restrict__ partial, CgState *cg) {
+    if (cg->done) return;
+    // r.z of the previous iteration becomes current (read only by the last block)
+    if (blockIdx.x == 0 && threadIdx.x == 0) cg->rz = cg->rz_next;
     double d = 0.0;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double s = 0.0;
@@ -745,29 +787,28 @@ __global__ void k_spmv_dot(int32_t n, const int32_t *__restrict__ ptr, const int
         q[i] = s;
         d = fma(p[i], s, d);
     }
-    d = block_sum(d);
-    if (threadIdx.x == 0) partial[blockIdx.x] = d;
-}
-
-__global__ void k_cg_alpha(int nblk, const double *__restrict__ partial, CgState *cg) {
-    if (cg->done) return;
-    double pq = sum_partials(partial, nblk);
-    if (threadIdx.x == 0) {
+    double pq = 0.0;
+    if (cg_reduce(d, partial, &cg->ctr[CG_CTR_PQ], &pq) && threadIdx.x == 0) {
         cg->pq = pq;
         if (!(pq > 0.0) || !isfinite(pq)) {
             cg->iter += 1;
             cg->status = AMG_ERR_BREAKDOWN;
             cg->done = 1;
         } else {
-            cg->alpha = cg->rz / pq;
+            cg->alpha = __ldcg(&cg->rz) / pq;  // committed by block 0 of this kernel
         }
     }
 }
 
-__global__ void k_cg_update_ur(int32_t n, const CgState *cg, const double *__restrict__ p,
-                               const double *__restrict__ q, double *__restrict__ u, double *__restrict__ r,
-                               double *__restrict__ partial) {
-    if (cg->done) return;
+// u += alpha p, r -= alpha q; the last block checks the recurrence residual
+// (graph: opens the IF branch hb of the true-residual check when it meets tol)
+__global__ void k_cg_update_ur(int32_t n, CgState *cg, const double *__restrict__ p, const double *__restrict__ q,
+                               double *__restrict__ u, double *__restrict__ r, double *__restrict__ partial,
+                               int use_h, cudaGraphConditionalHandle hb) {
+    if (cg->done) {
+        if (use_h && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(hb, 0u);
+        return;
+    }
     const double alpha = cg->alpha;
     double s = 0.0;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -776,14 +817,8 @@ __global__ void k_cg_update_ur(int32_t n, const CgState *cg, const double *__res
         r[i] = ri;
         s = fma(ri, ri, s);
     }
-    s = block_sum(s);
-    if (threadIdx.x == 0) partial[blockIdx.x] = s;
-}
-
-__global__ void k_cg_check(int nblk, const double *__restrict__ partial, CgState *cg) {
-    if (cg->done) return;
-    double rr = sum_partials(partial, nblk);
-    if (threadIdx.x == 0) {
+    double rr = 0.0;
+    if (cg_reduce(s, partial, &cg->ctr[CG_CTR_RR], &rr) && threadIdx.x == 0) {
         cg->iter += 1;
         cg->rr = rr;
         cg->res = sqrt(rr) / cg->nf;
@@ -792,15 +827,17 @@ __global__ void k_cg_check(int nblk, const double *__restrict__ partial, CgState
             cg->done = 1;
             cg->status = AMG_NOT_CONVERGED;
         }
+        if (use_h) cudaGraphSetConditional(hb, (cg->need_true && !cg->done) ? 1u : 0u);
     }
 }
 
-// t = f - A u (the true residual), when the recurrence reports convergence
-// (or unconditionally with force)
+// t = f - A u, the true residual, when the recurrence reports convergence; the
+// last block accepts convergence or schedules the replacement of r (twice at
+// most).  With force: unconditionally, the final relative residual.
 __global__ void k_true_residual(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                                 const double *__restrict__ val, const double *__restrict__ f,
                                 const double *__restrict__ u, double *__restrict__ t, double *__restrict__ partial,
-                                const CgState *cg, int force) {
+                                CgState *cg, int force) {
     if (!force && (cg->done || !cg->need_true)) return;
     double d = 0.0;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -810,25 +847,20 @@ __global__ void k_true_residual(int32_t n, const int32_t *__restrict__ ptr, cons
         t[i] = ti;
         d = fma(ti, ti, d);
     }
-    d = block_sum(d);
-    if (threadIdx.x == 0) partial[blockIdx.x] = d;
-}
-
-// convergence needs the true residual too; otherwise replace r by it (twice at most)
-__global__ void k_true_check(int nblk, const double *__restrict__ partial, CgState *cg) {
-    if (cg->done || !cg->need_true) return;
-    double tt = sum_partials(partial, nblk);
-    if (threadIdx.x == 0) {
-        cg->tres = sqrt(tt) / cg->nf;
-        if (cg->tres <= cg->tol) {
-            cg->done = 1;
-            cg->status = AMG_OK;
-        } else if (cg->replacements >= 2 || cg->iter >= cg->maxiter) {
-            cg->done = 1;
-            cg->status = AMG_NOT_CONVERGED;
-        } else {
-            cg->replacements += 1;
-            cg->copy_r = 1;
+    double tt = 0.0;
+    if (cg_reduce(d, partial, &cg->ctr[CG_CTR_TT], &tt) && threadIdx.x == 0) {
+        cg->tres = cg->nf > 0.0 ? sqrt(tt) / cg->nf : 0.0;
+        if (!force) {
+            if (cg->tres <= cg->tol) {
+                cg->done = 1;
+                cg->status = AMG_OK;
+            } else if (cg->replacements >= 2 || cg->iter >= cg->maxiter) {
+                cg->done = 1;
+                cg->status = AMG_NOT_CONVERGED;
+            } else {
+                cg->replacements += 1;
+                cg->copy_r = 1;
+            }
         }
     }
 }
@@ -838,53 +870,32 @@ __global__ void k_replace_r(int32_t n, const CgState *cg, const double *__restri
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) r[i] = t[i];
 }
 
-// beta = (r.z)_new / (r.z)_old (flexible variant: minus r_new.z_old, kept in pq)
-__global__ void k_cg_beta(int nblk, const double *__restrict__ partial, CgState *cg) {
-    if (cg->done) return;
-    double rz = sum_partials(partial, nblk);
-    if (threadIdx.x == 0) {
-        cg->beta = rz / cg->rz;
-        cg->rz = rz;
-        cg->copy_r = 0;
-        cg->need_true = 0;
+// beta = (r.z_new - r.z_old) / (r.z)_old, the flexible form (r.z_old = 0 for
+// standard CG), p = z + beta p.  The new r.z becomes current in the next
+// iteration's first kernel.  In the graph this is the body's last kernel: it
+// keeps the while loop going while the iteration is not done, with a hard
+// cap of maxiter + 4 bodies.
+__global__ void k_cg_update_p(int32_t n, CgState *cg, const double *__restrict__ z, double *__restrict__ p,
+                              int use_h, cudaGraphConditionalHandle h) {
+    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+    if (cg->done) {
+        if (lead && use_h) cudaGraphSetConditional(h, 0u);
+        return;
     }
-}
-
-__global__ void k_cg_beta_flexible(int nblk, const double *__restrict__ partial,
-                                   const double *__restrict__ partial_old, CgState *cg) {
-    if (cg->done) return;
-    double rz = sum_partials(partial, nblk);
-    double rzo = sum_partials(partial_old, nblk);
-    if (threadIdx.x == 0) {
-        cg->beta = (rz - rzo) / cg->rz;
-        cg->rz = rz;
-        cg->copy_r = 0;
-        cg->need_true = 0;
-    }
-}
-
-__global__ void k_cg_update_p(int32_t n, const CgState *cg, const double *__restrict__ z, double *__restrict__ p) {
-    if (cg->done) return;
-    const double beta = cg->beta;
+    const double beta = (cg->rz_next - cg->rzo) / cg->rz;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         p[i] = fma(beta, p[i], z[i]);
-}
-
-// end of one captured CG iteration: keep looping while the iteration is not
-// done; a hard cap (maxiter + 4 bodies) ends the loop whatever the state says
-__global__ void k_cg_loop_control(CgState *cg, cudaGraphConditionalHandle h) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    cg->pad += 1;  // bodies executed
-    if (!cg->done && cg->pad > cg->maxiter + 4) {
-        cg->done = 1;
-        cg->status = AMG_NOT_CONVERGED;
+    if (lead) {
+        cg->beta = beta;
+        cg->copy_r = 0;
+        cg->need_true = 0;
+        cg->pad += 1;  // loop bodies executed
+        if (cg->pad > cg->maxiter + 4) {
+            cg->done = 1;
+            cg->status = AMG_NOT_CONVERGED;
+        }
+        if (use_h) cudaGraphSetConditional(h, cg->done ? 0u : 1u);
     }
-    cudaGraphSetConditional(h, cg->done ? 0u : 1u);
-}
-
-__global__ void k_cg_final_norm(int nblk, const double *__restrict__ partial, CgState *cg) {
-    double tt = sum_partials(partial, nblk);
-    if (threadIdx.x == 0) cg->tres = cg->nf > 0.0 ? sqrt(tt) / cg->nf : 0.0;
 }
 
 }  // namespace
@@ -1008,16 +1019,17 @@ void launch_smooth_sweep(const Level &L, const V *val, const V *m, const TF *f, 
 }
 template <class V>
 void launch_smooth_sweep_dot(const Level &L, const V *val, const V *m, const double *f, const V *u_in, double *z,
-                             double *partial, const int *skip, cudaStream_t s) {
+                             double *partial, CgState *cg, const int *skip, cudaStream_t s) {
     count_launch();
     const unsigned g = (unsigned)cg_blocks(L.n);
-    LPR_DISPATCH(L.lpr, (k_smooth_sweep_dot<V, P_><<<g, 256, 0, s>>>(L.n, L.A_ptr, L.A_col, val, m, f, u_in, z,
-                                                                      partial, skip)))
+    LPR_DISPATCH(L.lpr, (k_smooth_sweep_dot<V, P_><<<g, kCgThreads, 0, s>>>(L.n, L.A_ptr, L.A_col, val, m, f, u_in,
+                                                                             z, partial, cg, skip)))
 }
 template void launch_smooth_sweep_dot<double>(const Level &, const double *, const double *, const double *,
-                                              const double *, double *, double *, const int *, cudaStream_t);
+                                              const double *, double *, double *, CgState *, const int *,
+                                              cudaStream_t);
 template void launch_smooth_sweep_dot<float>(const Level &, const float *, const float *, const double *,
-                                             const float *, double *, double *, const int *, cudaStream_t);
+                                             const float *, double *, double *, CgState *, const int *, cudaStream_t);
 template <class V, class TF>
 void launch_residual(const Level &L, const V *val, const TF *f, const V *u, V *r, const int *skip, cudaStream_t s) {
     count_launch();
@@ -1090,75 +1102,43 @@ int cg_blocks(int64_t n) {
     if (b > kCgMaxBlocks) b = kCgMaxBlocks;
     return (int)(b < 1 ? 1 : b);
 }
-void launch_cg_init(int32_t n, const double *f, double *u, double *r, double *partial, cudaStream_t s) {
+void launch_cg_init(int32_t n, const double *f, double *u, double *r, double *partial, CgState *cg, double tol,
+                    int maxiter, cudaStream_t s) {
     count_launch();
-    k_cg_init<<<cg_blocks(n), kCgThreads, 0, s>>>(n, f, u, r, partial);
+    k_cg_init<<<cg_blocks(n), kCgThreads, 0, s>>>(n, f, u, r, partial, cg, tol, maxiter);
 }
-void launch_cg_start(int nblk, const double *partial, CgState *cg, double tol, int maxiter, cudaStream_t s) {
+void launch_dot(int32_t n, const double *x, const double *y, double *partial, const int *skip, CgState *cg, int target,
+                cudaStream_t s) {
     count_launch();
-    k_cg_start<<<1, 1024, 0, s>>>(nblk, partial, cg, tol, maxiter);
+    k_dot<<<cg_blocks(n), kCgThreads, 0, s>>>(n, x, y, partial, skip, cg, target);
 }
-void launch_dot(int32_t n, const double *x, const double *y, double *partial, const int *skip, cudaStream_t s) {
+void launch_cg_set_rz_p(int32_t n, const double *z, double *p, CgState *cg, cudaStream_t s) {
     count_launch();
-    k_dot<<<cg_blocks(n), kCgThreads, 0, s>>>(n, x, y, partial, skip);
-}
-void launch_cg_set_rz_p(int32_t n, int nblk, const double *partial, const double *z, double *p, CgState *cg,
-                        cudaStream_t s) {
-    count_launch();
-    k_cg_set_rz_p<<<cg_blocks(n), kCgThreads, 0, s>>>(n, nblk, partial, z, p, cg);
+    k_cg_set_rz_p<<<cg_blocks(n), kCgThreads, 0, s>>>(n, z, p, cg);
 }
 void launch_spmv_dot(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *p,
-                     double *q, double *partial, const int *skip, cudaStream_t s) {
+                     double *q, double *partial, CgState *cg, cudaStream_t s) {
     count_launch();
-    k_spmv_dot<<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, col, val, p, q, partial, skip);
+    k_spmv_dot<<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, col, val, p, q, partial, cg);
 }
-void launch_cg_alpha(int nblk, const double *partial, CgState *cg, cudaStream_t s) {
+void launch_cg_update_ur(int32_t n, CgState *cg, const double *p, const double *q, double *u, double *r,
+                         double *partial, int use_h, cudaGraphConditionalHandle hb, cudaStream_t s) {
     count_launch();
-    k_cg_alpha<<<1, 1024, 0, s>>>(nblk, partial, cg);
-}
-void launch_cg_update_ur(int32_t n, const CgState *cg, const double *p, const double *q, double *u, double *r,
-                         double *partial, cudaStream_t s) {
-    count_launch();
-    k_cg_update_ur<<<cg_blocks(n), kCgThreads, 0, s>>>(n, cg, p, q, u, r, partial);
-}
-void launch_cg_check(int nblk, const double *partial, CgState *cg, cudaStream_t s) {
-    count_launch();
-    k_cg_check<<<1, 1024, 0, s>>>(nblk, partial, cg);
+    k_cg_update_ur<<<cg_blocks(n), kCgThreads, 0, s>>>(n, cg, p, q, u, r, partial, use_h, hb);
 }
 void launch_true_residual(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *f,
-                          const double *u, double *t, double *partial, const CgState *cg, int force,
-                          cudaStream_t s) {
+                          const double *u, double *t, double *partial, CgState *cg, int force, cudaStream_t s) {
     count_launch();
     k_true_residual<<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, col, val, f, u, t, partial, cg, force);
-}
-void launch_true_check(int nblk, const double *partial, CgState *cg, cudaStream_t s) {
-    count_launch();
-    k_true_check<<<1, 1024, 0, s>>>(nblk, partial, cg);
 }
 void launch_replace_r(int32_t n, const CgState *cg, const double *t, double *r, cudaStream_t s) {
     count_launch();
     k_replace_r<<<cg_blocks(n), kCgThreads, 0, s>>>(n, cg, t, r);
 }
-void launch_cg_beta(int nblk, const double *partial, CgState *cg, cudaStream_t s) {
+void launch_cg_update_p(int32_t n, CgState *cg, const double *z, double *p, int use_h, cudaGraphConditionalHandle h,
+                        cudaStream_t s) {
     count_launch();
-    k_cg_beta<<<1, 1024, 0, s>>>(nblk, partial, cg);
-}
-void launch_cg_beta_flexible(int nblk, const double *partial, const double *partial_old, CgState *cg,
-                             cudaStream_t s) {
-    count_launch();
-    k_cg_beta_flexible<<<1, 1024, 0, s>>>(nblk, partial, partial_old, cg);
-}
-void launch_cg_update_p(int32_t n, const CgState *cg, const double *z, double *p, cudaStream_t s) {
-    count_launch();
-    k_cg_update_p<<<cg_blocks(n), kCgThreads, 0, s>>>(n, cg, z, p);
-}
-void launch_cg_loop_control(CgState *cg, cudaGraphConditionalHandle h, cudaStream_t s) {
-    count_launch();
-    k_cg_loop_control<<<1, 32, 0, s>>>(cg, h);
-}
-void launch_cg_final_norm(int nblk, const double *partial, CgState *cg, cudaStream_t s) {
-    count_launch();
-    k_cg_final_norm<<<1, 1024, 0, s>>>(nblk, partial, cg);
+    k_cg_update_p<<<cg_blocks(n), kCgThreads, 0, s>>>(n, cg, z, p, use_h, h);
 }
 
 }  // namespace amgpr
