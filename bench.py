@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--compare-steps", type=int, default=10,
                     help="timed steps of the full-rebuild and full-reuse comparison runs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--table2", action="store_true",
+                    help="instead of the benchmark line: every time step of the workload under each strategy "
+                         "and AMG flavour, accumulated like Table 2 of the paper (JSON)")
     return ap.parse_args()
 
 
@@ -394,8 +397,66 @@ def run_reference(args):
     }))
 
 
+def run_table2(args):
+    """Sec. 4, Table 2 on the synthetic workload: accumulated setup and solve
+    seconds over all T time steps, full rebuilds, average CG iterations, and
+    speedups (T_noreuse / T_strategy - 1) * 100 for each reuse strategy, for
+    the build's AMG flavour (smoothed aggregation + SPAI0) and the paper's own
+    (plain aggregation + damped Jacobi)."""
+    import torch
+    from paper_2108_02054_gb300 import amg as B
+
+    w = I.WORKLOADS[args.workload]
+    prec = B.PREC_MIXED if w.precision == "mixed" else B.PREC_FP64
+    ptr, col = B.poisson_pattern(w.dim, w.N)
+    f = torch.tensor(I.rhs(w.n), device="cuda")
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    flavours = {"smoothed aggregation + SPAI0": {}, "plain aggregation + damped Jacobi": {"smoothed": 0,
+                                                                                          "smoother": 1}}
+    strategies = {"no reuse": {"mode": B.MODE_FULL_REBUILD}, "full reuse": {"mode": B.MODE_FULL_REUSE},
+                  "partial reuse": {"mode": B.MODE_PARTIAL},
+                  "partial reuse + rebuild at 1.3x iterations": {"mode": B.MODE_PARTIAL, "rebuild_iter_growth": 1.3}}
+    rows = []
+    for fname, fkw in flavours.items():
+        base = None
+        for sname, skw in strategies.items():
+            G = B.AMG(precision=prec, **fkw, **skw)
+            u = torch.empty_like(f)
+            setup = solve = 0.0
+            iters = rebuilds = 0
+            converged = True
+            for k in range(w.T):
+                v = B.poisson_values(w.dim, w.N, torch.tensor(I.density(w.dim, w.N, k, w.T), device="cuda"), ptr)
+                flush.zero_()
+                e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                e0.record()
+                si = G.step(v, ptr, col)
+                e1.record()
+                _, info = G.solve(f, TOL, u=u)
+                e2.record()
+                torch.cuda.synchronize()
+                setup += e0.elapsed_time(e1) / 1e3
+                solve += e1.elapsed_time(e2) / 1e3
+                iters += info.iters
+                rebuilds += si.rebuilt
+                converged &= info.status == 0
+            G.close()
+            row = {"flavour": fname, "strategy": sname, "setup_s": setup, "solve_s": solve, "rebuilds": rebuilds,
+                   "avg_iters": iters / w.T, "all_converged": converged}
+            if base is None:
+                base = row
+            row["total_speedup_pct"] = 100 * ((base["setup_s"] + base["solve_s"]) / (setup + solve) - 1)
+            row["setup_speedup_pct"] = 100 * (base["setup_s"] / setup - 1)
+            rows.append(row)
+    print(json.dumps({"table2": rows, "workload": f"{args.workload}: {DESCR[args.workload]}", "steps": w.T,
+                      "tol": TOL}))
+
+
 def main():
     args = parse()
+    if args.table2:
+        run_table2(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -65,6 +65,14 @@ typedef struct {
     int32_t mode;          /* AMG_MODE_* used by amg_step (PARTIAL) */
     int32_t reuse_iter_limit; /* full reuse: rebuild after a solve that needed more (100) */
     int32_t maxiter;       /* CG iteration cap (100) */
+    /* PARTIAL mode, preventive full rebuilds (Sec. 3: "from time to time",
+     * regularly or on a convergence criterion); 0 disables each rule:
+     * rebuild_every: a full setup every this many steps;
+     * rebuild_iter_growth: a full setup when the previous solve needed more
+     * than this factor times the iterations of the first solve after the last
+     * full setup. */
+    int32_t rebuild_every;
+    double rebuild_iter_growth;
 } amg_params;
 
 typedef struct {

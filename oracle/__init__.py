@@ -288,25 +288,40 @@ class StepRecord:
 
 
 def run_time_steps(ptr, col, values_per_step, f, mode=MODE_PARTIAL, params=None, tol=1e-8, maxiter=100,
-                   reuse_iter_limit=None, keep_u=False):
+                   reuse_iter_limit=None, keep_u=False, rebuild_every=0, rebuild_iter_growth=0.0):
     """Time loop of Alg. 3 (full reuse), Alg. 4 (partial reuse) or no reuse.
 
     Full reuse rebuilds when the previous step's solve did not converge within
-    reuse_iter_limit iterations (default: maxiter), Sec. 3."""
+    reuse_iter_limit iterations (default: maxiter), Sec. 3.  Partial reuse may
+    add preventive full rebuilds (Sec. 3): every rebuild_every steps, or when
+    the previous solve needed more than rebuild_iter_growth times the
+    iterations of the first solve after the last full setup."""
     limit = maxiter if reuse_iter_limit is None else reuse_iter_limit
     recs = []
     H = None
     last_ok = True
+    last_it = 0
+    since_full = 0
+    base_it = -1
     for k, val in enumerate(values_per_step):
         rebuilt = False
-        if k == 0 or mode == MODE_FULL_REBUILD or (mode == MODE_FULL_REUSE and not last_ok):
+        preventive = mode == MODE_PARTIAL and k > 0 and (
+            (rebuild_every > 0 and since_full + 1 >= rebuild_every)
+            or (rebuild_iter_growth > 0 and base_it > 0 and last_it > rebuild_iter_growth * base_it))
+        if k == 0 or mode == MODE_FULL_REBUILD or (mode == MODE_FULL_REUSE and not last_ok) or preventive:
             H = Hierarchy(ptr, col, val, params)
             rebuilt = True
+            since_full = 0
+            base_it = -1
         elif mode == MODE_PARTIAL:
             st = H.rebuild(val)
             if st != OK:
                 raise RuntimeError(f"rebuild failed: {st}")
+            since_full += 1
         u, it, rr, st = H.pcg(f, tol, maxiter, sys_val=val)
         last_ok = (st == OK) and it <= limit
+        last_it = it
+        if base_it < 0 and st == OK:
+            base_it = it
         recs.append(StepRecord(k, it, rr, st, rebuilt, u if keep_u else None))
     return recs

@@ -47,6 +47,7 @@ class amg_params(ctypes.Structure):
         ("coarse_enough", ctypes.c_int32), ("max_levels", ctypes.c_int32), ("theta_halving", ctypes.c_int32),
         ("smoothed", ctypes.c_int32), ("precision", ctypes.c_int32), ("mode", ctypes.c_int32),
         ("reuse_iter_limit", ctypes.c_int32), ("maxiter", ctypes.c_int32),
+        ("rebuild_every", ctypes.c_int32), ("rebuild_iter_growth", ctypes.c_double),
     ]
 
 

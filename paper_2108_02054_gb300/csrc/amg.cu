@@ -81,6 +81,8 @@ struct amg_ctx {
     int last_iters = 0;
     int last_status = AMG_OK;
     int last_rebuilt = 0;
+    int steps_since_full = 0;   // partial rebuilds since the last full setup
+    int iters_after_full = -1;  // iterations of the first solve after it (-1: not yet known)
 };
 
 namespace {
@@ -869,6 +871,7 @@ amg_status finish_solve(amg_ctx *ctx, amg_info *info) {
     if (!h.done && st == AMG_OK) st = AMG_NOT_CONVERGED;
     ctx->last_iters = h.iter;
     ctx->last_status = st;
+    if (ctx->iters_after_full < 0 && st == AMG_OK) ctx->iters_after_full = h.iter;
     if (info) {
         info->iters = h.iter;
         info->rel_resid = h.tres;
@@ -932,6 +935,8 @@ amg_status amg_default_params(amg_params *prm) {
     prm->mode = AMG_MODE_PARTIAL;
     prm->reuse_iter_limit = 100;
     prm->maxiter = 100;
+    prm->rebuild_every = 0;
+    prm->rebuild_iter_growth = 0.0;
     return AMG_OK;
 }
 
@@ -944,6 +949,7 @@ amg_status amg_create(amg_ctx **out, const amg_params *prm, void *cuda_stream) {
     if (p.npre < 0 || p.npost < 0 || p.max_levels < 1 || p.coarse_enough < 1 || p.maxiter < 0 ||
         (p.smoother != AMG_SMOOTHER_SPAI0 && p.smoother != AMG_SMOOTHER_JACOBI) ||
         (p.precision != AMG_PREC_FP64 && p.precision != AMG_PREC_MIXED) || p.mode < 0 || p.mode > 2 ||
+        p.rebuild_every < 0 || !(p.rebuild_iter_growth >= 0.0) ||
         !(p.theta >= 0.0) || !std::isfinite(p.omega))
         return AMG_ERR_ARG;
     amg_ctx *ctx = new amg_ctx();
@@ -1007,6 +1013,8 @@ amg_status amg_full_setup(amg_ctx *ctx, int32_t n, int32_t nnz, const int32_t *d
         CK(cudaMemcpyAsync(ctx->A_sys_own, d_val, sizeof(double) * (size_t)nnz, cudaMemcpyDeviceToDevice, ctx->s));
     update_sys(ctx);
     ctx->last_rebuilt = 1;
+    ctx->steps_since_full = 0;
+    ctx->iters_after_full = -1;
     return AMG_OK;
 }
 
@@ -1025,6 +1033,7 @@ amg_status amg_partial_rebuild(amg_ctx *ctx, const double *d_val) {
     TRY(check_device(ctx, "partial rebuild"));
     update_sys(ctx);
     ctx->last_rebuilt = 0;
+    ctx->steps_since_full += 1;
     return AMG_OK;
 }
 
@@ -1039,7 +1048,23 @@ amg_status amg_step(amg_ctx *ctx, int32_t n, int32_t nnz, const int32_t *d_ptr, 
     if (!ctx->have_setup) {
         st = amg_full_setup(ctx, n, nnz, d_ptr, d_col, d_val);
     } else if (mode == AMG_MODE_PARTIAL) {
-        st = amg_partial_rebuild(ctx, d_val);
+        const amg_params &p = ctx->prm;
+        const bool regular = p.rebuild_every > 0 && ctx->steps_since_full + 1 >= p.rebuild_every;
+        const bool growth = p.rebuild_iter_growth > 0.0 && ctx->iters_after_full > 0 &&
+                            ctx->last_iters > p.rebuild_iter_growth * ctx->iters_after_full;
+        if (regular || growth) {
+            st = full_setup_impl(ctx, d_val);
+            if (st == AMG_OK) {
+                update_sys(ctx);
+                ctx->last_rebuilt = 1;
+                ctx->steps_since_full = 0;
+                ctx->iters_after_full = -1;
+            } else {
+                free_hierarchy(ctx);
+            }
+        } else {
+            st = amg_partial_rebuild(ctx, d_val);
+        }
     } else if (mode == AMG_MODE_FULL_REBUILD) {
         st = full_setup_impl(ctx, d_val);
         if (st == AMG_OK) { update_sys(ctx); ctx->last_rebuilt = 1; }

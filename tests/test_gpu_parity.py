@@ -318,3 +318,32 @@ def test_graph_solve_equals_eager_solve(precision):
     assert torch.equal(u1, u2) and torch.equal(u1, u3)
     u4, i4 = G.solve(f, 1e-11)          # a new tolerance rebuilds the graph
     assert i4.iters > i1.iters and i4.rel_resid <= 1e-11
+
+
+def test_preventive_rebuilds():
+    dim, N, T = 2, 32, 10
+    ptr, col, _ = gpu_problem(dim, N, 0, T)
+    f = I.rhs(N * N)
+    ft = torch.tensor(f, device="cuda")
+    vals = [oracle_problem(dim, N, k, T)[2] for k in range(T)]
+    # every 3rd step: the schedule and the iterations follow the oracle
+    G = B.AMG(rebuild_every=3)
+    recs = O.run_time_steps(*oracle_problem(dim, N, 0, T)[:2], vals, f, O.MODE_PARTIAL, rebuild_every=3)
+    for k in range(T):
+        si = G.step(gpu_problem(dim, N, k, T)[2], ptr, col)
+        _, info = G.solve(ft, 1e-8)
+        assert bool(si.rebuilt) == recs[k].rebuilt == (k % 3 == 0)
+        assert info.status == 0 and abs(info.iters - recs[k].iters) <= 1
+    # iteration growth: every decision follows the GPU's own iteration counts
+    G = B.AMG(rebuild_iter_growth=1.1)
+    base, last, rebuilt_any = None, None, False
+    for k in range(T):
+        si = G.step(gpu_problem(dim, N, k, T)[2], ptr, col)
+        _, info = G.solve(ft, 1e-8)
+        if k > 0:
+            assert bool(si.rebuilt) == (last > 1.1 * base)
+            rebuilt_any |= bool(si.rebuilt)
+        if si.rebuilt:
+            base = info.iters
+        last = info.iters
+    assert rebuilt_any

@@ -510,3 +510,23 @@ def test_adjoint_gradient_against_central_differences():
             e[cell] = h
             fd = (loss(theta + e) - loss(theta - e)) / (2 * h)
             assert g[cell] == pytest.approx(fd, rel=1e-6, abs=10 * np.finfo(float).eps * abs(L0) / h)
+
+
+def test_preventive_rebuild_rules():
+    """Sec. 3: preventive full rebuilds, regularly (every m-th step) or by a
+    convergence criterion (iteration growth over the last full setup's)."""
+    dim, N, T = 2, 24, 8
+    ptr, col, _ = O.poisson_assemble(dim, N, I.density(dim, N, 0, T))
+    vals = [O.poisson_assemble(dim, N, I.density(dim, N, k, T))[2] for k in range(T)]
+    f = I.rhs(N * N)
+    prm = O.Params(coarse_enough=20)
+    every = O.run_time_steps(ptr, col, vals, f, O.MODE_PARTIAL, prm, rebuild_every=3)
+    assert [r.rebuilt for r in every] == [k % 3 == 0 for k in range(T)]
+    grow = O.run_time_steps(ptr, col, vals, f, O.MODE_PARTIAL, prm, rebuild_iter_growth=1.1)
+    base = None
+    for k, r in enumerate(grow):
+        if k > 0:
+            assert r.rebuilt == (grow[k - 1].iters > 1.1 * base)
+        if r.rebuilt:
+            base = r.iters
+    assert any(r.rebuilt for r in grow[1:])
