@@ -68,6 +68,19 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def whole_job_step_time(step_s, world, device):
+    """Replicas: every rank runs its own time series.  The job's time per
+    step is the slowest rank's, shared by the world's steps (world > 1 needs
+    an initialised process group)."""
+    if world <= 1:
+        return step_s
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([step_s], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item()) / world
+
+
 def measured_traffic(workload, kernel):
     """DRAM bytes (read + write) per launch of `kernel` from a committed ncu
     summary line 'roofline-traffic: <workload> <kernel> <bytes>', else None."""
@@ -309,13 +322,7 @@ def run_ours(args):
     _, full, _, _ = run_mode(B, torch, w, B.MODE_FULL_REBUILD, ptr, col, vals, f, warm_idx, timed_idx[:nc], flush)
     _, reuse, _, _ = run_mode(B, torch, w, B.MODE_FULL_REUSE, ptr, col, vals, f, warm_idx, timed_idx[:nc], flush)
 
-    step_s = part["step_ms"] / 1e3
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([step_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_s = float(t.item())
-    value = step_s / world  # replicas: every rank runs its own time series
+    value = whole_job_step_time(part["step_ms"] / 1e3, world, "cuda")
 
     # roofline of the dominant kernel
     s = 4 if w.precision == "mixed" else 8
