@@ -73,6 +73,10 @@ def lib():
             L.orc_export_level_vec.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                                ctypes.c_void_p]
             L.orc_export_lu.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+            L.orc_levelset_assemble.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p, _i32p, _i32p, _f64p]
+            L.orc_bicgstab.argtypes = [ctypes.c_void_p, ctypes.c_void_p, _f64p, _f64p, ctypes.c_double, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
             L.orc_dense_lu.argtypes = [ctypes.c_int, _f64p, _i32p]
             L.orc_dense_lu_solve.argtypes = [ctypes.c_int, _f64p, _i32p, _f64p, _f64p]
             _lib = L
@@ -96,6 +100,22 @@ def poisson_assemble(dim: int, N: int, rho: np.ndarray, dirichlet_top: bool = Tr
     col = np.zeros(nnz, np.int32)
     val = np.zeros(nnz, np.float64)
     st = L.orc_poisson_assemble(dim, N, int(dirichlet_top), np.ascontiguousarray(rho, np.float64), ptr, col, val)
+    if st != OK:
+        raise ValueError(f"assembly failed: {st}")
+    return ptr, col, val
+
+
+def levelset_assemble(dim: int, N: int, fx, fy, fz):
+    """CSR of the level-set transport step (implicit upwind convection with
+    diffusion, the stand-in for eq. 5) on the pressure pattern."""
+    L = lib()
+    n = N ** dim
+    nnz = int(L.orc_poisson_nnz(dim, N))
+    ptr = np.zeros(n + 1, np.int32)
+    col = np.zeros(nnz, np.int32)
+    val = np.zeros(nnz, np.float64)
+    fx, fy, fz = (np.ascontiguousarray(a, np.float64) for a in (fx, fy, fz))
+    st = L.orc_levelset_assemble(dim, N, _ptr(fx), _ptr(fy), _ptr(fz) if fz.size else None, ptr, col, val)
     if st != OK:
         raise ValueError(f"assembly failed: {st}")
     return ptr, col, val
@@ -262,6 +282,16 @@ class Hierarchy:
         lib().orc_vcycle(self._h, np.ascontiguousarray(r, np.float64), z)
         return z
 
+    def bicgstab(self, f, tol=1e-8, maxiter=100, sys_val=None):
+        """BiCGStab (Sec. 4) right-preconditioned by one V-cycle; (u, iters, relres, status)."""
+        u = np.zeros(self.n, np.float64)
+        it = ctypes.c_int(0)
+        rr = ctypes.c_double(0.0)
+        sv = None if sys_val is None else np.ascontiguousarray(sys_val, np.float64)
+        st = lib().orc_bicgstab(self._h, _ptr(sv), np.ascontiguousarray(f, np.float64), u, float(tol), int(maxiter),
+                                ctypes.byref(it), ctypes.byref(rr))
+        return u, it.value, rr.value, int(st)
+
     def pcg(self, f, tol=1e-8, maxiter=100, sys_val=None):
         """CG preconditioned with one V-cycle; returns (u, iters, relres, status)."""
         u = np.zeros(self.n, np.float64)
@@ -288,7 +318,7 @@ class StepRecord:
 
 
 def run_time_steps(ptr, col, values_per_step, f, mode=MODE_PARTIAL, params=None, tol=1e-8, maxiter=100,
-                   reuse_iter_limit=None, keep_u=False, rebuild_every=0, rebuild_iter_growth=0.0):
+                   reuse_iter_limit=None, keep_u=False, rebuild_every=0, rebuild_iter_growth=0.0, solver="cg"):
     """Time loop of Alg. 3 (full reuse), Alg. 4 (partial reuse) or no reuse.
 
     Full reuse rebuilds when the previous step's solve did not converge within
@@ -318,7 +348,8 @@ def run_time_steps(ptr, col, values_per_step, f, mode=MODE_PARTIAL, params=None,
             if st != OK:
                 raise RuntimeError(f"rebuild failed: {st}")
             since_full += 1
-        u, it, rr, st = H.pcg(f, tol, maxiter, sys_val=val)
+        solve = H.pcg if solver == "cg" else H.bicgstab
+        u, it, rr, st = solve(f, tol, maxiter, sys_val=val)
         last_ok = (st == OK) and it <= limit
         last_it = it
         if base_it < 0 and st == OK:

@@ -137,6 +137,48 @@ int orc_poisson_assemble(int dim, int N, int dirichlet_top, const double *rho,
     return ORC_OK;
 }
 
+/* Level-set transport step (the stand-in for eq. 5 of Sec. 4): implicit
+ * upwind convection with diffusion on the same pattern,
+ *   A_cc = 1 + sum_f (max(w_f, 0) + 0.1),  A_cj = min(w_f, 0) - 0.1,
+ * where w_f is the outward (Courant-scaled) face velocity of cell c, taken
+ * from the face arrays fx ((N+1) x N (x N)), fy, fz (x fastest); the diagonal
+ * starts at 1 and adds the face terms in ascending neighbour order. */
+int orc_levelset_assemble(int dim, int N, const double *fx, const double *fy, const double *fz,
+                          int32_t *ptr, int32_t *col, double *val) {
+    if ((dim != 2 && dim != 3) || N < 1) return ORC_ERR_ARG;
+    long long n = (dim == 2) ? (long long)N * N : (long long)N * N * N;
+    long long pos = 0;
+    const long long N1 = N + 1;
+    for (long long c = 0; c < n; ++c) {
+        long long x = c % N, y = (c / N) % N, z = (dim == 3) ? c / ((long long)N * N) : 0;
+        long long nb[7];
+        double w[7];
+        int nnb = 0;
+        /* face arrays: fx[(z*N + y)*(N+1) + x_face], fy[(z*(N+1) + y_face)*N + x],
+         * fz[(z_face*N + y)*N + x] (2D: z = 0) */
+        if (dim == 3 && z > 0) { nb[nnb] = c - (long long)N * N; w[nnb++] = -fz[(z * N + y) * N + x]; }
+        if (y > 0) { nb[nnb] = c - N; w[nnb++] = -fy[(z * N1 + y) * N + x]; }
+        if (x > 0) { nb[nnb] = c - 1; w[nnb++] = -fx[(z * N + y) * N1 + x]; }
+        nb[nnb] = -1; w[nnb++] = 0.0;
+        if (x < N - 1) { nb[nnb] = c + 1; w[nnb++] = fx[(z * N + y) * N1 + x + 1]; }
+        if (y < N - 1) { nb[nnb] = c + N; w[nnb++] = fy[(z * N1 + y + 1) * N + x]; }
+        if (dim == 3 && z < N - 1) { nb[nnb] = c + (long long)N * N; w[nnb++] = fz[((z + 1) * N + y) * N + x]; }
+        ptr[c] = (int32_t)pos;
+        double diag = 1.0;
+        long long dpos = -1;
+        for (int t = 0; t < nnb; ++t) {
+            if (nb[t] < 0) { dpos = pos; col[pos++] = (int32_t)c; continue; }
+            const double wf = w[t];
+            diag = diag + ((wf > 0.0 ? wf : 0.0) + 0.1);
+            col[pos] = (int32_t)nb[t];
+            val[pos++] = (wf < 0.0 ? wf : 0.0) - 0.1;
+        }
+        val[dpos] = diag;
+    }
+    ptr[n] = (int32_t)pos;
+    return ORC_OK;
+}
+
 /* Adjoint gradient (chain rule of the assembly above).  With A u = f and
  * A lam = u - u*, dL/dk_f = -(lam_i - lam_j)(u_i - u_j) for an interior face,
  * dL/dA_ii = -lam_i u_i for the Dirichlet term 2/rho_i.  rho = exp(theta):
@@ -791,6 +833,96 @@ int orc_pcg(ohier *h, const double *sys_val, const double *f, double *u, double 
         for (int32_t i = 0; i < n; ++i) q[i] = f[i] - q[i];
         *relres = sqrt(dot(n, q, q)) / nf;
     }
+    return status;
+}
+
+/* Right-preconditioned BiCGStab (the Krylov solver of Sec. 4), one V-cycle
+ * per preconditioner application, x_0 = 0, shadow residual r^ = r_0 = f:
+ *   rho = (r^, r); beta = (rho / rho_old)(alpha / omega); p = r + beta (p - omega v);
+ *   p^ = M p; v = A p^; alpha = rho / (r^, v); s = r - alpha v;
+ *   if |s|/|f| <= tol: x += alpha p^ (half step) and confirm;
+ *   s^ = M s; t = A s^; omega = (t, s) / (t, t);
+ *   x += alpha p^ + omega s^; r = s - omega t.
+ * Convergence (recurrence |r|/|f| <= tol, or |s| at the half step) is
+ * confirmed by the true residual; if that misses tol, r is replaced by it
+ * (at most twice) and the iteration goes on.  Breakdown: rho, (r^, v) or
+ * (t, t) zero or not finite, or omega = 0. */
+int orc_bicgstab(ohier *h, const double *sys_val, const double *f, double *u, double tol, int maxiter,
+                 int *iters, double *relres) {
+    olevel *L = &h->lev[0];
+    int32_t n = L->A.nrows;
+    const double *av = sys_val ? sys_val : L->A.val;
+    double *r = (double *)xcalloc((size_t)n, sizeof(double));
+    double *rh = (double *)xcalloc((size_t)n, sizeof(double));
+    double *p = (double *)xcalloc((size_t)n, sizeof(double));
+    double *v = (double *)xcalloc((size_t)n, sizeof(double));
+    double *ph = (double *)xcalloc((size_t)n, sizeof(double));
+    double *sv = (double *)xcalloc((size_t)n, sizeof(double));
+    double *sh = (double *)xcalloc((size_t)n, sizeof(double));
+    double *t = (double *)xcalloc((size_t)n, sizeof(double));
+    for (int32_t i = 0; i < n; ++i) { u[i] = 0.0; r[i] = f[i]; rh[i] = f[i]; }
+    double nf = sqrt(dot(n, f, f));
+    *iters = 0;
+    *relres = 0.0;
+    int status = ORC_NOT_CONVERGED;
+    if (nf == 0.0) { status = ORC_OK; goto done; }
+    {
+        double rho_old = 1.0, alpha = 1.0, omega = 1.0;
+        int replacements = 0;
+        for (int it = 1; it <= maxiter; ++it) {
+            *iters = it;
+            double rho = dot(n, rh, r);
+            if (!(rho != 0.0) || !isfinite(rho)) { status = ORC_ERR_BREAKDOWN; break; }
+            double beta = (rho / rho_old) * (alpha / omega);
+            for (int32_t i = 0; i < n; ++i) p[i] = fma(beta, fma(-omega, v[i], p[i]), r[i]);
+            orc_vcycle(h, p, ph);
+            spmv(&L->A, av, ph, v);
+            double rv = dot(n, rh, v);
+            if (!(rv != 0.0) || !isfinite(rv)) { status = ORC_ERR_BREAKDOWN; break; }
+            alpha = rho / rv;
+            rho_old = rho;
+            for (int32_t i = 0; i < n; ++i) sv[i] = fma(-alpha, v[i], r[i]);
+            int conv = 0;
+            double sres = sqrt(dot(n, sv, sv)) / nf;
+            if (sres <= tol) {
+                for (int32_t i = 0; i < n; ++i) u[i] = fma(alpha, ph[i], u[i]);
+                for (int32_t i = 0; i < n; ++i) r[i] = sv[i];
+                conv = 1;
+            } else {
+                orc_vcycle(h, sv, sh);
+                spmv(&L->A, av, sh, t);
+                double ts = dot(n, t, sv), tt = dot(n, t, t);
+                if (!(tt != 0.0) || !isfinite(tt)) { status = ORC_ERR_BREAKDOWN; break; }
+                omega = ts / tt;
+                if (!(omega != 0.0) || !isfinite(omega)) { status = ORC_ERR_BREAKDOWN; break; }
+                for (int32_t i = 0; i < n; ++i) {
+                    u[i] = fma(omega, sh[i], fma(alpha, ph[i], u[i]));
+                    r[i] = fma(-omega, t[i], sv[i]);
+                }
+                double res = sqrt(dot(n, r, r)) / nf;
+                *relres = res;
+                conv = res <= tol;
+            }
+            if (conv) {
+                spmv(&L->A, av, u, t);
+                for (int32_t i = 0; i < n; ++i) t[i] = f[i] - t[i];
+                double tres = sqrt(dot(n, t, t)) / nf;
+                *relres = tres;
+                if (tres <= tol) { status = ORC_OK; break; }
+                if (replacements >= 2) { status = ORC_NOT_CONVERGED; break; }
+                ++replacements;
+                for (int32_t i = 0; i < n; ++i) r[i] = t[i];
+            }
+        }
+    }
+    {
+        double *q = t;
+        spmv(&L->A, av, u, q);
+        for (int32_t i = 0; i < n; ++i) q[i] = f[i] - q[i];
+        *relres = sqrt(dot(n, q, q)) / nf;
+    }
+done:
+    free(r); free(rh); free(p); free(v); free(ph); free(sv); free(sh); free(t);
     return status;
 }
 

@@ -115,3 +115,31 @@ def random_spd_like(n: int, density_: float, seed: int) -> tuple[np.ndarray, np.
         val.extend(M[i, nz].tolist())
         ptr.append(len(col))
     return np.asarray(ptr, np.int32), np.asarray(col, np.int32), np.asarray(val, np.float64)
+
+
+# ---------------------------------------------------------------- level-set transport stand-in
+LEVELSET_COURANT = 2.0
+
+
+def levelset_faces(dim: int, N: int, k: int, T: int, courant: float = LEVELSET_COURANT):
+    """Face-normal velocities of the level-set stand-in (Sec. 4, eq. 5) at step k.
+
+    A divergence-free rotating flow, in the x-y plane (2D) or the x-z plane
+    (3D): u_x = -sin(pi x) cos(pi w), u_w = cos(pi x) sin(pi w), with w = y or z,
+    scaled by s(t) = 1 + 0.5 sin(2 pi k / T) and by the Courant number, and
+    sampled at the face centres.  It has no normal flow through the walls.
+    Layouts (x fastest): fx[(z N + y)(N + 1) + x_face],
+    fy[(z (N + 1) + y_face) N + x], fz[(z_face N + y) N + x]; in 2D z = 0 and
+    fz is empty."""
+    c = (np.arange(N, dtype=np.float64) + 0.5) / N
+    e = np.arange(N + 1, dtype=np.float64) / N
+    s = courant * (1.0 + 0.5 * np.sin(2.0 * np.pi * k / T))
+    if dim == 2:
+        fx = -np.sin(np.pi * e)[None, :] * np.cos(np.pi * c)[:, None]           # [y, x_face]
+        fy = np.cos(np.pi * c)[None, :] * np.sin(np.pi * e)[:, None]            # [y_face, x]
+        return (s * fx).reshape(-1), (s * fy).reshape(-1), np.zeros(0)
+    ones = np.ones(N)
+    fx = -np.sin(np.pi * e)[None, None, :] * np.cos(np.pi * c)[:, None, None] * ones[None, :, None]  # [z, y, xf]
+    fy = np.zeros((N, N + 1, N))                                                                        # [z, yf, x]
+    fz = np.cos(np.pi * c)[None, None, :] * np.sin(np.pi * e)[:, None, None] * ones[None, :, None]   # [zf, y, x]
+    return (s * fx).reshape(-1), (s * fy).reshape(-1), (s * fz).reshape(-1)

@@ -530,3 +530,78 @@ def test_preventive_rebuild_rules():
         if r.rebuilt:
             base = r.iters
     assert any(r.rebuilt for r in grow[1:])
+
+
+# ---------------------------------------------------------------- level-set stand-in and BiCGStab (Sec. 4)
+@pytest.mark.parametrize("dim,N", [(2, 9), (3, 6)])
+def test_levelset_assembly_identities(dim, N):
+    """Every entry is pinned by three identities of the upwind scheme: for a
+    face with outward velocity w from c to j, A_cj - A_jc = w and
+    A_cj + A_jc = -|w| - 0.2; and the row sum is 1 + (net outflow of c)."""
+    fx, fy, fz = I.levelset_faces(dim, N, 3, 10)
+    ptr, col, val = O.levelset_assemble(dim, N, fx, fy, fz)
+    n = N ** dim
+    A = O.CSR(ptr, col, val, n).dense()
+    assert not np.allclose(A, A.T)
+    # outward face velocities from the face arrays
+    W = np.zeros((n, n))
+    idx = lambda x, y, z: x + N * y + N * N * z  # noqa: E731
+    for z in range(N if dim == 3 else 1):
+        for y in range(N):
+            for x in range(N):
+                c = idx(x, y, z)
+                if x < N - 1:
+                    w = fx[(z * N + y) * (N + 1) + x + 1]
+                    W[c, idx(x + 1, y, z)] = w
+                    W[idx(x + 1, y, z), c] = -w
+                if y < N - 1:
+                    w = fy[(z * (N + 1) + y + 1) * N + x]
+                    W[c, idx(x, y + 1, z)] = w
+                    W[idx(x, y + 1, z), c] = -w
+                if dim == 3 and z < N - 1:
+                    w = fz[((z + 1) * N + y) * N + x]
+                    W[c, idx(x, y, z + 1)] = w
+                    W[idx(x, y, z + 1), c] = -w
+    face = np.zeros((n, n), bool)
+    for i in range(n):
+        for p in range(ptr[i], ptr[i + 1]):
+            if col[p] != i:
+                face[i, col[p]] = True
+    # A_cj - A_jc = min(w,0) - min(-w,0) = w  (w outward from c toward j)
+    assert np.allclose((A - A.T)[face], W[face], atol=1e-13)
+    assert np.allclose((A + A.T)[face], -np.abs(W[face]) - 0.2, atol=1e-13)
+    assert np.allclose(A.sum(axis=1), 1.0 + W.sum(axis=1), atol=1e-12)
+
+
+def test_bicgstab_against_direct_solve_and_exact_preconditioner():
+    dim, N = 3, 10
+    fx, fy, fz = I.levelset_faces(dim, N, 2, 10)
+    ptr, col, val = O.levelset_assemble(dim, N, fx, fy, fz)
+    f = I.rhs(N ** 3)
+    A = O.CSR(ptr, col, val, N ** 3).dense()
+    H = O.Hierarchy(ptr, col, val, O.Params(coarse_enough=30))
+    assert H.nlevels >= 2
+    u, it, rr, st = H.bicgstab(f, 1e-10)
+    assert st == O.OK and 0 < it < 30 and rr <= 1e-10
+    assert np.allclose(u, np.linalg.solve(A, f), rtol=1e-8, atol=1e-10)
+    # one level: the preconditioner is A^-1, one half step solves the system
+    H1 = O.Hierarchy(ptr, col, val, O.Params(coarse_enough=10 ** 4))
+    u, it, rr, st = H1.bicgstab(f, 1e-10)
+    assert st == O.OK and it == 1
+    # zero right-hand side
+    u, it, rr, st = H.bicgstab(np.zeros(N ** 3))
+    assert st == O.OK and it == 0 and np.all(u == 0)
+
+
+def test_levelset_partial_reuse_keeps_iterations():
+    """Sec. 4, Table 2 (level set): partial reuse keeps the iteration count of
+    the no-reuse strategy on a slowly changing transport matrix."""
+    dim, N, T = 3, 12, 6
+    vals = [O.levelset_assemble(dim, N, *I.levelset_faces(dim, N, k, T))[2] for k in range(T)]
+    ptr, col, _ = O.levelset_assemble(dim, N, *I.levelset_faces(dim, N, 0, T))
+    f = I.rhs(N ** 3)
+    prm = O.Params(coarse_enough=30)
+    full = O.run_time_steps(ptr, col, vals, f, O.MODE_FULL_REBUILD, prm, solver="bicgstab")
+    part = O.run_time_steps(ptr, col, vals, f, O.MODE_PARTIAL, prm, solver="bicgstab")
+    assert all(r.status == O.OK for r in full + part)
+    assert sum(r.iters for r in part) <= 1.5 * sum(r.iters for r in full)
