@@ -50,6 +50,7 @@ typedef enum {
 enum { AMG_SMOOTHER_SPAI0 = 0, AMG_SMOOTHER_JACOBI = 1 };
 enum { AMG_PREC_FP64 = 0, AMG_PREC_MIXED = 1 };
 enum { AMG_MODE_PARTIAL = 0, AMG_MODE_FULL_REBUILD = 1, AMG_MODE_FULL_REUSE = 2 };
+enum { AMG_SOLVER_CG = 0, AMG_SOLVER_BICGSTAB = 1 };
 
 typedef struct {
     double theta;          /* strength threshold on the finest level (0.08) */
@@ -73,10 +74,14 @@ typedef struct {
      * full setup. */
     int32_t rebuild_every;
     double rebuild_iter_growth;
+    /* Krylov solver of amg_solve (Sec. 4): AMG_SOLVER_CG for the symmetric
+     * pressure systems, AMG_SOLVER_BICGSTAB (right-preconditioned) for the
+     * nonsymmetric level-set systems.  (CG) */
+    int32_t solver;
 } amg_params;
 
 typedef struct {
-    int32_t iters;         /* CG iterations of the last solve */
+    int32_t iters;         /* Krylov iterations of the last solve */
     int32_t rebuilt;       /* 1 if the last amg_step ran a full setup */
     int32_t nlevels;       /* levels of the current hierarchy */
     int32_t status;        /* status of the last solve */
@@ -116,10 +121,17 @@ amg_status amg_partial_rebuild(amg_ctx *ctx, const double *d_val);
 amg_status amg_step(amg_ctx *ctx, int32_t n, int32_t nnz, const int32_t *d_ptr,
                     const int32_t *d_col, const double *d_val, amg_info *info);
 
-/* Solve A u = f with CG preconditioned by one V-cycle per iteration (Sec. 2,
- * Alg. 2), u_0 = 0, to |f - A u| / |f| <= tol or params.maxiter iterations.
- * A is the system matrix of the last setup / step.  d_f, d_u: n doubles.
- * Returns AMG_OK, AMG_NOT_CONVERGED or an error; info may be NULL. */
+/* Solve A u = f with a Krylov solver preconditioned by one V-cycle per
+ * application (Sec. 2, Alg. 2), u_0 = 0, to |f - A u| / |f| <= tol or
+ * params.maxiter iterations.  params.solver picks CG (one V-cycle per
+ * iteration) or right-preconditioned BiCGStab (two per iteration; converged
+ * at the half step when |s| / |f| <= tol).  Convergence reported by the
+ * recurrence is confirmed on the true residual, which replaces the recurrence
+ * residual (at most twice) when it is above tol.  A is the system matrix of
+ * the last setup / step.  d_f, d_u: n doubles.  Returns AMG_OK,
+ * AMG_NOT_CONVERGED, AMG_ERR_BREAKDOWN (CG: p'Ap <= 0; BiCGStab: a zero or
+ * non-finite (r^, r), (r^, v), (t, t) or omega) or another error; info may
+ * be NULL. */
 amg_status amg_solve(amg_ctx *ctx, const double *d_f, double *d_u, double tol, amg_info *info);
 
 /* Apply one V-cycle z = B r from a zero initial guess (Alg. 2). */
@@ -184,6 +196,19 @@ int64_t amg_poisson_nnz(int32_t dim, int32_t N);
 amg_status amg_poisson_pattern(int32_t dim, int32_t N, int32_t *d_ptr, int32_t *d_col, void *cuda_stream);
 amg_status amg_poisson_values(int32_t dim, int32_t N, int32_t dirichlet_top, const double *d_rho,
                               const int32_t *d_ptr, double *d_val, void *cuda_stream);
+/* Level-set transport stand-in (Sec. 4, eq. 5): an implicit upwind
+ * convection-diffusion step on the same pattern as amg_poisson_pattern (a
+ * nonsymmetric M-matrix).  Row c, with w_f the outward flux through face f
+ * (+velocity on the high face, -velocity on the low face, walls excluded):
+ * A_cj = min(w_f, 0) - 0.1, A_cc = 1 + sum over faces in column order of
+ * (max(w_f, 0) + 0.1).  Face velocities (device, FP64, x fastest):
+ * d_fx[(z N + y)(N + 1) + x_face], d_fy[(z (N + 1) + y_face) N + x],
+ * d_fz[(z_face N + y) N + x] (dim 3; ignored and may be NULL in 2D, where
+ * z = 0).  d_val: nnz doubles in the order of amg_poisson_pattern's columns.
+ * Asynchronous on cuda_stream. */
+amg_status amg_levelset_values(int32_t dim, int32_t N, const double *d_fx, const double *d_fy,
+                               const double *d_fz, const int32_t *d_ptr, double *d_val,
+                               void *cuda_stream);
 /* Adjoint chain rule for theta = log rho: given u (A u = f) and lam
  * (A lam = dL/du), grad = dL/dtheta per cell (n doubles). */
 amg_status amg_poisson_grad_theta(int32_t dim, int32_t N, int32_t dirichlet_top, const double *d_rho,

@@ -27,6 +27,7 @@ STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", -1: "ERR_ARG", -2: "ERR_STATE", -3:
 SMOOTHER_SPAI0, SMOOTHER_JACOBI = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 MODE_PARTIAL, MODE_FULL_REBUILD, MODE_FULL_REUSE = 0, 1, 2
+SOLVER_CG, SOLVER_BICGSTAB = 0, 1
 
 # every entry point declared in include/amgpr.h
 EXPORTS = [
@@ -34,7 +35,7 @@ EXPORTS = [
     "amg_step", "amg_solve", "amg_apply_vcycle", "amg_step_solve_host", "amg_num_levels", "amg_level_sizes",
     "amg_export_csr", "amg_export_level_vec", "amg_export_coarse_lu", "amg_poisson_nnz", "amg_poisson_pattern",
     "amg_poisson_values", "amg_poisson_grad_theta", "amg_profile", "amg_profile_read", "amg_kernel_launches",
-    "amg_poisson_pattern_noalloc",
+    "amg_poisson_pattern_noalloc", "amg_levelset_values",
 ]
 PROF_SLOTS = ["cg_spmv", "smooth0_l0", "sweep_l0", "restrict_l0", "prolong_l0", "ap_l0", "rap_l0", "ingest", "lu",
               "inv", "cg_update", "cg_p", "dot", "coarse"]
@@ -48,6 +49,7 @@ class amg_params(ctypes.Structure):
         ("smoothed", ctypes.c_int32), ("precision", ctypes.c_int32), ("mode", ctypes.c_int32),
         ("reuse_iter_limit", ctypes.c_int32), ("maxiter", ctypes.c_int32),
         ("rebuild_every", ctypes.c_int32), ("rebuild_iter_growth", ctypes.c_double),
+        ("solver", ctypes.c_int32),
     ]
 
 
@@ -100,6 +102,7 @@ def lib():
                 "amg_profile_read": (_i32, [_vp, _i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
                 "amg_kernel_launches": (ctypes.c_int64, []),
                 "amg_poisson_pattern_noalloc": (_i32, [_i32, _i32, _vp, _vp, _vp]),
+                "amg_levelset_values": (_i32, [_i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -305,6 +308,20 @@ def poisson_values(dim: int, N: int, rho, ptr, dirichlet_top: bool = True, out=N
                                   _vp(_stream(stream)))
     if st != AMG_OK:
         raise AmgError(st, "amg_poisson_values failed")
+    return val
+
+
+def levelset_values(dim: int, N: int, fx, fy, fz, ptr, out=None, stream=None):
+    """Device values of the upwind convection-diffusion (level-set) matrix on
+    the pattern from poisson_pattern; fx, fy, fz are the face velocities (fz
+    is ignored in 2D)."""
+    import torch
+    val = out if out is not None else torch.empty(poisson_nnz(dim, N), dtype=torch.float64, device="cuda")
+    fz_p = _dptr(fz) if (dim == 3 or (fz is not None and fz.numel() > 0)) else 0
+    st = lib().amg_levelset_values(dim, N, _dptr(fx), _dptr(fy), fz_p, _dptr(ptr), _dptr(val),
+                                   _vp(_stream(stream)))
+    if st != AMG_OK:
+        raise AmgError(st, "amg_levelset_values failed")
     return val
 
 

@@ -62,6 +62,10 @@ struct amg_ctx {
     double *part_pq = nullptr, *part_rr = nullptr, *part_rz = nullptr, *part_rzo = nullptr, *part_tt = nullptr;
     CgState *cg = nullptr;
     CgState *h_cg = nullptr;  // pinned
+    // BiCGStab: r^, s, s^ (r, p, p^, v, t reuse cg_r, cg_p, cg_z, cg_q, cg_t)
+    double *bi_rh = nullptr, *bi_s = nullptr, *bi_sh = nullptr;
+    BiState *bi = nullptr;
+    BiState *h_bi = nullptr;  // pinned
     int *d_st = nullptr;
     int *h_st = nullptr;      // pinned
     // host-buffer staging
@@ -520,6 +524,13 @@ amg_status ensure_persistent(amg_ctx *ctx, int32_t n, int32_t nnz) {
     TRY(alloc(ctx, &ctx->cg, 1, true));
     // the reduction counters inside must start at zero; kernels leave them zero
     CK(cudaMemsetAsync(ctx->cg, 0, sizeof(CgState), ctx->s));
+    if (ctx->prm.solver == AMG_SOLVER_BICGSTAB) {
+        TRY(alloc(ctx, &ctx->bi_rh, (size_t)n, true));
+        TRY(alloc(ctx, &ctx->bi_s, (size_t)n, true));
+        TRY(alloc(ctx, &ctx->bi_sh, (size_t)n, true));
+        TRY(alloc(ctx, &ctx->bi, 1, true));
+        CK(cudaMemsetAsync(ctx->bi, 0, sizeof(BiState), ctx->s));
+    }
     TRY(alloc(ctx, &ctx->stage_val, (size_t)nnz, true));
     TRY(alloc(ctx, &ctx->stage_f, (size_t)n, true));
     TRY(alloc(ctx, &ctx->stage_u, (size_t)n, true));
@@ -884,8 +895,142 @@ amg_status finish_solve(amg_ctx *ctx, amg_info *info) {
     return st;
 }
 
+// ---------------------------------------------------------------- BiCGStab
+// Right-preconditioned BiCGStab (Sec. 4, the level-set systems): per
+// iteration p^ = B p and s^ = B s, one V-cycle each.  Vectors: r = cg_r,
+// p = cg_p, p^ = cg_z, v = cg_q, t = cg_t, with r^, s, s^ of their own.  The
+// second half of an iteration skips itself (state flag `skip`) when |s|
+// already meets the tolerance, and the true-residual check skips itself
+// unless the recurrence reports convergence.
+void enqueue_bi_prologue(amg_ctx *ctx, const double *f, double *u, double tol) {
+    launch_bi_init(ctx->n, f, u, ctx->cg_r, ctx->bi_rh, ctx->cg_p, ctx->cg_q, ctx->partial, ctx->bi, tol,
+                   ctx->prm.maxiter, ctx->s);
+}
+
+void enqueue_bi_iter(amg_ctx *ctx, const double *f, double *u, int use_h, cudaGraphConditionalHandle h) {
+    const int32_t n = ctx->n;
+    BiState *st = ctx->bi;
+    double *part = ctx->partial;
+    launch_bi_rho(n, ctx->bi_rh, ctx->cg_r, part, st, ctx->s);
+    launch_bi_p(n, ctx->cg_r, ctx->cg_q, ctx->cg_p, st, ctx->s);
+    vcycle(ctx, ctx->cg_p, ctx->cg_z, &st->done);
+    launch_bi_spmv_rv(n, ctx->fine_ptr, ctx->fine_col, ctx->A_sys, ctx->cg_z, ctx->cg_q, ctx->bi_rh, part, st, ctx->s);
+    launch_bi_s(n, ctx->cg_r, ctx->cg_q, ctx->bi_s, part, st, ctx->s);
+    launch_bi_half(n, ctx->cg_z, ctx->bi_s, u, ctx->cg_r, st, ctx->s);
+    vcycle(ctx, ctx->bi_s, ctx->bi_sh, &st->skip);
+    launch_bi_spmv_t(n, ctx->fine_ptr, ctx->fine_col, ctx->A_sys, ctx->bi_sh, ctx->bi_s, ctx->cg_t, part, st, ctx->s);
+    launch_bi_xr(n, ctx->cg_z, ctx->bi_sh, ctx->bi_s, ctx->cg_t, u, ctx->cg_r, part, st, ctx->s);
+    launch_bi_true(n, ctx->fine_ptr, ctx->fine_col, ctx->A_sys, f, u, ctx->cg_t, part, st, 0, ctx->s);
+    launch_bi_replace(n, ctx->cg_t, ctx->cg_r, st, ctx->s);
+    launch_bi_end(st, use_h, h, ctx->s);
+}
+
+void enqueue_bi_epilogue(amg_ctx *ctx, const double *f, double *u) {
+    launch_bi_true(ctx->n, ctx->fine_ptr, ctx->fine_col, ctx->A_sys, f, u, ctx->cg_t, ctx->partial, ctx->bi, 1,
+                   ctx->s);
+}
+
+// the whole BiCGStab solve as one graph: prologue, a WHILE node over one
+// iteration (its last kernel sets the loop condition), epilogue
+amg_status build_bi_graph(amg_ctx *ctx, double tol) {
+    drop_graph(ctx);
+    CK(cudaStreamSynchronize(ctx->s));
+    cudaStream_t user_s = ctx->s;
+    const double *f = ctx->cg_f;
+    double *u = ctx->cg_u;
+    const int64_t c0 = launch_total();
+    int64_t c1 = c0, c2 = c0;
+    CK(cudaStreamBeginCapture(ctx->s_cap_main, cudaStreamCaptureModeThreadLocal));
+    ctx->s = ctx->s_cap_main;
+    enqueue_bi_prologue(ctx, f, u, tol);
+    c1 = launch_total();
+    cudaGraphConditionalHandle h_loop = 0;
+    cudaGraphNode_t loop_node = nullptr;
+    cudaGraph_t body = nullptr;
+    cudaError_t e = add_conditional(ctx->s_cap_main, cudaGraphCondTypeWhile, 1, &h_loop, &loop_node, &body);
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(ctx->s_cap, body, nullptr, nullptr, 0,
+                                                            cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        ctx->s = ctx->s_cap;
+        enqueue_bi_iter(ctx, f, u, 1, h_loop);
+        c2 = launch_total();
+        ctx->s = ctx->s_cap_main;
+        cudaGraph_t tmp = nullptr;
+        e = cudaStreamEndCapture(ctx->s_cap, &tmp);
+    }
+    if (e == cudaSuccess)
+        e = cudaStreamUpdateCaptureDependencies(ctx->s_cap_main, &loop_node, nullptr, 1,
+                                                cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess) enqueue_bi_epilogue(ctx, f, u);
+    const int64_t c3 = launch_total();
+    add_launches(c0 - c3);
+    ctx->graph_pro = c1 - c0;
+    ctx->graph_body = c2 - c1;
+    ctx->graph_epi = c3 - c2;
+    ctx->graph_branch = 0;
+    ctx->s = user_s;
+    cudaGraph_t done_graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(ctx->s_cap_main, &done_graph);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) {
+        if (done_graph) cudaGraphDestroy(done_graph);
+        cudaGetLastError();
+        return set_err(ctx, AMG_ERR_CUDA, std::string("building the BiCGStab graph: ") + cudaGetErrorString(e));
+    }
+    ctx->graph = done_graph;
+    CK(cudaGraphInstantiate(&ctx->graph_exec, ctx->graph, 0));
+    ctx->graph_tol = tol;
+    ctx->graph_valid = true;
+    return AMG_OK;
+}
+
+amg_status finish_bi(amg_ctx *ctx, amg_info *info) {
+    CK(cudaMemcpyAsync(ctx->h_bi, ctx->bi, sizeof(BiState), cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    CK(cudaGetLastError());
+    const BiState &h = *ctx->h_bi;
+    amg_status st = (amg_status)h.status;
+    if (!h.done && st == AMG_OK) st = AMG_NOT_CONVERGED;
+    ctx->last_iters = h.iter;
+    ctx->last_status = st;
+    if (ctx->iters_after_full < 0 && st == AMG_OK) ctx->iters_after_full = h.iter;
+    if (info) {
+        info->iters = h.iter;
+        info->rel_resid = h.tres;
+        info->status = st;
+        info->rebuilt = ctx->last_rebuilt;
+        info->nlevels = ctx->nlev;
+    }
+    if (st == AMG_ERR_BREAKDOWN) set_err(ctx, st, "BiCGStab breakdown: a zero or non-finite scalar");
+    else if (st == AMG_NOT_CONVERGED) set_err(ctx, st, "BiCGStab reached maxiter");
+    return st;
+}
+
+amg_status solve_bi(amg_ctx *ctx, const double *f, double *u, double tol, amg_info *info) {
+    const int32_t n = ctx->n;
+    if (ctx->use_graph && !ctx->prof.on) {
+        if (!ctx->graph_valid || ctx->graph_tol != tol) TRY(build_bi_graph(ctx, tol));
+        CK(cudaMemcpyAsync(ctx->cg_f, f, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, ctx->s));
+        CK(cudaGraphLaunch(ctx->graph_exec, ctx->s));
+        CK(cudaMemcpyAsync(u, ctx->cg_u, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, ctx->s));
+        amg_status st = finish_bi(ctx, info);
+        add_launches(ctx->graph_pro + ctx->graph_epi + ctx->graph_body * (int64_t)ctx->h_bi->pad);
+        return st;
+    }
+    enqueue_bi_prologue(ctx, f, u, tol);
+    for (int it = 1; it <= ctx->prm.maxiter; ++it) {
+        enqueue_bi_iter(ctx, f, u, 0, 0);
+        CK(cudaMemcpyAsync(ctx->h_bi, ctx->bi, sizeof(BiState), cudaMemcpyDeviceToHost, ctx->s));
+        CK(cudaStreamSynchronize(ctx->s));
+        if (ctx->h_bi->done) break;
+    }
+    enqueue_bi_epilogue(ctx, f, u);
+    return finish_bi(ctx, info);
+}
+
 amg_status solve_impl(amg_ctx *ctx, const double *f, double *u, double tol, amg_info *info) {
     const int32_t n = ctx->n;
+    if (ctx->prm.solver == AMG_SOLVER_BICGSTAB) return solve_bi(ctx, f, u, tol, info);
     if (ctx->use_graph && !ctx->prof.on) {
         if (!ctx->graph_valid || ctx->graph_tol != tol) TRY(build_solve_graph(ctx, tol));
         CK(cudaMemcpyAsync(ctx->cg_f, f, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, ctx->s));
@@ -937,6 +1082,7 @@ amg_status amg_default_params(amg_params *prm) {
     prm->maxiter = 100;
     prm->rebuild_every = 0;
     prm->rebuild_iter_growth = 0.0;
+    prm->solver = AMG_SOLVER_CG;
     return AMG_OK;
 }
 
@@ -950,6 +1096,7 @@ amg_status amg_create(amg_ctx **out, const amg_params *prm, void *cuda_stream) {
         (p.smoother != AMG_SMOOTHER_SPAI0 && p.smoother != AMG_SMOOTHER_JACOBI) ||
         (p.precision != AMG_PREC_FP64 && p.precision != AMG_PREC_MIXED) || p.mode < 0 || p.mode > 2 ||
         p.rebuild_every < 0 || !(p.rebuild_iter_growth >= 0.0) ||
+        (p.solver != AMG_SOLVER_CG && p.solver != AMG_SOLVER_BICGSTAB) ||
         !(p.theta >= 0.0) || !std::isfinite(p.omega))
         return AMG_ERR_ARG;
     amg_ctx *ctx = new amg_ctx();
@@ -968,6 +1115,7 @@ amg_status amg_create(amg_ctx **out, const amg_params *prm, void *cuda_stream) {
         cudaStreamCreateWithFlags(&ctx->s_cap_main, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&ctx->s_cap_if, cudaStreamNonBlocking) != cudaSuccess ||
         cudaMallocHost(&ctx->h_cg, sizeof(CgState)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_bi, sizeof(BiState)) != cudaSuccess ||
         cudaMallocHost(&ctx->h_st, sizeof(int)) != cudaSuccess ||
         cudaMalloc(&ctx->d_st, sizeof(int)) != cudaSuccess) {
         amg_destroy(ctx);
@@ -992,6 +1140,7 @@ void amg_destroy(amg_ctx *ctx) {
     for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
     if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     if (ctx->h_cg) cudaFreeHost(ctx->h_cg);
+    if (ctx->h_bi) cudaFreeHost(ctx->h_bi);
     if (ctx->h_st) cudaFreeHost(ctx->h_st);
     if (ctx->d_st) cudaFree(ctx->d_st);
     delete ctx;
@@ -1241,6 +1390,16 @@ amg_status amg_poisson_values(int32_t dim, int32_t N, int32_t dirichlet_top, con
     if ((dim != 2 && dim != 3) || N < 1 || !d_rho || !d_ptr || !d_val) return AMG_ERR_ARG;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     launch_poisson_vals(dim, N, dirichlet_top, d_rho, d_ptr, d_val, s);
+    if (cudaGetLastError() != cudaSuccess) return AMG_ERR_CUDA;
+    return AMG_OK;
+}
+
+amg_status amg_levelset_values(int32_t dim, int32_t N, const double *d_fx, const double *d_fy, const double *d_fz,
+                               const int32_t *d_ptr, double *d_val, void *cuda_stream) {
+    if ((dim != 2 && dim != 3) || N < 1 || !d_fx || !d_fy || (dim == 3 && !d_fz) || !d_ptr || !d_val)
+        return AMG_ERR_ARG;
+    if (amg_poisson_nnz(dim, N) > INT32_MAX) return AMG_ERR_ARG;
+    launch_levelset_vals(dim, N, d_fx, d_fy, d_fz, d_ptr, d_val, (cudaStream_t)cuda_stream);
     if (cudaGetLastError() != cudaSuccess) return AMG_ERR_CUDA;
     return AMG_OK;
 }

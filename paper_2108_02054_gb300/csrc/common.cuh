@@ -38,6 +38,14 @@ struct CgState {
     int pad;  // loop bodies executed (graph path)
 };
 
+// Device-resident state of the BiCGStab iteration (same scheme as CgState).
+enum { BI_CTR_INIT = 0, BI_CTR_RHO, BI_CTR_RV, BI_CTR_SS, BI_CTR_T, BI_CTR_RR, BI_CTR_TRUE, BI_NCTR = 8 };
+struct BiState {
+    double rho, rho_old, alpha, omega, beta, rv, ts, tt, nf, res, sres, tres, tol;
+    unsigned ctr[BI_NCTR];
+    int iter, maxiter, done, status, replacements, half, need_true, copy_r, skip, pad;
+};
+
 template <class V>
 struct VecSet {
     V *u = nullptr, *f = nullptr, *r = nullptr, *t = nullptr;
@@ -97,6 +105,8 @@ void launch_poisson_vals(int dim, int N, int top, const double *rho, const int32
                          cudaStream_t s);
 void launch_poisson_grad(int dim, int N, int top, const double *rho, const double *u, const double *lam,
                          double *grad, cudaStream_t s);
+void launch_levelset_vals(int dim, int N, const double *fx, const double *fy, const double *fz, const int32_t *ptr,
+                          double *val, cudaStream_t s);
 
 void launch_check_pattern(int32_t n, const int32_t *ptr, const int32_t *col, int32_t *dia, int *st,
                           cudaStream_t s);
@@ -210,5 +220,24 @@ void launch_true_residual(int32_t n, const int32_t *ptr, const int32_t *col, con
 void launch_replace_r(int32_t n, const CgState *cg, const double *t, double *r, cudaStream_t s);
 void launch_cg_update_p(int32_t n, CgState *cg, const double *z, double *p, int use_h, cudaGraphConditionalHandle h,
                         cudaStream_t s);
+
+// BiCGStab (FP64), right-preconditioned; partial: 3 * cg_blocks(n) doubles
+void launch_bi_init(int32_t n, const double *f, double *x, double *r, double *rh, double *p, double *v,
+                    double *partial, BiState *st, double tol, int maxiter, cudaStream_t s);
+void launch_bi_rho(int32_t n, const double *rh, const double *r, double *partial, BiState *st, cudaStream_t s);
+void launch_bi_p(int32_t n, const double *r, const double *v, double *p, BiState *st, cudaStream_t s);
+void launch_bi_spmv_rv(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *ph,
+                       double *v, const double *rh, double *partial, BiState *st, cudaStream_t s);
+void launch_bi_s(int32_t n, const double *r, const double *v, double *sv, double *partial, BiState *st,
+                 cudaStream_t s);
+void launch_bi_half(int32_t n, const double *ph, const double *sv, double *x, double *r, BiState *st, cudaStream_t s);
+void launch_bi_spmv_t(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *sh,
+                      const double *sv, double *t, double *partial, BiState *st, cudaStream_t s);
+void launch_bi_xr(int32_t n, const double *ph, const double *sh, const double *sv, const double *t, double *x,
+                  double *r, double *partial, BiState *st, cudaStream_t s);
+void launch_bi_true(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *f,
+                    const double *x, double *t, double *partial, BiState *st, int force, cudaStream_t s);
+void launch_bi_replace(int32_t n, const double *t, double *r, BiState *st, cudaStream_t s);
+void launch_bi_end(BiState *st, int use_h, cudaGraphConditionalHandle h, cudaStream_t s);
 
 }  // namespace amgpr

@@ -193,6 +193,42 @@ __global__ void k_poisson_vals(int dim, int N, int64_t n, int top, const double 
     val[dpos] = diag;
 }
 
+// Level-set transport stand-in (Sec. 4, eq. 5): implicit upwind
+// convection-diffusion on the Poisson pattern.  With w_f the outward face
+// flux of cell c (the face velocity, sign-flipped on the low faces):
+// off-diagonal min(w_f, 0) - 0.1, diagonal 1 + sum over faces, in the
+// neighbour order, of (max(w_f, 0) + 0.1).  Face arrays, x fastest:
+// fx[(z N + y)(N + 1) + x_face], fy[(z (N + 1) + y_face) N + x],
+// fz[(z_face N + y) N + x].
+__global__ void k_levelset_vals(int dim, int N, int64_t n, const double *__restrict__ fx,
+                                const double *__restrict__ fy, const double *__restrict__ fz,
+                                const int32_t *__restrict__ ptr, double *__restrict__ val) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    int64_t x, y, z;
+    cell_coords(dim, N, c, x, y, z);
+    const int64_t N1 = N + 1;
+    double w[7];
+    int nnb = 0, dslot = 0;
+    if (dim == 3 && z > 0) w[nnb++] = -fz[(z * N + y) * N + x];
+    if (y > 0) w[nnb++] = -fy[(z * N1 + y) * N + x];
+    if (x > 0) w[nnb++] = -fx[(z * N + y) * N1 + x];
+    dslot = nnb;
+    w[nnb++] = 0.0;
+    if (x < N - 1) w[nnb++] = fx[(z * N + y) * N1 + x + 1];
+    if (y < N - 1) w[nnb++] = fy[(z * N1 + y + 1) * N + x];
+    if (dim == 3 && z < N - 1) w[nnb++] = fz[((z + 1) * N + y) * N + x];
+    double diag = 1.0;
+    const int32_t p0 = ptr[c];
+    for (int t = 0; t < nnb; ++t) {
+        if (t == dslot) continue;
+        const double wf = w[t];
+        diag = diag + ((wf > 0.0 ? wf : 0.0) + 0.1);
+        val[p0 + t] = (wf < 0.0 ? wf : 0.0) - 0.1;
+    }
+    val[p0 + dslot] = diag;
+}
+
 // dL/dtheta for theta = log rho, gathered per cell (no atomics): every face
 // of cell c contributes dL/dk_f * dk_f/dtheta_c with
 // dL/dk_f = -(lam_c - lam_j)(u_c - u_j), dk_f/dtheta_c = -2 rho_c/(rho_c + rho_j)^2;
@@ -798,6 +834,13 @@ void launch_poisson_grad(int dim, int N, int top, const double *rho, const doubl
     int64_t n = dim == 2 ? (int64_t)N * N : (int64_t)N * N * N;
     count_launch();
     k_poisson_grad<<<nblocks(n), kThreads, 0, s>>>(dim, N, n, top, rho, u, lam, grad);
+}
+
+void launch_levelset_vals(int dim, int N, const double *fx, const double *fy, const double *fz, const int32_t *ptr,
+                          double *val, cudaStream_t s) {
+    int64_t n = dim == 2 ? (int64_t)N * N : (int64_t)N * N * N;
+    count_launch();
+    k_levelset_vals<<<nblocks(n), kThreads, 0, s>>>(dim, N, n, fx, fy, fz, ptr, val);
 }
 
 void launch_check_pattern(int32_t n, const int32_t *ptr, const int32_t *col, int32_t *dia, int *st,

@@ -898,6 +898,246 @@ __global__ void k_cg_update_p(int32_t n, CgState *cg, const double *__restrict__
     }
 }
 
+// ------------------------------------------------------------------ BiCGStab (FP64)
+// Right-preconditioned BiCGStab (the Krylov solver of Sec. 4) with the same
+// device-resident control as CG: every kernel returns at once when the state
+// says done; scalars are formed by the last block of the producing kernel.
+
+// two sums published together; the last block returns both totals
+__device__ bool bi_reduce2(double a, double b, double *pa, double *pb, unsigned *counter, double *ta, double *tb) {
+    a = block_sum(a);
+    b = block_sum(b);
+    if (threadIdx.x == 0) {
+        pa[blockIdx.x] = a;
+        pb[blockIdx.x] = b;
+    }
+    if (!cg_last_block(counter)) return false;
+    const double sa = cg_sum_partials(pa, gridDim.x);
+    const double sb = cg_sum_partials(pb, gridDim.x);
+    if (threadIdx.x == 0) {
+        *ta = sa;
+        *tb = sb;
+        *counter = 0u;
+    }
+    return true;
+}
+
+// x = 0, r = r^ = f, p = v = 0; the last block initialises the state from |f|
+__global__ void k_bi_init(int32_t n, const double *__restrict__ f, double *__restrict__ x, double *__restrict__ r,
+                          double *__restrict__ rh, double *__restrict__ p, double *__restrict__ v,
+                          double *__restrict__ partial, BiState *st, double tol, int maxiter) {
+    double s = 0.0;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double fi = f[i];
+        x[i] = 0.0;
+        r[i] = fi;
+        rh[i] = fi;
+        p[i] = 0.0;
+        v[i] = 0.0;
+        s = fma(fi, fi, s);
+    }
+    double ff = 0.0;
+    if (cg_reduce(s, partial, &st->ctr[BI_CTR_INIT], &ff) && threadIdx.x == 0) {
+        st->nf = sqrt(ff);
+        st->tol = tol;
+        st->maxiter = maxiter;
+        st->done = (st->nf == 0.0) || maxiter <= 0;
+        st->status = (maxiter <= 0 && st->nf != 0.0) ? AMG_NOT_CONVERGED : AMG_OK;
+        st->rho_old = st->alpha = st->omega = 1.0;
+        st->rho = st->beta = st->rv = st->ts = st->tt = st->res = st->sres = st->tres = 0.0;
+        st->iter = st->replacements = st->half = st->need_true = st->copy_r = st->pad = 0;
+        st->skip = st->done;
+    }
+}
+
+// rho = (r^, r); beta = (rho / rho_old)(alpha / omega)
+__global__ void k_bi_rho(int32_t n, const double *__restrict__ rh, const double *__restrict__ r,
+                         double *__restrict__ partial, BiState *st) {
+    if (st->done) return;
+    double d = 0.0;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) d = fma(rh[i], r[i], d);
+    double rho = 0.0;
+    if (cg_reduce(d, partial, &st->ctr[BI_CTR_RHO], &rho) && threadIdx.x == 0) {
+        st->iter += 1;
+        if (!(rho != 0.0) || !isfinite(rho)) {
+            st->status = AMG_ERR_BREAKDOWN;
+            st->done = st->skip = 1;
+        } else {
+            st->rho = rho;
+            st->beta = (rho / st->rho_old) * (st->alpha / st->omega);
+        }
+    }
+}
+
+// p = r + beta (p - omega v)
+__global__ void k_bi_p(int32_t n, const double *__restrict__ r, const double *__restrict__ v, double *__restrict__ p,
+                       const BiState *st) {
+    if (st->done) return;
+    const double beta = st->beta, omega = st->omega;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        p[i] = fma(beta, fma(-omega, v[i], p[i]), r[i]);
+}
+
+// v = A p^, (r^, v); alpha = rho / (r^, v)
+__global__ void k_bi_spmv_rv(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                             const double *__restrict__ val, const double *__restrict__ ph, double *__restrict__ v,
+                             const double *__restrict__ rh, double *__restrict__ partial, BiState *st) {
+    if (st->done) return;
+    double d = 0.0;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int32_t e = ptr[i]; e < ptr[i + 1]; ++e) s = fma(val[e], ph[col[e]], s);
+        v[i] = s;
+        d = fma(rh[i], s, d);
+    }
+    double rv = 0.0;
+    if (cg_reduce(d, partial, &st->ctr[BI_CTR_RV], &rv) && threadIdx.x == 0) {
+        st->rv = rv;
+        if (!(rv != 0.0) || !isfinite(rv)) {
+            st->status = AMG_ERR_BREAKDOWN;
+            st->done = st->skip = 1;
+        } else {
+            st->alpha = st->rho / rv;
+            st->rho_old = st->rho;
+        }
+    }
+}
+
+// s = r - alpha v and |s|: converged at the half step when |s|/|f| <= tol
+__global__ void k_bi_s(int32_t n, const double *__restrict__ r, const double *__restrict__ v, double *__restrict__ sv,
+                       double *__restrict__ partial, BiState *st) {
+    if (st->done) return;
+    const double alpha = st->alpha;
+    double d = 0.0;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double si = fma(-alpha, v[i], r[i]);
+        sv[i] = si;
+        d = fma(si, si, d);
+    }
+    double ss = 0.0;
+    if (cg_reduce(d, partial, &st->ctr[BI_CTR_SS], &ss) && threadIdx.x == 0) {
+        st->sres = sqrt(ss) / st->nf;
+        st->half = st->sres <= st->tol;
+        st->need_true = st->half;
+        st->skip = st->half;
+    }
+}
+
+// half step: x += alpha p^, r = s
+__global__ void k_bi_half(int32_t n, const double *__restrict__ ph, const double *__restrict__ sv,
+                          double *__restrict__ x, double *__restrict__ r, const BiState *st) {
+    if (st->done || !st->half) return;
+    const double alpha = st->alpha;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        x[i] = fma(alpha, ph[i], x[i]);
+        r[i] = sv[i];
+    }
+}
+
+// t = A s^, (t, s), (t, t); omega = (t, s) / (t, t)
+__global__ void k_bi_spmv_t(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                            const double *__restrict__ val, const double *__restrict__ sh,
+                            const double *__restrict__ sv, double *__restrict__ t, double *__restrict__ partial,
+                            BiState *st) {
+    if (st->skip) return;
+    double a = 0.0, b = 0.0;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int32_t e = ptr[i]; e < ptr[i + 1]; ++e) s = fma(val[e], sh[col[e]], s);
+        t[i] = s;
+        a = fma(s, sv[i], a);
+        b = fma(s, s, b);
+    }
+    const int nb = gridDim.x;
+    double ts = 0.0, tt = 0.0;
+    if (bi_reduce2(a, b, partial, partial + nb, &st->ctr[BI_CTR_T], &ts, &tt) && threadIdx.x == 0) {
+        st->ts = ts;
+        st->tt = tt;
+        const double omega = ts / tt;
+        if (!(tt != 0.0) || !isfinite(tt) || !(omega != 0.0) || !isfinite(omega)) {
+            st->status = AMG_ERR_BREAKDOWN;
+            st->done = st->skip = 1;
+        } else {
+            st->omega = omega;
+        }
+    }
+}
+
+// x += alpha p^ + omega s^, r = s - omega t, |r|
+__global__ void k_bi_xr(int32_t n, const double *__restrict__ ph, const double *__restrict__ sh,
+                        const double *__restrict__ sv, const double *__restrict__ t, double *__restrict__ x,
+                        double *__restrict__ r, double *__restrict__ partial, BiState *st) {
+    if (st->skip) return;
+    const double alpha = st->alpha, omega = st->omega;
+    double d = 0.0;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        x[i] = fma(omega, sh[i], fma(alpha, ph[i], x[i]));
+        const double ri = fma(-omega, t[i], sv[i]);
+        r[i] = ri;
+        d = fma(ri, ri, d);
+    }
+    double rr = 0.0;
+    if (cg_reduce(d, partial, &st->ctr[BI_CTR_RR], &rr) && threadIdx.x == 0) {
+        st->res = sqrt(rr) / st->nf;
+        st->need_true = st->res <= st->tol;
+    }
+}
+
+// the true residual when the recurrence (or the half step) reports
+// convergence: accept, or replace r by it (twice at most); with force, the
+// final relative residual
+__global__ void k_bi_true(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                          const double *__restrict__ val, const double *__restrict__ f, const double *__restrict__ x,
+                          double *__restrict__ t, double *__restrict__ partial, BiState *st, int force) {
+    if (!force && (st->done || !st->need_true)) return;
+    double d = 0.0;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int32_t e = ptr[i]; e < ptr[i + 1]; ++e) s = fma(val[e], x[col[e]], s);
+        const double ti = f[i] - s;
+        t[i] = ti;
+        d = fma(ti, ti, d);
+    }
+    double tt = 0.0;
+    if (cg_reduce(d, partial, &st->ctr[BI_CTR_TRUE], &tt) && threadIdx.x == 0) {
+        st->tres = st->nf > 0.0 ? sqrt(tt) / st->nf : 0.0;
+        if (!force) {
+            if (st->tres <= st->tol) {
+                st->done = 1;
+                st->status = AMG_OK;
+            } else if (st->replacements >= 2) {
+                st->done = 1;
+                st->status = AMG_NOT_CONVERGED;
+            } else {
+                st->replacements += 1;
+                st->copy_r = 1;
+            }
+        }
+    }
+}
+
+__global__ void k_bi_replace(int32_t n, const double *__restrict__ t, double *__restrict__ r, const BiState *st) {
+    if (st->done || !st->copy_r) return;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) r[i] = t[i];
+}
+
+// end of an iteration: count it, clear the per-iteration flags, stop at
+// maxiter (and, in the graph, keep the while loop going; hard cap maxiter + 4
+// bodies)
+__global__ void k_bi_end(BiState *st, int use_h, cudaGraphConditionalHandle h) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    st->pad += 1;  // bodies run (the graph's launch count)
+    if (!st->done) {
+        if (st->iter >= st->maxiter || st->pad > st->maxiter + 4) {
+            st->done = 1;
+            st->status = AMG_NOT_CONVERGED;
+        }
+    }
+    st->half = st->need_true = st->copy_r = 0;
+    st->skip = st->done;
+    if (use_h) cudaGraphSetConditional(h, st->done ? 0u : 1u);
+}
+
 }  // namespace
 
 // ======================================================================= launchers
@@ -1139,6 +1379,58 @@ void launch_cg_update_p(int32_t n, CgState *cg, const double *z, double *p, int 
                         cudaStream_t s) {
     count_launch();
     k_cg_update_p<<<cg_blocks(n), kCgThreads, 0, s>>>(n, cg, z, p, use_h, h);
+}
+
+
+void launch_bi_init(int32_t n, const double *f, double *x, double *r, double *rh, double *p, double *v,
+                    double *partial, BiState *st, double tol, int maxiter, cudaStream_t s) {
+    count_launch();
+    k_bi_init<<<cg_blocks(n), kCgThreads, 0, s>>>(n, f, x, r, rh, p, v, partial, st, tol, maxiter);
+}
+void launch_bi_rho(int32_t n, const double *rh, const double *r, double *partial, BiState *st, cudaStream_t s) {
+    count_launch();
+    k_bi_rho<<<cg_blocks(n), kCgThreads, 0, s>>>(n, rh, r, partial, st);
+}
+void launch_bi_p(int32_t n, const double *r, const double *v, double *p, BiState *st, cudaStream_t s) {
+    count_launch();
+    k_bi_p<<<cg_blocks(n), kCgThreads, 0, s>>>(n, r, v, p, st);
+}
+void launch_bi_spmv_rv(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *ph,
+                       double *v, const double *rh, double *partial, BiState *st, cudaStream_t s) {
+    count_launch();
+    k_bi_spmv_rv<<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, col, val, ph, v, rh, partial, st);
+}
+void launch_bi_s(int32_t n, const double *r, const double *v, double *sv, double *partial, BiState *st,
+                 cudaStream_t s) {
+    count_launch();
+    k_bi_s<<<cg_blocks(n), kCgThreads, 0, s>>>(n, r, v, sv, partial, st);
+}
+void launch_bi_half(int32_t n, const double *ph, const double *sv, double *x, double *r, BiState *st, cudaStream_t s) {
+    count_launch();
+    k_bi_half<<<cg_blocks(n), kCgThreads, 0, s>>>(n, ph, sv, x, r, st);
+}
+void launch_bi_spmv_t(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *sh,
+                      const double *sv, double *t, double *partial, BiState *st, cudaStream_t s) {
+    count_launch();
+    k_bi_spmv_t<<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, col, val, sh, sv, t, partial, st);
+}
+void launch_bi_xr(int32_t n, const double *ph, const double *sh, const double *sv, const double *t, double *x,
+                  double *r, double *partial, BiState *st, cudaStream_t s) {
+    count_launch();
+    k_bi_xr<<<cg_blocks(n), kCgThreads, 0, s>>>(n, ph, sh, sv, t, x, r, partial, st);
+}
+void launch_bi_true(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *f,
+                    const double *x, double *t, double *partial, BiState *st, int force, cudaStream_t s) {
+    count_launch();
+    k_bi_true<<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, col, val, f, x, t, partial, st, force);
+}
+void launch_bi_replace(int32_t n, const double *t, double *r, BiState *st, cudaStream_t s) {
+    count_launch();
+    k_bi_replace<<<cg_blocks(n), kCgThreads, 0, s>>>(n, t, r, st);
+}
+void launch_bi_end(BiState *st, int use_h, cudaGraphConditionalHandle h, cudaStream_t s) {
+    count_launch();
+    k_bi_end<<<1, 32, 0, s>>>(st, use_h, h);
 }
 
 }  // namespace amgpr
