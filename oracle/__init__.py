@@ -8,7 +8,9 @@ Every function cites the part of the paper it follows (arXiv 2108.02054):
   Alg. 1  full setup                  -> Hierarchy(...)
   Alg. 4  partial reuse update        -> Hierarchy.rebuild(values)
   Alg. 2  V-cycle (one per PCG step)  -> Hierarchy.vcycle(r)
-  Sec. 4  Krylov solve (CG here)      -> Hierarchy.pcg(f, tol)
+  Sec. 4  Krylov solve                -> Hierarchy.pcg / Hierarchy.bicgstab
+  Sec. 4  4 x 4 block systems         -> BlockHierarchy (non-smoothed aggregation,
+                                         damped block Jacobi, BiCGStab)
   Alg. 3  full reuse / no reuse modes -> run_time_steps(...)
 Parity: every function is pinned by tests under tests/test_oracle_*.py.
 """
@@ -77,6 +79,27 @@ def lib():
                                                 ctypes.c_void_p, _i32p, _i32p, _f64p]
             L.orc_bicgstab.argtypes = [ctypes.c_void_p, ctypes.c_void_p, _f64p, _f64p, ctypes.c_double, ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+            L.orc_stokes_assemble.argtypes = [ctypes.c_int, _f64p, _f64p, _f64p, _f64p, _f64p, ctypes.c_double,
+                                              _i32p, _i32p, _f64p]
+            L.orc_block_norm.restype = ctypes.c_double
+            L.orc_block_norm.argtypes = [_f64p]
+            L.orc_inv4.argtypes = [_f64p, _f64p]
+            L.orc_block_setup.restype = ctypes.c_void_p
+            L.orc_block_setup.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p, _i32p,
+                                          ctypes.POINTER(ctypes.c_int)]
+            L.orc_block_rebuild.argtypes = [ctypes.c_void_p, _f64p]
+            L.orc_block_destroy.argtypes = [ctypes.c_void_p]
+            L.orc_block_vcycle.argtypes = [ctypes.c_void_p, _f64p, _f64p]
+            L.orc_block_bicgstab.argtypes = [ctypes.c_void_p, ctypes.c_void_p, _f64p, _f64p, ctypes.c_double,
+                                             ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                             ctypes.POINTER(ctypes.c_double)]
+            L.orc_block_nlevels.argtypes = [ctypes.c_void_p]
+            L.orc_block_level_sizes.argtypes = [ctypes.c_void_p, ctypes.c_int, _i64p]
+            L.orc_block_export_csr.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                               ctypes.c_void_p, ctypes.c_void_p]
+            L.orc_block_export_vec.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_void_p, ctypes.c_void_p]
+            L.orc_block_export_lu.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
             L.orc_dense_lu.argtypes = [ctypes.c_int, _f64p, _i32p]
             L.orc_dense_lu_solve.argtypes = [ctypes.c_int, _f64p, _i32p, _f64p, _f64p]
             _lib = L
@@ -128,6 +151,35 @@ def poisson_grad_theta(dim, N, rho, u, lam, dirichlet_top=True):
     lib().orc_poisson_grad_theta(dim, N, int(dirichlet_top), np.ascontiguousarray(rho, np.float64),
                                  np.ascontiguousarray(u, np.float64), np.ascontiguousarray(lam, np.float64), g)
     return g
+
+
+def stokes_assemble(N: int, rho, mu, fx, fy, fz, mass: float):
+    """Block CSR (ptr, col, val[nnz, 16]) of the synthetic monolithic Oseen-type
+    system (the stand-in for the Sec. 4 Navier-Stokes matrices, 4 x 4 blocks
+    (u, v, w, p) per cell) on the N^3 pressure pattern."""
+    L = lib()
+    n = N ** 3
+    nnz = int(L.orc_poisson_nnz(3, N))
+    ptr = np.zeros(n + 1, np.int32)
+    col = np.zeros(nnz, np.int32)
+    val = np.zeros(16 * nnz, np.float64)
+    a = [np.ascontiguousarray(x, np.float64) for x in (rho, mu, fx, fy, fz)]
+    st = L.orc_stokes_assemble(N, *a, float(mass), ptr, col, val)
+    if st != OK:
+        raise ValueError(f"assembly failed: {st}")
+    return ptr, col, val.reshape(nnz, 16)
+
+
+def block_norm(b) -> float:
+    """Frobenius norm of a 4 x 4 block, as the block hierarchy computes it."""
+    return float(lib().orc_block_norm(np.ascontiguousarray(b, np.float64).reshape(16)))
+
+
+def inv4(a):
+    """(inverse, ok) of a 4 x 4 block by the hierarchy's Gauss-Jordan routine."""
+    inv = np.zeros(16, np.float64)
+    ok = lib().orc_inv4(np.ascontiguousarray(a, np.float64).reshape(16), inv)
+    return inv.reshape(4, 4), bool(ok)
 
 
 def priority(i: int) -> int:
@@ -304,6 +356,124 @@ class Hierarchy:
 
 
 # --------------------------------------------------------------------------
+# Block-valued (4 x 4) hierarchy (Sec. 4, the monolithic Navier-Stokes systems)
+
+def block_params(**kw) -> Params:
+    """The paper's configuration for the block systems: non-smoothed
+    aggregation, damped Jacobi (coarse_enough counts nodes)."""
+    kw.setdefault("smoother", 1)
+    kw.setdefault("smoothed", 0)
+    return Params(**kw)
+
+
+@dataclass
+class BlockLevel:
+    A: CSR              # val: (nnz, 16) block values
+    P: CSR | None
+    R: CSR | None
+    agg: np.ndarray
+    strong: np.ndarray
+    minv: np.ndarray     # (n, 16) damped block-Jacobi inverses
+    norms: np.ndarray    # block norms of the node graph (setup values)
+    nagg: int = 0
+
+
+class BlockHierarchy:
+    """Alg. 1 on a 4 x 4 block matrix (node graph of block norms,
+    non-smoothed aggregation, damped block Jacobi); rebuild() is Alg. 4."""
+
+    def __init__(self, ptr, col, bval, params: Params | None = None):
+        self.params = params or block_params()
+        L = lib()
+        self._ptr = np.ascontiguousarray(ptr, np.int32)
+        self._col = np.ascontiguousarray(col, np.int32)
+        d, i = self.params.arrays()
+        st = ctypes.c_int(0)
+        h = L.orc_block_setup(int(self._ptr.size - 1), self._ptr, self._col,
+                              np.ascontiguousarray(bval, np.float64).reshape(-1), d, i, ctypes.byref(st))
+        self.status = st.value
+        if not h:
+            raise ValueError(f"oracle block setup failed: status {st.value}")
+        if st.value == ERR_SINGULAR:
+            L.orc_block_destroy(h)
+            raise ValueError("oracle block setup: coarsest matrix singular")
+        self._h = h
+        self.nodes = int(self._ptr.size - 1)
+        self.n = 4 * self.nodes
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().orc_block_destroy(h)
+            self._h = None
+
+    @property
+    def nlevels(self) -> int:
+        return int(lib().orc_block_nlevels(self._h))
+
+    def sizes(self, l: int):
+        s = np.zeros(6, np.int64)
+        lib().orc_block_level_sizes(self._h, l, s)
+        return s
+
+    def level(self, l: int) -> BlockLevel:
+        n, nnzA, nnzP, nnzR, _, nagg = (int(x) for x in self.sizes(l))
+
+        def csr(which, nrows, nnz, ncols, width):
+            ptr = np.zeros(nrows + 1, np.int32)
+            col = np.zeros(nnz, np.int32)
+            val = np.zeros(nnz * width, np.float64)
+            lib().orc_block_export_csr(self._h, l, which, _ptr(ptr), _ptr(col), _ptr(val))
+            return CSR(ptr, col, val.reshape(nnz, 16) if width == 16 else val, ncols)
+
+        A = csr(0, n, nnzA, n, 16)
+        P = R = None
+        if l < self.nlevels - 1:
+            P = csr(1, n, nnzP, nagg, 1)
+            R = csr(2, nagg, nnzR, n, 1)
+        agg = np.zeros(n, np.int32)
+        strong = np.zeros(nnzA, np.uint8)
+        minv = np.zeros(16 * n, np.float64)
+        norms = np.zeros(nnzA, np.float64)
+        lib().orc_block_export_vec(self._h, l, _ptr(agg), _ptr(strong), _ptr(minv), _ptr(norms))
+        return BlockLevel(A, P, R, agg, strong, minv.reshape(n, 16), norms, nagg)
+
+    def lu(self):
+        nL = 4 * int(self.sizes(self.nlevels - 1)[0])
+        lu = np.zeros((nL, nL), np.float64)
+        piv = np.zeros(nL, np.int32)
+        lib().orc_block_export_lu(self._h, _ptr(lu), _ptr(piv))
+        return lu, piv
+
+    def rebuild(self, bval) -> int:
+        return int(lib().orc_block_rebuild(self._h, np.ascontiguousarray(bval, np.float64).reshape(-1)))
+
+    def vcycle(self, r) -> np.ndarray:
+        z = np.zeros(self.n, np.float64)
+        lib().orc_block_vcycle(self._h, np.ascontiguousarray(r, np.float64), z)
+        return z
+
+    def bicgstab(self, f, tol=1e-8, maxiter=100, sys_val=None):
+        """BiCGStab on the 4n unknowns, one block V-cycle per preconditioner
+        application; (u, iters, relres, status)."""
+        u = np.zeros(self.n, np.float64)
+        it = ctypes.c_int(0)
+        rr = ctypes.c_double(0.0)
+        sv = None if sys_val is None else np.ascontiguousarray(sys_val, np.float64).reshape(-1)
+        st = lib().orc_block_bicgstab(self._h, _ptr(sv), np.ascontiguousarray(f, np.float64), u, float(tol),
+                                      int(maxiter), ctypes.byref(it), ctypes.byref(rr))
+        return u, it.value, rr.value, int(st)
+
+
+def block_to_scipy(ptr, col, bval, ncols=None):
+    """The expanded scalar matrix of a block CSR (4n x 4n), for the pins."""
+    import scipy.sparse as sp
+    n = ptr.size - 1
+    ncols = n if ncols is None else ncols
+    return sp.bsr_matrix((np.asarray(bval).reshape(-1, 4, 4), col, ptr), shape=(4 * n, 4 * ncols)).tocsr()
+
+
+# --------------------------------------------------------------------------
 MODE_PARTIAL, MODE_FULL_REBUILD, MODE_FULL_REUSE = 0, 1, 2
 
 
@@ -318,7 +488,8 @@ class StepRecord:
 
 
 def run_time_steps(ptr, col, values_per_step, f, mode=MODE_PARTIAL, params=None, tol=1e-8, maxiter=100,
-                   reuse_iter_limit=None, keep_u=False, rebuild_every=0, rebuild_iter_growth=0.0, solver="cg"):
+                   reuse_iter_limit=None, keep_u=False, rebuild_every=0, rebuild_iter_growth=0.0, solver="cg",
+                   block=False):
     """Time loop of Alg. 3 (full reuse), Alg. 4 (partial reuse) or no reuse.
 
     Full reuse rebuilds when the previous step's solve did not converge within
@@ -339,7 +510,7 @@ def run_time_steps(ptr, col, values_per_step, f, mode=MODE_PARTIAL, params=None,
             (rebuild_every > 0 and since_full + 1 >= rebuild_every)
             or (rebuild_iter_growth > 0 and base_it > 0 and last_it > rebuild_iter_growth * base_it))
         if k == 0 or mode == MODE_FULL_REBUILD or (mode == MODE_FULL_REUSE and not last_ok) or preventive:
-            H = Hierarchy(ptr, col, val, params)
+            H = BlockHierarchy(ptr, col, val, params) if block else Hierarchy(ptr, col, val, params)
             rebuilt = True
             since_full = 0
             base_it = -1

@@ -17,6 +17,11 @@
  *     (Sec. 2: a single V-cycle per preconditioning step).
  *   - The adjoint gradient of L = 1/2 |u - u*|^2 w.r.t. log-density per cell
  *     for the variable-coefficient Poisson assembly below.
+ *   - Sec. 4's nonsymmetric systems: a level-set transport stand-in solved
+ *     with right-preconditioned BiCGStab, and a monolithic 4 x 4 block
+ *     (u, v, w, p) system standing in for the Navier-Stokes matrices, with a
+ *     block-valued hierarchy (non-smoothed aggregation on the node graph of
+ *     block norms, damped block Jacobi, BiCGStab), as the paper runs them.
  *
  * The paper delegates the smoothed-aggregation construction to its library;
  * the readings used here (strength test, aggregation order, P smoothing, the
@@ -847,11 +852,12 @@ int orc_pcg(ohier *h, const double *sys_val, const double *f, double *u, double 
  * confirmed by the true residual; if that misses tol, r is replaced by it
  * (at most twice) and the iteration goes on.  Breakdown: rho, (r^, v) or
  * (t, t) zero or not finite, or omega = 0. */
-int orc_bicgstab(ohier *h, const double *sys_val, const double *f, double *u, double tol, int maxiter,
-                 int *iters, double *relres) {
-    olevel *L = &h->lev[0];
-    int32_t n = L->A.nrows;
-    const double *av = sys_val ? sys_val : L->A.val;
+typedef void (*orc_apply_fn)(void *ctx, const double *x, double *y);
+
+/* The iteration itself, for any operator y = A x and preconditioner y = M x
+ * on n unknowns. */
+static int bicgstab_core(int32_t n, orc_apply_fn apply_A, orc_apply_fn apply_M, void *ctx, const double *f,
+                         double *u, double tol, int maxiter, int *iters, double *relres) {
     double *r = (double *)xcalloc((size_t)n, sizeof(double));
     double *rh = (double *)xcalloc((size_t)n, sizeof(double));
     double *p = (double *)xcalloc((size_t)n, sizeof(double));
@@ -875,8 +881,8 @@ int orc_bicgstab(ohier *h, const double *sys_val, const double *f, double *u, do
             if (!(rho != 0.0) || !isfinite(rho)) { status = ORC_ERR_BREAKDOWN; break; }
             double beta = (rho / rho_old) * (alpha / omega);
             for (int32_t i = 0; i < n; ++i) p[i] = fma(beta, fma(-omega, v[i], p[i]), r[i]);
-            orc_vcycle(h, p, ph);
-            spmv(&L->A, av, ph, v);
+            apply_M(ctx, p, ph);
+            apply_A(ctx, ph, v);
             double rv = dot(n, rh, v);
             if (!(rv != 0.0) || !isfinite(rv)) { status = ORC_ERR_BREAKDOWN; break; }
             alpha = rho / rv;
@@ -889,8 +895,8 @@ int orc_bicgstab(ohier *h, const double *sys_val, const double *f, double *u, do
                 for (int32_t i = 0; i < n; ++i) r[i] = sv[i];
                 conv = 1;
             } else {
-                orc_vcycle(h, sv, sh);
-                spmv(&L->A, av, sh, t);
+                apply_M(ctx, sv, sh);
+                apply_A(ctx, sh, t);
                 double ts = dot(n, t, sv), tt = dot(n, t, t);
                 if (!(tt != 0.0) || !isfinite(tt)) { status = ORC_ERR_BREAKDOWN; break; }
                 omega = ts / tt;
@@ -904,7 +910,7 @@ int orc_bicgstab(ohier *h, const double *sys_val, const double *f, double *u, do
                 conv = res <= tol;
             }
             if (conv) {
-                spmv(&L->A, av, u, t);
+                apply_A(ctx, u, t);
                 for (int32_t i = 0; i < n; ++i) t[i] = f[i] - t[i];
                 double tres = sqrt(dot(n, t, t)) / nf;
                 *relres = tres;
@@ -917,13 +923,26 @@ int orc_bicgstab(ohier *h, const double *sys_val, const double *f, double *u, do
     }
     {
         double *q = t;
-        spmv(&L->A, av, u, q);
+        apply_A(ctx, u, q);
         for (int32_t i = 0; i < n; ++i) q[i] = f[i] - q[i];
         *relres = sqrt(dot(n, q, q)) / nf;
     }
 done:
     free(r); free(rh); free(p); free(v); free(ph); free(sv); free(sh); free(t);
     return status;
+}
+
+typedef struct { ohier *h; const double *av; } scalar_ops;
+static void scalar_apply_A(void *c, const double *x, double *y) {
+    scalar_ops *o = (scalar_ops *)c;
+    spmv(&o->h->lev[0].A, o->av, x, y);
+}
+static void scalar_apply_M(void *c, const double *x, double *y) { orc_vcycle(((scalar_ops *)c)->h, x, y); }
+
+int orc_bicgstab(ohier *h, const double *sys_val, const double *f, double *u, double tol, int maxiter,
+                 int *iters, double *relres) {
+    scalar_ops o = {h, sys_val ? sys_val : h->lev[0].A.val};
+    return bicgstab_core(h->lev[0].A.nrows, scalar_apply_A, scalar_apply_M, &o, f, u, tol, maxiter, iters, relres);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -973,3 +992,454 @@ int orc_dense_lu(int n, double *a, int32_t *piv) { return dense_lu(n, a, piv); }
 void orc_dense_lu_solve(int n, const double *a, const int32_t *piv, const double *b, double *x) {
     dense_lu_solve(n, a, piv, b, x);
 }
+
+/* ======================================================================== */
+/* Block-valued (4 x 4) hierarchy: the monolithic Navier-Stokes systems of
+ * Sec. 4, which the paper solves with BiCGStab preconditioned by
+ * non-smoothed aggregation AMG with damped Jacobi smoothing, on a backend
+ * whose matrix values are statically sized 4 x 4 blocks.
+ * Block CSR: the pattern is a scalar CSR over nodes; entry e holds 16
+ * doubles, row-major (component r of the row node, component c of the column
+ * node), at val[16 e].  Vectors hold the 4 components of a node
+ * consecutively, so the block matrix is the scalar matrix of 4n unknowns
+ * with entry (4i + r, 4j + c) = block (i, j)[r][c]. */
+#define OB2 16
+
+/* Synthetic monolithic Oseen-type system on an N^3 cell grid (a stand-in for
+ * the stabilised P1 Navier-Stokes matrices of Sec. 4), unknowns (u, v, w, p)
+ * per cell, on the 7-point pattern of orc_poisson_assemble.  For the face f
+ * between cell c and its neighbour j in direction d with side s = -1 / +1
+ * (outward flux phi = s * face velocity, face viscosity
+ * mu_f = (2 mu_c mu_j) / (mu_c + mu_j), pressure coefficient
+ * tau_f = 2 / (rho_c + rho_j)):
+ *   off-diagonal block: velocity rows min(phi, 0) - mu_f on the diagonal of
+ *   the 3 x 3 velocity part; (u_d, p) = (p, u_d) = s / 2; (p, p) = -tau_f.
+ *   diagonal block: velocity a = mass rho_c + sum over faces in neighbour
+ *   order of (mu_f + max(phi, 0)), plus 2 mu_c per wall face (no-slip
+ *   ghost); (u_d, p) = g_d = sum of s / 2 over the wall faces of direction d
+ *   (zero-gradient ghost pressure), (p, u_d) = -g_d; (p, p) = sum of tau_f in
+ *   neighbour order, plus 2 / rho_c on the top face (z = N - 1).
+ * The pressure part is exactly the pressure Poisson matrix; the
+ * velocity-pressure coupling is skew-symmetric, so the symmetric part of the
+ * matrix is block diagonal (velocity, pressure) and positive definite.
+ * Faces are visited in ascending neighbour order z-, y-, x-, x+, y+, z+. */
+int orc_stokes_assemble(int N, const double *rho, const double *mu, const double *fx, const double *fy,
+                        const double *fz, double mass, int32_t *ptr, int32_t *col, double *bval) {
+    if (N < 1) return ORC_ERR_ARG;
+    const long long n = (long long)N * N * N, s3 = (long long)N * N, N1 = N + 1;
+    long long pos = 0;
+    for (long long c = 0; c < n; ++c) {
+        const long long x = c % N, y = (c / N) % N, z = c / s3;
+        const int has[6] = {z > 0, y > 0, x > 0, x < N - 1, y < N - 1, z < N - 1};
+        const long long nbr[6] = {c - s3, c - N, c - 1, c + 1, c + N, c + s3};
+        const int dir[6] = {2, 1, 0, 0, 1, 2};
+        const double sg[6] = {-1.0, -1.0, -1.0, 1.0, 1.0, 1.0};
+        const double wv[6] = {fz[(z * N + y) * N + x], fy[(z * N1 + y) * N + x], fx[(z * N + y) * N1 + x],
+                              fx[(z * N + y) * N1 + x + 1], fy[(z * N1 + y + 1) * N + x],
+                              fz[((z + 1) * N + y) * N + x]};
+        ptr[c] = (int32_t)pos;
+        const double kap_c = mass * rho[c] + 6.0 * mu[c];
+        const double rinv_c = 1.0 / kap_c;
+        double a = mass * rho[c], s = 0.0;
+        double g[3] = {0.0, 0.0, 0.0};
+        long long dpos = -1;
+        for (int t = 0; t < 7; ++t) {
+            if (t == 3) { dpos = pos; col[pos++] = (int32_t)c; continue; }
+            const int q = t < 3 ? t : t - 1;
+            const int d = dir[q];
+            const double sig = sg[q];
+            if (!has[q]) {
+                a = a + 2.0 * mu[c];
+                g[d] = g[d] + (0.5 * sig) * kap_c;
+                continue;
+            }
+            const long long j = nbr[q];
+            const double phi = sig * wv[q];
+            const double muf = (2.0 * mu[c] * mu[j]) / (mu[c] + mu[j]);
+            const double rinv_j = 1.0 / (mass * rho[j] + 6.0 * mu[j]);
+            const double beta = 2.0 / (rinv_c + rinv_j);
+            double *B = bval + OB2 * pos;
+            for (int k = 0; k < OB2; ++k) B[k] = 0.0;
+            const double off = (phi < 0.0 ? phi : 0.0) - muf;
+            B[0] = off; B[5] = off; B[10] = off;
+            B[d * 4 + 3] = (0.5 * sig) * beta;
+            B[12 + d] = (0.5 * sig) * beta;
+            B[15] = -beta;
+            a = a + (muf + (phi > 0.0 ? phi : 0.0));
+            s = s + beta;
+            col[pos++] = (int32_t)j;
+        }
+        if (z == N - 1) s = s + 2.0 / rinv_c;
+        double *D = bval + OB2 * dpos;
+        for (int k = 0; k < OB2; ++k) D[k] = 0.0;
+        D[0] = a; D[5] = a; D[10] = a;
+        for (int d = 0; d < 3; ++d) { D[d * 4 + 3] = g[d]; D[12 + d] = -g[d]; }
+        D[15] = s;
+    }
+    ptr[n] = (int32_t)pos;
+    return ORC_OK;
+}
+
+/* Frobenius norm of a block: the square root of the sum, in storage order
+ * with fma, of the squared entries.  The node graph that strength and
+ * aggregation see carries these norms as its values. */
+static double block_norm(const double *b) {
+    double s = 0.0;
+    for (int k = 0; k < OB2; ++k) s = fma(b[k], b[k], s);
+    return sqrt(s);
+}
+
+/* 4 x 4 inverse by Gauss-Jordan elimination with partial pivoting (pivot:
+ * first entry of largest magnitude in the column, rows swapped; pivot row
+ * divided by the pivot, then eliminated from every other row with fma).
+ * Returns 0 for a singular (or non-finite) block. */
+static int inv4(const double *a_in, double *inv) {
+    double a[OB2];
+    memcpy(a, a_in, sizeof a);
+    for (int k = 0; k < OB2; ++k) inv[k] = (k % 5 == 0) ? 1.0 : 0.0;
+    for (int k = 0; k < 4; ++k) {
+        int p = k;
+        double best = fabs(a[k * 4 + k]);
+        for (int r = k + 1; r < 4; ++r) {
+            double v = fabs(a[r * 4 + k]);
+            if (v > best) { best = v; p = r; }
+        }
+        if (!(best > 0.0) || !isfinite(best)) return 0;
+        if (p != k)
+            for (int c = 0; c < 4; ++c) {
+                double t = a[k * 4 + c]; a[k * 4 + c] = a[p * 4 + c]; a[p * 4 + c] = t;
+                t = inv[k * 4 + c]; inv[k * 4 + c] = inv[p * 4 + c]; inv[p * 4 + c] = t;
+            }
+        const double pv = a[k * 4 + k];
+        for (int c = 0; c < 4; ++c) { a[k * 4 + c] = a[k * 4 + c] / pv; inv[k * 4 + c] = inv[k * 4 + c] / pv; }
+        for (int r = 0; r < 4; ++r) {
+            if (r == k) continue;
+            const double f = a[r * 4 + k];
+            for (int c = 0; c < 4; ++c) {
+                a[r * 4 + c] = fma(-f, a[k * 4 + c], a[r * 4 + c]);
+                inv[r * 4 + c] = fma(-f, inv[k * 4 + c], inv[r * 4 + c]);
+            }
+        }
+    }
+    return 1;
+}
+
+typedef struct {
+    ocsr S;            /* node graph: pattern of A, values = block norms (setup only) */
+    double *bv;        /* block values of A (16 per entry) */
+    ocsr P, R;         /* scalar transfer operators: non-smoothed, P = P_tent, R = P^T */
+    ocsr AP;           /* pattern of A P */
+    double *apb;       /* block values of A P (scratch of the Galerkin product) */
+    int32_t *agg;
+    uint8_t *strong;
+    int32_t nroots;
+    double *Minv;      /* damped block Jacobi: w_J inv(A_ii), 16 per node (0 if singular) */
+    double *u, *f, *r; /* 4 per node */
+} oblevel;
+
+typedef struct {
+    oparams prm;
+    int nlev;
+    oblevel lev[32];
+    int nL;            /* unknowns of the coarsest system (4 per node) */
+    double *LU;
+    int32_t *piv;
+} obhier;
+
+/* Block Galerkin product A_c = R (A P) with scalar P and R (each block is
+ * scaled by the scalar entry, component by component): the loops and the
+ * summation order of spgemm_numeric, one fma per term and component. */
+static int block_galerkin(oblevel *L, oblevel *C) {
+    const ocsr *A = &L->S, *P = &L->P, *R = &L->R;
+    ocsr *AP = &L->AP, *Ac = &C->S;
+    int32_t nmax = A->ncols > P->ncols ? A->ncols : P->ncols;
+    int32_t *pos = (int32_t *)xcalloc((size_t)nmax, sizeof(int32_t));
+    for (int32_t c = 0; c < nmax; ++c) pos[c] = -1;
+    int st = ORC_OK;
+    for (int32_t i = 0; i < A->nrows && st == ORC_OK; ++i) {
+        for (int32_t e = AP->ptr[i]; e < AP->ptr[i + 1]; ++e) {
+            pos[AP->col[e]] = e;
+            for (int k = 0; k < OB2; ++k) L->apb[(size_t)OB2 * e + k] = 0.0;
+        }
+        for (int32_t p = A->ptr[i]; p < A->ptr[i + 1]; ++p) {
+            const int32_t j = A->col[p];
+            for (int32_t q = P->ptr[j]; q < P->ptr[j + 1]; ++q) {
+                const int32_t e = pos[P->col[q]];
+                if (e < 0) { st = ORC_ERR_PATTERN; break; }
+                for (int k = 0; k < OB2; ++k)
+                    L->apb[(size_t)OB2 * e + k] = fma(L->bv[(size_t)OB2 * p + k], P->val[q], L->apb[(size_t)OB2 * e + k]);
+            }
+        }
+        for (int32_t e = AP->ptr[i]; e < AP->ptr[i + 1]; ++e) pos[AP->col[e]] = -1;
+    }
+    for (int32_t I = 0; I < R->nrows && st == ORC_OK; ++I) {
+        for (int32_t e = Ac->ptr[I]; e < Ac->ptr[I + 1]; ++e) {
+            pos[Ac->col[e]] = e;
+            for (int k = 0; k < OB2; ++k) C->bv[(size_t)OB2 * e + k] = 0.0;
+        }
+        for (int32_t p = R->ptr[I]; p < R->ptr[I + 1]; ++p) {
+            const int32_t i = R->col[p];
+            for (int32_t q = AP->ptr[i]; q < AP->ptr[i + 1]; ++q) {
+                const int32_t e = pos[AP->col[q]];
+                if (e < 0) { st = ORC_ERR_PATTERN; break; }
+                for (int k = 0; k < OB2; ++k)
+                    C->bv[(size_t)OB2 * e + k] = fma(R->val[p], L->apb[(size_t)OB2 * q + k], C->bv[(size_t)OB2 * e + k]);
+            }
+        }
+        for (int32_t e = Ac->ptr[I]; e < Ac->ptr[I + 1]; ++e) pos[Ac->col[e]] = -1;
+    }
+    free(pos);
+    return st;
+}
+
+static void block_level_free(oblevel *L) {
+    csr_free(&L->S); csr_free(&L->P); csr_free(&L->R); csr_free(&L->AP);
+    free(L->bv); free(L->apb); free(L->agg); free(L->strong); free(L->Minv);
+    free(L->u); free(L->f); free(L->r);
+    memset(L, 0, sizeof(*L));
+}
+
+void orc_block_destroy(obhier *h) {
+    if (!h) return;
+    for (int l = 0; l < h->nlev; ++l) block_level_free(&h->lev[l]);
+    free(h->LU); free(h->piv);
+    free(h);
+}
+
+/* Coarsest level: the block matrix expanded to 4 n_L scalar unknowns, dense
+ * LU with partial pivoting. */
+static int block_coarse_factor(obhier *h) {
+    const oblevel *L = &h->lev[h->nlev - 1];
+    const int n4 = h->nL;
+    memset(h->LU, 0, sizeof(double) * (size_t)n4 * (size_t)n4);
+    for (int32_t i = 0; i < L->S.nrows; ++i)
+        for (int32_t p = L->S.ptr[i]; p < L->S.ptr[i + 1]; ++p)
+            for (int r = 0; r < 4; ++r)
+                for (int c = 0; c < 4; ++c)
+                    h->LU[(size_t)(4 * i + r) * n4 + 4 * L->S.col[p] + c] = L->bv[(size_t)OB2 * p + 4 * r + c];
+    return dense_lu(n4, h->LU, h->piv);
+}
+
+/* Alg. 4 body for the block hierarchy: new fine block values, the damped
+ * block-Jacobi inverses and the Galerkin blocks of every level over the kept
+ * P, R and patterns, the coarsest LU. */
+int orc_block_rebuild(obhier *h, const double *bval) {
+    if (!h) return ORC_ERR_STATE;
+    oblevel *L0 = &h->lev[0];
+    memcpy(L0->bv, bval, sizeof(double) * OB2 * (size_t)L0->S.ptr[L0->S.nrows]);
+    for (int l = 0; l + 1 < h->nlev; ++l) {
+        oblevel *L = &h->lev[l];
+        int32_t *dia = diag_positions(&L->S);
+        for (int32_t i = 0; i < L->S.nrows; ++i) {
+            double inv[OB2];
+            int ok = inv4(L->bv + (size_t)OB2 * dia[i], inv);
+            for (int k = 0; k < OB2; ++k) L->Minv[(size_t)OB2 * i + k] = ok ? h->prm.jacobi_omega * inv[k] : 0.0;
+        }
+        free(dia);
+        int st = block_galerkin(L, &h->lev[l + 1]);
+        if (st) return st;
+    }
+    return block_coarse_factor(h);
+}
+
+/* Alg. 1 for the block matrix (n nodes, block CSR).  Strength of connection
+ * and aggregation run on the node graph whose values are the block norms
+ * (the scalar routines above: the test ||A_ij||^2 > eps^2 ||A_ii|| ||A_jj||);
+ * P is the tentative prolongation (non-smoothed aggregation, as the paper
+ * uses for these systems), so every coarse block is a sum of fine blocks.
+ * Parameters as orc_setup; smoother must be damped Jacobi (1) and smoothed 0;
+ * coarse_enough counts nodes. */
+obhier *orc_block_setup(int32_t n, const int32_t *ptr, const int32_t *col, const double *bval,
+                        const double *dprm, const int32_t *iprm, int *status) {
+    *status = ORC_OK;
+    if (iprm[0] != 1 || iprm[6] != 0) { *status = ORC_ERR_ARG; return NULL; }
+    if (n <= 0 || check_pattern(n, ptr, col) != ORC_OK) { *status = ORC_ERR_PATTERN; return NULL; }
+    obhier *h = (obhier *)xcalloc(1, sizeof(obhier));
+    h->prm.theta = dprm[0]; h->prm.omega = dprm[1]; h->prm.jacobi_omega = dprm[2];
+    h->prm.smoother = iprm[0]; h->prm.npre = iprm[1]; h->prm.npost = iprm[2];
+    h->prm.coarse_enough = iprm[3]; h->prm.max_levels = iprm[4];
+    h->prm.theta_halving = iprm[5]; h->prm.smoothed = 0;
+    if (h->prm.max_levels > 32) h->prm.max_levels = 32;
+    if (h->prm.max_levels < 1) h->prm.max_levels = 1;
+    oblevel *L = &h->lev[0];
+    const int32_t nnz = ptr[n];
+    L->S.nrows = L->S.ncols = n;
+    L->S.ptr = (int32_t *)xcalloc((size_t)n + 1, sizeof(int32_t));
+    L->S.col = (int32_t *)xcalloc((size_t)nnz, sizeof(int32_t));
+    L->S.val = (double *)xcalloc((size_t)nnz, sizeof(double));
+    L->bv = (double *)xcalloc((size_t)OB2 * nnz, sizeof(double));
+    memcpy(L->S.ptr, ptr, sizeof(int32_t) * ((size_t)n + 1));
+    memcpy(L->S.col, col, sizeof(int32_t) * (size_t)nnz);
+    memcpy(L->bv, bval, sizeof(double) * OB2 * (size_t)nnz);
+    for (int32_t e = 0; e < nnz; ++e) L->S.val[e] = block_norm(L->bv + (size_t)OB2 * e);
+    h->nlev = 1;
+    double theta = h->prm.theta;
+    for (;;) {
+        L = &h->lev[h->nlev - 1];
+        const int32_t nl = L->S.nrows;
+        L->u = (double *)xcalloc(4 * (size_t)nl, sizeof(double));
+        L->f = (double *)xcalloc(4 * (size_t)nl, sizeof(double));
+        L->r = (double *)xcalloc(4 * (size_t)nl, sizeof(double));
+        L->Minv = (double *)xcalloc((size_t)OB2 * nl, sizeof(double));
+        L->agg = (int32_t *)xcalloc((size_t)nl, sizeof(int32_t));
+        for (int32_t i = 0; i < nl; ++i) L->agg[i] = -1;
+        L->strong = (uint8_t *)xcalloc((size_t)L->S.ptr[nl], 1);
+        if (nl <= h->prm.coarse_enough || h->nlev >= h->prm.max_levels) break;
+        int32_t *dia = diag_positions(&L->S);
+        strength(&L->S, theta * theta, L->strong, dia);
+        int32_t nagg = aggregate(&L->S, L->strong, L->agg);
+        if (nagg < 0) { free(dia); *status = nagg; orc_block_destroy(h); return NULL; }
+        if (nagg == 0 || nagg >= nl) {
+            for (int32_t i = 0; i < nl; ++i) L->agg[i] = -1;
+            memset(L->strong, 0, (size_t)L->S.ptr[nl]);
+            free(dia);
+            break;
+        }
+        L->nroots = nagg;
+        build_P(&L->S, L->strong, dia, L->agg, nagg, h->prm.omega, 0, &L->P);
+        free(dia);
+        transpose(&L->P, &L->R);
+        spgemm_pattern(&L->S, &L->P, 0, &L->AP);
+        oblevel *C = &h->lev[h->nlev];
+        spgemm_pattern(&L->R, &L->AP, 1, &C->S);
+        C->S.ncols = nagg;
+        L->apb = (double *)xcalloc((size_t)OB2 * L->AP.ptr[L->AP.nrows], sizeof(double));
+        C->bv = (double *)xcalloc((size_t)OB2 * C->S.ptr[nagg], sizeof(double));
+        /* the next level's strength test needs its block values now */
+        int gst = block_galerkin(L, C);
+        for (int32_t e = 0; e < C->S.ptr[nagg]; ++e) C->S.val[e] = block_norm(C->bv + (size_t)OB2 * e);
+        h->nlev++;
+        if (gst) { *status = gst; orc_block_destroy(h); return NULL; }
+        if (h->prm.theta_halving) theta = theta * 0.5;
+    }
+    h->nL = 4 * h->lev[h->nlev - 1].S.nrows;
+    h->LU = (double *)xcalloc((size_t)h->nL * (size_t)h->nL, sizeof(double));
+    h->piv = (int32_t *)xcalloc((size_t)h->nL, sizeof(int32_t));
+    int st = orc_block_rebuild(h, bval);
+    if (st == ORC_ERR_SINGULAR) { *status = st; return h; }
+    if (st) { *status = st; orc_block_destroy(h); return NULL; }
+    return h;
+}
+
+/* y = A x for the block matrix: component r of node i sums, in entry order
+ * and within an entry in component order, A_e[r][c] x_j[c] with fma (the row
+ * order of the expanded scalar matrix). */
+static void block_spmv(const ocsr *S, const double *bv, const double *x, double *y) {
+    for (int32_t i = 0; i < S->nrows; ++i)
+        for (int r = 0; r < 4; ++r) {
+            double s = 0.0;
+            for (int32_t p = S->ptr[i]; p < S->ptr[i + 1]; ++p)
+                for (int c = 0; c < 4; ++c) s = fma(bv[(size_t)OB2 * p + 4 * r + c], x[4 * (size_t)S->col[p] + c], s);
+            y[4 * (size_t)i + r] = s;
+        }
+}
+
+/* damped block Jacobi: u_i <- u_i + Minv_i (f - A u)_i */
+static void block_sweep(const oblevel *L, double *u, const double *f, double *tmp) {
+    const int32_t n = L->S.nrows;
+    block_spmv(&L->S, L->bv, u, tmp);
+    for (int32_t k = 0; k < 4 * n; ++k) tmp[k] = f[k] - tmp[k];
+    for (int32_t i = 0; i < n; ++i) {
+        double t[4];
+        for (int c = 0; c < 4; ++c) t[c] = tmp[4 * (size_t)i + c];
+        for (int r = 0; r < 4; ++r) {
+            double s = u[4 * (size_t)i + r];
+            for (int c = 0; c < 4; ++c) s = fma(L->Minv[(size_t)OB2 * i + 4 * r + c], t[c], s);
+            u[4 * (size_t)i + r] = s;
+        }
+    }
+}
+
+static void block_vcycle_level(obhier *h, int l) {
+    oblevel *L = &h->lev[l];
+    const int32_t n = L->S.nrows;
+    if (l == h->nlev - 1) {
+        dense_lu_solve(h->nL, h->LU, h->piv, L->f, L->u);
+        return;
+    }
+    for (int32_t k = 0; k < 4 * n; ++k) L->u[k] = 0.0;
+    for (int s = 0; s < h->prm.npre; ++s) block_sweep(L, L->u, L->f, L->r);
+    block_spmv(&L->S, L->bv, L->u, L->r);
+    for (int32_t k = 0; k < 4 * n; ++k) L->r[k] = L->f[k] - L->r[k];
+    oblevel *C = &h->lev[l + 1];
+    for (int32_t I = 0; I < L->R.nrows; ++I)
+        for (int c = 0; c < 4; ++c) {
+            double s = 0.0;
+            for (int32_t p = L->R.ptr[I]; p < L->R.ptr[I + 1]; ++p)
+                s = fma(L->R.val[p], L->r[4 * (size_t)L->R.col[p] + c], s);
+            C->f[4 * (size_t)I + c] = s;
+        }
+    block_vcycle_level(h, l + 1);
+    for (int32_t i = 0; i < n; ++i)
+        for (int c = 0; c < 4; ++c) {
+            double s = L->u[4 * (size_t)i + c];
+            for (int32_t p = L->P.ptr[i]; p < L->P.ptr[i + 1]; ++p)
+                s = fma(L->P.val[p], C->u[4 * (size_t)L->P.col[p] + c], s);
+            L->u[4 * (size_t)i + c] = s;
+        }
+    for (int s = 0; s < h->prm.npost; ++s) block_sweep(L, L->u, L->f, L->r);
+}
+
+void orc_block_vcycle(obhier *h, const double *r, double *z) {
+    oblevel *L = &h->lev[0];
+    memcpy(L->f, r, sizeof(double) * 4 * (size_t)L->S.nrows);
+    block_vcycle_level(h, 0);
+    memcpy(z, L->u, sizeof(double) * 4 * (size_t)L->S.nrows);
+}
+
+typedef struct { obhier *h; const double *bv; } block_ops;
+static void block_apply_A(void *c, const double *x, double *y) {
+    block_ops *o = (block_ops *)c;
+    block_spmv(&o->h->lev[0].S, o->bv, x, y);
+}
+static void block_apply_M(void *c, const double *x, double *y) { orc_block_vcycle(((block_ops *)c)->h, x, y); }
+
+/* BiCGStab (as orc_bicgstab) on the 4n unknowns of the block system,
+ * preconditioned by one block V-cycle. */
+int orc_block_bicgstab(obhier *h, const double *sys_bval, const double *f, double *u, double tol, int maxiter,
+                       int *iters, double *relres) {
+    block_ops o = {h, sys_bval ? sys_bval : h->lev[0].bv};
+    return bicgstab_core(4 * h->lev[0].S.nrows, block_apply_A, block_apply_M, &o, f, u, tol, maxiter, iters,
+                         relres);
+}
+
+/* Accessors for the tests. */
+int orc_block_nlevels(const obhier *h) { return h->nlev; }
+void orc_block_level_sizes(const obhier *h, int l, int64_t *sizes) {
+    const oblevel *L = &h->lev[l];
+    sizes[0] = L->S.nrows;
+    sizes[1] = L->S.ptr[L->S.nrows];
+    sizes[2] = L->P.ptr ? L->P.ptr[L->P.nrows] : 0;
+    sizes[3] = L->R.ptr ? L->R.ptr[L->R.nrows] : 0;
+    sizes[4] = L->AP.ptr ? L->AP.ptr[L->AP.nrows] : 0;
+    sizes[5] = L->nroots;
+}
+/* which: 0 = A (val: 16 per entry), 1 = P, 2 = R (scalar) */
+void orc_block_export_csr(const obhier *h, int l, int which, int32_t *ptr, int32_t *col, double *val) {
+    const oblevel *L = &h->lev[l];
+    const ocsr *a = which == 0 ? &L->S : which == 1 ? &L->P : &L->R;
+    if (!a->ptr) return;
+    const int32_t nnz = a->ptr[a->nrows];
+    if (ptr) memcpy(ptr, a->ptr, sizeof(int32_t) * ((size_t)a->nrows + 1));
+    if (col) memcpy(col, a->col, sizeof(int32_t) * (size_t)nnz);
+    if (val) {
+        if (which == 0) memcpy(val, L->bv, sizeof(double) * OB2 * (size_t)nnz);
+        else memcpy(val, a->val, sizeof(double) * (size_t)nnz);
+    }
+}
+/* aggregates, strong flags, block-Jacobi inverses (16 per node), block norms
+ * of the node graph (per entry); any pointer may be NULL */
+void orc_block_export_vec(const obhier *h, int l, int32_t *agg, uint8_t *strong, double *minv, double *norms) {
+    const oblevel *L = &h->lev[l];
+    const int32_t n = L->S.nrows, nnz = L->S.ptr[n];
+    if (agg) memcpy(agg, L->agg, sizeof(int32_t) * (size_t)n);
+    if (strong) memcpy(strong, L->strong, (size_t)nnz);
+    if (minv) memcpy(minv, L->Minv, sizeof(double) * OB2 * (size_t)n);
+    if (norms) memcpy(norms, L->S.val, sizeof(double) * (size_t)nnz);
+}
+void orc_block_export_lu(const obhier *h, double *lu, int32_t *piv) {
+    if (lu) memcpy(lu, h->LU, sizeof(double) * (size_t)h->nL * (size_t)h->nL);
+    if (piv) memcpy(piv, h->piv, sizeof(int32_t) * (size_t)h->nL);
+}
+int orc_inv4(const double *a, double *inv) { return inv4(a, inv); }
+double orc_block_norm(const double *b) { return block_norm(b); }

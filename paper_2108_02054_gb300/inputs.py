@@ -143,3 +143,20 @@ def levelset_faces(dim: int, N: int, k: int, T: int, courant: float = LEVELSET_C
     fy = np.zeros((N, N + 1, N))                                                                        # [z, yf, x]
     fz = np.cos(np.pi * c)[None, None, :] * np.sin(np.pi * e)[:, None, None] * ones[None, :, None]   # [zf, y, x]
     return (s * fx).reshape(-1), (s * fy).reshape(-1), (s * fz).reshape(-1)
+
+
+# ---------------------------------------------------------------- monolithic Navier-Stokes stand-in
+NS_MASS = 0.1          # mass coefficient: the velocity diagonal starts at NS_MASS * rho
+NS_MU_WATER = 1.0      # dynamic viscosity in the water column
+NS_MU_AIR = 0.018      # and in the air (about the water / air ratio)
+
+
+def ns_fields(N: int, k: int, T: int, courant: float = LEVELSET_COURANT):
+    """Per-cell density and viscosity (the collapsing water column at step k)
+    and the face velocities of the level-set flow: the inputs of the 4 x 4
+    block system standing in for the monolithic Navier-Stokes matrices of
+    Sec. 4 (3D, N^3 cells).  Returns (rho, mu, fx, fy, fz)."""
+    rho = density(3, N, k, T)
+    mu = np.where(rho == RHO_WATER, NS_MU_WATER, NS_MU_AIR)
+    fx, fy, fz = levelset_faces(3, N, k, T, courant)
+    return rho, mu, fx, fy, fz
