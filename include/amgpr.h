@@ -78,6 +78,19 @@ typedef struct {
      * pressure systems, AMG_SOLVER_BICGSTAB (right-preconditioned) for the
      * nonsymmetric level-set systems.  (CG) */
     int32_t solver;
+    /* 1: scalar matrices.  4: 4 x 4 block-valued matrices (Sec. 4, the
+     * monolithic Navier-Stokes systems): n and nnz of every call count nodes
+     * and blocks, values are 16 doubles per block (row-major: component r of
+     * the row node, component c of the column node), vectors hold the 4
+     * components of each node consecutively (4 n doubles).  The hierarchy
+     * then takes the paper's configuration for these systems and requires
+     * smoothed = 0, smoother = JACOBI (damped block Jacobi), precision = FP64
+     * and solver = BICGSTAB (else amg_create returns AMG_ERR_ARG).  Strength
+     * and aggregation run on the node graph of the block Frobenius norms;
+     * coarse_enough counts nodes.  amg_export_csr(which = 0) returns 16
+     * values per entry and amg_export_level_vec's d_m the block-Jacobi
+     * inverses w_J A_ii^-1 (16 per node).  (1) */
+    int32_t block_size;
 } amg_params;
 
 typedef struct {
@@ -209,6 +222,26 @@ amg_status amg_poisson_values(int32_t dim, int32_t N, int32_t dirichlet_top, con
 amg_status amg_levelset_values(int32_t dim, int32_t N, const double *d_fx, const double *d_fy,
                                const double *d_fz, const int32_t *d_ptr, double *d_val,
                                void *cuda_stream);
+/* Monolithic Navier-Stokes stand-in (Sec. 4), 4 x 4 blocks (u, v, w, p)
+ * per cell of an N^3 grid, on the pattern of amg_poisson_pattern(3, N): an
+ * Oseen-type system in balanced form (pressure unknowns scaled by
+ * kappa = mass rho + 6 mu).  For the face f between cells c and j in
+ * direction d, side s = -1 / +1, outward flux phi = s * face velocity,
+ * mu_f = (2 mu_c mu_j) / (mu_c + mu_j), beta_f = 2 / (1/kappa_c + 1/kappa_j):
+ *   block (c, j): velocity diagonal min(phi, 0) - mu_f; (u_d, p) = (p, u_d)
+ *     = (s / 2) beta_f; (p, p) = -beta_f.
+ *   block (c, c): velocity diagonal mass rho_c + sum of (mu_f + max(phi, 0))
+ *     + 2 mu_c per wall face; (u_d, p) = -(p, u_d) = sum over the wall
+ *     faces of direction d of (s / 2) kappa_c; (p, p) = sum of beta_f, plus
+ *     2 kappa_c on the top face (z = N - 1).
+ * The pressure part is the pressure Poisson matrix of density 1/kappa, the
+ * velocity-pressure coupling is skew-symmetric and the symmetric part is
+ * positive definite.  d_rho, d_mu: N^3 doubles; face velocities as in
+ * amg_levelset_values (dim 3); d_val: 16 * amg_poisson_nnz(3, N) doubles.
+ * Asynchronous on cuda_stream. */
+amg_status amg_stokes_values(int32_t N, const double *d_rho, const double *d_mu, const double *d_fx,
+                             const double *d_fy, const double *d_fz, double mass, const int32_t *d_ptr,
+                             double *d_val, void *cuda_stream);
 /* Adjoint chain rule for theta = log rho: given u (A u = f) and lam
  * (A lam = dL/du), grad = dL/dtheta per cell (n doubles). */
 amg_status amg_poisson_grad_theta(int32_t dim, int32_t N, int32_t dirichlet_top, const double *d_rho,

@@ -35,7 +35,7 @@ EXPORTS = [
     "amg_step", "amg_solve", "amg_apply_vcycle", "amg_step_solve_host", "amg_num_levels", "amg_level_sizes",
     "amg_export_csr", "amg_export_level_vec", "amg_export_coarse_lu", "amg_poisson_nnz", "amg_poisson_pattern",
     "amg_poisson_values", "amg_poisson_grad_theta", "amg_profile", "amg_profile_read", "amg_kernel_launches",
-    "amg_poisson_pattern_noalloc", "amg_levelset_values",
+    "amg_poisson_pattern_noalloc", "amg_levelset_values", "amg_stokes_values",
 ]
 PROF_SLOTS = ["cg_spmv", "smooth0_l0", "sweep_l0", "restrict_l0", "prolong_l0", "ap_l0", "rap_l0", "ingest", "lu",
               "inv", "cg_update", "cg_p", "dot", "coarse"]
@@ -49,7 +49,7 @@ class amg_params(ctypes.Structure):
         ("smoothed", ctypes.c_int32), ("precision", ctypes.c_int32), ("mode", ctypes.c_int32),
         ("reuse_iter_limit", ctypes.c_int32), ("maxiter", ctypes.c_int32),
         ("rebuild_every", ctypes.c_int32), ("rebuild_iter_growth", ctypes.c_double),
-        ("solver", ctypes.c_int32),
+        ("solver", ctypes.c_int32), ("block_size", ctypes.c_int32),
     ]
 
 
@@ -103,6 +103,7 @@ def lib():
                 "amg_kernel_launches": (ctypes.c_int64, []),
                 "amg_poisson_pattern_noalloc": (_i32, [_i32, _i32, _vp, _vp, _vp]),
                 "amg_levelset_values": (_i32, [_i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp]),
+                "amg_stokes_values": (_i32, [_i32, _vp, _vp, _vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -238,22 +239,25 @@ class AMG:
         n, nnzA, nnzP, nnzR, nnzAP, nagg = self.level_sizes(level)
         dev = torch.device("cuda", torch.cuda.current_device())
         out = {"n": n, "nagg": nagg, "nnzAP": nnzAP}
+        bw = 16 if self.params.block_size == 4 else 1   # values per entry of A / per node of m
         for which, name, nrows, nnz in ((0, "A", n, nnzA), (1, "P", n, nnzP), (2, "R", nagg, nnzR)):
             if which > 0 and nnzP == 0:
                 out[name] = None
                 continue
             ptr = torch.empty(nrows + 1, dtype=torch.int32, device=dev)
             col = torch.empty(max(nnz, 1), dtype=torch.int32, device=dev)
-            val = torch.empty(max(nnz, 1), dtype=torch.float64, device=dev)
+            w = bw if which == 0 else 1
+            val = torch.empty(max(nnz, 1) * w, dtype=torch.float64, device=dev)
             self._check(lib().amg_export_csr(self._h, level, which, _dptr(ptr), _dptr(col), _dptr(val)))
-            out[name] = (ptr.cpu().numpy(), col[:nnz].cpu().numpy(), val[:nnz].cpu().numpy())
+            v = val[:nnz * w].cpu().numpy()
+            out[name] = (ptr.cpu().numpy(), col[:nnz].cpu().numpy(), v.reshape(nnz, 16) if w == 16 else v)
         agg = torch.empty(n, dtype=torch.int32, device=dev)
         strong = torch.empty(max(nnzA, 1), dtype=torch.uint8, device=dev)
-        m = torch.empty(n, dtype=torch.float64, device=dev)
+        m = torch.zeros(n * bw, dtype=torch.float64, device=dev)
         self._check(lib().amg_export_level_vec(self._h, level, _dptr(agg), _dptr(strong), _dptr(m)))
         out["agg"] = agg.cpu().numpy()
         out["strong"] = strong[:nnzA].cpu().numpy()
-        out["m"] = m.cpu().numpy()
+        out["m"] = m.cpu().numpy().reshape(n, 16) if bw == 16 else m.cpu().numpy()
         return out
 
     def profile(self, enable: bool = True):
@@ -271,7 +275,7 @@ class AMG:
 
     def coarse_lu(self):
         import torch
-        nL = self.level_sizes(self.nlevels - 1)[0]
+        nL = self.level_sizes(self.nlevels - 1)[0] * self.params.block_size
         lu = torch.empty(nL * nL, dtype=torch.float64, device="cuda")
         piv = torch.empty(nL, dtype=torch.int32, device="cuda")
         self._check(lib().amg_export_coarse_lu(self._h, _dptr(lu), _dptr(piv)))
@@ -323,6 +327,27 @@ def levelset_values(dim: int, N: int, fx, fy, fz, ptr, out=None, stream=None):
     if st != AMG_OK:
         raise AmgError(st, "amg_levelset_values failed")
     return val
+
+
+def stokes_values(N: int, rho, mu, fx, fy, fz, mass: float, ptr, out=None, stream=None):
+    """Device block values (nnz x 16) of the 4 x 4 monolithic Navier-Stokes
+    stand-in on the pattern from poisson_pattern(3, N)."""
+    import torch
+    nnz = poisson_nnz(3, N)
+    val = out if out is not None else torch.empty((nnz, 16), dtype=torch.float64, device="cuda")
+    st = lib().amg_stokes_values(N, _dptr(rho), _dptr(mu), _dptr(fx), _dptr(fy), _dptr(fz), float(mass),
+                                 _dptr(ptr), _dptr(val), _vp(_stream(stream)))
+    if st != AMG_OK:
+        raise AmgError(st, "amg_stokes_values failed")
+    return val
+
+
+def block_params(**overrides) -> amg_params:
+    """The paper's configuration for the 4 x 4 block systems (Sec. 4):
+    non-smoothed aggregation, damped block Jacobi, BiCGStab, FP64."""
+    kw = dict(block_size=4, smoothed=0, smoother=SMOOTHER_JACOBI, solver=SOLVER_BICGSTAB, precision=PREC_FP64)
+    kw.update(overrides)
+    return default_params(**kw)
 
 
 def poisson_grad_theta(dim: int, N: int, rho, u, lam, dirichlet_top: bool = True, stream=None):

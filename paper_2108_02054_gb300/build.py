@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB_PATH = os.path.join(HERE, "libamgpr.so")
-SOURCES = ["setup_kernels.cu", "solve_kernels.cu", "amg.cu", "noalloc.cu"]
+SOURCES = ["setup_kernels.cu", "solve_kernels.cu", "amg.cu", "noalloc.cu", "block.cu"]
 HEADERS = [os.path.join(CSRC, "common.cuh"), os.path.join(ROOT, "include", "amgpr.h")]
 
 NVCC_FLAGS = [

@@ -202,8 +202,21 @@ amg_status scan(amg_ctx *ctx, const int32_t *in, int32_t *out, int64_t n) {
 }
 
 bool mixed(const amg_ctx *ctx) { return ctx->prm.precision == AMG_PREC_MIXED; }
+// 4 x 4 block-valued matrices (amg_params.block_size = 4)
+bool blockmode(const amg_ctx *ctx) { return ctx->prm.block_size == 4; }
+// unknowns of a vector on the fine level, values of the fine matrix
+int64_t nvec(const amg_ctx *ctx) { return (int64_t)ctx->n * ctx->prm.block_size; }
+size_t nvals(const amg_ctx *ctx) { return (size_t)ctx->nnz * (size_t)(ctx->prm.block_size * ctx->prm.block_size); }
 
 amg_status alloc_level_vectors(amg_ctx *ctx, Level &L) {
+    if (blockmode(ctx)) {
+        TRY(alloc(ctx, &L.vd.u, 4 * (size_t)L.n));
+        TRY(alloc(ctx, &L.vd.f, 4 * (size_t)L.n));
+        TRY(alloc(ctx, &L.vd.r, 4 * (size_t)L.n));
+        TRY(alloc(ctx, &L.vd.t, 4 * (size_t)L.n));
+        TRY(alloc(ctx, &L.Minv, 16 * (size_t)L.n));
+        return AMG_OK;
+    }
     if (mixed(ctx)) {
         TRY(alloc(ctx, &L.vf.u, L.n));
         TRY(alloc(ctx, &L.vf.f, L.n));
@@ -265,6 +278,14 @@ int choose_lpr(int64_t rows, int64_t nnz) {
 // the coarsest direct solver: dense LU (FP64) and its explicit inverse
 amg_status coarse_factor(amg_ctx *ctx) {
     Level &C = ctx->lev[ctx->nlev - 1];
+    if (blockmode(ctx)) {
+        const int32_t n4 = ctx->nL;
+        CK(cudaMemsetAsync(ctx->lu, 0, sizeof(double) * (size_t)n4 * (size_t)n4, ctx->s));
+        launch_block_to_dense(C.n, C.A_ptr, C.A_col, C.Ab, ctx->lu, ctx->s);
+        { ProfScope ps_(ctx, AMG_PROF_LU, true); launch_dense_lu(n4, ctx->lu, ctx->piv, ctx->d_st, ctx->s); }
+        { ProfScope ps_(ctx, AMG_PROF_INV, true); launch_lu_inverse(n4, ctx->lu, ctx->piv, ctx->inv, ctx->s); }
+        return AMG_OK;
+    }
     const bool mx = mixed(ctx);
     launch_csr_to_dense(C.n, C.A_ptr, C.A_col, mx ? nullptr : C.A_val, mx ? C.A_valf : nullptr, ctx->lu, ctx->s);
     { ProfScope ps_(ctx, AMG_PROF_LU, true); launch_dense_lu(C.n, ctx->lu, ctx->piv, ctx->d_st, ctx->s); }
@@ -308,8 +329,30 @@ amg_status build_gather(amg_ctx *ctx, int l) {
     return AMG_OK;
 }
 
+// Alg. 4 body for the 4 x 4 block hierarchy: new fine blocks, then per
+// level the damped block-Jacobi inverses and (galerkin) the coarse blocks
+// through the fixed gather operators, then the coarsest factorisation
+amg_status block_numeric_rebuild(amg_ctx *ctx, const double *d_val, bool galerkin) {
+    Level &F = ctx->lev[0];
+    if (d_val != F.Ab) {
+        launch_check_finite((int64_t)nvals(ctx), d_val, ctx->d_st, ctx->s);
+        { ProfScope ps_(ctx, AMG_PROF_INGEST); CK(cudaMemcpyAsync(F.Ab, d_val, sizeof(double) * nvals(ctx), cudaMemcpyDeviceToDevice, ctx->s)); }
+    }
+    for (int l = 0; l + 1 < ctx->nlev; ++l) {
+        Level &L = ctx->lev[l];
+        Level &C = ctx->lev[l + 1];
+        launch_block_jacobi(L.n, L.dia, L.Ab, ctx->prm.jacobi_omega, L.Minv, ctx->s);
+        if (galerkin) {
+            { ProfScope ps_(ctx, AMG_PROF_AP_L0, l == 0); launch_block_gather(L.nnzAP, L.g1_ptr, L.g1_idx, L.g1_w, L.Ab, L.APb, ctx->s); }
+            { ProfScope ps_(ctx, AMG_PROF_RAP_L0, l == 0); launch_block_gather(C.nnz, L.g2_ptr, L.g2_idx, L.g2_w, L.APb, C.Ab, ctx->s); }
+        }
+    }
+    return coarse_factor(ctx);
+}
+
 // numeric part shared by the full setup and the partial rebuild (Alg. 4 body)
 amg_status numeric_rebuild(amg_ctx *ctx, const double *d_val, bool galerkin) {
+    if (blockmode(ctx)) return block_numeric_rebuild(ctx, d_val, galerkin);
     const amg_params &p = ctx->prm;
     Level &F = ctx->lev[0];
     const bool mx = mixed(ctx);
@@ -360,8 +403,15 @@ amg_status full_setup_impl(amg_ctx *ctx, const double *d_val) {
     TRY(alloc(ctx, &F.A_val, (size_t)nnz));
     TRY(alloc(ctx, &F.dia, (size_t)n));
     launch_check_pattern(n, F.A_ptr, F.A_col, F.dia, ctx->d_st, ctx->s);
-    launch_check_finite(nnz, d_val, ctx->d_st, ctx->s);
-    CK(cudaMemcpyAsync(F.A_val, d_val, sizeof(double) * (size_t)nnz, cudaMemcpyDeviceToDevice, ctx->s));
+    launch_check_finite((int64_t)nvals(ctx), d_val, ctx->d_st, ctx->s);
+    if (blockmode(ctx)) {
+        // the node graph carries the block norms
+        TRY(alloc(ctx, &F.Ab, nvals(ctx)));
+        CK(cudaMemcpyAsync(F.Ab, d_val, sizeof(double) * nvals(ctx), cudaMemcpyDeviceToDevice, ctx->s));
+        launch_block_norms(nnz, F.Ab, F.A_val, ctx->s);
+    } else {
+        CK(cudaMemcpyAsync(F.A_val, d_val, sizeof(double) * (size_t)nnz, cudaMemcpyDeviceToDevice, ctx->s));
+    }
     TRY(check_device(ctx, "full setup input"));
     ctx->nlev = 1;
     double theta = p.theta;
@@ -467,8 +517,18 @@ amg_status full_setup_impl(amg_ctx *ctx, const double *d_val) {
         launch_t2_fill(nagg, L.R_ptr, L.R_col, L.AP_ptr, L.AP_col, C.A_ptr, C.A_col, L.t2ptr, L.slot2, ctx->d_st,
                        ctx->s);
         // numeric values of the next level now: its strength test needs them
-        launch_ap_numeric_f64(L, L.A_val, ctx->s);
-        launch_rap_numeric_f64(L, C.A_ptr, C.A_val, ctx->s);
+        if (blockmode(ctx)) {
+            // coarse blocks through the gather operators, then their norms
+            TRY(build_gather(ctx, ctx->nlev - 1));
+            TRY(alloc(ctx, &L.APb, 16 * (size_t)L.nnzAP));
+            TRY(alloc(ctx, &C.Ab, 16 * (size_t)C.nnz));
+            launch_block_gather(L.nnzAP, L.g1_ptr, L.g1_idx, L.g1_w, L.Ab, L.APb, ctx->s);
+            launch_block_gather(C.nnz, L.g2_ptr, L.g2_idx, L.g2_w, L.APb, C.Ab, ctx->s);
+            launch_block_norms(C.nnz, C.Ab, C.A_val, ctx->s);
+        } else {
+            launch_ap_numeric_f64(L, L.A_val, ctx->s);
+            launch_rap_numeric_f64(L, C.A_ptr, C.A_val, ctx->s);
+        }
         TRY(check_device(ctx, "Galerkin product"));
         if (mixed(ctx)) {
             TRY(alloc(ctx, &L.P_valf, (size_t)L.nnzP));
@@ -482,15 +542,16 @@ amg_status full_setup_impl(amg_ctx *ctx, const double *d_val) {
     }
     // coarsest solver storage
     Level &C = ctx->lev[ctx->nlev - 1];
-    ctx->nL = C.n;
-    if ((int64_t)C.n * C.n > (int64_t)1 << 28)
+    ctx->nL = C.n * p.block_size;
+    const int64_t nL = ctx->nL;
+    if (nL * nL > (int64_t)1 << 28)
         return set_err(ctx, AMG_ERR_CAPACITY, "coarsest level too large for a dense LU");
-    TRY(alloc(ctx, &ctx->lu, (size_t)C.n * C.n));
-    TRY(alloc(ctx, &ctx->inv, (size_t)C.n * C.n));
-    TRY(alloc(ctx, &ctx->piv, (size_t)C.n));
+    TRY(alloc(ctx, &ctx->lu, (size_t)(nL * nL)));
+    TRY(alloc(ctx, &ctx->inv, (size_t)(nL * nL)));
+    TRY(alloc(ctx, &ctx->piv, (size_t)nL));
     if (mixed(ctx))
         for (int l = 1; l < ctx->nlev; ++l) launch_cast_f32(ctx->lev[l].nnz, ctx->lev[l].A_val, ctx->lev[l].A_valf, ctx->s);
-    TRY(numeric_rebuild(ctx, ctx->lev[0].A_val, false));
+    TRY(numeric_rebuild(ctx, blockmode(ctx) ? ctx->lev[0].Ab : ctx->lev[0].A_val, false));
     TRY(check_device(ctx, "full setup"));
     ctx->have_setup = true;
     return AMG_OK;
@@ -504,16 +565,17 @@ amg_status ensure_persistent(amg_ctx *ctx, int32_t n, int32_t nnz) {
     ctx->nnz = nnz;
     TRY(alloc(ctx, &ctx->fine_ptr, (size_t)n + 1, true));
     TRY(alloc(ctx, &ctx->fine_col, (size_t)nnz, true));
-    TRY(alloc(ctx, &ctx->cg_r, (size_t)n, true));
-    TRY(alloc(ctx, &ctx->cg_z, (size_t)n, true));
-    TRY(alloc(ctx, &ctx->cg_p, (size_t)n, true));
-    TRY(alloc(ctx, &ctx->cg_q, (size_t)n, true));
-    TRY(alloc(ctx, &ctx->cg_t, (size_t)n, true));
-    TRY(alloc(ctx, &ctx->cg_f, (size_t)n, true));
-    TRY(alloc(ctx, &ctx->cg_u, (size_t)n, true));
+    const size_t nv = (size_t)nvec(ctx);
+    TRY(alloc(ctx, &ctx->cg_r, nv, true));
+    TRY(alloc(ctx, &ctx->cg_z, nv, true));
+    TRY(alloc(ctx, &ctx->cg_p, nv, true));
+    TRY(alloc(ctx, &ctx->cg_q, nv, true));
+    TRY(alloc(ctx, &ctx->cg_t, nv, true));
+    TRY(alloc(ctx, &ctx->cg_f, nv, true));
+    TRY(alloc(ctx, &ctx->cg_u, nv, true));
     ctx->graph_valid = false;
     {
-        const size_t nb = (size_t)cg_blocks(n);
+        const size_t nb = (size_t)cg_blocks((int64_t)nv);
         TRY(alloc(ctx, &ctx->partial, 5 * nb, true));
         ctx->part_pq = ctx->partial;
         ctx->part_rr = ctx->partial + nb;
@@ -525,17 +587,17 @@ amg_status ensure_persistent(amg_ctx *ctx, int32_t n, int32_t nnz) {
     // the reduction counters inside must start at zero; kernels leave them zero
     CK(cudaMemsetAsync(ctx->cg, 0, sizeof(CgState), ctx->s));
     if (ctx->prm.solver == AMG_SOLVER_BICGSTAB) {
-        TRY(alloc(ctx, &ctx->bi_rh, (size_t)n, true));
-        TRY(alloc(ctx, &ctx->bi_s, (size_t)n, true));
-        TRY(alloc(ctx, &ctx->bi_sh, (size_t)n, true));
+        TRY(alloc(ctx, &ctx->bi_rh, nv, true));
+        TRY(alloc(ctx, &ctx->bi_s, nv, true));
+        TRY(alloc(ctx, &ctx->bi_sh, nv, true));
         TRY(alloc(ctx, &ctx->bi, 1, true));
         CK(cudaMemsetAsync(ctx->bi, 0, sizeof(BiState), ctx->s));
     }
-    TRY(alloc(ctx, &ctx->stage_val, (size_t)nnz, true));
-    TRY(alloc(ctx, &ctx->stage_f, (size_t)n, true));
-    TRY(alloc(ctx, &ctx->stage_u, (size_t)n, true));
+    TRY(alloc(ctx, &ctx->stage_val, nvals(ctx), true));
+    TRY(alloc(ctx, &ctx->stage_f, nv, true));
+    TRY(alloc(ctx, &ctx->stage_u, nv, true));
     ctx->A_sys_own = nullptr;
-    if (ctx->prm.mode == AMG_MODE_FULL_REUSE) TRY(alloc(ctx, &ctx->A_sys_own, (size_t)nnz, true));
+    if (ctx->prm.mode == AMG_MODE_FULL_REUSE) TRY(alloc(ctx, &ctx->A_sys_own, nvals(ctx), true));
     return AMG_OK;
 }
 
@@ -549,7 +611,7 @@ amg_status set_pattern(amg_ctx *ctx, int32_t n, int32_t nnz, const int32_t *d_pt
 }
 
 void update_sys(amg_ctx *ctx) {
-    ctx->A_sys = ctx->A_sys_own ? ctx->A_sys_own : ctx->lev[0].A_val;
+    ctx->A_sys = ctx->A_sys_own ? ctx->A_sys_own : blockmode(ctx) ? ctx->lev[0].Ab : ctx->lev[0].A_val;
 }
 
 // ---------------------------------------------------------------- V-cycle
@@ -684,9 +746,58 @@ void enqueue_vcycle(amg_ctx *ctx, const double *r, double *z, const int *skip, d
     up_finest<V>(ctx, r, cur[0], z, rz_partial, skip);
 }
 
+// Alg. 2 on the 4 x 4 block hierarchy (damped block Jacobi, zero initial
+// guess on every level, dense inverse on the coarsest), z = B r
+void enqueue_block_vcycle(amg_ctx *ctx, const double *r, double *z, const int *skip) {
+    const int nl = ctx->nlev;
+    const int npre = ctx->prm.npre, npost = ctx->prm.npost;
+    if (nl == 1) {
+        launch_coarse_solve<double, double, double>(ctx->nL, ctx->inv, r, z, skip, ctx->s);
+        return;
+    }
+    double *cur[kMaxLevels];
+    for (int l = 0; l < nl - 1; ++l) {
+        Level &L = ctx->lev[l];
+        const double *f = l == 0 ? r : L.vd.f;
+        double *u = L.vd.u, *t = L.vd.t;
+        if (npre <= 0) {
+            (void)(cudaMemsetAsync(u, 0, sizeof(double) * 4 * (size_t)L.n, ctx->s));
+        } else {
+            { ProfScope ps_(ctx, AMG_PROF_SMOOTH0_L0, l == 0); launch_block_smooth0(L.n, L.Minv, f, u, skip, ctx->s); }
+            for (int k = 1; k < npre; ++k) {
+                launch_block_sweep(L.n, L.A_ptr, L.A_col, L.Ab, L.Minv, f, u, t, skip, ctx->s);
+                std::swap(u, t);
+            }
+        }
+        launch_block_residual(L.n, L.A_ptr, L.A_col, L.Ab, f, u, L.vd.r, skip, ctx->s);
+        { ProfScope ps_(ctx, AMG_PROF_RESTRICT_L0, l == 0); launch_block_restrict(L.nc, L.R_ptr, L.R_col, L.R_val, L.vd.r, ctx->lev[l + 1].vd.f, skip, ctx->s); }
+        cur[l] = u;
+    }
+    Level &Cst = ctx->lev[nl - 1];
+    { ProfScope ps_(ctx, AMG_PROF_COARSE, true); launch_coarse_solve<double, double, double>(ctx->nL, ctx->inv, Cst.vd.f, Cst.vd.u, skip, ctx->s); }
+    cur[nl - 1] = Cst.vd.u;
+    for (int l = nl - 2; l >= 0; --l) {
+        Level &L = ctx->lev[l];
+        const double *f = l == 0 ? r : L.vd.f;
+        { ProfScope ps_(ctx, AMG_PROF_PROLONG_L0, l == 0); launch_block_prolong(L.n, L.P_ptr, L.P_col, L.P_val, cur[l + 1], cur[l], skip, ctx->s); }
+        double *u = cur[l];
+        double *t = (u == L.vd.u) ? L.vd.t : L.vd.u;
+        for (int k = 0; k < npost; ++k) {
+            double *out = (l == 0 && k == npost - 1) ? z : t;
+            { ProfScope ps_(ctx, AMG_PROF_SWEEP_L0, l == 0 && k == npost - 1); launch_block_sweep(L.n, L.A_ptr, L.A_col, L.Ab, L.Minv, f, u, out, skip, ctx->s); }
+            if (out == z) { u = z; break; }
+            std::swap(u, t);
+        }
+        if (l == 0 && u != z)
+            (void)(cudaMemcpyAsync(z, u, sizeof(double) * 4 * (size_t)L.n, cudaMemcpyDeviceToDevice, ctx->s));
+        cur[l] = u;
+    }
+}
+
 // z = B r; with rz_partial, also the per-block partials of r.z
 void vcycle(amg_ctx *ctx, const double *r, double *z, const int *skip, double *rz_partial = nullptr) {
-    if (mixed(ctx)) enqueue_vcycle<float>(ctx, r, z, skip, rz_partial);
+    if (blockmode(ctx)) enqueue_block_vcycle(ctx, r, z, skip);
+    else if (mixed(ctx)) enqueue_vcycle<float>(ctx, r, z, skip, rz_partial);
     else enqueue_vcycle<double>(ctx, r, z, skip, rz_partial);
 }
 
@@ -903,30 +1014,31 @@ amg_status finish_solve(amg_ctx *ctx, amg_info *info) {
 // already meets the tolerance, and the true-residual check skips itself
 // unless the recurrence reports convergence.
 void enqueue_bi_prologue(amg_ctx *ctx, const double *f, double *u, double tol) {
-    launch_bi_init(ctx->n, f, u, ctx->cg_r, ctx->bi_rh, ctx->cg_p, ctx->cg_q, ctx->partial, ctx->bi, tol,
+    launch_bi_init((int32_t)nvec(ctx), f, u, ctx->cg_r, ctx->bi_rh, ctx->cg_p, ctx->cg_q, ctx->partial, ctx->bi, tol,
                    ctx->prm.maxiter, ctx->s);
 }
 
 void enqueue_bi_iter(amg_ctx *ctx, const double *f, double *u, int use_h, cudaGraphConditionalHandle h) {
-    const int32_t n = ctx->n;
+    const int32_t n = (int32_t)nvec(ctx);
+    const int bs = ctx->prm.block_size;
     BiState *st = ctx->bi;
     double *part = ctx->partial;
     launch_bi_rho(n, ctx->bi_rh, ctx->cg_r, part, st, ctx->s);
     launch_bi_p(n, ctx->cg_r, ctx->cg_q, ctx->cg_p, st, ctx->s);
     vcycle(ctx, ctx->cg_p, ctx->cg_z, &st->done);
-    launch_bi_spmv_rv(n, ctx->fine_ptr, ctx->fine_col, ctx->A_sys, ctx->cg_z, ctx->cg_q, ctx->bi_rh, part, st, ctx->s);
+    launch_bi_spmv_rv(n, bs, ctx->fine_ptr, ctx->fine_col, ctx->A_sys, ctx->cg_z, ctx->cg_q, ctx->bi_rh, part, st, ctx->s);
     launch_bi_s(n, ctx->cg_r, ctx->cg_q, ctx->bi_s, part, st, ctx->s);
     launch_bi_half(n, ctx->cg_z, ctx->bi_s, u, ctx->cg_r, st, ctx->s);
     vcycle(ctx, ctx->bi_s, ctx->bi_sh, &st->skip);
-    launch_bi_spmv_t(n, ctx->fine_ptr, ctx->fine_col, ctx->A_sys, ctx->bi_sh, ctx->bi_s, ctx->cg_t, part, st, ctx->s);
+    launch_bi_spmv_t(n, bs, ctx->fine_ptr, ctx->fine_col, ctx->A_sys, ctx->bi_sh, ctx->bi_s, ctx->cg_t, part, st, ctx->s);
     launch_bi_xr(n, ctx->cg_z, ctx->bi_sh, ctx->bi_s, ctx->cg_t, u, ctx->cg_r, part, st, ctx->s);
-    launch_bi_true(n, ctx->fine_ptr, ctx->fine_col, ctx->A_sys, f, u, ctx->cg_t, part, st, 0, ctx->s);
+    launch_bi_true(n, bs, ctx->fine_ptr, ctx->fine_col, ctx->A_sys, f, u, ctx->cg_t, part, st, 0, ctx->s);
     launch_bi_replace(n, ctx->cg_t, ctx->cg_r, st, ctx->s);
     launch_bi_end(st, use_h, h, ctx->s);
 }
 
 void enqueue_bi_epilogue(amg_ctx *ctx, const double *f, double *u) {
-    launch_bi_true(ctx->n, ctx->fine_ptr, ctx->fine_col, ctx->A_sys, f, u, ctx->cg_t, ctx->partial, ctx->bi, 1,
+    launch_bi_true((int32_t)nvec(ctx), ctx->prm.block_size, ctx->fine_ptr, ctx->fine_col, ctx->A_sys, f, u, ctx->cg_t, ctx->partial, ctx->bi, 1,
                    ctx->s);
 }
 
@@ -1007,7 +1119,7 @@ amg_status finish_bi(amg_ctx *ctx, amg_info *info) {
 }
 
 amg_status solve_bi(amg_ctx *ctx, const double *f, double *u, double tol, amg_info *info) {
-    const int32_t n = ctx->n;
+    const int64_t n = nvec(ctx);
     if (ctx->use_graph && !ctx->prof.on) {
         if (!ctx->graph_valid || ctx->graph_tol != tol) TRY(build_bi_graph(ctx, tol));
         CK(cudaMemcpyAsync(ctx->cg_f, f, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, ctx->s));
@@ -1083,6 +1195,7 @@ amg_status amg_default_params(amg_params *prm) {
     prm->rebuild_every = 0;
     prm->rebuild_iter_growth = 0.0;
     prm->solver = AMG_SOLVER_CG;
+    prm->block_size = 1;
     return AMG_OK;
 }
 
@@ -1097,6 +1210,9 @@ amg_status amg_create(amg_ctx **out, const amg_params *prm, void *cuda_stream) {
         (p.precision != AMG_PREC_FP64 && p.precision != AMG_PREC_MIXED) || p.mode < 0 || p.mode > 2 ||
         p.rebuild_every < 0 || !(p.rebuild_iter_growth >= 0.0) ||
         (p.solver != AMG_SOLVER_CG && p.solver != AMG_SOLVER_BICGSTAB) ||
+        (p.block_size != 1 && p.block_size != 4) ||
+        (p.block_size == 4 && (p.smoothed != 0 || p.smoother != AMG_SMOOTHER_JACOBI ||
+                               p.precision != AMG_PREC_FP64 || p.solver != AMG_SOLVER_BICGSTAB)) ||
         !(p.theta >= 0.0) || !std::isfinite(p.omega))
         return AMG_ERR_ARG;
     amg_ctx *ctx = new amg_ctx();
@@ -1159,7 +1275,7 @@ amg_status amg_full_setup(amg_ctx *ctx, int32_t n, int32_t nnz, const int32_t *d
         return st;
     }
     if (ctx->A_sys_own)
-        CK(cudaMemcpyAsync(ctx->A_sys_own, d_val, sizeof(double) * (size_t)nnz, cudaMemcpyDeviceToDevice, ctx->s));
+        CK(cudaMemcpyAsync(ctx->A_sys_own, d_val, sizeof(double) * nvals(ctx), cudaMemcpyDeviceToDevice, ctx->s));
     update_sys(ctx);
     ctx->last_rebuilt = 1;
     ctx->steps_since_full = 0;
@@ -1177,7 +1293,7 @@ amg_status amg_partial_rebuild(amg_ctx *ctx, const double *d_val) {
             if (!ctx->lev[l].gather_ready) TRY(build_gather(ctx, l));
     TRY(numeric_rebuild(ctx, d_val, true));
     if (ctx->A_sys_own)
-        CK(cudaMemcpyAsync(ctx->A_sys_own, d_val, sizeof(double) * (size_t)ctx->nnz, cudaMemcpyDeviceToDevice,
+        CK(cudaMemcpyAsync(ctx->A_sys_own, d_val, sizeof(double) * nvals(ctx), cudaMemcpyDeviceToDevice,
                            ctx->s));
     TRY(check_device(ctx, "partial rebuild"));
     update_sys(ctx);
@@ -1225,7 +1341,7 @@ amg_status amg_step(amg_ctx *ctx, int32_t n, int32_t nnz, const int32_t *d_ptr, 
             if (st != AMG_OK) free_hierarchy(ctx);
         }
         if (st == AMG_OK) {
-            CK(cudaMemcpyAsync(ctx->A_sys_own, d_val, sizeof(double) * (size_t)ctx->nnz, cudaMemcpyDeviceToDevice,
+            CK(cudaMemcpyAsync(ctx->A_sys_own, d_val, sizeof(double) * nvals(ctx), cudaMemcpyDeviceToDevice,
                                ctx->s));
             update_sys(ctx);
             ctx->last_rebuilt = rebuild ? 1 : 0;
@@ -1249,7 +1365,15 @@ amg_status amg_apply_vcycle(amg_ctx *ctx, const double *d_r, double *d_z) {
     if (!ctx) return AMG_ERR_ARG;
     if (!ctx->have_setup) return set_err(ctx, AMG_ERR_STATE, "V-cycle before a setup");
     if (!d_r || !d_z) return set_err(ctx, AMG_ERR_ARG, "null vector");
-    vcycle(ctx, d_r, d_z, nullptr);
+    if (blockmode(ctx)) {
+        // the block kernels load 16-byte pairs: run on the context's own vectors
+        const size_t bytes = sizeof(double) * (size_t)nvec(ctx);
+        CK(cudaMemcpyAsync(ctx->cg_r, d_r, bytes, cudaMemcpyDeviceToDevice, ctx->s));
+        vcycle(ctx, ctx->cg_r, ctx->cg_z, nullptr);
+        CK(cudaMemcpyAsync(d_z, ctx->cg_z, bytes, cudaMemcpyDeviceToDevice, ctx->s));
+    } else {
+        vcycle(ctx, d_r, d_z, nullptr);
+    }
     CK(cudaStreamSynchronize(ctx->s));
     CK(cudaGetLastError());
     return AMG_OK;
@@ -1260,13 +1384,13 @@ amg_status amg_step_solve_host(amg_ctx *ctx, const double *h_val, const double *
     if (!ctx) return AMG_ERR_ARG;
     if (!ctx->fine_ptr) return set_err(ctx, AMG_ERR_STATE, "no pattern: call amg_full_setup or amg_step first");
     if (!h_val || !h_f || !h_u) return set_err(ctx, AMG_ERR_ARG, "null host buffer");
-    CK(cudaMemcpyAsync(ctx->stage_val, h_val, sizeof(double) * (size_t)ctx->nnz, cudaMemcpyHostToDevice, ctx->s));
-    CK(cudaMemcpyAsync(ctx->stage_f, h_f, sizeof(double) * (size_t)ctx->n, cudaMemcpyHostToDevice, ctx->s));
+    CK(cudaMemcpyAsync(ctx->stage_val, h_val, sizeof(double) * nvals(ctx), cudaMemcpyHostToDevice, ctx->s));
+    CK(cudaMemcpyAsync(ctx->stage_f, h_f, sizeof(double) * (size_t)nvec(ctx), cudaMemcpyHostToDevice, ctx->s));
     amg_status st = amg_step(ctx, ctx->n, ctx->nnz, ctx->fine_ptr, ctx->fine_col, ctx->stage_val, info);
     if (st != AMG_OK) return st;
     st = amg_solve(ctx, ctx->stage_f, ctx->stage_u, tol, info);
     if (st != AMG_OK && st != AMG_NOT_CONVERGED) return st;
-    CK(cudaMemcpyAsync(h_u, ctx->stage_u, sizeof(double) * (size_t)ctx->n, cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaMemcpyAsync(h_u, ctx->stage_u, sizeof(double) * (size_t)nvec(ctx), cudaMemcpyDeviceToHost, ctx->s));
     CK(cudaStreamSynchronize(ctx->s));
     return st;
 }
@@ -1303,7 +1427,9 @@ amg_status amg_export_csr(amg_ctx *ctx, int32_t level, int32_t which, int32_t *d
     if (d_ptr) CK(cudaMemcpyAsync(d_ptr, ptr, sizeof(int32_t) * ((size_t)nrows + 1), cudaMemcpyDeviceToDevice, ctx->s));
     if (d_col) CK(cudaMemcpyAsync(d_col, col, sizeof(int32_t) * (size_t)nnz, cudaMemcpyDeviceToDevice, ctx->s));
     if (d_val) {
-        if (mixed(ctx) && valf) launch_copy_cast<float, double>(nnz, valf, d_val, nullptr, ctx->s);
+        if (blockmode(ctx) && which == 0)
+            CK(cudaMemcpyAsync(d_val, L.Ab, sizeof(double) * 16 * (size_t)nnz, cudaMemcpyDeviceToDevice, ctx->s));
+        else if (mixed(ctx) && valf) launch_copy_cast<float, double>(nnz, valf, d_val, nullptr, ctx->s);
         else CK(cudaMemcpyAsync(d_val, val, sizeof(double) * (size_t)nnz, cudaMemcpyDeviceToDevice, ctx->s));
     }
     CK(cudaStreamSynchronize(ctx->s));
@@ -1316,7 +1442,10 @@ amg_status amg_export_level_vec(amg_ctx *ctx, int32_t level, int32_t *d_agg, uin
     if (d_agg) CK(cudaMemcpyAsync(d_agg, L.agg, sizeof(int32_t) * (size_t)L.n, cudaMemcpyDeviceToDevice, ctx->s));
     if (d_strong) CK(cudaMemcpyAsync(d_strong, L.strong, (size_t)L.nnz, cudaMemcpyDeviceToDevice, ctx->s));
     if (d_m) {
-        if (mixed(ctx)) launch_copy_cast<float, double>(L.n, L.mf, d_m, nullptr, ctx->s);
+        if (blockmode(ctx)) {
+            if (L.Minv)
+                CK(cudaMemcpyAsync(d_m, L.Minv, sizeof(double) * 16 * (size_t)L.n, cudaMemcpyDeviceToDevice, ctx->s));
+        } else if (mixed(ctx)) launch_copy_cast<float, double>(L.n, L.mf, d_m, nullptr, ctx->s);
         else CK(cudaMemcpyAsync(d_m, L.m, sizeof(double) * (size_t)L.n, cudaMemcpyDeviceToDevice, ctx->s));
     }
     CK(cudaStreamSynchronize(ctx->s));
@@ -1400,6 +1529,17 @@ amg_status amg_levelset_values(int32_t dim, int32_t N, const double *d_fx, const
         return AMG_ERR_ARG;
     if (amg_poisson_nnz(dim, N) > INT32_MAX) return AMG_ERR_ARG;
     launch_levelset_vals(dim, N, d_fx, d_fy, d_fz, d_ptr, d_val, (cudaStream_t)cuda_stream);
+    if (cudaGetLastError() != cudaSuccess) return AMG_ERR_CUDA;
+    return AMG_OK;
+}
+
+amg_status amg_stokes_values(int32_t N, const double *d_rho, const double *d_mu, const double *d_fx,
+                             const double *d_fy, const double *d_fz, double mass, const int32_t *d_ptr, double *d_val,
+                             void *cuda_stream) {
+    if (N < 1 || !d_rho || !d_mu || !d_fx || !d_fy || !d_fz || !d_ptr || !d_val || !std::isfinite(mass))
+        return AMG_ERR_ARG;
+    if (amg_poisson_nnz(3, N) > INT32_MAX / 16) return AMG_ERR_ARG;
+    launch_stokes_vals(N, d_rho, d_mu, d_fx, d_fy, d_fz, mass, d_ptr, d_val, (cudaStream_t)cuda_stream);
     if (cudaGetLastError() != cudaSuccess) return AMG_ERR_CUDA;
     return AMG_OK;
 }

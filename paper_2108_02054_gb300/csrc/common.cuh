@@ -88,6 +88,10 @@ struct Level {
     // V-cycle vectors
     VecSet<double> vd;
     VecSet<float> vf;
+    // 4 x 4 block mode: block values of A and A P (16 per entry; A_val then
+    // holds the block norms that strength and aggregation see), damped
+    // block-Jacobi inverses (16 per node); vd vectors hold 4 per node
+    double *Ab = nullptr, *APb = nullptr, *Minv = nullptr;
 };
 
 // ------------------------------------------------------------------ launchers
@@ -226,18 +230,39 @@ void launch_bi_init(int32_t n, const double *f, double *x, double *r, double *rh
                     double *partial, BiState *st, double tol, int maxiter, cudaStream_t s);
 void launch_bi_rho(int32_t n, const double *rh, const double *r, double *partial, BiState *st, cudaStream_t s);
 void launch_bi_p(int32_t n, const double *r, const double *v, double *p, BiState *st, cudaStream_t s);
-void launch_bi_spmv_rv(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *ph,
-                       double *v, const double *rh, double *partial, BiState *st, cudaStream_t s);
+void launch_bi_spmv_rv(int32_t n, int bs, const int32_t *ptr, const int32_t *col, const double *val,
+                       const double *ph, double *v, const double *rh, double *partial, BiState *st, cudaStream_t s);
 void launch_bi_s(int32_t n, const double *r, const double *v, double *sv, double *partial, BiState *st,
                  cudaStream_t s);
 void launch_bi_half(int32_t n, const double *ph, const double *sv, double *x, double *r, BiState *st, cudaStream_t s);
-void launch_bi_spmv_t(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *sh,
-                      const double *sv, double *t, double *partial, BiState *st, cudaStream_t s);
+void launch_bi_spmv_t(int32_t n, int bs, const int32_t *ptr, const int32_t *col, const double *val,
+                      const double *sh, const double *sv, double *t, double *partial, BiState *st, cudaStream_t s);
 void launch_bi_xr(int32_t n, const double *ph, const double *sh, const double *sv, const double *t, double *x,
                   double *r, double *partial, BiState *st, cudaStream_t s);
-void launch_bi_true(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *f,
+void launch_bi_true(int32_t n, int bs, const int32_t *ptr, const int32_t *col, const double *val, const double *f,
                     const double *x, double *t, double *partial, BiState *st, int force, cudaStream_t s);
 void launch_bi_replace(int32_t n, const double *t, double *r, BiState *st, cudaStream_t s);
 void launch_bi_end(BiState *st, int use_h, cudaGraphConditionalHandle h, cudaStream_t s);
+// (BiCGStab vectors have n = bs * nodes entries; bs = 4 for the block matrix)
+
+// 4 x 4 block-valued hierarchy (block.cu): block CSR, 16 doubles per entry
+void launch_stokes_vals(int N, const double *rho, const double *mu, const double *fx, const double *fy,
+                        const double *fz, double mass, const int32_t *ptr, double *val, cudaStream_t s);
+void launch_block_norms(int64_t nnz, const double *bv, double *out, cudaStream_t s);
+void launch_block_gather(int64_t nout, const int32_t *eptr, const int32_t *idx, const double *w, const double *x,
+                         double *y, cudaStream_t s);
+void launch_block_jacobi(int32_t n, const int32_t *dia, const double *bv, double wj, double *minv, cudaStream_t s);
+void launch_block_to_dense(int32_t n, const int32_t *ptr, const int32_t *col, const double *bv, double *dense,
+                           cudaStream_t s);
+void launch_block_smooth0(int32_t n, const double *minv, const double *f, double *u, const int *skip,
+                          cudaStream_t s);
+void launch_block_sweep(int32_t n, const int32_t *ptr, const int32_t *col, const double *bv, const double *minv,
+                        const double *f, const double *uin, double *uout, const int *skip, cudaStream_t s);
+void launch_block_residual(int32_t n, const int32_t *ptr, const int32_t *col, const double *bv, const double *f,
+                           const double *u, double *r, const int *skip, cudaStream_t s);
+void launch_block_restrict(int32_t nc, const int32_t *Rptr, const int32_t *Rcol, const double *Rval, const double *r,
+                           double *fc, const int *skip, cudaStream_t s);
+void launch_block_prolong(int32_t n, const int32_t *Pptr, const int32_t *Pcol, const double *Pval, const double *uc,
+                          double *u, const int *skip, cudaStream_t s);
 
 }  // namespace amgpr

@@ -903,6 +903,29 @@ __global__ void k_cg_update_p(int32_t n, CgState *cg, const double *__restrict__
 // device-resident control as CG: every kernel returns at once when the state
 // says done; scalars are formed by the last block of the producing kernel.
 
+// row i of y = A x for the scalar matrix (BS = 1) or the 4 x 4 block matrix
+// seen as 4 n scalar rows (BS = 4: node i / 4, component i % 4; entry order,
+// then component order)
+template <int BS>
+__device__ __forceinline__ double bi_row(int32_t i, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                                         const double *__restrict__ val, const double *__restrict__ x) {
+    double s = 0.0;
+    if (BS == 1) {
+        for (int32_t e = ptr[i]; e < ptr[i + 1]; ++e) s = fma(val[e], x[col[e]], s);
+    } else {
+        const int32_t node = i >> 2, r = i & 3;
+        for (int32_t e = ptr[node]; e < ptr[node + 1]; ++e) {
+            const double *b = val + (int64_t)16 * e + 4 * r;
+            const double *xv = x + (int64_t)4 * col[e];
+            s = fma(b[0], xv[0], s);
+            s = fma(b[1], xv[1], s);
+            s = fma(b[2], xv[2], s);
+            s = fma(b[3], xv[3], s);
+        }
+    }
+    return s;
+}
+
 // two sums published together; the last block returns both totals
 __device__ bool bi_reduce2(double a, double b, double *pa, double *pb, unsigned *counter, double *ta, double *tb) {
     a = block_sum(a);
@@ -979,14 +1002,14 @@ __global__ void k_bi_p(int32_t n, const double *__restrict__ r, const double *__
 }
 
 // v = A p^, (r^, v); alpha = rho / (r^, v)
+template <int BS>
 __global__ void k_bi_spmv_rv(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                              const double *__restrict__ val, const double *__restrict__ ph, double *__restrict__ v,
                              const double *__restrict__ rh, double *__restrict__ partial, BiState *st) {
     if (st->done) return;
     double d = 0.0;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int32_t e = ptr[i]; e < ptr[i + 1]; ++e) s = fma(val[e], ph[col[e]], s);
+        const double s = bi_row<BS>(i, ptr, col, val, ph);
         v[i] = s;
         d = fma(rh[i], s, d);
     }
@@ -1035,6 +1058,7 @@ __global__ void k_bi_half(int32_t n, const double *__restrict__ ph, const double
 }
 
 // t = A s^, (t, s), (t, t); omega = (t, s) / (t, t)
+template <int BS>
 __global__ void k_bi_spmv_t(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                             const double *__restrict__ val, const double *__restrict__ sh,
                             const double *__restrict__ sv, double *__restrict__ t, double *__restrict__ partial,
@@ -1042,8 +1066,7 @@ __global__ void k_bi_spmv_t(int32_t n, const int32_t *__restrict__ ptr, const in
     if (st->skip) return;
     double a = 0.0, b = 0.0;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int32_t e = ptr[i]; e < ptr[i + 1]; ++e) s = fma(val[e], sh[col[e]], s);
+        const double s = bi_row<BS>(i, ptr, col, val, sh);
         t[i] = s;
         a = fma(s, sv[i], a);
         b = fma(s, s, b);
@@ -1086,14 +1109,14 @@ __global__ void k_bi_xr(int32_t n, const double *__restrict__ ph, const double *
 // the true residual when the recurrence (or the half step) reports
 // convergence: accept, or replace r by it (twice at most); with force, the
 // final relative residual
+template <int BS>
 __global__ void k_bi_true(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                           const double *__restrict__ val, const double *__restrict__ f, const double *__restrict__ x,
                           double *__restrict__ t, double *__restrict__ partial, BiState *st, int force) {
     if (!force && (st->done || !st->need_true)) return;
     double d = 0.0;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int32_t e = ptr[i]; e < ptr[i + 1]; ++e) s = fma(val[e], x[col[e]], s);
+        const double s = bi_row<BS>(i, ptr, col, val, x);
         const double ti = f[i] - s;
         t[i] = ti;
         d = fma(ti, ti, d);
@@ -1395,10 +1418,11 @@ void launch_bi_p(int32_t n, const double *r, const double *v, double *p, BiState
     count_launch();
     k_bi_p<<<cg_blocks(n), kCgThreads, 0, s>>>(n, r, v, p, st);
 }
-void launch_bi_spmv_rv(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *ph,
-                       double *v, const double *rh, double *partial, BiState *st, cudaStream_t s) {
+void launch_bi_spmv_rv(int32_t n, int bs, const int32_t *ptr, const int32_t *col, const double *val,
+                       const double *ph, double *v, const double *rh, double *partial, BiState *st, cudaStream_t s) {
     count_launch();
-    k_bi_spmv_rv<<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, col, val, ph, v, rh, partial, st);
+    if (bs == 4) k_bi_spmv_rv<4><<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, col, val, ph, v, rh, partial, st);
+    else k_bi_spmv_rv<1><<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, col, val, ph, v, rh, partial, st);
 }
 void launch_bi_s(int32_t n, const double *r, const double *v, double *sv, double *partial, BiState *st,
                  cudaStream_t s) {
@@ -1409,20 +1433,22 @@ void launch_bi_half(int32_t n, const double *ph, const double *sv, double *x, do
     count_launch();
     k_bi_half<<<cg_blocks(n), kCgThreads, 0, s>>>(n, ph, sv, x, r, st);
 }
-void launch_bi_spmv_t(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *sh,
-                      const double *sv, double *t, double *partial, BiState *st, cudaStream_t s) {
+void launch_bi_spmv_t(int32_t n, int bs, const int32_t *ptr, const int32_t *col, const double *val,
+                      const double *sh, const double *sv, double *t, double *partial, BiState *st, cudaStream_t s) {
     count_launch();
-    k_bi_spmv_t<<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, col, val, sh, sv, t, partial, st);
+    if (bs == 4) k_bi_spmv_t<4><<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, col, val, sh, sv, t, partial, st);
+    else k_bi_spmv_t<1><<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, col, val, sh, sv, t, partial, st);
 }
 void launch_bi_xr(int32_t n, const double *ph, const double *sh, const double *sv, const double *t, double *x,
                   double *r, double *partial, BiState *st, cudaStream_t s) {
     count_launch();
     k_bi_xr<<<cg_blocks(n), kCgThreads, 0, s>>>(n, ph, sh, sv, t, x, r, partial, st);
 }
-void launch_bi_true(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *f,
+void launch_bi_true(int32_t n, int bs, const int32_t *ptr, const int32_t *col, const double *val, const double *f,
                     const double *x, double *t, double *partial, BiState *st, int force, cudaStream_t s) {
     count_launch();
-    k_bi_true<<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, col, val, f, x, t, partial, st, force);
+    if (bs == 4) k_bi_true<4><<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, col, val, f, x, t, partial, st, force);
+    else k_bi_true<1><<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, col, val, f, x, t, partial, st, force);
 }
 void launch_bi_replace(int32_t n, const double *t, double *r, BiState *st, cudaStream_t s) {
     count_launch();
