@@ -174,8 +174,8 @@ def algorithmic_bytes(slot, lv, s):
     nnzc = lv[1]["nnz"] if len(lv) > 1 else 0
     if slot == "cg_spmv":      # q = A p, p.q: ptr, col, val(f64), p, q
         return 4 * (n + 1) + 12 * nnz + 16 * n
-    if slot == "smooth0_l0":   # u = m f, r = f - A(m f): ptr, col, val, m, f(f64), u, r
-        return 4 * (n + 1) + nnz * (4 + s) + n * s + 8 * n + 2 * n * s
+    if slot == "smooth0_l0":   # r = f - A u0 (u0 = m o f, written with f): ptr, col, val, u0, f(f64), r
+        return 4 * (n + 1) + nnz * (4 + s) + n * s + 8 * n + n * s
     if slot == "sweep_l0":     # z = u + m (f - A u): ptr, col, val, m, f(f64), u, z(f64)
         return 4 * (n + 1) + nnz * (4 + s) + n * s + 8 * n + n * s + 8 * n
     if slot == "restrict_l0":  # f_c = R r
@@ -186,10 +186,10 @@ def algorithmic_bytes(slot, lv, s):
         return 4 * (n + 1) + nnz * (4 + s) + 4 * (n + 1) + nnzP * s
     if slot == "rap_l0":       # stage 2: R (ptr, col, val), A_c values out
         return 4 * (nc + 1) + nnzP * (4 + s) + nnzc * s
-    if slot == "ingest":       # fine values in (f64), hierarchy copy out, smoother diagonal
-        return 4 * (n + 1) + 8 * nnz + (8 if s == 8 else 12) * nnz + n * s
-    if slot in ("cg_update",):  # u, p, q, r in; u, r out
-        return 8 * n * 6
+    if slot == "ingest":       # fine values in (f64); CSR and SELL-32 copies out (f64, + f32 when mixed); diagonal
+        return 4 * (n + 1) + 8 * nnz + (16 if s == 8 else 24) * nnz + n * s
+    if slot in ("cg_update",):  # u, p, q, r in; u, r out; u0 = m o r (m in, u0 out)
+        return 8 * n * 6 + 2 * n * s
     if slot == "cg_p":
         return 8 * n * 3
     if slot == "dot":

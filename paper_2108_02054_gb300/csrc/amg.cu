@@ -54,6 +54,10 @@ struct amg_ctx {
     // system matrix of the solve (aliases level 0 except under full reuse)
     double *A_sys = nullptr;
     double *A_sys_own = nullptr;
+    // SELL-32 copy of the system matrix for the Krylov kernels (the finest
+    // level's own copy, or sl_sys_own filled from A_sys_own under full reuse)
+    SellRef sell_sys;
+    double *sl_sys_own = nullptr;
     // CG
     double *cg_r = nullptr, *cg_z = nullptr, *cg_p = nullptr, *cg_q = nullptr, *cg_t = nullptr;
     // per-block partial sums of the CG reductions, one set per reduction so
@@ -161,6 +165,8 @@ void free_hierarchy(amg_ctx *ctx) {
     ctx->have_setup = false;
     ctx->lu = ctx->inv = nullptr;
     ctx->piv = nullptr;
+    ctx->sl_sys_own = nullptr;
+    ctx->sell_sys = SellRef{};
     ctx->graph_valid = false;
 }
 
@@ -360,7 +366,7 @@ amg_status numeric_rebuild(amg_ctx *ctx, const double *d_val, bool galerkin) {
         ProfScope ps_(ctx, AMG_PROF_INGEST);
         launch_ingest_fine(F.n, F.A_ptr, d_val, F.dia, p.smoother, p.jacobi_omega,
                            d_val == F.A_val ? nullptr : F.A_val, mx ? F.A_valf : nullptr, mx ? nullptr : F.m,
-                           mx ? F.mf : nullptr, ctx->d_st, ctx->s);
+                           mx ? F.mf : nullptr, ctx->d_st, F.sl_ptr, F.sl_val, mx ? F.sl_valf : nullptr, ctx->s);
     }
     for (int l = 0; l + 1 < ctx->nlev; ++l) {
         Level &L = ctx->lev[l];
@@ -388,6 +394,27 @@ amg_status numeric_rebuild(amg_ctx *ctx, const double *d_val, bool galerkin) {
         }
     }
     return coarse_factor(ctx);
+}
+
+// SELL-32 layout of the finest level's pattern (one lane per row): slice
+// offsets, columns; values are written at every ingest of new fine values
+amg_status build_sell(amg_ctx *ctx, Level &L) {
+    const int32_t nsl = (L.n + 31) / 32;
+    int32_t *slots = nullptr;
+    TRY(alloc(ctx, &slots, (size_t)nsl));
+    TRY(alloc(ctx, &L.sl_ptr, (size_t)nsl + 1));
+    launch_sell_slots(L.n, L.A_ptr, slots, ctx->s);
+    TRY(scan(ctx, slots, L.sl_ptr, nsl));
+    TRY(check_device(ctx, "SELL layout"));
+    int32_t total = 0;
+    TRY(read_scalar(ctx, L.sl_ptr + nsl, &total));
+    TRY(alloc(ctx, &L.sl_col, (size_t)total));
+    TRY(alloc(ctx, &L.sl_val, (size_t)total));
+    if (mixed(ctx)) TRY(alloc(ctx, &L.sl_valf, (size_t)total));
+    ctx->sl_sys_own = nullptr;
+    if (ctx->A_sys_own) TRY(alloc(ctx, &ctx->sl_sys_own, (size_t)total));
+    launch_sell_cols(L.n, L.A_ptr, L.A_col, L.sl_ptr, L.sl_col, ctx->s);
+    return AMG_OK;
 }
 
 amg_status full_setup_impl(amg_ctx *ctx, const double *d_val) {
@@ -423,6 +450,7 @@ amg_status full_setup_impl(amg_ctx *ctx, const double *d_val) {
         CK(cudaMemsetAsync(L.agg, 0xff, sizeof(int32_t) * (size_t)L.n, ctx->s));
         CK(cudaMemsetAsync(L.strong, 0, (size_t)L.nnz, ctx->s));
         L.lpr = choose_lpr(L.n, L.nnz);
+        if (ctx->nlev == 1 && L.lpr == 1 && !blockmode(ctx)) TRY(build_sell(ctx, L));
         if (L.n <= p.coarse_enough || ctx->nlev >= p.max_levels || ctx->nlev >= kMaxLevels) break;
         // strength and aggregation
         int32_t *deg = nullptr, *root_id = nullptr, *agg1 = nullptr, *root_of = nullptr;
@@ -612,6 +640,15 @@ amg_status set_pattern(amg_ctx *ctx, int32_t n, int32_t nnz, const int32_t *d_pt
 
 void update_sys(amg_ctx *ctx) {
     ctx->A_sys = ctx->A_sys_own ? ctx->A_sys_own : blockmode(ctx) ? ctx->lev[0].Ab : ctx->lev[0].A_val;
+    const Level &F = ctx->lev[0];
+    ctx->sell_sys = SellRef{};
+    if (!F.sl_ptr) return;
+    if (ctx->A_sys == F.A_val) {
+        ctx->sell_sys = SellRef{F.sl_ptr, F.sl_col, F.sl_val};
+    } else if (ctx->sl_sys_own) {
+        launch_sell_vals(F.n, F.A_ptr, F.sl_ptr, ctx->A_sys, ctx->sl_sys_own, ctx->s);
+        ctx->sell_sys = SellRef{F.sl_ptr, F.sl_col, ctx->sl_sys_own};
+    }
 }
 
 // ---------------------------------------------------------------- V-cycle
@@ -635,9 +672,10 @@ struct Vops<float> {
 };
 
 // pre-smoothing from a zero guess and the residual on level l (input f of type TF);
-// returns the level's current iterate pointer
+// returns the level's current iterate pointer.  u0_ready: the producer of f
+// has already written the first smoothing step u = m o f into the level's u.
 template <class V, class TF>
-V *down_level(amg_ctx *ctx, int l, const TF *f, const int *skip) {
+V *down_level(amg_ctx *ctx, int l, const TF *f, const int *skip, bool u0_ready) {
     Level &L = ctx->lev[l];
     VecSet<V> &v = Vops<V>::vec(L);
     const V *A = Vops<V>::A(L), *m = Vops<V>::m(L);
@@ -646,6 +684,14 @@ V *down_level(amg_ctx *ctx, int l, const TF *f, const int *skip) {
     if (npre <= 0) {
         cudaMemsetAsync(u, 0, sizeof(V) * (size_t)L.n, ctx->s);
         launch_copy_cast<TF, V>(L.n, f, v.r, skip, ctx->s);
+        return u;
+    }
+    if (u0_ready) {
+        for (int k = 1; k < npre; ++k) {
+            launch_smooth_sweep<V, TF, V>(L, A, m, f, u, t, skip, ctx->s);
+            std::swap(u, t);
+        }
+        { ProfScope ps_(ctx, AMG_PROF_SMOOTH0_L0, l == 0); launch_residual<V, TF>(L, A, f, u, v.r, skip, ctx->s); }
         return u;
     }
     { ProfScope ps_(ctx, AMG_PROF_SMOOTH0_L0, l == 0); launch_smooth0_residual<V, TF>(L, A, m, f, u, v.r, skip, ctx->s); }
@@ -706,24 +752,29 @@ void up_level(amg_ctx *ctx, int l, const TF *f, V *u, TO *out, const int *skip) 
 }
 
 template <class V>
-void enqueue_vcycle(amg_ctx *ctx, const double *r, double *z, const int *skip, double *rz_partial) {
+void enqueue_vcycle(amg_ctx *ctx, const double *r, double *z, const int *skip, double *rz_partial, bool u0_ready) {
     const int nl = ctx->nlev;
     if (nl == 1) {
         launch_coarse_solve<V, double, double>(ctx->lev[0].n, ctx->inv, r, z, skip, ctx->s);
         if (rz_partial) launch_dot(ctx->n, r, z, rz_partial, skip, ctx->cg, 1, ctx->s);
         return;
     }
+    // the restriction into a smoothed level also writes that level's u0 = m o f
+    const bool pre = ctx->prm.npre > 0;
+    auto m_of = [&](int l) -> const V * { return (pre && l < nl - 1) ? Vops<V>::m(ctx->lev[l]) : nullptr; };
+    auto u_of = [&](int l) -> V * { return (pre && l < nl - 1) ? Vops<V>::vec(ctx->lev[l]).u : nullptr; };
     V *cur[kMaxLevels];
-    cur[0] = down_level<V, double>(ctx, 0, r, skip);
+    cur[0] = down_level<V, double>(ctx, 0, r, skip, u0_ready);
     {
         ProfScope ps_(ctx, AMG_PROF_RESTRICT_L0);
         launch_restrict<V>(ctx->lev[0], Vops<V>::R(ctx->lev[0]), Vops<V>::vec(ctx->lev[0]).r,
-                           Vops<V>::vec(ctx->lev[1]).f, skip, ctx->s);
+                           Vops<V>::vec(ctx->lev[1]).f, m_of(1), u_of(1), skip, ctx->s);
     }
     for (int l = 1; l < nl - 1; ++l) {
         Level &L = ctx->lev[l];
-        cur[l] = down_level<V, V>(ctx, l, Vops<V>::vec(L).f, skip);
-        launch_restrict<V>(L, Vops<V>::R(L), Vops<V>::vec(L).r, Vops<V>::vec(ctx->lev[l + 1]).f, skip, ctx->s);
+        cur[l] = down_level<V, V>(ctx, l, Vops<V>::vec(L).f, skip, pre);
+        launch_restrict<V>(L, Vops<V>::R(L), Vops<V>::vec(L).r, Vops<V>::vec(ctx->lev[l + 1]).f, m_of(l + 1),
+                           u_of(l + 1), skip, ctx->s);
     }
     Level &Cst = ctx->lev[nl - 1];
     { ProfScope ps_(ctx, AMG_PROF_COARSE, true); launch_coarse_solve<V, V, V>(Cst.n, ctx->inv, Vops<V>::vec(Cst).f, Vops<V>::vec(Cst).u, skip, ctx->s); }
@@ -795,19 +846,33 @@ void enqueue_block_vcycle(amg_ctx *ctx, const double *r, double *z, const int *s
 }
 
 // z = B r; with rz_partial, also the per-block partials of r.z
-void vcycle(amg_ctx *ctx, const double *r, double *z, const int *skip, double *rz_partial = nullptr) {
+// u0_ready: the producer of r has written the finest level's u0 (cg_smooth0)
+void vcycle(amg_ctx *ctx, const double *r, double *z, const int *skip, double *rz_partial = nullptr,
+            bool u0_ready = false) {
     if (blockmode(ctx)) enqueue_block_vcycle(ctx, r, z, skip);
-    else if (mixed(ctx)) enqueue_vcycle<float>(ctx, r, z, skip, rz_partial);
-    else enqueue_vcycle<double>(ctx, r, z, skip, rz_partial);
+    else if (mixed(ctx)) enqueue_vcycle<float>(ctx, r, z, skip, rz_partial, u0_ready);
+    else enqueue_vcycle<double>(ctx, r, z, skip, rz_partial, u0_ready);
 }
 
 // ---------------------------------------------------------------- CG
 // CG prologue: u = 0, r = f, z = B r, p = z, rz = r.z (device state in ctx->cg)
+// the CG kernels that produce r also write the V-cycle's first finest-level
+// smoothing step from zero, u0 = m o r (when the V-cycle has a smoothed level)
+Smooth0Out cg_smooth0(amg_ctx *ctx) {
+    Smooth0Out z0;
+    if (ctx->nlev < 2 || ctx->prm.npre < 1 || blockmode(ctx)) return z0;
+    Level &F = ctx->lev[0];
+    if (mixed(ctx)) { z0.mf = F.mf; z0.uf = F.vf.u; }
+    else { z0.m = F.m; z0.u = F.vd.u; }
+    return z0;
+}
+bool cg_u0(amg_ctx *ctx) { return ctx->nlev >= 2 && ctx->prm.npre >= 1 && !blockmode(ctx); }
+
 void enqueue_cg_prologue(amg_ctx *ctx, const double *f, double *u, double tol) {
     const int32_t n = ctx->n;
     CgState *cg = ctx->cg;
-    launch_cg_init(n, f, u, ctx->cg_r, ctx->part_rr, cg, tol, ctx->prm.maxiter, ctx->s);
-    vcycle(ctx, ctx->cg_r, ctx->cg_z, &cg->done, ctx->part_rz);
+    launch_cg_init(n, f, u, ctx->cg_r, ctx->part_rr, cg, tol, ctx->prm.maxiter, cg_smooth0(ctx), ctx->s);
+    vcycle(ctx, ctx->cg_r, ctx->cg_z, &cg->done, ctx->part_rz, cg_u0(ctx));
     launch_cg_set_rz_p(n, ctx->cg_z, ctx->cg_p, cg, ctx->s);
 }
 
@@ -818,11 +883,12 @@ void enqueue_cg_iter_a(amg_ctx *ctx, double *u, int use_h, cudaGraphConditionalH
     CgState *cg = ctx->cg;
     {
         ProfScope ps_(ctx, AMG_PROF_CG_SPMV, true);
-        launch_spmv_dot(n, ctx->fine_ptr, ctx->fine_col, ctx->A_sys, ctx->cg_p, ctx->cg_q, ctx->part_pq, cg, ctx->s);
+        launch_spmv_dot(n, ctx->fine_ptr, ctx->fine_col, ctx->A_sys, ctx->sell_sys, ctx->cg_p, ctx->cg_q, ctx->part_pq, cg,
+                        ctx->s);
     }
     {
         ProfScope ps_(ctx, AMG_PROF_CG_UPDATE, true);
-        launch_cg_update_ur(n, cg, ctx->cg_p, ctx->cg_q, u, ctx->cg_r, ctx->part_rr, use_h, hb, ctx->s);
+        launch_cg_update_ur(n, cg, ctx->cg_p, ctx->cg_q, u, ctx->cg_r, ctx->part_rr, use_h, hb, cg_smooth0(ctx), ctx->s);
     }
 }
 
@@ -831,8 +897,9 @@ void enqueue_cg_iter_a(amg_ctx *ctx, double *u, int use_h, cudaGraphConditionalH
 void enqueue_cg_iter_b(amg_ctx *ctx, const double *f, double *u) {
     const int32_t n = ctx->n;
     CgState *cg = ctx->cg;
-    launch_true_residual(n, ctx->fine_ptr, ctx->fine_col, ctx->A_sys, f, u, ctx->cg_t, ctx->part_tt, cg, 0, ctx->s);
-    launch_replace_r(n, cg, ctx->cg_t, ctx->cg_r, ctx->s);
+    launch_true_residual(n, ctx->fine_ptr, ctx->fine_col, ctx->A_sys, ctx->sell_sys, f, u, ctx->cg_t, ctx->part_tt,
+                         cg, 0, ctx->s);
+    launch_replace_r(n, cg, ctx->cg_t, ctx->cg_r, cg_smooth0(ctx), ctx->s);
 }
 
 // C: z = B r with the partials of r.z, beta and p (and the loop condition)
@@ -841,7 +908,7 @@ void enqueue_cg_iter_c(amg_ctx *ctx, int use_h, cudaGraphConditionalHandle h) {
     const bool flex = mixed(ctx);
     CgState *cg = ctx->cg;
     if (flex) launch_dot(n, ctx->cg_r, ctx->cg_z, ctx->part_rzo, &cg->done, cg, 2, ctx->s);
-    vcycle(ctx, ctx->cg_r, ctx->cg_z, &cg->done, ctx->part_rz);
+    vcycle(ctx, ctx->cg_r, ctx->cg_z, &cg->done, ctx->part_rz, cg_u0(ctx));
     {
         ProfScope ps_(ctx, AMG_PROF_CG_P, true);
         launch_cg_update_p(n, cg, ctx->cg_z, ctx->cg_p, use_h, h, ctx->s);
@@ -851,7 +918,8 @@ void enqueue_cg_iter_c(amg_ctx *ctx, int use_h, cudaGraphConditionalHandle h) {
 // the true relative residual of the returned iterate
 void enqueue_cg_epilogue(amg_ctx *ctx, const double *f, double *u) {
     const int32_t n = ctx->n;
-    launch_true_residual(n, ctx->fine_ptr, ctx->fine_col, ctx->A_sys, f, u, ctx->cg_t, ctx->part_tt, ctx->cg, 1,
+    launch_true_residual(n, ctx->fine_ptr, ctx->fine_col, ctx->A_sys, ctx->sell_sys, f, u, ctx->cg_t, ctx->part_tt,
+                         ctx->cg, 1,
                          ctx->s);
 }
 

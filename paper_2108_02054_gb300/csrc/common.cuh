@@ -92,6 +92,11 @@ struct Level {
     // holds the block norms that strength and aggregation see), damped
     // block-Jacobi inverses (16 per node); vd vectors hold 4 per node
     double *Ab = nullptr, *APb = nullptr, *Minv = nullptr;
+    // SELL-32 copy of the matrix (finest level, one lane per row): slice
+    // offsets, columns, values (FP64; FP32 as well in mixed precision)
+    int32_t *sl_ptr = nullptr, *sl_col = nullptr;
+    double *sl_val = nullptr;
+    float *sl_valf = nullptr;
 };
 
 // ------------------------------------------------------------------ launchers
@@ -174,8 +179,8 @@ void launch_smoother_f32(int32_t n, const int32_t *ptr, const float *val, const 
                          float *m, cudaStream_t s);
 // level-0 ingest: copy new values to the hierarchy (and the FP32 copy), check them, build the smoother
 void launch_ingest_fine(int32_t n, const int32_t *ptr, const double *val_in, const int32_t *dia, int type,
-                        double wj, double *val_out, float *valf_out, double *m, float *mf, int *st,
-                        cudaStream_t s);
+                        double wj, double *val_out, float *valf_out, double *m, float *mf, int *st, const int32_t *sl,
+                        double *sl_val, float *sl_valf, cudaStream_t s);
 void launch_cast_f32(int64_t n, const double *in, float *out, cudaStream_t s);
 
 // coarsest level: dense LU and explicit inverse
@@ -198,7 +203,8 @@ template <class V>
 void launch_smooth_sweep_dot(const Level &L, const V *val, const V *m, const double *f, const V *u_in, double *z,
                              double *partial, CgState *cg, const int *skip, cudaStream_t s);
 template <class V>
-void launch_restrict(const Level &L, const V *Rval, const V *r, V *fc, const int *skip, cudaStream_t s);
+void launch_restrict(const Level &L, const V *Rval, const V *r, V *fc, const V *mc, V *uc, const int *skip,
+                     cudaStream_t s);
 template <class V>
 void launch_prolong(const Level &L, const V *Pval, const V *uc, V *u, const int *skip, cudaStream_t s);
 template <class V, class TF, class TO>
@@ -208,20 +214,43 @@ void launch_copy_cast(int64_t n, const TI *in, TO *out, const int *skip, cudaStr
 
 // CG (FP64); reductions finish in the last block of the producing kernel
 int cg_blocks(int64_t n);
+// The V-cycle's first pre-smoothing step from u = 0 on the finest level,
+// u0 = m o r, written by the kernel that produces r (so that step needs no
+// per-entry product); at most one of the two pointer pairs is set.
+struct Smooth0Out {
+    const double *m = nullptr;
+    double *u = nullptr;
+    const float *mf = nullptr;
+    float *uf = nullptr;
+};
 void launch_cg_init(int32_t n, const double *f, double *u, double *r, double *partial, CgState *cg, double tol,
-                    int maxiter, cudaStream_t s);
+                    int maxiter, const Smooth0Out &z0, cudaStream_t s);
 // x.y into per-block partials; with cg, the last block stores the total
 // (target 1: the new r.z, target 2: r_new.z_old)
 void launch_dot(int32_t n, const double *x, const double *y, double *partial, const int *skip, CgState *cg, int target,
                 cudaStream_t s);
 void launch_cg_set_rz_p(int32_t n, const double *z, double *p, CgState *cg, cudaStream_t s);
-void launch_spmv_dot(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *p,
-                     double *q, double *partial, CgState *cg, cudaStream_t s);
+// SELL-32 copy of a matrix (slice offsets, columns, FP64 values); ptr == nullptr: none
+struct SellRef {
+    const int32_t *ptr = nullptr, *col = nullptr;
+    const double *val = nullptr;
+};
+void launch_spmv_dot(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const SellRef &sell,
+                     const double *p, double *q, double *partial, CgState *cg, cudaStream_t s);
 void launch_cg_update_ur(int32_t n, CgState *cg, const double *p, const double *q, double *u, double *r,
-                         double *partial, int use_h, cudaGraphConditionalHandle hb, cudaStream_t s);
-void launch_true_residual(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *f,
-                          const double *u, double *t, double *partial, CgState *cg, int force, cudaStream_t s);
-void launch_replace_r(int32_t n, const CgState *cg, const double *t, double *r, cudaStream_t s);
+                         double *partial, int use_h, cudaGraphConditionalHandle hb, const Smooth0Out &z0,
+                         cudaStream_t s);
+void launch_true_residual(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const SellRef &sell,
+                          const double *f, const double *u, double *t, double *partial, CgState *cg, int force,
+                          cudaStream_t s);
+// SELL-32 structure of a CSR pattern: slots per slice (to be scanned into the
+// slice offsets, n / 32 rounded up slices), columns, values
+void launch_sell_slots(int32_t n, const int32_t *ptr, int32_t *slots, cudaStream_t s);
+void launch_sell_cols(int32_t n, const int32_t *ptr, const int32_t *col, const int32_t *sl, int32_t *sl_col,
+                      cudaStream_t s);
+void launch_sell_vals(int32_t n, const int32_t *ptr, const int32_t *sl, const double *val, double *sl_val,
+                      cudaStream_t s);
+void launch_replace_r(int32_t n, const CgState *cg, const double *t, double *r, const Smooth0Out &z0, cudaStream_t s);
 void launch_cg_update_p(int32_t n, CgState *cg, const double *z, double *p, int use_h, cudaGraphConditionalHandle h,
                         cudaStream_t s);
 

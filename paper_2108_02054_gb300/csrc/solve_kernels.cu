@@ -279,17 +279,23 @@ __global__ void k_smoother(int32_t n, const int32_t *__restrict__ ptr, const V *
 // copy as well), flag non-finite entries and build the smoother in one pass
 __global__ void k_ingest_fine(int32_t n, const int32_t *__restrict__ ptr, const double *__restrict__ in,
                               const int32_t *__restrict__ dia, int type, double wj, double *__restrict__ out,
-                              float *__restrict__ outf, double *__restrict__ m, float *__restrict__ mf, int *st) {
+                              float *__restrict__ outf, double *__restrict__ m, float *__restrict__ mf, int *st,
+                              const int32_t *__restrict__ sl, double *__restrict__ sl_val,
+                              float *__restrict__ sl_valf) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double s = 0.0;
     bool finite = true;
-    for (int32_t p = ptr[i]; p < ptr[i + 1]; ++p) {
+    const int32_t b = ptr[i];
+    const int64_t sb = sl ? (int64_t)sl[i >> 5] + (i & 31) : 0;
+    for (int32_t p = b; p < ptr[i + 1]; ++p) {
         const double v = in[p];
         finite = finite && isfinite(v);
         s = fma(v, v, s);
         if (out) out[p] = v;
         if (outf) outf[p] = (float)v;
+        if (sl_val) sl_val[sb + 32 * (int64_t)(p - b)] = v;
+        if (sl_valf) sl_valf[sb + 32 * (int64_t)(p - b)] = (float)v;
     }
     if (!finite) atomicOr(st, DEV_ERR_NONFINITE);
     const double aii = in[dia[i]];
@@ -303,6 +309,35 @@ __global__ void k_ingest_fine(int32_t n, const int32_t *__restrict__ ptr, const 
 __global__ void k_cast_f32(int64_t n, const double *__restrict__ in, float *__restrict__ out) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = (float)in[i];
+}
+
+// SELL-32 structure: stored entries per slice (32 x its longest row) ...
+__global__ void k_sell_slots(int32_t n, const int32_t *__restrict__ ptr, int32_t *__restrict__ slots) {
+    const int32_t sl = blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t nsl = (n + 31) / 32;
+    if (sl >= nsl) return;
+    int32_t w = 0;
+    for (int32_t i = 32 * sl; i < n && i < 32 * sl + 32; ++i) w = max(w, ptr[i + 1] - ptr[i]);
+    slots[sl] = 32 * w;
+}
+// ... and the columns (padding: the row's own index, never read)
+__global__ void k_sell_cols(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                            const int32_t *__restrict__ sl, int32_t *__restrict__ sl_col) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t base = (int64_t)sl[i >> 5] + (i & 31);
+    const int32_t w = (sl[(i >> 5) + 1] - sl[i >> 5]) / 32;
+    const int32_t b = ptr[i], len = ptr[i + 1] - b;
+    for (int32_t k = 0; k < w; ++k) sl_col[base + 32 * (int64_t)k] = k < len ? col[b + k] : i;
+}
+// values of a CSR matrix into the SELL-32 layout (padding untouched)
+__global__ void k_sell_vals(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ sl,
+                            const double *__restrict__ val, double *__restrict__ sl_val) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t base = (int64_t)sl[i >> 5] + (i & 31);
+    const int32_t b = ptr[i], len = ptr[i + 1] - b;
+    for (int32_t k = 0; k < len; ++k) sl_val[base + 32 * (int64_t)k] = val[b + k];
 }
 
 // ------------------------------------------------------------------ coarsest level
@@ -463,7 +498,9 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // explicit inverse from the LU factors: one warp per column j of A^-1, in
 // column (axpy) form so that no step needs a reduction; the factors, the
-// pivots and each warp's column are staged in shared memory when they fit
+// pivots, the reciprocals of U's diagonal and each warp's column are staged
+// in shared memory when they fit (the reciprocals keep an FP64 division off
+// every back-substitution step)
 constexpr int kInvWarps = 4;
 __global__ void __launch_bounds__(kInvWarps * 32)
 k_lu_inverse(int32_t n, const double *__restrict__ lu_g, const int32_t *__restrict__ piv, double *__restrict__ inv) {
@@ -473,12 +510,16 @@ k_lu_inverse(int32_t n, const double *__restrict__ lu_g, const int32_t *__restri
     const int64_t nn = (int64_t)n * n;
     const double *lu = lu_g;
     const int32_t *pv = piv;
+    const double *rd = nullptr;
     if (staged) {
         for (int64_t e = threadIdx.x; e < nn; e += blockDim.x) sm_inv[e] = lu_g[e];
-        int32_t *spv = (int32_t *)(sm_inv + nn + (int64_t)kInvWarps * n);
+        double *srd = sm_inv + nn + (int64_t)kInvWarps * n;
+        for (int32_t e = threadIdx.x; e < n; e += blockDim.x) srd[e] = 1.0 / lu_g[(int64_t)e * n + e];
+        int32_t *spv = (int32_t *)(srd + n);
         for (int32_t e = threadIdx.x; e < n; e += blockDim.x) spv[e] = piv[e];
         lu = sm_inv;
         pv = spv;
+        rd = srd;
     }
     __syncthreads();
     const int32_t j = blockIdx.x * kInvWarps + w;
@@ -505,7 +546,7 @@ k_lu_inverse(int32_t n, const double *__restrict__ lu_g, const int32_t *__restri
     }
     // U x = y
     for (int32_t k = n - 1; k >= 0; --k) {
-        if (lane == 0) x[k * xs] = x[k * xs] / lu[(int64_t)k * n + k];
+        if (lane == 0) x[k * xs] = rd ? x[k * xs] * rd[k] : x[k * xs] / lu[(int64_t)k * n + k];
         __syncwarp();
         const double xk = x[k * xs];
         for (int32_t r = lane; r < k; r += 32) x[r * xs] = fma(-lu[(int64_t)r * n + k], xk, x[r * xs]);
@@ -540,17 +581,43 @@ __device__ __forceinline__ V group_sum(V s) {
     return s;
 }
 
+// Row access.  CSR: entry k of row i at ptr[i] + k.  SELL-32 (slices of 32
+// consecutive rows, no reordering; used with one lane per row): entry k of
+// row i at sl[i / 32] + i % 32 + 32 k, so that a warp's k-th loads are 32
+// consecutive words; the row length still comes from ptr, the entry order is
+// the CSR order and every sum is unchanged.
+template <bool SELL>
+__device__ __forceinline__ void row_span(int32_t i, const int32_t *__restrict__ ptr, const int32_t *__restrict__ sl,
+                                         int64_t &p0, int32_t &cnt) {
+    const int32_t b = ptr[i];
+    cnt = ptr[i + 1] - b;
+    p0 = SELL ? (int64_t)sl[i >> 5] + (i & 31) : (int64_t)b;
+}
+template <bool SELL>
+__device__ __forceinline__ int64_t row_at(int64_t p0, int32_t k) { return p0 + (SELL ? 32 * (int64_t)k : (int64_t)k); }
+
 // zero-guess pre-smoothing fused with the residual: u = m o f, r = f - A u
-template <class V, class TF, int LPR>
+template <class V, class TF, int LPR, bool SELL = false>
 __global__ void k_smooth0_residual(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                                    const V *__restrict__ val, const V *__restrict__ m, const TF *__restrict__ f,
-                                   V *__restrict__ u, V *__restrict__ r, const int *skip) {
+                                   V *__restrict__ u, V *__restrict__ r, const int *skip, const int32_t *sl) {
     if (skipped(skip)) return;
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int32_t i = (int32_t)(gt / LPR);
     const int sub = (int)(gt % LPR);
     V s = 0;
-    if (i < n)
+    if (SELL) {
+        if (i < n) {
+            int64_t p0;
+            int32_t cnt;
+            row_span<true>(i, ptr, sl, p0, cnt);
+            for (int32_t k = 0; k < cnt; ++k) {
+                const int64_t p = row_at<true>(p0, k);
+                const int32_t j = col[p];
+                s = fma(val[p], m[j] * (V)f[j], s);
+            }
+        }
+    } else if (i < n)
         for (int32_t p = ptr[i] + sub; p < ptr[i + 1]; p += LPR) {
             const int32_t j = col[p];
             s = fma(val[p], m[j] * (V)f[j], s);
@@ -564,16 +631,27 @@ __global__ void k_smooth0_residual(int32_t n, const int32_t *__restrict__ ptr, c
 }
 
 // u_out = u_in + m o (f - A u_in)
-template <class V, class TF, class TO, int LPR>
+template <class V, class TF, class TO, int LPR, bool SELL = false>
 __global__ void k_smooth_sweep(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                                const V *__restrict__ val, const V *__restrict__ m, const TF *__restrict__ f,
-                               const V *__restrict__ u_in, TO *__restrict__ u_out, const int *skip) {
+                               const V *__restrict__ u_in, TO *__restrict__ u_out, const int *skip,
+                               const int32_t *sl) {
     if (skipped(skip)) return;
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int32_t i = (int32_t)(gt / LPR);
     const int sub = (int)(gt % LPR);
     V s = 0;
-    if (i < n)
+    if (SELL) {
+        if (i < n) {
+            int64_t p0;
+            int32_t cnt;
+            row_span<true>(i, ptr, sl, p0, cnt);
+            for (int32_t k = 0; k < cnt; ++k) {
+                const int64_t p = row_at<true>(p0, k);
+                s = fma(val[p], u_in[col[p]], s);
+            }
+        }
+    } else if (i < n)
         for (int32_t p = ptr[i] + sub; p < ptr[i + 1]; p += LPR) s = fma(val[p], u_in[col[p]], s);
     s = group_sum<LPR>(s);
     if (i < n && sub == 0) u_out[i] = (TO)fma(m[i], (V)f[i] - s, u_in[i]);
@@ -583,11 +661,11 @@ __global__ void k_smooth_sweep(int32_t n, const int32_t *__restrict__ ptr, const
 // z = u_in + m o (r - A u_in) and a per-block partial of r.z (block_sum order)
 __device__ double block_sum(double v);
 __device__ bool cg_reduce(double d, double *partial, unsigned *counter, double *total);
-template <class V, int LPR>
+template <class V, int LPR, bool SELL = false>
 __global__ void k_smooth_sweep_dot(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                                    const V *__restrict__ val, const V *__restrict__ m, const double *__restrict__ f,
                                    const V *__restrict__ u_in, double *__restrict__ z, double *__restrict__ partial,
-                                   CgState *cg, const int *skip) {
+                                   CgState *cg, const int *skip, const int32_t *sl) {
     if (skipped(skip)) return;
     const int64_t total = (int64_t)n * LPR;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -597,7 +675,17 @@ __global__ void k_smooth_sweep_dot(int32_t n, const int32_t *__restrict__ ptr, c
         const int32_t i = (int32_t)(gt / LPR);
         const int sub = (int)(gt % LPR);
         V s = 0;
-        if (gt < total)
+        if (SELL) {
+            if (gt < total) {
+                int64_t p0;
+                int32_t cnt;
+                row_span<true>(i, ptr, sl, p0, cnt);
+                for (int32_t k = 0; k < cnt; ++k) {
+                    const int64_t p = row_at<true>(p0, k);
+                    s = fma(val[p], u_in[col[p]], s);
+                }
+            }
+        } else if (gt < total)
             for (int32_t p = ptr[i] + sub; p < ptr[i + 1]; p += LPR) s = fma(val[p], u_in[col[p]], s);
         s = group_sum<LPR>(s);
         if (gt < total && sub == 0) {
@@ -612,16 +700,26 @@ __global__ void k_smooth_sweep_dot(int32_t n, const int32_t *__restrict__ ptr, c
     if (cg_reduce(d, partial, &cg->ctr[CG_CTR_RZ], &rz) && threadIdx.x == 0) cg->rz_next = rz;
 }
 
-template <class V, class TF, int LPR>
+template <class V, class TF, int LPR, bool SELL = false>
 __global__ void k_residual(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                            const V *__restrict__ val, const TF *__restrict__ f, const V *__restrict__ u,
-                           V *__restrict__ r, const int *skip) {
+                           V *__restrict__ r, const int *skip, const int32_t *sl) {
     if (skipped(skip)) return;
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int32_t i = (int32_t)(gt / LPR);
     const int sub = (int)(gt % LPR);
     V s = 0;
-    if (i < n)
+    if (SELL) {
+        if (i < n) {
+            int64_t p0;
+            int32_t cnt;
+            row_span<true>(i, ptr, sl, p0, cnt);
+            for (int32_t k = 0; k < cnt; ++k) {
+                const int64_t p = row_at<true>(p0, k);
+                s = fma(val[p], u[col[p]], s);
+            }
+        }
+    } else if (i < n)
         for (int32_t p = ptr[i] + sub; p < ptr[i + 1]; p += LPR) s = fma(val[p], u[col[p]], s);
     s = group_sum<LPR>(s);
     if (i < n && sub == 0) r[i] = (V)f[i] - s;
@@ -631,7 +729,7 @@ __global__ void k_residual(int32_t n, const int32_t *__restrict__ ptr, const int
 template <class V, int LPR>
 __global__ void k_restrict(int32_t nc, const int32_t *__restrict__ R_ptr, const int32_t *__restrict__ R_col,
                            const V *__restrict__ R_val, const V *__restrict__ r, V *__restrict__ fc,
-                           const int *skip) {
+                           const V *__restrict__ mc, V *__restrict__ uc, const int *skip) {
     if (skipped(skip)) return;
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int32_t I = (int32_t)(gt / LPR);
@@ -640,7 +738,11 @@ __global__ void k_restrict(int32_t nc, const int32_t *__restrict__ R_ptr, const 
     if (I < nc)
         for (int32_t p = R_ptr[I] + sub; p < R_ptr[I + 1]; p += LPR) s = fma(R_val[p], r[R_col[p]], s);
     s = group_sum<LPR>(s);
-    if (I < nc && sub == 0) fc[I] = s;
+    if (I < nc && sub == 0) {
+        fc[I] = s;
+        // the coarse level's first smoothing step from zero, u0 = m o f
+        if (uc) uc[I] = mc[I] * s;
+    }
 }
 
 // u += P u_c
@@ -720,14 +822,20 @@ __device__ bool cg_reduce(double d, double *partial, unsigned *counter, double *
     return true;
 }
 
+__device__ __forceinline__ void put_smooth0(const Smooth0Out &z0, int32_t i, double ri) {
+    if (z0.u) z0.u[i] = z0.m[i] * ri;
+    if (z0.uf) z0.uf[i] = z0.mf[i] * (float)ri;
+}
+
 // u = 0, r = f; the last block initialises the iteration state from |f|
 __global__ void k_cg_init(int32_t n, const double *__restrict__ f, double *__restrict__ u, double *__restrict__ r,
-                          double *__restrict__ partial, CgState *cg, double tol, int maxiter) {
+                          double *__restrict__ partial, CgState *cg, double tol, int maxiter, Smooth0Out z0) {
     double s = 0.0;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double fi = f[i];
         u[i] = 0.0;
         r[i] = fi;
+        put_smooth0(z0, i, fi);
         s = fma(fi, fi, s);
     }
     double ff = 0.0;
@@ -774,16 +882,23 @@ __global__ void k_cg_set_rz_p(int32_t n, const double *__restrict__ z, double *_
 }
 
 // q = A p; the last block forms p.q and alpha = r.z / p.q (breakdown: p.q <= 0)
+template <bool SELL>
 __global__ void k_spmv_dot(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                            const double *__restrict__ val, const double *__restrict__ p, double *__restrict__ q,
-                           double *__restrict__ partial, CgState *cg) {
+                           double *__restrict__ partial, CgState *cg, const int32_t *sl) {
     if (cg->done) return;
     // r.z of the previous iteration becomes current (read only by the last block)
     if (blockIdx.x == 0 && threadIdx.x == 0) cg->rz = cg->rz_next;
     double d = 0.0;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double s = 0.0;
-        for (int32_t e = ptr[i]; e < ptr[i + 1]; ++e) s = fma(val[e], p[col[e]], s);
+        int64_t p0;
+        int32_t cnt;
+        row_span<SELL>(i, ptr, sl, p0, cnt);
+        for (int32_t k = 0; k < cnt; ++k) {
+            const int64_t e = row_at<SELL>(p0, k);
+            s = fma(val[e], p[col[e]], s);
+        }
         q[i] = s;
         d = fma(p[i], s, d);
     }
@@ -804,7 +919,7 @@ __global__ void k_spmv_dot(int32_t n, const int32_t *__restrict__ ptr, const int
 // (graph: opens the IF branch hb of the true-residual check when it meets tol)
 __global__ void k_cg_update_ur(int32_t n, CgState *cg, const double *__restrict__ p, const double *__restrict__ q,
                                double *__restrict__ u, double *__restrict__ r, double *__restrict__ partial,
-                               int use_h, cudaGraphConditionalHandle hb) {
+                               int use_h, cudaGraphConditionalHandle hb, Smooth0Out z0) {
     if (cg->done) {
         if (use_h && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(hb, 0u);
         return;
@@ -815,6 +930,7 @@ __global__ void k_cg_update_ur(int32_t n, CgState *cg, const double *__restrict_
         u[i] = fma(alpha, p[i], u[i]);
         const double ri = fma(-alpha, q[i], r[i]);
         r[i] = ri;
+        put_smooth0(z0, i, ri);
         s = fma(ri, ri, s);
     }
     double rr = 0.0;
@@ -834,15 +950,22 @@ __global__ void k_cg_update_ur(int32_t n, CgState *cg, const double *__restrict_
 // t = f - A u, the true residual, when the recurrence reports convergence; the
 // last block accepts convergence or schedules the replacement of r (twice at
 // most).  With force: unconditionally, the final relative residual.
+template <bool SELL>
 __global__ void k_true_residual(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                                 const double *__restrict__ val, const double *__restrict__ f,
                                 const double *__restrict__ u, double *__restrict__ t, double *__restrict__ partial,
-                                CgState *cg, int force) {
+                                CgState *cg, int force, const int32_t *sl) {
     if (!force && (cg->done || !cg->need_true)) return;
     double d = 0.0;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double s = 0.0;
-        for (int32_t e = ptr[i]; e < ptr[i + 1]; ++e) s = fma(val[e], u[col[e]], s);
+        int64_t p0;
+        int32_t cnt;
+        row_span<SELL>(i, ptr, sl, p0, cnt);
+        for (int32_t k = 0; k < cnt; ++k) {
+            const int64_t e = row_at<SELL>(p0, k);
+            s = fma(val[e], u[col[e]], s);
+        }
         const double ti = f[i] - s;
         t[i] = ti;
         d = fma(ti, ti, d);
@@ -865,9 +988,14 @@ __global__ void k_true_residual(int32_t n, const int32_t *__restrict__ ptr, cons
     }
 }
 
-__global__ void k_replace_r(int32_t n, const CgState *cg, const double *__restrict__ t, double *__restrict__ r) {
+__global__ void k_replace_r(int32_t n, const CgState *cg, const double *__restrict__ t, double *__restrict__ r,
+                            Smooth0Out z0) {
     if (cg->done || !cg->copy_r) return;
-    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) r[i] = t[i];
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double ti = t[i];
+        r[i] = ti;
+        put_smooth0(z0, i, ti);
+    }
 }
 
 // beta = (r.z_new - r.z_old) / (r.z)_old, the flexible form (r.z_old = 0 for
@@ -882,7 +1010,12 @@ __global__ void k_cg_update_p(int32_t n, CgState *cg, const double *__restrict__
         if (lead && use_h) cudaGraphSetConditional(h, 0u);
         return;
     }
-    const double beta = (cg->rz_next - cg->rzo) / cg->rz;
+    // one FP64 division per block, not per thread (FP64 runs at a small
+    // fraction of the FP32 rate on this part)
+    __shared__ double s_beta;
+    if (threadIdx.x == 0) s_beta = (cg->rz_next - cg->rzo) / cg->rz;
+    __syncthreads();
+    const double beta = s_beta;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         p[i] = fma(beta, p[i], z[i]);
     if (lead) {
@@ -1210,10 +1343,11 @@ void launch_smoother_f32(int32_t n, const int32_t *ptr, const float *val, const 
     k_smoother<float><<<nblocks(n), kThreads, 0, s>>>(n, ptr, val, dia, type, (float)wj, m);
 }
 void launch_ingest_fine(int32_t n, const int32_t *ptr, const double *val_in, const int32_t *dia, int type,
-                        double wj, double *val_out, float *valf_out, double *m, float *mf, int *st,
-                        cudaStream_t s) {
+                        double wj, double *val_out, float *valf_out, double *m, float *mf, int *st, const int32_t *sl,
+                        double *sl_val, float *sl_valf, cudaStream_t s) {
     count_launch();
-    k_ingest_fine<<<nblocks(n), kThreads, 0, s>>>(n, ptr, val_in, dia, type, wj, val_out, valf_out, m, mf, st);
+    k_ingest_fine<<<nblocks(n), kThreads, 0, s>>>(n, ptr, val_in, dia, type, wj, val_out, valf_out, m, mf, st, sl,
+                                                  sl_val, sl_valf);
 }
 void launch_cast_f32(int64_t n, const double *in, float *out, cudaStream_t s) {
     int64_t b = nblocks(n);
@@ -1242,14 +1376,15 @@ void launch_dense_lu(int32_t n, double *a, int32_t *piv, int *st, cudaStream_t s
 }
 void launch_lu_inverse(int32_t n, const double *lu, const int32_t *piv, double *inv, cudaStream_t s) {
     static bool attr = false;
-    const int max_bytes = (kLuSmemN * kLuSmemN + kInvWarps * kLuSmemN) * (int)sizeof(double) +
+    const int max_bytes = (kLuSmemN * kLuSmemN + (kInvWarps + 1) * kLuSmemN) * (int)sizeof(double) +
                           kLuSmemN * (int)sizeof(int32_t);
     if (!attr) {
         cudaFuncSetAttribute(k_lu_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         attr = true;
     }
-    const size_t bytes =
-        n <= kLuSmemN ? ((size_t)n * n + (size_t)kInvWarps * n) * sizeof(double) + (size_t)n * sizeof(int32_t) : 0;
+    const size_t bytes = n <= kLuSmemN ? ((size_t)n * n + (size_t)(kInvWarps + 1) * n) * sizeof(double) +
+                                             (size_t)n * sizeof(int32_t)
+                                       : 0;
     count_launch();
     k_lu_inverse<<<(unsigned)((n + kInvWarps - 1) / kInvWarps), kInvWarps * 32, bytes, s>>>(n, lu, piv, inv);
 }
@@ -1264,29 +1399,52 @@ void launch_lu_inverse(int32_t n, const double *lu, const int32_t *piv, double *
         default: { constexpr int P_ = 32; KCALL; } break; \
     }
 
+// the level's SELL-32 copy of the values `val` (one lane per row), if it has one
+const double *sell_of(const Level &L, const double *val) {
+    return (L.sl_ptr && L.lpr == 1 && val == L.A_val) ? L.sl_val : nullptr;
+}
+const float *sell_of(const Level &L, const float *val) {
+    return (L.sl_ptr && L.lpr == 1 && val == L.A_valf) ? L.sl_valf : nullptr;
+}
+
 template <class V, class TF>
 void launch_smooth0_residual(const Level &L, const V *val, const V *m, const TF *f, V *u, V *r, const int *skip,
                              cudaStream_t s) {
     count_launch();
+    if (const V *sv = sell_of(L, val)) {
+        k_smooth0_residual<V, TF, 1, true><<<nblocks(L.n), kThreads, 0, s>>>(L.n, L.A_ptr, L.sl_col, sv, m, f, u, r,
+                                                                            skip, L.sl_ptr);
+        return;
+    }
     const unsigned g = (unsigned)nblocks((int64_t)L.n * L.lpr);
     LPR_DISPATCH(L.lpr, (k_smooth0_residual<V, TF, P_><<<g, kThreads, 0, s>>>(L.n, L.A_ptr, L.A_col, val, m, f, u,
-                                                                              r, skip)))
+                                                                              r, skip, nullptr)))
 }
 template <class V, class TF, class TO>
 void launch_smooth_sweep(const Level &L, const V *val, const V *m, const TF *f, const V *u_in, TO *u_out,
                          const int *skip, cudaStream_t s) {
     count_launch();
+    if (const V *sv = sell_of(L, val)) {
+        k_smooth_sweep<V, TF, TO, 1, true><<<nblocks(L.n), kThreads, 0, s>>>(L.n, L.A_ptr, L.sl_col, sv, m, f, u_in,
+                                                                            u_out, skip, L.sl_ptr);
+        return;
+    }
     const unsigned g = (unsigned)nblocks((int64_t)L.n * L.lpr);
     LPR_DISPATCH(L.lpr, (k_smooth_sweep<V, TF, TO, P_><<<g, kThreads, 0, s>>>(L.n, L.A_ptr, L.A_col, val, m, f,
-                                                                              u_in, u_out, skip)))
+                                                                              u_in, u_out, skip, nullptr)))
 }
 template <class V>
 void launch_smooth_sweep_dot(const Level &L, const V *val, const V *m, const double *f, const V *u_in, double *z,
                              double *partial, CgState *cg, const int *skip, cudaStream_t s) {
     count_launch();
     const unsigned g = (unsigned)cg_blocks(L.n);
+    if (const V *sv = sell_of(L, val)) {
+        k_smooth_sweep_dot<V, 1, true><<<g, kCgThreads, 0, s>>>(L.n, L.A_ptr, L.sl_col, sv, m, f, u_in, z, partial,
+                                                                cg, skip, L.sl_ptr);
+        return;
+    }
     LPR_DISPATCH(L.lpr, (k_smooth_sweep_dot<V, P_><<<g, kCgThreads, 0, s>>>(L.n, L.A_ptr, L.A_col, val, m, f, u_in,
-                                                                             z, partial, cg, skip)))
+                                                                             z, partial, cg, skip, nullptr)))
 }
 template void launch_smooth_sweep_dot<double>(const Level &, const double *, const double *, const double *,
                                               const double *, double *, double *, CgState *, const int *,
@@ -1296,14 +1454,22 @@ template void launch_smooth_sweep_dot<float>(const Level &, const float *, const
 template <class V, class TF>
 void launch_residual(const Level &L, const V *val, const TF *f, const V *u, V *r, const int *skip, cudaStream_t s) {
     count_launch();
+    if (const V *sv = sell_of(L, val)) {
+        k_residual<V, TF, 1, true><<<nblocks(L.n), kThreads, 0, s>>>(L.n, L.A_ptr, L.sl_col, sv, f, u, r, skip,
+                                                                    L.sl_ptr);
+        return;
+    }
     const unsigned g = (unsigned)nblocks((int64_t)L.n * L.lpr);
-    LPR_DISPATCH(L.lpr, (k_residual<V, TF, P_><<<g, kThreads, 0, s>>>(L.n, L.A_ptr, L.A_col, val, f, u, r, skip)))
+    LPR_DISPATCH(L.lpr, (k_residual<V, TF, P_><<<g, kThreads, 0, s>>>(L.n, L.A_ptr, L.A_col, val, f, u, r, skip,
+                                                                      nullptr)))
 }
 template <class V>
-void launch_restrict(const Level &L, const V *Rval, const V *r, V *fc, const int *skip, cudaStream_t s) {
+void launch_restrict(const Level &L, const V *Rval, const V *r, V *fc, const V *mc, V *uc, const int *skip,
+                     cudaStream_t s) {
     count_launch();
     const unsigned g = (unsigned)nblocks((int64_t)L.nc * L.lpr_r);
-    LPR_DISPATCH(L.lpr_r, (k_restrict<V, P_><<<g, kThreads, 0, s>>>(L.nc, L.R_ptr, L.R_col, Rval, r, fc, skip)))
+    LPR_DISPATCH(L.lpr_r, (k_restrict<V, P_><<<g, kThreads, 0, s>>>(L.nc, L.R_ptr, L.R_col, Rval, r, fc, mc, uc,
+                                                                    skip)))
 }
 template <class V>
 void launch_prolong(const Level &L, const V *Pval, const V *uc, V *u, const int *skip, cudaStream_t s) {
@@ -1343,9 +1509,10 @@ template void launch_residual<float, float>(const Level &, const float *, const 
                                             const int *, cudaStream_t);
 template void launch_residual<float, double>(const Level &, const float *, const double *, const float *, float *,
                                              const int *, cudaStream_t);
-template void launch_restrict<double>(const Level &, const double *, const double *, double *, const int *,
-                                      cudaStream_t);
-template void launch_restrict<float>(const Level &, const float *, const float *, float *, const int *, cudaStream_t);
+template void launch_restrict<double>(const Level &, const double *, const double *, double *, const double *,
+                                      double *, const int *, cudaStream_t);
+template void launch_restrict<float>(const Level &, const float *, const float *, float *, const float *, float *,
+                                     const int *, cudaStream_t);
 template void launch_prolong<double>(const Level &, const double *, const double *, double *, const int *,
                                      cudaStream_t);
 template void launch_prolong<float>(const Level &, const float *, const float *, float *, const int *, cudaStream_t);
@@ -1360,15 +1527,21 @@ template void launch_copy_cast<double, double>(int64_t, const double *, double *
 template void launch_copy_cast<double, float>(int64_t, const double *, float *, const int *, cudaStream_t);
 template void launch_copy_cast<float, double>(int64_t, const float *, double *, const int *, cudaStream_t);
 
+// Grid of the Krylov kernels (grid-stride loops, one partial per block).  The
+// last-block reduction costs grow with the number of blocks (each block's
+// partial, fence and counter update sit on the final block's critical path),
+// so vectors up to about 1.2 M entries run on two blocks per SM; longer ones
+// need the full occupancy of eight to keep enough loads in flight.
 int cg_blocks(int64_t n) {
     int64_t b = (n + kCgThreads - 1) / kCgThreads;
-    if (b > kCgMaxBlocks) b = kCgMaxBlocks;
+    const int64_t cap = n >= (int64_t)kCgMaxBlocks * kCgThreads * 4 ? kCgMaxBlocks : 152 * 2;
+    if (b > cap) b = cap;
     return (int)(b < 1 ? 1 : b);
 }
 void launch_cg_init(int32_t n, const double *f, double *u, double *r, double *partial, CgState *cg, double tol,
-                    int maxiter, cudaStream_t s) {
+                    int maxiter, const Smooth0Out &z0, cudaStream_t s) {
     count_launch();
-    k_cg_init<<<cg_blocks(n), kCgThreads, 0, s>>>(n, f, u, r, partial, cg, tol, maxiter);
+    k_cg_init<<<cg_blocks(n), kCgThreads, 0, s>>>(n, f, u, r, partial, cg, tol, maxiter, z0);
 }
 void launch_dot(int32_t n, const double *x, const double *y, double *partial, const int *skip, CgState *cg, int target,
                 cudaStream_t s) {
@@ -1379,24 +1552,49 @@ void launch_cg_set_rz_p(int32_t n, const double *z, double *p, CgState *cg, cuda
     count_launch();
     k_cg_set_rz_p<<<cg_blocks(n), kCgThreads, 0, s>>>(n, z, p, cg);
 }
-void launch_spmv_dot(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *p,
-                     double *q, double *partial, CgState *cg, cudaStream_t s) {
+void launch_spmv_dot(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const SellRef &sell,
+                     const double *p, double *q, double *partial, CgState *cg, cudaStream_t s) {
     count_launch();
-    k_spmv_dot<<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, col, val, p, q, partial, cg);
+    if (sell.ptr)
+        k_spmv_dot<true><<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, sell.col, sell.val, p, q, partial, cg, sell.ptr);
+    else
+        k_spmv_dot<false><<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, col, val, p, q, partial, cg, nullptr);
 }
 void launch_cg_update_ur(int32_t n, CgState *cg, const double *p, const double *q, double *u, double *r,
-                         double *partial, int use_h, cudaGraphConditionalHandle hb, cudaStream_t s) {
+                         double *partial, int use_h, cudaGraphConditionalHandle hb, const Smooth0Out &z0,
+                         cudaStream_t s) {
     count_launch();
-    k_cg_update_ur<<<cg_blocks(n), kCgThreads, 0, s>>>(n, cg, p, q, u, r, partial, use_h, hb);
+    k_cg_update_ur<<<cg_blocks(n), kCgThreads, 0, s>>>(n, cg, p, q, u, r, partial, use_h, hb, z0);
 }
-void launch_true_residual(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *f,
-                          const double *u, double *t, double *partial, CgState *cg, int force, cudaStream_t s) {
+void launch_true_residual(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const SellRef &sell,
+                          const double *f, const double *u, double *t, double *partial, CgState *cg, int force,
+                          cudaStream_t s) {
     count_launch();
-    k_true_residual<<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, col, val, f, u, t, partial, cg, force);
+    if (sell.ptr)
+        k_true_residual<true><<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, sell.col, sell.val, f, u, t, partial, cg,
+                                                                  force, sell.ptr);
+    else
+        k_true_residual<false><<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, col, val, f, u, t, partial, cg, force,
+                                                                   nullptr);
 }
-void launch_replace_r(int32_t n, const CgState *cg, const double *t, double *r, cudaStream_t s) {
+
+void launch_sell_slots(int32_t n, const int32_t *ptr, int32_t *slots, cudaStream_t s) {
     count_launch();
-    k_replace_r<<<cg_blocks(n), kCgThreads, 0, s>>>(n, cg, t, r);
+    k_sell_slots<<<nblocks((n + 31) / 32), kThreads, 0, s>>>(n, ptr, slots);
+}
+void launch_sell_cols(int32_t n, const int32_t *ptr, const int32_t *col, const int32_t *sl, int32_t *sl_col,
+                      cudaStream_t s) {
+    count_launch();
+    k_sell_cols<<<nblocks(n), kThreads, 0, s>>>(n, ptr, col, sl, sl_col);
+}
+void launch_sell_vals(int32_t n, const int32_t *ptr, const int32_t *sl, const double *val, double *sl_val,
+                      cudaStream_t s) {
+    count_launch();
+    k_sell_vals<<<nblocks(n), kThreads, 0, s>>>(n, ptr, sl, val, sl_val);
+}
+void launch_replace_r(int32_t n, const CgState *cg, const double *t, double *r, const Smooth0Out &z0, cudaStream_t s) {
+    count_launch();
+    k_replace_r<<<cg_blocks(n), kCgThreads, 0, s>>>(n, cg, t, r, z0);
 }
 void launch_cg_update_p(int32_t n, CgState *cg, const double *z, double *p, int use_h, cudaGraphConditionalHandle h,
                         cudaStream_t s) {

@@ -156,7 +156,7 @@ def test_partial_rebuild_on_unchanged_values_equals_full_setup_bitwise():
 
 
 # ------------------------------------------------------------------ V-cycle and solve
-@pytest.mark.parametrize("dim,N", [(2, 32), (3, 48)])
+@pytest.mark.parametrize("dim,N", [(2, 32), (3, 48), (3, 64)])
 def test_vcycle_matches_oracle(dim, N):
     ptr, col, v = gpu_problem(dim, N, 1, 5)
     G = B.AMG()
@@ -347,3 +347,29 @@ def test_preventive_rebuilds():
             base = info.iters
         last = info.iters
     assert rebuilt_any
+
+
+def test_sell_layout_full_reuse_series_64cubed():
+    """64^3: the finest level runs one lane per row on its SELL-32 copy (and,
+    under full reuse, on the copy of the system matrix filled every step);
+    the time loop follows the oracle's."""
+    dim, N, T = 3, 64, 50
+    ptr, col, _ = gpu_problem(dim, N, 0, T)
+    f = I.rhs(N ** 3)
+    ft = torch.tensor(f, device="cuda")
+    steps = [0, 1, 2, 3]
+    vals = [oracle_problem(dim, N, k, T)[2] for k in steps]
+    for mode in (B.MODE_PARTIAL, B.MODE_FULL_REUSE):
+        recs = O.run_time_steps(*oracle_problem(dim, N, 0, T)[:2], vals, f, mode)
+        G = B.AMG(mode=mode)
+        for j, k in enumerate(steps):
+            si = G.step(gpu_problem(dim, N, k, T)[2], ptr, col)
+            u, info = G.solve(ft, 1e-8)
+            # (full reuse: the kept hierarchy misses the tolerance on some steps, as in the oracle)
+            assert bool(si.rebuilt) == recs[j].rebuilt and info.status == recs[j].status
+            assert abs(info.iters - recs[j].iters) <= 1, (mode, k, info.iters, recs[j].iters)
+            A = _sp(*oracle_problem(dim, N, k, T), N ** 3)
+            res = np.linalg.norm(f - A @ u.cpu().numpy()) / np.linalg.norm(f)
+            assert abs(res - info.rel_resid) <= 1e-6 * res + 1e-15
+            if info.status == 0:
+                assert res <= 1e-8
