@@ -175,10 +175,16 @@ amg_status amg_export_coarse_lu(amg_ctx *ctx, double *d_lu, int32_t *d_piv);
 /* Instrumentation (no counterpart in the paper; used to report per-kernel
  * time against the memory roofline).  amg_profile(ctx, 1) records a CUDA
  * event pair on the context's stream around every launch of the kernels named
- * by the AMG_PROF_* slots; amg_profile_read synchronises the stream, returns
- * the summed milliseconds and the number of timed launches of one slot and
- * clears it.  amg_kernel_launches returns the number of kernels this library
- * has launched in the process so far (all contexts). */
+ * by the AMG_PROF_* slots.  A CG solve is then run twice: once unprofiled (to
+ * learn its iteration count K), then as one straight-line CUDA graph of K
+ * iterations with event-record nodes, the last iteration untimed, so that the
+ * timings carry no host launch gaps.  amg_profile(ctx, 2) times the
+ * host-driven launch loop instead (each launch submitted from the host, the
+ * state read back after every iteration); 0 switches timing off.
+ * amg_profile_read synchronises the stream, returns the summed milliseconds
+ * and the number of timed launches of one slot and clears it.
+ * amg_kernel_launches returns the number of kernels this library has launched
+ * in the process so far (all contexts). */
 enum {
     AMG_PROF_CG_SPMV = 0,      /* CG: q = A p fused with p.q (fine level, FP64) */
     AMG_PROF_SMOOTH0_L0 = 1,   /* V-cycle, finest level: zero-guess smoothing + residual */
@@ -194,7 +200,8 @@ enum {
     AMG_PROF_CG_P = 11,        /* CG: p = z + beta p */
     AMG_PROF_DOT = 12,         /* CG: r.z */
     AMG_PROF_COARSE = 13,      /* coarsest solve (dense inverse times vector) */
-    AMG_PROF_NSLOTS = 14
+    AMG_PROF_EMPTY = 14,       /* an empty event pair in the same stream or graph: the timing overhead */
+    AMG_PROF_NSLOTS = 15
 };
 amg_status amg_profile(amg_ctx *ctx, int32_t enable);
 amg_status amg_profile_read(amg_ctx *ctx, int32_t slot, double *total_ms, int64_t *launches);

@@ -38,7 +38,7 @@ EXPORTS = [
     "amg_poisson_pattern_noalloc", "amg_levelset_values", "amg_stokes_values",
 ]
 PROF_SLOTS = ["cg_spmv", "smooth0_l0", "sweep_l0", "restrict_l0", "prolong_l0", "ap_l0", "rap_l0", "ingest", "lu",
-              "inv", "cg_update", "cg_p", "dot", "coarse"]
+              "inv", "cg_update", "cg_p", "dot", "coarse", "empty"]
 
 
 class amg_params(ctypes.Structure):
@@ -260,7 +260,8 @@ class AMG:
         out["m"] = m.cpu().numpy().reshape(n, 16) if bw == 16 else m.cpu().numpy()
         return out
 
-    def profile(self, enable: bool = True):
+    def profile(self, enable=True):
+        """Per-kernel timing: True / 1 (unrolled graph), 2 (host-driven loop), False / 0 off."""
         self._check(lib().amg_profile(self._h, int(enable)))
 
     def profile_read(self) -> dict:

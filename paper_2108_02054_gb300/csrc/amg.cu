@@ -30,6 +30,7 @@ int64_t launch_total() { return g_launches.load(std::memory_order_relaxed); }
 // amg_profile(ctx, 1)); slot numbers are the AMG_PROF_* values of amgpr.h
 struct ProfData {
     bool on = false;
+    bool eager = false;  // time the host-driven launch loop instead of an unrolled graph
     std::vector<cudaEvent_t> pool;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> rec[AMG_PROF_NSLOTS];
 };
@@ -111,6 +112,16 @@ cudaEvent_t prof_event(amg_ctx *c) {
     return e;
 }
 
+// record a timing event; on a capturing stream as an event-record node of
+// the graph (a plain record there would only mark a capture dependency)
+void prof_record(cudaEvent_t e, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+    else
+        cudaEventRecord(e, s);
+}
+
 struct ProfScope {
     amg_ctx *c;
     int slot;
@@ -118,13 +129,13 @@ struct ProfScope {
     ProfScope(amg_ctx *c_, int slot_, bool active = true) : c(c_), slot(slot_) {
         if (c->prof.on && active) {
             b = prof_event(c);
-            cudaEventRecord(b, c->s);
+            prof_record(b, c->s);
         }
     }
     ~ProfScope() {
         if (!b) return;
         cudaEvent_t e = prof_event(c);
-        cudaEventRecord(e, c->s);
+        prof_record(e, c->s);
         c->prof.rec[slot].push_back({b, e});
     }
 };
@@ -1208,9 +1219,57 @@ amg_status solve_bi(amg_ctx *ctx, const double *f, double *u, double tol, amg_in
     return finish_bi(ctx, info);
 }
 
+amg_status solve_impl(amg_ctx *ctx, const double *f, double *u, double tol, amg_info *info);
+
+// Per-kernel timing of a CG solve (amg_profile on).  The host-driven loop
+// leaves the GPU waiting for the next launch between short kernels, which
+// would inflate every timed launch; instead the solve first runs unprofiled
+// (the whole-solve graph) to learn its iteration count K, then once more as
+// one straight-line graph of K iterations whose event-record nodes bracket
+// the timed kernels (the last iteration, whose preconditioner kernels return
+// at once, is not timed); every timed iteration also brackets nothing, which
+// measures the overhead of an event pair in the graph (slot AMG_PROF_EMPTY).
+// Both runs compute the same iterates.
+amg_status solve_cg_profiled(amg_ctx *ctx, const double *f, double *u, double tol, amg_info *info) {
+    ctx->prof.on = false;
+    amg_status st = solve_impl(ctx, f, u, tol, nullptr);
+    ctx->prof.on = true;
+    if (st != AMG_OK && st != AMG_NOT_CONVERGED) return st;
+    const int K = ctx->h_cg->iter;
+    CK(cudaStreamSynchronize(ctx->s));
+    cudaStream_t user_s = ctx->s;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    CK(cudaStreamBeginCapture(ctx->s_cap_main, cudaStreamCaptureModeThreadLocal));
+    ctx->s = ctx->s_cap_main;
+    enqueue_cg_prologue(ctx, f, u, tol);
+    for (int it = 1; it <= K; ++it) {
+        if (it == K) ctx->prof.on = false;
+        { ProfScope cal_(ctx, AMG_PROF_EMPTY, true); }  // two adjacent event nodes: the timing overhead
+        enqueue_cg_iter_a(ctx, u, 0, 0);
+        enqueue_cg_iter_b(ctx, f, u);
+        enqueue_cg_iter_c(ctx, 0, 0);
+    }
+    ctx->prof.on = true;
+    enqueue_cg_epilogue(ctx, f, u);
+    ctx->s = user_s;
+    cudaError_t e = cudaStreamEndCapture(ctx->s_cap_main, &g);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ge, ctx->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->s);
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(ctx, AMG_ERR_CUDA, std::string("profiled solve graph: ") + cudaGetErrorString(e));
+    }
+    return finish_solve(ctx, info);
+}
+
 amg_status solve_impl(amg_ctx *ctx, const double *f, double *u, double tol, amg_info *info) {
     const int32_t n = ctx->n;
     if (ctx->prm.solver == AMG_SOLVER_BICGSTAB) return solve_bi(ctx, f, u, tol, info);
+    if (ctx->prof.on && !ctx->prof.eager && ctx->use_graph) return solve_cg_profiled(ctx, f, u, tol, info);
     if (ctx->use_graph && !ctx->prof.on) {
         if (!ctx->graph_valid || ctx->graph_tol != tol) TRY(build_solve_graph(ctx, tol));
         CK(cudaMemcpyAsync(ctx->cg_f, f, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, ctx->s));
@@ -1531,7 +1590,9 @@ amg_status amg_export_coarse_lu(amg_ctx *ctx, double *d_lu, int32_t *d_piv) {
 
 amg_status amg_profile(amg_ctx *ctx, int32_t enable) {
     if (!ctx) return AMG_ERR_ARG;
+    if (enable < 0 || enable > 2) return AMG_ERR_ARG;
     ctx->prof.on = enable != 0;
+    ctx->prof.eager = enable == 2;
     return AMG_OK;
 }
 
@@ -1539,16 +1600,24 @@ amg_status amg_profile_read(amg_ctx *ctx, int32_t slot, double *total_ms, int64_
     if (!ctx || slot < 0 || slot >= AMG_PROF_NSLOTS || !total_ms || !launches) return AMG_ERR_ARG;
     CK(cudaStreamSynchronize(ctx->s));
     double ms = 0.0;
+    cudaError_t first_err = cudaSuccess;
+    // every pair goes back to the pool, whatever happens (each event is owned
+    // by exactly one of the two lists)
     for (auto &pr : ctx->prof.rec[slot]) {
         float t = 0.f;
-        CK(cudaEventElapsedTime(&t, pr.first, pr.second));
-        ms += t;
+        const cudaError_t e = cudaEventElapsedTime(&t, pr.first, pr.second);
+        if (e == cudaSuccess) ms += t;
+        else if (first_err == cudaSuccess) first_err = e;
         ctx->prof.pool.push_back(pr.first);
         ctx->prof.pool.push_back(pr.second);
     }
     *total_ms = ms;
     *launches = (int64_t)ctx->prof.rec[slot].size();
     ctx->prof.rec[slot].clear();
+    if (first_err != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(ctx, AMG_ERR_CUDA, std::string("reading a timing event: ") + cudaGetErrorString(first_err));
+    }
     return AMG_OK;
 }
 

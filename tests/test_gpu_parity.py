@@ -310,12 +310,15 @@ def test_graph_solve_equals_eager_solve(precision):
     f = torch.tensor(I.rhs(40 ** 3), device="cuda")
     u1, i1 = G.solve(f, 1e-8)
     u2, i2 = G.solve(f, 1e-8)           # graph reused
-    G.profile(True)                     # per-kernel timing forces the eager loop
+    G.profile(2)                        # timing of the host-driven launch loop
     u3, i3 = G.solve(f, 1e-8)
+    G.profile(1)                        # timing through an unrolled graph
+    u5, i5 = G.solve(f, 1e-8)
     G.profile(False)
-    G.profile_read()
-    assert i1.iters == i2.iters == i3.iters and i1.status == i3.status == 0
-    assert torch.equal(u1, u2) and torch.equal(u1, u3)
+    prof = G.profile_read()
+    assert prof["cg_spmv"][1] > 0 and prof["cg_spmv"][0] > 0
+    assert i1.iters == i2.iters == i3.iters == i5.iters and i1.status == i3.status == i5.status == 0
+    assert torch.equal(u1, u2) and torch.equal(u1, u3) and torch.equal(u1, u5)
     u4, i4 = G.solve(f, 1e-11)          # a new tolerance rebuilds the graph
     assert i4.iters > i1.iters and i4.rel_resid <= 1e-11
 
