@@ -41,6 +41,10 @@ DESCR = {
              "FP64 outer CG, 100 time steps",
     "3d192": "3D 7-point collapsing-column pressure Poisson, 192^3 cells (7,077,888 unknowns), FP32 hierarchy / "
              "FP64 outer CG, 100 time steps",
+    "ns32": "monolithic 4x4 block (u, v, w, p) Navier-Stokes stand-in, 32^3 cells (131,072 unknowns), FP64, "
+            "20 time steps (--table2 --system ns)",
+    "ns48": "monolithic 4x4 block (u, v, w, p) Navier-Stokes stand-in, 48^3 cells (442,368 unknowns), FP64, "
+            "50 time steps (--table2 --system ns)",
 }
 
 
@@ -57,9 +61,10 @@ def parse():
     ap.add_argument("--table2", action="store_true",
                     help="instead of the benchmark line: every time step of the workload under each strategy "
                          "and AMG flavour, accumulated like Table 2 of the paper (JSON)")
-    ap.add_argument("--system", default="pressure", choices=["pressure", "levelset"],
-                    help="with --table2: the pressure Poisson systems (CG) or the level-set transport "
-                         "systems (BiCGStab) on the workload's grid and step count")
+    ap.add_argument("--system", default="pressure", choices=["pressure", "levelset", "ns"],
+                    help="with --table2: the pressure Poisson systems (CG), the level-set transport "
+                         "systems (BiCGStab) on the workload's grid and step count, or the monolithic 4x4 "
+                         "block Navier-Stokes stand-in (BiCGStab; workloads ns32 / ns48)")
     return ap.parse_args()
 
 
@@ -458,14 +463,20 @@ def run_table2(args):
     import torch
     from paper_2108_02054_gb300 import amg as B
 
-    w = I.WORKLOADS[args.workload]
+    ns = args.system == "ns"
+    if ns != args.workload.startswith("ns"):
+        raise SystemExit("--system ns goes with the ns32 / ns48 workloads, and only with them")
+    w = I.NS_WORKLOADS[args.workload] if ns else I.WORKLOADS[args.workload]
     prec = B.PREC_MIXED if w.precision == "mixed" else B.PREC_FP64
     ptr, col = B.poisson_pattern(w.dim, w.N)
-    f = torch.tensor(I.rhs(w.n), device="cuda")
+    f = torch.tensor(I.rhs(4 * w.n if ns else w.n), device="cuda")
     levelset = args.system == "levelset"
-    solver = B.SOLVER_BICGSTAB if levelset else B.SOLVER_CG
+    solver = B.SOLVER_BICGSTAB if (levelset or ns) else B.SOLVER_CG
 
     def values(k):
+        if ns:
+            return B.stokes_values(w.N, *(torch.tensor(a, device="cuda") for a in I.ns_fields(w.N, k, w.T)),
+                                   I.NS_MASS, ptr)
         if levelset:
             fx, fy, fz = (torch.tensor(a, device="cuda") for a in I.levelset_faces(w.dim, w.N, k, w.T))
             return B.levelset_values(w.dim, w.N, fx, fy, fz, ptr)
@@ -474,6 +485,10 @@ def run_table2(args):
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     flavours = {"smoothed aggregation + SPAI0": {}, "plain aggregation + damped Jacobi": {"smoothed": 0,
                                                                                           "smoother": 1}}
+    if ns:
+        # the paper's configuration for these systems (the only one the block hierarchy has)
+        flavours = {"plain aggregation + damped block Jacobi (4x4)": {"block_size": 4, "smoothed": 0,
+                                                                        "smoother": 1}}
     strategies = {"no reuse": {"mode": B.MODE_FULL_REBUILD}, "full reuse": {"mode": B.MODE_FULL_REUSE},
                   "partial reuse": {"mode": B.MODE_PARTIAL},
                   "partial reuse + rebuild at 1.3x iterations": {"mode": B.MODE_PARTIAL, "rebuild_iter_growth": 1.3}}
@@ -510,6 +525,9 @@ def run_table2(args):
             row["setup_speedup_pct"] = 100 * (base["setup_s"] / setup - 1)
             rows.append(row)
     descr = DESCR[args.workload]
+    if ns:
+        descr = (f"monolithic 4x4 block Oseen-type stand-in (collapsing column, rotating flow, mass "
+                 f"{I.NS_MASS:g}), {4 * w.n:,} unknowns, BiCGStab")
     if levelset:
         descr = (f"level-set transport stand-in (implicit upwind convection-diffusion, rotating flow, Courant "
                  f"{I.LEVELSET_COURANT:g}) on the grid of {args.workload}, BiCGStab")
@@ -522,6 +540,8 @@ def main():
     if args.table2:
         run_table2(args)
         return
+    if args.workload.startswith("ns"):
+        raise SystemExit("the 4x4 block workloads are measured with --table2 --system ns")
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -49,7 +49,7 @@ struct amg_ctx {
     int nlev = 0;
     Level lev[kMaxLevels];
     int32_t nL = 0;
-    double *lu = nullptr, *inv = nullptr;
+    double *lu = nullptr, *inv = nullptr, *luT = nullptr;
     int32_t *piv = nullptr;
     bool have_setup = false;
     // system matrix of the solve (aliases level 0 except under full reuse)
@@ -174,7 +174,7 @@ void free_hierarchy(amg_ctx *ctx) {
     for (int l = 0; l < kMaxLevels; ++l) ctx->lev[l] = Level{};
     ctx->nlev = 0;
     ctx->have_setup = false;
-    ctx->lu = ctx->inv = nullptr;
+    ctx->lu = ctx->inv = ctx->luT = nullptr;
     ctx->piv = nullptr;
     ctx->sl_sys_own = nullptr;
     ctx->sell_sys = SellRef{};
@@ -299,14 +299,14 @@ amg_status coarse_factor(amg_ctx *ctx) {
         const int32_t n4 = ctx->nL;
         CK(cudaMemsetAsync(ctx->lu, 0, sizeof(double) * (size_t)n4 * (size_t)n4, ctx->s));
         launch_block_to_dense(C.n, C.A_ptr, C.A_col, C.Ab, ctx->lu, ctx->s);
-        { ProfScope ps_(ctx, AMG_PROF_LU, true); launch_dense_lu(n4, ctx->lu, ctx->piv, ctx->d_st, ctx->s); }
-        { ProfScope ps_(ctx, AMG_PROF_INV, true); launch_lu_inverse(n4, ctx->lu, ctx->piv, ctx->inv, ctx->s); }
+        { ProfScope ps_(ctx, AMG_PROF_LU, true); launch_dense_lu(n4, ctx->lu, ctx->piv, ctx->d_st, ctx->s, ctx->luT); }
+        { ProfScope ps_(ctx, AMG_PROF_INV, true); launch_lu_inverse(n4, ctx->lu, ctx->piv, ctx->inv, ctx->s, ctx->luT); }
         return AMG_OK;
     }
     const bool mx = mixed(ctx);
     launch_csr_to_dense(C.n, C.A_ptr, C.A_col, mx ? nullptr : C.A_val, mx ? C.A_valf : nullptr, ctx->lu, ctx->s);
-    { ProfScope ps_(ctx, AMG_PROF_LU, true); launch_dense_lu(C.n, ctx->lu, ctx->piv, ctx->d_st, ctx->s); }
-    { ProfScope ps_(ctx, AMG_PROF_INV, true); launch_lu_inverse(C.n, ctx->lu, ctx->piv, ctx->inv, ctx->s); }
+    { ProfScope ps_(ctx, AMG_PROF_LU, true); launch_dense_lu(C.n, ctx->lu, ctx->piv, ctx->d_st, ctx->s, ctx->luT); }
+    { ProfScope ps_(ctx, AMG_PROF_INV, true); launch_lu_inverse(C.n, ctx->lu, ctx->piv, ctx->inv, ctx->s, ctx->luT); }
     return AMG_OK;
 }
 
@@ -588,6 +588,8 @@ amg_status full_setup_impl(amg_ctx *ctx, const double *d_val) {
     TRY(alloc(ctx, &ctx->lu, (size_t)(nL * nL)));
     TRY(alloc(ctx, &ctx->inv, (size_t)(nL * nL)));
     TRY(alloc(ctx, &ctx->piv, (size_t)nL));
+    ctx->luT = nullptr;
+    if (lu_wants_transpose((int32_t)nL)) TRY(alloc(ctx, &ctx->luT, (size_t)(nL * nL)));
     if (mixed(ctx))
         for (int l = 1; l < ctx->nlev; ++l) launch_cast_f32(ctx->lev[l].nnz, ctx->lev[l].A_val, ctx->lev[l].A_valf, ctx->s);
     TRY(numeric_rebuild(ctx, blockmode(ctx) ? ctx->lev[0].Ab : ctx->lev[0].A_val, false));

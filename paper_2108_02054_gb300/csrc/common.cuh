@@ -186,8 +186,12 @@ void launch_cast_f32(int64_t n, const double *in, float *out, cudaStream_t s);
 // coarsest level: dense LU and explicit inverse
 void launch_csr_to_dense(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const float *valf,
                          double *dense, cudaStream_t s);
-void launch_dense_lu(int32_t n, double *a, int32_t *piv, int *st, cudaStream_t s);
-void launch_lu_inverse(int32_t n, const double *lu, const int32_t *piv, double *inv, cudaStream_t s);
+// aT (optional, n x n): a column-major copy of the factors, written when
+// lu_wants_transpose(n); the inverse then reads it
+bool lu_wants_transpose(int32_t n);
+void launch_dense_lu(int32_t n, double *a, int32_t *piv, int *st, cudaStream_t s, double *aT = nullptr);
+void launch_lu_inverse(int32_t n, const double *lu, const int32_t *piv, double *inv, cudaStream_t s,
+                       const double *luT = nullptr);
 
 // V-cycle pieces; `skip` (may be null) makes the kernel return at once when *skip != 0
 template <class V, class TF>

@@ -10,6 +10,8 @@
 //   * V-cycle pieces and the device-driven CG iteration.
 #include <cfloat>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 
 namespace amgpr {
@@ -376,6 +378,7 @@ __device__ __forceinline__ KeyIdx better(KeyIdx a, KeyIdx b) {
 // perm[i] names the physical row at position i, and the factors are written
 // out in position order at the end.  Larger ones use the global-memory kernel.
 constexpr int kLuSmemN = 160;
+constexpr int kLuClusterN = 448;   // 8 CTAs x 56 rows x 448 columns fit in 227 KB each
 constexpr int kLuThreads = 1024;
 __global__ void __launch_bounds__(kLuThreads) k_dense_lu_smem(int32_t n, double *__restrict__ g,
                                                               int32_t *__restrict__ piv, int *st) {
@@ -440,6 +443,126 @@ __global__ void __launch_bounds__(kLuThreads) k_dense_lu_smem(int32_t n, double 
         for (int32_t r = k + 1 + tid; r < n; r += kLuThreads) piv[r] = r;
     }
     for (int64_t e = tid; e < nn; e += kLuThreads) g[e] = a[(int64_t)perm[e / n] * n + e % n];
+}
+
+// Mid-size matrices (kLuSmemN < n <= kLuClusterN) are factorised by one
+// thread-block cluster of eight CTAs (eight SMs' FP64 pipes): physical row r
+// lives in the shared memory of CTA r % 8.  Each step, every CTA ranks its own
+// rows (positions >= k; ties to the lower position), the CTAs read the eight
+// candidates from one another's shared memory and all pick the same pivot,
+// copy the pivot row from its owner, and update their own rows; two cluster
+// barriers per step.  The permutation is kept lazily (perm / pos_of,
+// replicated in every CTA), the divisions and fma updates are those of the
+// one-block kernel, so factors and pivots are identical to it.  The factors
+// are written in position order, and column-major as well for the inverse.
+namespace cgr = cooperative_groups;
+constexpr int kLuClusterCtas = 8;
+constexpr int kLuClusterThreads = 512;
+__global__ void __cluster_dims__(kLuClusterCtas, 1, 1) __launch_bounds__(kLuClusterThreads)
+k_dense_lu_cluster(int32_t n, double *__restrict__ g, double *__restrict__ gT, int32_t *__restrict__ piv, int *st) {
+    cgr::cluster_group cluster = cgr::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    extern __shared__ double sm_lu[];
+    const int32_t nloc = (n + kLuClusterCtas - 1) / kLuClusterCtas;
+    double *a = sm_lu;                          // nloc rows of n
+    double *prow = a + (int64_t)nloc * n;       // the step's pivot row
+    double *lbuf = prow + n;                    // multipliers of this CTA's rows
+    int32_t *perm = (int32_t *)(lbuf + nloc);   // position -> physical row
+    int32_t *pos_of = perm + n;                 // physical row -> position
+    __shared__ KeyIdx cand;
+    __shared__ KeyIdx wbest[kLuClusterThreads / 32];
+    __shared__ int s_sing;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int nw = kLuClusterThreads / 32;
+    const int32_t nmine = rank < n ? (n - rank + kLuClusterCtas - 1) / kLuClusterCtas : 0;
+    for (int64_t e = tid; e < (int64_t)nmine * n; e += kLuClusterThreads) {
+        const int32_t li = (int32_t)(e / n), c = (int32_t)(e % n);
+        a[(int64_t)li * n + c] = g[(int64_t)(rank + kLuClusterCtas * li) * n + c];
+    }
+    for (int32_t i = tid; i < n; i += kLuClusterThreads) {
+        perm[i] = i;
+        pos_of[i] = i;
+    }
+    __syncthreads();
+    int32_t k = 0;
+    for (; k < n; ++k) {
+        // this CTA's candidate
+        KeyIdx best{0ull, n};
+        for (int32_t li = tid; li < nmine; li += kLuClusterThreads) {
+            const int32_t q = pos_of[rank + kLuClusterCtas * li];
+            if (q >= k) best = better(best, KeyIdx{mag_key(a[(int64_t)li * n + k]), q});
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            KeyIdx other{__shfl_xor_sync(0xffffffffu, best.k, o), __shfl_xor_sync(0xffffffffu, best.i, o)};
+            best = better(best, other);
+        }
+        if (lane == 0) wbest[warp] = best;
+        __syncthreads();
+        if (warp == 0) {
+            KeyIdx bb = lane < nw ? wbest[lane] : KeyIdx{0ull, n};
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                KeyIdx other{__shfl_xor_sync(0xffffffffu, bb.k, o), __shfl_xor_sync(0xffffffffu, bb.i, o)};
+                bb = better(bb, other);
+            }
+            if (lane == 0) cand = bb;
+        }
+        cluster.sync();
+        // the pivot: the best of the eight candidates, the same in every CTA
+        if (warp == 0) {
+            KeyIdx c{0ull, n};
+            if (lane < kLuClusterCtas) c = *cluster.map_shared_rank(&cand, lane);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                KeyIdx other{__shfl_xor_sync(0xffffffffu, c.k, o), __shfl_xor_sync(0xffffffffu, c.i, o)};
+                c = better(c, other);
+            }
+            if (lane == 0) {
+                const int sing = c.k == 0ull || c.i < k || c.i >= n;
+                const int32_t pos = sing ? k : c.i;
+                s_sing = sing;
+                if (rank == 0) piv[k] = pos;
+                const int32_t pk = perm[k], pp = perm[pos];
+                perm[k] = pp;
+                perm[pos] = pk;
+                pos_of[pp] = k;
+                pos_of[pk] = pos;
+            }
+        }
+        __syncthreads();
+        if (s_sing) break;  // the same decision in every CTA
+        const int32_t pr = perm[k];
+        const double *src =
+            cluster.map_shared_rank(a + (int64_t)(pr / kLuClusterCtas) * n, (unsigned)(pr % kLuClusterCtas));
+        for (int32_t c = k + tid; c < n; c += kLuClusterThreads) prow[c] = src[c];
+        __syncthreads();
+        const double akk = prow[k];
+        for (int32_t li = tid; li < nmine; li += kLuClusterThreads)
+            if (pos_of[rank + kLuClusterCtas * li] > k) lbuf[li] = a[(int64_t)li * n + k] / akk;
+        __syncthreads();
+        for (int32_t li = warp; li < nmine; li += nw) {
+            if (pos_of[rank + kLuClusterCtas * li] <= k) continue;
+            const double l = lbuf[li];
+            double *row = a + (int64_t)li * n;
+            if (lane == 0) row[k] = l;
+            for (int32_t c = k + 1 + lane; c < n; c += 32) row[c] = fma(-l, prow[c], row[c]);
+        }
+        cluster.sync();
+    }
+    if (k < n && rank == 0) {
+        if (tid == 0) atomicOr(st, DEV_ERR_SINGULAR);
+        for (int32_t r = k + 1 + tid; r < n; r += kLuClusterThreads) piv[r] = r;
+    }
+    for (int64_t e = tid; e < (int64_t)nmine * n; e += kLuClusterThreads) {
+        const int32_t li = (int32_t)(e / n), c = (int32_t)(e % n);
+        const int64_t q = pos_of[rank + kLuClusterCtas * li];
+        const double v = a[(int64_t)li * n + c];
+        g[q * n + c] = v;
+        if (gT) gT[(int64_t)c * n + q] = v;
+    }
+    // no CTA leaves while another may still read its shared memory
+    cluster.sync();
 }
 
 __global__ void __launch_bounds__(1024) k_dense_lu(int32_t n, double *__restrict__ a, int32_t *__restrict__ piv,
@@ -554,6 +677,51 @@ k_lu_inverse(int32_t n, const double *__restrict__ lu_g, const int32_t *__restri
     }
     if (staged)
         for (int32_t r = lane; r < n; r += 32) inv[(int64_t)r * n + j] = x[r];
+}
+
+// explicit inverse from column-major factors (n > kLuSmemN): the factors stay
+// in global memory (L2) and every step's loads are contiguous across lanes;
+// the pivots, the reciprocals of U's diagonal and each warp's column live in
+// shared memory
+__global__ void __launch_bounds__(kInvWarps * 32)
+k_lu_inverse_t(int32_t n, const double *__restrict__ luT, const int32_t *__restrict__ piv, double *__restrict__ inv) {
+    extern __shared__ double sm_it[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double *xs = sm_it;                                   // kInvWarps columns
+    double *rd = xs + (int64_t)kInvWarps * n;             // 1 / u_kk
+    int32_t *pv = (int32_t *)(rd + n);
+    for (int32_t e = threadIdx.x; e < n; e += blockDim.x) {
+        rd[e] = 1.0 / luT[(int64_t)e * n + e];
+        pv[e] = piv[e];
+    }
+    __syncthreads();
+    const int32_t j = blockIdx.x * kInvWarps + w;
+    if (j >= n) return;  // warp-uniform; no block barrier follows
+    double *x = xs + (int64_t)w * n;
+    int32_t pos = j;
+    for (int32_t k = 0; k < n; ++k) {
+        const int32_t p = pv[k];
+        if (p < 0 || p >= n || p == k) continue;
+        if (pos == k) pos = p;
+        else if (pos == p) pos = k;
+    }
+    for (int32_t r = lane; r < n; r += 32) x[r] = (r == pos) ? 1.0 : 0.0;
+    __syncwarp();
+    for (int32_t k = pos; k < n - 1; ++k) {
+        const double xk = x[k];
+        const double *colk = luT + (int64_t)k * n;
+        for (int32_t r = k + 1 + lane; r < n; r += 32) x[r] = fma(-colk[r], xk, x[r]);
+        __syncwarp();
+    }
+    for (int32_t k = n - 1; k >= 0; --k) {
+        if (lane == 0) x[k] = x[k] * rd[k];
+        __syncwarp();
+        const double xk = x[k];
+        const double *colk = luT + (int64_t)k * n;
+        for (int32_t r = lane; r < k; r += 32) x[r] = fma(-colk[r], xk, x[r]);
+        __syncwarp();
+    }
+    for (int32_t r = lane; r < n; r += 32) inv[(int64_t)r * n + j] = x[r];
 }
 
 // u = A_L^-1 f, one warp per row
@@ -1361,20 +1529,39 @@ void launch_csr_to_dense(int32_t n, const int32_t *ptr, const int32_t *col, cons
     count_launch();
     k_csr_to_dense<<<nblocks(n), kThreads, 0, s>>>(n, ptr, col, val, valf, dense);
 }
-void launch_dense_lu(int32_t n, double *a, int32_t *piv, int *st, cudaStream_t s) {
+size_t lu_cluster_smem(int32_t n) {
+    const size_t nloc = (size_t)(n + kLuClusterCtas - 1) / kLuClusterCtas;
+    return (nloc * n + n + nloc) * sizeof(double) + 2 * (size_t)n * sizeof(int32_t);
+}
+bool lu_wants_transpose(int32_t n) { return n > kLuSmemN && n <= kLuClusterN; }
+void launch_dense_lu(int32_t n, double *a, int32_t *piv, int *st, cudaStream_t s, double *aT) {
     static bool attr = false;
     const int max_bytes = kLuSmemN * kLuSmemN * (int)sizeof(double);
     if (!attr) {
         cudaFuncSetAttribute(k_dense_lu_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(k_dense_lu_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)lu_cluster_smem(kLuClusterN));
+        cudaFuncSetAttribute(k_lu_inverse_t, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(((size_t)(kInvWarps + 1) * kLuClusterN) * sizeof(double) +
+                                   (size_t)kLuClusterN * sizeof(int32_t)));
         attr = true;
     }
     count_launch();
     if (n <= kLuSmemN)
         k_dense_lu_smem<<<1, kLuThreads, (size_t)n * n * sizeof(double), s>>>(n, a, piv, st);
+    else if (n <= kLuClusterN)
+        k_dense_lu_cluster<<<kLuClusterCtas, kLuClusterThreads, lu_cluster_smem(n), s>>>(n, a, aT, piv, st);
     else
         k_dense_lu<<<1, 1024, 0, s>>>(n, a, piv, st);
 }
-void launch_lu_inverse(int32_t n, const double *lu, const int32_t *piv, double *inv, cudaStream_t s) {
+void launch_lu_inverse(int32_t n, const double *lu, const int32_t *piv, double *inv, cudaStream_t s,
+                       const double *luT) {
+    if (luT && n > kLuSmemN && n <= kLuClusterN) {
+        count_launch();
+        const size_t bytes = ((size_t)(kInvWarps + 1) * n) * sizeof(double) + (size_t)n * sizeof(int32_t);
+        k_lu_inverse_t<<<(unsigned)((n + kInvWarps - 1) / kInvWarps), kInvWarps * 32, bytes, s>>>(n, luT, piv, inv);
+        return;
+    }
     static bool attr = false;
     const int max_bytes = (kLuSmemN * kLuSmemN + (kInvWarps + 1) * kLuSmemN) * (int)sizeof(double) +
                           kLuSmemN * (int)sizeof(int32_t);

@@ -151,6 +151,14 @@ NS_MU_WATER = 1.0      # dynamic viscosity in the water column
 NS_MU_AIR = 0.018      # and in the air (about the water / air ratio)
 
 
+# the 4 x 4 block workloads (unknowns 4 N^3): 48^3 has 110,592 nodes / 442,368
+# unknowns, about the size of Sec. 4's Navier-Stokes system (417,604 unknowns)
+NS_WORKLOADS = {
+    "ns32": Workload("ns32", 3, 32, 20, "fp64"),
+    "ns48": Workload("ns48", 3, 48, 50, "fp64"),
+}
+
+
 def ns_fields(N: int, k: int, T: int, courant: float = LEVELSET_COURANT):
     """Per-cell density and viscosity (the collapsing water column at step k)
     and the face velocities of the level-set flow: the inputs of the 4 x 4

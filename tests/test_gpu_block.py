@@ -67,8 +67,10 @@ def _compare(G, H):
     assert np.allclose(lu, olu, rtol=1e-12, atol=1e-14 * np.abs(olu).max())
 
 
-@pytest.mark.parametrize("N,ce", [(12, 16), (20, 64), (33, 64)])
+@pytest.mark.parametrize("N,ce", [(12, 16), (20, 64), (33, 64), (20, 100)])
 def test_block_hierarchy_matches_oracle(N, ce):
+    """(20, 100): an 86-node coarsest level, 344 unknowns, factorised by the
+    cluster LU kernel."""
     T = 10
     ptr, col, v0 = gpu_ns(N, 0, T)
     G = B.AMG(B.block_params(coarse_enough=ce))

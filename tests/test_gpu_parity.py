@@ -376,3 +376,29 @@ def test_sell_layout_full_reuse_series_64cubed():
             assert abs(res - info.rel_resid) <= 1e-6 * res + 1e-15
             if info.status == 0:
                 assert res <= 1e-8
+
+
+@pytest.mark.parametrize("N,ce,nL", [(32, 250, 191), (40, 400, 369)])
+def test_cluster_lu_for_mid_size_coarsest_level(N, ce, nL):
+    """A coarsest level between 160 and 448 rows is factorised by the
+    eight-CTA cluster kernel: pivots identical to the oracle's, factors within
+    1e-12, and the V-cycle (which uses the inverse from the column-major
+    factors) and the solve as the oracle's."""
+    dim, T = 3, 10
+    ptr, col, v = gpu_problem(dim, N, 3, T)
+    G = B.AMG(coarse_enough=ce)
+    G.full_setup(ptr, col, v)
+    H = O.Hierarchy(*oracle_problem(dim, N, 3, T), O.Params(coarse_enough=ce))
+    assert G.nlevels == H.nlevels and H.sizes(H.nlevels - 1)[0] == nL
+    lu, piv = G.coarse_lu()
+    olu, opiv = H.lu()
+    assert np.array_equal(piv, opiv)
+    assert np.allclose(lu, olu, rtol=1e-12, atol=1e-14 * np.abs(olu).max())
+    r = I.rhs(N ** dim, seed=5)
+    z = G.vcycle(torch.tensor(r, device="cuda")).cpu().numpy()
+    zo = H.vcycle(r)
+    assert np.linalg.norm(z - zo) <= 1e-11 * np.linalg.norm(zo)
+    f = I.rhs(N ** dim)
+    u, info = G.solve(torch.tensor(f, device="cuda"), 1e-8)
+    _, it, _, st = H.pcg(f, 1e-8)
+    assert info.status == 0 and st == O.OK and abs(info.iters - it) <= 1
