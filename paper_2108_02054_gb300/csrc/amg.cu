@@ -55,10 +55,6 @@ struct amg_ctx {
     // system matrix of the solve (aliases level 0 except under full reuse)
     double *A_sys = nullptr;
     double *A_sys_own = nullptr;
-    // SELL-32 copy of the system matrix for the Krylov kernels (the finest
-    // level's own copy, or sl_sys_own filled from A_sys_own under full reuse)
-    SellRef sell_sys;
-    double *sl_sys_own = nullptr;
     // CG
     double *cg_r = nullptr, *cg_z = nullptr, *cg_p = nullptr, *cg_q = nullptr, *cg_t = nullptr;
     // per-block partial sums of the CG reductions, one set per reduction so
@@ -176,8 +172,6 @@ void free_hierarchy(amg_ctx *ctx) {
     ctx->have_setup = false;
     ctx->lu = ctx->inv = ctx->luT = nullptr;
     ctx->piv = nullptr;
-    ctx->sl_sys_own = nullptr;
-    ctx->sell_sys = SellRef{};
     ctx->graph_valid = false;
 }
 
@@ -377,7 +371,7 @@ amg_status numeric_rebuild(amg_ctx *ctx, const double *d_val, bool galerkin) {
         ProfScope ps_(ctx, AMG_PROF_INGEST);
         launch_ingest_fine(F.n, F.A_ptr, d_val, F.dia, p.smoother, p.jacobi_omega,
                            d_val == F.A_val ? nullptr : F.A_val, mx ? F.A_valf : nullptr, mx ? nullptr : F.m,
-                           mx ? F.mf : nullptr, ctx->d_st, F.sl_ptr, F.sl_val, mx ? F.sl_valf : nullptr, ctx->s);
+                           mx ? F.mf : nullptr, ctx->d_st, ctx->s);
     }
     for (int l = 0; l + 1 < ctx->nlev; ++l) {
         Level &L = ctx->lev[l];
@@ -405,27 +399,6 @@ amg_status numeric_rebuild(amg_ctx *ctx, const double *d_val, bool galerkin) {
         }
     }
     return coarse_factor(ctx);
-}
-
-// SELL-32 layout of the finest level's pattern (one lane per row): slice
-// offsets, columns; values are written at every ingest of new fine values
-amg_status build_sell(amg_ctx *ctx, Level &L) {
-    const int32_t nsl = (L.n + 31) / 32;
-    int32_t *slots = nullptr;
-    TRY(alloc(ctx, &slots, (size_t)nsl));
-    TRY(alloc(ctx, &L.sl_ptr, (size_t)nsl + 1));
-    launch_sell_slots(L.n, L.A_ptr, slots, ctx->s);
-    TRY(scan(ctx, slots, L.sl_ptr, nsl));
-    TRY(check_device(ctx, "SELL layout"));
-    int32_t total = 0;
-    TRY(read_scalar(ctx, L.sl_ptr + nsl, &total));
-    TRY(alloc(ctx, &L.sl_col, (size_t)total));
-    TRY(alloc(ctx, &L.sl_val, (size_t)total));
-    if (mixed(ctx)) TRY(alloc(ctx, &L.sl_valf, (size_t)total));
-    ctx->sl_sys_own = nullptr;
-    if (ctx->A_sys_own) TRY(alloc(ctx, &ctx->sl_sys_own, (size_t)total));
-    launch_sell_cols(L.n, L.A_ptr, L.A_col, L.sl_ptr, L.sl_col, ctx->s);
-    return AMG_OK;
 }
 
 amg_status full_setup_impl(amg_ctx *ctx, const double *d_val) {
@@ -461,7 +434,6 @@ amg_status full_setup_impl(amg_ctx *ctx, const double *d_val) {
         CK(cudaMemsetAsync(L.agg, 0xff, sizeof(int32_t) * (size_t)L.n, ctx->s));
         CK(cudaMemsetAsync(L.strong, 0, (size_t)L.nnz, ctx->s));
         L.lpr = choose_lpr(L.n, L.nnz);
-        if (ctx->nlev == 1 && L.lpr == 1 && !blockmode(ctx)) TRY(build_sell(ctx, L));
         if (L.n <= p.coarse_enough || ctx->nlev >= p.max_levels || ctx->nlev >= kMaxLevels) break;
         // strength and aggregation
         int32_t *deg = nullptr, *root_id = nullptr, *agg1 = nullptr, *root_of = nullptr;
@@ -653,15 +625,6 @@ amg_status set_pattern(amg_ctx *ctx, int32_t n, int32_t nnz, const int32_t *d_pt
 
 void update_sys(amg_ctx *ctx) {
     ctx->A_sys = ctx->A_sys_own ? ctx->A_sys_own : blockmode(ctx) ? ctx->lev[0].Ab : ctx->lev[0].A_val;
-    const Level &F = ctx->lev[0];
-    ctx->sell_sys = SellRef{};
-    if (!F.sl_ptr) return;
-    if (ctx->A_sys == F.A_val) {
-        ctx->sell_sys = SellRef{F.sl_ptr, F.sl_col, F.sl_val};
-    } else if (ctx->sl_sys_own) {
-        launch_sell_vals(F.n, F.A_ptr, F.sl_ptr, ctx->A_sys, ctx->sl_sys_own, ctx->s);
-        ctx->sell_sys = SellRef{F.sl_ptr, F.sl_col, ctx->sl_sys_own};
-    }
 }
 
 // ---------------------------------------------------------------- V-cycle
@@ -896,7 +859,7 @@ void enqueue_cg_iter_a(amg_ctx *ctx, double *u, int use_h, cudaGraphConditionalH
     CgState *cg = ctx->cg;
     {
         ProfScope ps_(ctx, AMG_PROF_CG_SPMV, true);
-        launch_spmv_dot(n, ctx->fine_ptr, ctx->fine_col, ctx->A_sys, ctx->sell_sys, ctx->cg_p, ctx->cg_q, ctx->part_pq, cg,
+        launch_spmv_dot(n, ctx->fine_ptr, ctx->fine_col, ctx->A_sys, ctx->cg_p, ctx->cg_q, ctx->part_pq, cg,
                         ctx->s);
     }
     {
@@ -910,7 +873,7 @@ void enqueue_cg_iter_a(amg_ctx *ctx, double *u, int use_h, cudaGraphConditionalH
 void enqueue_cg_iter_b(amg_ctx *ctx, const double *f, double *u) {
     const int32_t n = ctx->n;
     CgState *cg = ctx->cg;
-    launch_true_residual(n, ctx->fine_ptr, ctx->fine_col, ctx->A_sys, ctx->sell_sys, f, u, ctx->cg_t, ctx->part_tt,
+    launch_true_residual(n, ctx->fine_ptr, ctx->fine_col, ctx->A_sys, f, u, ctx->cg_t, ctx->part_tt,
                          cg, 0, ctx->s);
     launch_replace_r(n, cg, ctx->cg_t, ctx->cg_r, cg_smooth0(ctx), ctx->s);
 }
@@ -931,7 +894,7 @@ void enqueue_cg_iter_c(amg_ctx *ctx, int use_h, cudaGraphConditionalHandle h) {
 // the true relative residual of the returned iterate
 void enqueue_cg_epilogue(amg_ctx *ctx, const double *f, double *u) {
     const int32_t n = ctx->n;
-    launch_true_residual(n, ctx->fine_ptr, ctx->fine_col, ctx->A_sys, ctx->sell_sys, f, u, ctx->cg_t, ctx->part_tt,
+    launch_true_residual(n, ctx->fine_ptr, ctx->fine_col, ctx->A_sys, f, u, ctx->cg_t, ctx->part_tt,
                          ctx->cg, 1,
                          ctx->s);
 }

@@ -92,11 +92,6 @@ struct Level {
     // holds the block norms that strength and aggregation see), damped
     // block-Jacobi inverses (16 per node); vd vectors hold 4 per node
     double *Ab = nullptr, *APb = nullptr, *Minv = nullptr;
-    // SELL-32 copy of the matrix (finest level, one lane per row): slice
-    // offsets, columns, values (FP64; FP32 as well in mixed precision)
-    int32_t *sl_ptr = nullptr, *sl_col = nullptr;
-    double *sl_val = nullptr;
-    float *sl_valf = nullptr;
 };
 
 // ------------------------------------------------------------------ launchers
@@ -179,8 +174,7 @@ void launch_smoother_f32(int32_t n, const int32_t *ptr, const float *val, const 
                          float *m, cudaStream_t s);
 // level-0 ingest: copy new values to the hierarchy (and the FP32 copy), check them, build the smoother
 void launch_ingest_fine(int32_t n, const int32_t *ptr, const double *val_in, const int32_t *dia, int type,
-                        double wj, double *val_out, float *valf_out, double *m, float *mf, int *st, const int32_t *sl,
-                        double *sl_val, float *sl_valf, cudaStream_t s);
+                        double wj, double *val_out, float *valf_out, double *m, float *mf, int *st, cudaStream_t s);
 void launch_cast_f32(int64_t n, const double *in, float *out, cudaStream_t s);
 
 // coarsest level: dense LU and explicit inverse
@@ -234,26 +228,13 @@ void launch_cg_init(int32_t n, const double *f, double *u, double *r, double *pa
 void launch_dot(int32_t n, const double *x, const double *y, double *partial, const int *skip, CgState *cg, int target,
                 cudaStream_t s);
 void launch_cg_set_rz_p(int32_t n, const double *z, double *p, CgState *cg, cudaStream_t s);
-// SELL-32 copy of a matrix (slice offsets, columns, FP64 values); ptr == nullptr: none
-struct SellRef {
-    const int32_t *ptr = nullptr, *col = nullptr;
-    const double *val = nullptr;
-};
-void launch_spmv_dot(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const SellRef &sell,
-                     const double *p, double *q, double *partial, CgState *cg, cudaStream_t s);
+void launch_spmv_dot(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *p,
+                     double *q, double *partial, CgState *cg, cudaStream_t s);
 void launch_cg_update_ur(int32_t n, CgState *cg, const double *p, const double *q, double *u, double *r,
                          double *partial, int use_h, cudaGraphConditionalHandle hb, const Smooth0Out &z0,
                          cudaStream_t s);
-void launch_true_residual(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const SellRef &sell,
-                          const double *f, const double *u, double *t, double *partial, CgState *cg, int force,
-                          cudaStream_t s);
-// SELL-32 structure of a CSR pattern: slots per slice (to be scanned into the
-// slice offsets, n / 32 rounded up slices), columns, values
-void launch_sell_slots(int32_t n, const int32_t *ptr, int32_t *slots, cudaStream_t s);
-void launch_sell_cols(int32_t n, const int32_t *ptr, const int32_t *col, const int32_t *sl, int32_t *sl_col,
-                      cudaStream_t s);
-void launch_sell_vals(int32_t n, const int32_t *ptr, const int32_t *sl, const double *val, double *sl_val,
-                      cudaStream_t s);
+void launch_true_residual(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *f,
+                          const double *u, double *t, double *partial, CgState *cg, int force, cudaStream_t s);
 void launch_replace_r(int32_t n, const CgState *cg, const double *t, double *r, const Smooth0Out &z0, cudaStream_t s);
 void launch_cg_update_p(int32_t n, CgState *cg, const double *z, double *p, int use_h, cudaGraphConditionalHandle h,
                         cudaStream_t s);

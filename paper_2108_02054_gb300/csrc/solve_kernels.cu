@@ -281,23 +281,17 @@ __global__ void k_smoother(int32_t n, const int32_t *__restrict__ ptr, const V *
 // copy as well), flag non-finite entries and build the smoother in one pass
 __global__ void k_ingest_fine(int32_t n, const int32_t *__restrict__ ptr, const double *__restrict__ in,
                               const int32_t *__restrict__ dia, int type, double wj, double *__restrict__ out,
-                              float *__restrict__ outf, double *__restrict__ m, float *__restrict__ mf, int *st,
-                              const int32_t *__restrict__ sl, double *__restrict__ sl_val,
-                              float *__restrict__ sl_valf) {
+                              float *__restrict__ outf, double *__restrict__ m, float *__restrict__ mf, int *st) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double s = 0.0;
     bool finite = true;
-    const int32_t b = ptr[i];
-    const int64_t sb = sl ? (int64_t)sl[i >> 5] + (i & 31) : 0;
-    for (int32_t p = b; p < ptr[i + 1]; ++p) {
+    for (int32_t p = ptr[i]; p < ptr[i + 1]; ++p) {
         const double v = in[p];
         finite = finite && isfinite(v);
         s = fma(v, v, s);
         if (out) out[p] = v;
         if (outf) outf[p] = (float)v;
-        if (sl_val) sl_val[sb + 32 * (int64_t)(p - b)] = v;
-        if (sl_valf) sl_valf[sb + 32 * (int64_t)(p - b)] = (float)v;
     }
     if (!finite) atomicOr(st, DEV_ERR_NONFINITE);
     const double aii = in[dia[i]];
@@ -311,35 +305,6 @@ __global__ void k_ingest_fine(int32_t n, const int32_t *__restrict__ ptr, const 
 __global__ void k_cast_f32(int64_t n, const double *__restrict__ in, float *__restrict__ out) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = (float)in[i];
-}
-
-// SELL-32 structure: stored entries per slice (32 x its longest row) ...
-__global__ void k_sell_slots(int32_t n, const int32_t *__restrict__ ptr, int32_t *__restrict__ slots) {
-    const int32_t sl = blockIdx.x * blockDim.x + threadIdx.x;
-    const int32_t nsl = (n + 31) / 32;
-    if (sl >= nsl) return;
-    int32_t w = 0;
-    for (int32_t i = 32 * sl; i < n && i < 32 * sl + 32; ++i) w = max(w, ptr[i + 1] - ptr[i]);
-    slots[sl] = 32 * w;
-}
-// ... and the columns (padding: the row's own index, never read)
-__global__ void k_sell_cols(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
-                            const int32_t *__restrict__ sl, int32_t *__restrict__ sl_col) {
-    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int64_t base = (int64_t)sl[i >> 5] + (i & 31);
-    const int32_t w = (sl[(i >> 5) + 1] - sl[i >> 5]) / 32;
-    const int32_t b = ptr[i], len = ptr[i + 1] - b;
-    for (int32_t k = 0; k < w; ++k) sl_col[base + 32 * (int64_t)k] = k < len ? col[b + k] : i;
-}
-// values of a CSR matrix into the SELL-32 layout (padding untouched)
-__global__ void k_sell_vals(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ sl,
-                            const double *__restrict__ val, double *__restrict__ sl_val) {
-    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int64_t base = (int64_t)sl[i >> 5] + (i & 31);
-    const int32_t b = ptr[i], len = ptr[i + 1] - b;
-    for (int32_t k = 0; k < len; ++k) sl_val[base + 32 * (int64_t)k] = val[b + k];
 }
 
 // ------------------------------------------------------------------ coarsest level
@@ -749,43 +714,17 @@ __device__ __forceinline__ V group_sum(V s) {
     return s;
 }
 
-// Row access.  CSR: entry k of row i at ptr[i] + k.  SELL-32 (slices of 32
-// consecutive rows, no reordering; used with one lane per row): entry k of
-// row i at sl[i / 32] + i % 32 + 32 k, so that a warp's k-th loads are 32
-// consecutive words; the row length still comes from ptr, the entry order is
-// the CSR order and every sum is unchanged.
-template <bool SELL>
-__device__ __forceinline__ void row_span(int32_t i, const int32_t *__restrict__ ptr, const int32_t *__restrict__ sl,
-                                         int64_t &p0, int32_t &cnt) {
-    const int32_t b = ptr[i];
-    cnt = ptr[i + 1] - b;
-    p0 = SELL ? (int64_t)sl[i >> 5] + (i & 31) : (int64_t)b;
-}
-template <bool SELL>
-__device__ __forceinline__ int64_t row_at(int64_t p0, int32_t k) { return p0 + (SELL ? 32 * (int64_t)k : (int64_t)k); }
-
 // zero-guess pre-smoothing fused with the residual: u = m o f, r = f - A u
-template <class V, class TF, int LPR, bool SELL = false>
+template <class V, class TF, int LPR>
 __global__ void k_smooth0_residual(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                                    const V *__restrict__ val, const V *__restrict__ m, const TF *__restrict__ f,
-                                   V *__restrict__ u, V *__restrict__ r, const int *skip, const int32_t *sl) {
+                                   V *__restrict__ u, V *__restrict__ r, const int *skip) {
     if (skipped(skip)) return;
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int32_t i = (int32_t)(gt / LPR);
     const int sub = (int)(gt % LPR);
     V s = 0;
-    if (SELL) {
-        if (i < n) {
-            int64_t p0;
-            int32_t cnt;
-            row_span<true>(i, ptr, sl, p0, cnt);
-            for (int32_t k = 0; k < cnt; ++k) {
-                const int64_t p = row_at<true>(p0, k);
-                const int32_t j = col[p];
-                s = fma(val[p], m[j] * (V)f[j], s);
-            }
-        }
-    } else if (i < n)
+    if (i < n)
         for (int32_t p = ptr[i] + sub; p < ptr[i + 1]; p += LPR) {
             const int32_t j = col[p];
             s = fma(val[p], m[j] * (V)f[j], s);
@@ -799,27 +738,16 @@ __global__ void k_smooth0_residual(int32_t n, const int32_t *__restrict__ ptr, c
 }
 
 // u_out = u_in + m o (f - A u_in)
-template <class V, class TF, class TO, int LPR, bool SELL = false>
+template <class V, class TF, class TO, int LPR>
 __global__ void k_smooth_sweep(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                                const V *__restrict__ val, const V *__restrict__ m, const TF *__restrict__ f,
-                               const V *__restrict__ u_in, TO *__restrict__ u_out, const int *skip,
-                               const int32_t *sl) {
+                               const V *__restrict__ u_in, TO *__restrict__ u_out, const int *skip) {
     if (skipped(skip)) return;
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int32_t i = (int32_t)(gt / LPR);
     const int sub = (int)(gt % LPR);
     V s = 0;
-    if (SELL) {
-        if (i < n) {
-            int64_t p0;
-            int32_t cnt;
-            row_span<true>(i, ptr, sl, p0, cnt);
-            for (int32_t k = 0; k < cnt; ++k) {
-                const int64_t p = row_at<true>(p0, k);
-                s = fma(val[p], u_in[col[p]], s);
-            }
-        }
-    } else if (i < n)
+    if (i < n)
         for (int32_t p = ptr[i] + sub; p < ptr[i + 1]; p += LPR) s = fma(val[p], u_in[col[p]], s);
     s = group_sum<LPR>(s);
     if (i < n && sub == 0) u_out[i] = (TO)fma(m[i], (V)f[i] - s, u_in[i]);
@@ -829,11 +757,11 @@ __global__ void k_smooth_sweep(int32_t n, const int32_t *__restrict__ ptr, const
 // z = u_in + m o (r - A u_in) and a per-block partial of r.z (block_sum order)
 __device__ double block_sum(double v);
 __device__ bool cg_reduce(double d, double *partial, unsigned *counter, double *total);
-template <class V, int LPR, bool SELL = false>
+template <class V, int LPR>
 __global__ void k_smooth_sweep_dot(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                                    const V *__restrict__ val, const V *__restrict__ m, const double *__restrict__ f,
                                    const V *__restrict__ u_in, double *__restrict__ z, double *__restrict__ partial,
-                                   CgState *cg, const int *skip, const int32_t *sl) {
+                                   CgState *cg, const int *skip) {
     if (skipped(skip)) return;
     const int64_t total = (int64_t)n * LPR;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -843,17 +771,7 @@ __global__ void k_smooth_sweep_dot(int32_t n, const int32_t *__restrict__ ptr, c
         const int32_t i = (int32_t)(gt / LPR);
         const int sub = (int)(gt % LPR);
         V s = 0;
-        if (SELL) {
-            if (gt < total) {
-                int64_t p0;
-                int32_t cnt;
-                row_span<true>(i, ptr, sl, p0, cnt);
-                for (int32_t k = 0; k < cnt; ++k) {
-                    const int64_t p = row_at<true>(p0, k);
-                    s = fma(val[p], u_in[col[p]], s);
-                }
-            }
-        } else if (gt < total)
+        if (gt < total)
             for (int32_t p = ptr[i] + sub; p < ptr[i + 1]; p += LPR) s = fma(val[p], u_in[col[p]], s);
         s = group_sum<LPR>(s);
         if (gt < total && sub == 0) {
@@ -868,26 +786,16 @@ __global__ void k_smooth_sweep_dot(int32_t n, const int32_t *__restrict__ ptr, c
     if (cg_reduce(d, partial, &cg->ctr[CG_CTR_RZ], &rz) && threadIdx.x == 0) cg->rz_next = rz;
 }
 
-template <class V, class TF, int LPR, bool SELL = false>
+template <class V, class TF, int LPR>
 __global__ void k_residual(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                            const V *__restrict__ val, const TF *__restrict__ f, const V *__restrict__ u,
-                           V *__restrict__ r, const int *skip, const int32_t *sl) {
+                           V *__restrict__ r, const int *skip) {
     if (skipped(skip)) return;
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int32_t i = (int32_t)(gt / LPR);
     const int sub = (int)(gt % LPR);
     V s = 0;
-    if (SELL) {
-        if (i < n) {
-            int64_t p0;
-            int32_t cnt;
-            row_span<true>(i, ptr, sl, p0, cnt);
-            for (int32_t k = 0; k < cnt; ++k) {
-                const int64_t p = row_at<true>(p0, k);
-                s = fma(val[p], u[col[p]], s);
-            }
-        }
-    } else if (i < n)
+    if (i < n)
         for (int32_t p = ptr[i] + sub; p < ptr[i + 1]; p += LPR) s = fma(val[p], u[col[p]], s);
     s = group_sum<LPR>(s);
     if (i < n && sub == 0) r[i] = (V)f[i] - s;
@@ -1050,23 +958,16 @@ __global__ void k_cg_set_rz_p(int32_t n, const double *__restrict__ z, double *_
 }
 
 // q = A p; the last block forms p.q and alpha = r.z / p.q (breakdown: p.q <= 0)
-template <bool SELL>
 __global__ void k_spmv_dot(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                            const double *__restrict__ val, const double *__restrict__ p, double *__restrict__ q,
-                           double *__restrict__ partial, CgState *cg, const int32_t *sl) {
+                           double *__restrict__ partial, CgState *cg) {
     if (cg->done) return;
     // r.z of the previous iteration becomes current (read only by the last block)
     if (blockIdx.x == 0 && threadIdx.x == 0) cg->rz = cg->rz_next;
     double d = 0.0;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double s = 0.0;
-        int64_t p0;
-        int32_t cnt;
-        row_span<SELL>(i, ptr, sl, p0, cnt);
-        for (int32_t k = 0; k < cnt; ++k) {
-            const int64_t e = row_at<SELL>(p0, k);
-            s = fma(val[e], p[col[e]], s);
-        }
+        for (int32_t e = ptr[i]; e < ptr[i + 1]; ++e) s = fma(val[e], p[col[e]], s);
         q[i] = s;
         d = fma(p[i], s, d);
     }
@@ -1118,22 +1019,15 @@ __global__ void k_cg_update_ur(int32_t n, CgState *cg, const double *__restrict_
 // t = f - A u, the true residual, when the recurrence reports convergence; the
 // last block accepts convergence or schedules the replacement of r (twice at
 // most).  With force: unconditionally, the final relative residual.
-template <bool SELL>
 __global__ void k_true_residual(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                                 const double *__restrict__ val, const double *__restrict__ f,
                                 const double *__restrict__ u, double *__restrict__ t, double *__restrict__ partial,
-                                CgState *cg, int force, const int32_t *sl) {
+                                CgState *cg, int force) {
     if (!force && (cg->done || !cg->need_true)) return;
     double d = 0.0;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double s = 0.0;
-        int64_t p0;
-        int32_t cnt;
-        row_span<SELL>(i, ptr, sl, p0, cnt);
-        for (int32_t k = 0; k < cnt; ++k) {
-            const int64_t e = row_at<SELL>(p0, k);
-            s = fma(val[e], u[col[e]], s);
-        }
+        for (int32_t e = ptr[i]; e < ptr[i + 1]; ++e) s = fma(val[e], u[col[e]], s);
         const double ti = f[i] - s;
         t[i] = ti;
         d = fma(ti, ti, d);
@@ -1511,11 +1405,9 @@ void launch_smoother_f32(int32_t n, const int32_t *ptr, const float *val, const 
     k_smoother<float><<<nblocks(n), kThreads, 0, s>>>(n, ptr, val, dia, type, (float)wj, m);
 }
 void launch_ingest_fine(int32_t n, const int32_t *ptr, const double *val_in, const int32_t *dia, int type,
-                        double wj, double *val_out, float *valf_out, double *m, float *mf, int *st, const int32_t *sl,
-                        double *sl_val, float *sl_valf, cudaStream_t s) {
+                        double wj, double *val_out, float *valf_out, double *m, float *mf, int *st, cudaStream_t s) {
     count_launch();
-    k_ingest_fine<<<nblocks(n), kThreads, 0, s>>>(n, ptr, val_in, dia, type, wj, val_out, valf_out, m, mf, st, sl,
-                                                  sl_val, sl_valf);
+    k_ingest_fine<<<nblocks(n), kThreads, 0, s>>>(n, ptr, val_in, dia, type, wj, val_out, valf_out, m, mf, st);
 }
 void launch_cast_f32(int64_t n, const double *in, float *out, cudaStream_t s) {
     int64_t b = nblocks(n);
@@ -1586,52 +1478,29 @@ void launch_lu_inverse(int32_t n, const double *lu, const int32_t *piv, double *
         default: { constexpr int P_ = 32; KCALL; } break; \
     }
 
-// the level's SELL-32 copy of the values `val` (one lane per row), if it has one
-const double *sell_of(const Level &L, const double *val) {
-    return (L.sl_ptr && L.lpr == 1 && val == L.A_val) ? L.sl_val : nullptr;
-}
-const float *sell_of(const Level &L, const float *val) {
-    return (L.sl_ptr && L.lpr == 1 && val == L.A_valf) ? L.sl_valf : nullptr;
-}
-
 template <class V, class TF>
 void launch_smooth0_residual(const Level &L, const V *val, const V *m, const TF *f, V *u, V *r, const int *skip,
                              cudaStream_t s) {
     count_launch();
-    if (const V *sv = sell_of(L, val)) {
-        k_smooth0_residual<V, TF, 1, true><<<nblocks(L.n), kThreads, 0, s>>>(L.n, L.A_ptr, L.sl_col, sv, m, f, u, r,
-                                                                            skip, L.sl_ptr);
-        return;
-    }
     const unsigned g = (unsigned)nblocks((int64_t)L.n * L.lpr);
     LPR_DISPATCH(L.lpr, (k_smooth0_residual<V, TF, P_><<<g, kThreads, 0, s>>>(L.n, L.A_ptr, L.A_col, val, m, f, u,
-                                                                              r, skip, nullptr)))
+                                                                              r, skip)))
 }
 template <class V, class TF, class TO>
 void launch_smooth_sweep(const Level &L, const V *val, const V *m, const TF *f, const V *u_in, TO *u_out,
                          const int *skip, cudaStream_t s) {
     count_launch();
-    if (const V *sv = sell_of(L, val)) {
-        k_smooth_sweep<V, TF, TO, 1, true><<<nblocks(L.n), kThreads, 0, s>>>(L.n, L.A_ptr, L.sl_col, sv, m, f, u_in,
-                                                                            u_out, skip, L.sl_ptr);
-        return;
-    }
     const unsigned g = (unsigned)nblocks((int64_t)L.n * L.lpr);
     LPR_DISPATCH(L.lpr, (k_smooth_sweep<V, TF, TO, P_><<<g, kThreads, 0, s>>>(L.n, L.A_ptr, L.A_col, val, m, f,
-                                                                              u_in, u_out, skip, nullptr)))
+                                                                              u_in, u_out, skip)))
 }
 template <class V>
 void launch_smooth_sweep_dot(const Level &L, const V *val, const V *m, const double *f, const V *u_in, double *z,
                              double *partial, CgState *cg, const int *skip, cudaStream_t s) {
     count_launch();
     const unsigned g = (unsigned)cg_blocks(L.n);
-    if (const V *sv = sell_of(L, val)) {
-        k_smooth_sweep_dot<V, 1, true><<<g, kCgThreads, 0, s>>>(L.n, L.A_ptr, L.sl_col, sv, m, f, u_in, z, partial,
-                                                                cg, skip, L.sl_ptr);
-        return;
-    }
     LPR_DISPATCH(L.lpr, (k_smooth_sweep_dot<V, P_><<<g, kCgThreads, 0, s>>>(L.n, L.A_ptr, L.A_col, val, m, f, u_in,
-                                                                             z, partial, cg, skip, nullptr)))
+                                                                             z, partial, cg, skip)))
 }
 template void launch_smooth_sweep_dot<double>(const Level &, const double *, const double *, const double *,
                                               const double *, double *, double *, CgState *, const int *,
@@ -1641,14 +1510,8 @@ template void launch_smooth_sweep_dot<float>(const Level &, const float *, const
 template <class V, class TF>
 void launch_residual(const Level &L, const V *val, const TF *f, const V *u, V *r, const int *skip, cudaStream_t s) {
     count_launch();
-    if (const V *sv = sell_of(L, val)) {
-        k_residual<V, TF, 1, true><<<nblocks(L.n), kThreads, 0, s>>>(L.n, L.A_ptr, L.sl_col, sv, f, u, r, skip,
-                                                                    L.sl_ptr);
-        return;
-    }
     const unsigned g = (unsigned)nblocks((int64_t)L.n * L.lpr);
-    LPR_DISPATCH(L.lpr, (k_residual<V, TF, P_><<<g, kThreads, 0, s>>>(L.n, L.A_ptr, L.A_col, val, f, u, r, skip,
-                                                                      nullptr)))
+    LPR_DISPATCH(L.lpr, (k_residual<V, TF, P_><<<g, kThreads, 0, s>>>(L.n, L.A_ptr, L.A_col, val, f, u, r, skip)))
 }
 template <class V>
 void launch_restrict(const Level &L, const V *Rval, const V *r, V *fc, const V *mc, V *uc, const int *skip,
@@ -1739,13 +1602,10 @@ void launch_cg_set_rz_p(int32_t n, const double *z, double *p, CgState *cg, cuda
     count_launch();
     k_cg_set_rz_p<<<cg_blocks(n), kCgThreads, 0, s>>>(n, z, p, cg);
 }
-void launch_spmv_dot(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const SellRef &sell,
-                     const double *p, double *q, double *partial, CgState *cg, cudaStream_t s) {
+void launch_spmv_dot(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *p,
+                     double *q, double *partial, CgState *cg, cudaStream_t s) {
     count_launch();
-    if (sell.ptr)
-        k_spmv_dot<true><<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, sell.col, sell.val, p, q, partial, cg, sell.ptr);
-    else
-        k_spmv_dot<false><<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, col, val, p, q, partial, cg, nullptr);
+    k_spmv_dot<<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, col, val, p, q, partial, cg);
 }
 void launch_cg_update_ur(int32_t n, CgState *cg, const double *p, const double *q, double *u, double *r,
                          double *partial, int use_h, cudaGraphConditionalHandle hb, const Smooth0Out &z0,
@@ -1753,31 +1613,10 @@ void launch_cg_update_ur(int32_t n, CgState *cg, const double *p, const double *
     count_launch();
     k_cg_update_ur<<<cg_blocks(n), kCgThreads, 0, s>>>(n, cg, p, q, u, r, partial, use_h, hb, z0);
 }
-void launch_true_residual(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const SellRef &sell,
-                          const double *f, const double *u, double *t, double *partial, CgState *cg, int force,
-                          cudaStream_t s) {
+void launch_true_residual(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *f,
+                          const double *u, double *t, double *partial, CgState *cg, int force, cudaStream_t s) {
     count_launch();
-    if (sell.ptr)
-        k_true_residual<true><<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, sell.col, sell.val, f, u, t, partial, cg,
-                                                                  force, sell.ptr);
-    else
-        k_true_residual<false><<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, col, val, f, u, t, partial, cg, force,
-                                                                   nullptr);
-}
-
-void launch_sell_slots(int32_t n, const int32_t *ptr, int32_t *slots, cudaStream_t s) {
-    count_launch();
-    k_sell_slots<<<nblocks((n + 31) / 32), kThreads, 0, s>>>(n, ptr, slots);
-}
-void launch_sell_cols(int32_t n, const int32_t *ptr, const int32_t *col, const int32_t *sl, int32_t *sl_col,
-                      cudaStream_t s) {
-    count_launch();
-    k_sell_cols<<<nblocks(n), kThreads, 0, s>>>(n, ptr, col, sl, sl_col);
-}
-void launch_sell_vals(int32_t n, const int32_t *ptr, const int32_t *sl, const double *val, double *sl_val,
-                      cudaStream_t s) {
-    count_launch();
-    k_sell_vals<<<nblocks(n), kThreads, 0, s>>>(n, ptr, sl, val, sl_val);
+    k_true_residual<<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, col, val, f, u, t, partial, cg, force);
 }
 void launch_replace_r(int32_t n, const CgState *cg, const double *t, double *r, const Smooth0Out &z0, cudaStream_t s) {
     count_launch();

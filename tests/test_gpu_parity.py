@@ -352,10 +352,9 @@ def test_preventive_rebuilds():
     assert rebuilt_any
 
 
-def test_sell_layout_full_reuse_series_64cubed():
-    """64^3: the finest level runs one lane per row on its SELL-32 copy (and,
-    under full reuse, on the copy of the system matrix filled every step);
-    the time loop follows the oracle's."""
+def test_time_series_64cubed_partial_and_full_reuse():
+    """64^3, the benchmark's grid (one lane per finest-level row): the time
+    loop under partial and full reuse follows the oracle's."""
     dim, N, T = 3, 64, 50
     ptr, col, _ = gpu_problem(dim, N, 0, T)
     f = I.rhs(N ** 3)
