@@ -60,3 +60,4 @@ def test_reference_arm_prints_the_contract_line():
     assert line["unit"] == "s/time step" and line["value"] > 0 and line["higher_is_better"] is False
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    assert line["steps"] == 2 and line["warmup"] == 1
