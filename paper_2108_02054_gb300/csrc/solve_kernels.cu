@@ -245,7 +245,19 @@ __global__ void k_gather_apply<double>(int64_t nout, const int32_t *__restrict__
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nout) return;
     double acc = 0.0;
-    for (int32_t t = eptr[e]; t < eptr[e + 1]; ++t) acc = fma(w[t], x[idx[t]], acc);
+    const int32_t t0 = eptr[e], t1 = eptr[e + 1];
+    int32_t t = t0;
+    // four terms' loads in flight at once; the fmas keep the term order
+    for (; t + 4 <= t1; t += 4) {
+        const int32_t i0 = idx[t], i1 = idx[t + 1], i2 = idx[t + 2], i3 = idx[t + 3];
+        const double w0 = w[t], w1 = w[t + 1], w2 = w[t + 2], w3 = w[t + 3];
+        const double x0 = x[i0], x1 = x[i1], x2 = x[i2], x3 = x[i3];
+        acc = fma(w0, x0, acc);
+        acc = fma(w1, x1, acc);
+        acc = fma(w2, x2, acc);
+        acc = fma(w3, x3, acc);
+    }
+    for (; t < t1; ++t) acc = fma(w[t], x[idx[t]], acc);
     y[e] = acc;
 }
 template <>
@@ -255,7 +267,18 @@ __global__ void k_gather_apply<float>(int64_t nout, const int32_t *__restrict__ 
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nout) return;
     float hi = 0.f, lo = 0.f;
-    for (int32_t t = eptr[e]; t < eptr[e + 1]; ++t) df_acc(hi, lo, w[t], x[idx[t]]);
+    const int32_t t0 = eptr[e], t1 = eptr[e + 1];
+    int32_t t = t0;
+    for (; t + 4 <= t1; t += 4) {
+        const int32_t i0 = idx[t], i1 = idx[t + 1], i2 = idx[t + 2], i3 = idx[t + 3];
+        const float w0 = w[t], w1 = w[t + 1], w2 = w[t + 2], w3 = w[t + 3];
+        const float x0 = x[i0], x1 = x[i1], x2 = x[i2], x3 = x[i3];
+        df_acc(hi, lo, w0, x0);
+        df_acc(hi, lo, w1, x1);
+        df_acc(hi, lo, w2, x2);
+        df_acc(hi, lo, w3, x3);
+    }
+    for (; t < t1; ++t) df_acc(hi, lo, w[t], x[idx[t]]);
     y[e] = hi + lo;
 }
 
@@ -344,11 +367,10 @@ __device__ __forceinline__ KeyIdx better(KeyIdx a, KeyIdx b) {
 // out in position order at the end.  Larger ones use the global-memory kernel.
 constexpr int kLuSmemN = 160;
 constexpr int kLuClusterN = 448;   // 8 CTAs x 56 rows x 448 columns fit in 227 KB each
-constexpr int kLuThreads = 1024;
+constexpr int kLuThreads = 512;
 __global__ void __launch_bounds__(kLuThreads) k_dense_lu_smem(int32_t n, double *__restrict__ g,
                                                               int32_t *__restrict__ piv, int *st) {
     extern __shared__ double a[];
-    __shared__ KeyIdx wbest[kLuThreads / 32];
     __shared__ int32_t perm[kLuSmemN];
     __shared__ int s_sing;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -359,31 +381,29 @@ __global__ void __launch_bounds__(kLuThreads) k_dense_lu_smem(int32_t n, double 
     __syncthreads();
     int32_t k = 0;
     for (; k < n; ++k) {
-        KeyIdx best{0ull, n};
-        for (int32_t i = k + tid; i < n; i += kLuThreads) best = better(best, KeyIdx{mag_key(a[(int64_t)perm[i] * n + k]), i});
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            KeyIdx other{__shfl_xor_sync(0xffffffffu, best.k, o), __shfl_xor_sync(0xffffffffu, best.i, o)};
-            best = better(best, other);
-        }
-        if (lane == 0) wbest[warp] = best;
-        __syncthreads();
         if (warp == 0) {
-            KeyIdx bb = lane < nw ? wbest[lane] : KeyIdx{0ull, n};
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                KeyIdx other{__shfl_xor_sync(0xffffffffu, bb.k, o), __shfl_xor_sync(0xffffffffu, bb.i, o)};
-                bb = better(bb, other);
+            // pivot search by one warp: the largest magnitude key, then the
+            // lowest position among equal keys (three warp reductions)
+            unsigned long long key = 0ull;
+            int32_t pos = n;
+            for (int32_t i = k + lane; i < n; i += 32) {
+                const unsigned long long q = mag_key(a[(int64_t)perm[i] * n + k]);
+                if (q > key) { key = q; pos = i; }
             }
+            const unsigned hi = (unsigned)(key >> 32), lo = (unsigned)key;
+            const unsigned mh = __reduce_max_sync(0xffffffffu, hi);
+            const unsigned ml = __reduce_max_sync(0xffffffffu, hi == mh ? lo : 0u);
+            const bool top = hi == mh && lo == ml && pos < n;
+            const int32_t bi = (int32_t)__reduce_min_sync(0xffffffffu, top ? (unsigned)pos : (unsigned)n);
             if (lane == 0) {
                 // no usable pivot (zero or NaN column): singular, identity pivots from here on
-                const int sing = bb.k == 0ull || bb.i < k || bb.i >= n;
-                const int32_t pos = sing ? k : bb.i;
+                const int sing = (mh | ml) == 0u || bi < k || bi >= n;
+                const int32_t pp = sing ? k : bi;
                 s_sing = sing;
-                piv[k] = pos;
+                piv[k] = pp;
                 const int32_t t = perm[k];
-                perm[k] = perm[pos];
-                perm[pos] = t;
+                perm[k] = perm[pp];
+                perm[pp] = t;
             }
         }
         __syncthreads();
