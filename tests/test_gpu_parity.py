@@ -377,6 +377,43 @@ def test_time_series_64cubed_partial_and_full_reuse():
                 assert res <= 1e-8
 
 
+def _dense_csr(M):
+    n = M.shape[0]
+    ptr = np.arange(0, n * n + 1, n, dtype=np.int32)
+    col = np.tile(np.arange(n, dtype=np.int32), n)
+    return ptr, col, np.ascontiguousarray(M, np.float64).ravel()
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 31, 32, 33, 87, 128, 129, 160, 161, 250, 448, 449, 500])
+@pytest.mark.parametrize("dup", [False, True])
+def test_coarsest_lu_with_tied_pivots_and_singular_input(n, dup):
+    """The coarsest dense LU of every kernel size class (one block up to 160
+    rows, the eight-CTA cluster up to 448, the global-memory kernel above) on
+    a one-level hierarchy whose matrix is dense with small-integer entries, so
+    that many candidates tie in magnitude: the pivots (first position of the
+    largest magnitude) and the factors equal the oracle's bit for bit.  With a
+    duplicated row the matrix is singular: the setup reports ERR_SINGULAR
+    exactly when the oracle's elimination meets an all-zero column."""
+    rng = np.random.default_rng(1000 + n)
+    M = rng.integers(-3, 4, (n, n)).astype(np.float64)
+    if dup and n >= 2:
+        M[n // 2] = M[0]
+    olu, opiv, ost = O.dense_lu(M)
+    ptr, col, val = (torch.tensor(a, device="cuda") for a in _dense_csr(M))
+    G = B.AMG(coarse_enough=n)
+    if ost == O.ERR_SINGULAR:
+        with pytest.raises(B.AmgError) as e:
+            G.full_setup(ptr, col, val)
+        assert e.value.status == B.AMG_ERR_SINGULAR
+        return
+    assert ost == O.OK
+    G.full_setup(ptr, col, val)
+    assert G.nlevels == 1
+    lu, piv = G.coarse_lu()
+    assert np.array_equal(piv, opiv)
+    assert np.array_equal(lu, olu)
+
+
 @pytest.mark.parametrize("N,ce,nL", [(32, 250, 191), (40, 400, 369)])
 def test_cluster_lu_for_mid_size_coarsest_level(N, ce, nL):
     """A coarsest level between 160 and 448 rows is factorised by the
