@@ -2,6 +2,7 @@
 // libamgpr.so (partial-reuse smoothed-aggregation AMG, arXiv 2108.02054).
 #pragma once
 #include <cuda_runtime.h>
+#include <utility>
 
 #include <cstdint>
 #include <cstdio>
@@ -98,6 +99,29 @@ struct Level {
 // (all enqueue on `s`; `st` is the device status word)
 // every launcher counts its kernel launches (process-wide)
 void count_launch();
+
+// Programmatic dependent launch for the solve's kernel chain: the launch of
+// a kernel may be processed while its predecessor in the stream (or graph)
+// completes, and the kernel's first statement, pdl_wait(), blocks until the
+// predecessor has finished and its memory is visible.  Without a
+// programmatic predecessor pdl_wait() returns at once.
+__device__ __forceinline__ void pdl_wait() { cudaGridDependencySynchronize(); }
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args &&...args) {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    // a launch error stays the runtime's last error, read by the status check
+    (void)cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 void add_launches(int64_t d);
 int64_t launch_total();
 void scan_counts(const int32_t *in, int32_t *out, int64_t n, int *st, int64_t *tmp, cudaStream_t s);

@@ -713,6 +713,7 @@ k_lu_inverse_t(int32_t n, const double *__restrict__ luT, const int32_t *__restr
 template <class TF, class TO>
 __global__ void k_coarse_solve(int32_t n, const double *__restrict__ inv, const TF *__restrict__ f,
                                TO *__restrict__ u, const int *skip) {
+    pdl_wait();
     if (skipped(skip)) return;
     const int lane = threadIdx.x & 31;
     const int32_t r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -739,6 +740,7 @@ template <class V, class TF, int LPR>
 __global__ void k_smooth0_residual(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                                    const V *__restrict__ val, const V *__restrict__ m, const TF *__restrict__ f,
                                    V *__restrict__ u, V *__restrict__ r, const int *skip) {
+    pdl_wait();
     if (skipped(skip)) return;
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int32_t i = (int32_t)(gt / LPR);
@@ -762,6 +764,7 @@ template <class V, class TF, class TO, int LPR>
 __global__ void k_smooth_sweep(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                                const V *__restrict__ val, const V *__restrict__ m, const TF *__restrict__ f,
                                const V *__restrict__ u_in, TO *__restrict__ u_out, const int *skip) {
+    pdl_wait();
     if (skipped(skip)) return;
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int32_t i = (int32_t)(gt / LPR);
@@ -782,6 +785,7 @@ __global__ void k_smooth_sweep_dot(int32_t n, const int32_t *__restrict__ ptr, c
                                    const V *__restrict__ val, const V *__restrict__ m, const double *__restrict__ f,
                                    const V *__restrict__ u_in, double *__restrict__ z, double *__restrict__ partial,
                                    CgState *cg, const int *skip) {
+    pdl_wait();
     if (skipped(skip)) return;
     const int64_t total = (int64_t)n * LPR;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -810,6 +814,7 @@ template <class V, class TF, int LPR>
 __global__ void k_residual(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                            const V *__restrict__ val, const TF *__restrict__ f, const V *__restrict__ u,
                            V *__restrict__ r, const int *skip) {
+    pdl_wait();
     if (skipped(skip)) return;
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int32_t i = (int32_t)(gt / LPR);
@@ -826,6 +831,7 @@ template <class V, int LPR>
 __global__ void k_restrict(int32_t nc, const int32_t *__restrict__ R_ptr, const int32_t *__restrict__ R_col,
                            const V *__restrict__ R_val, const V *__restrict__ r, V *__restrict__ fc,
                            const V *__restrict__ mc, V *__restrict__ uc, const int *skip) {
+    pdl_wait();
     if (skipped(skip)) return;
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int32_t I = (int32_t)(gt / LPR);
@@ -846,6 +852,7 @@ template <class V>
 __global__ void k_prolong(int32_t n, const int32_t *__restrict__ P_ptr, const int32_t *__restrict__ P_col,
                           const V *__restrict__ P_val, const V *__restrict__ uc, V *__restrict__ u,
                           const int *skip) {
+    pdl_wait();
     if (skipped(skip)) return;
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -856,6 +863,7 @@ __global__ void k_prolong(int32_t n, const int32_t *__restrict__ P_ptr, const in
 
 template <class TI, class TO>
 __global__ void k_copy_cast(int64_t n, const TI *__restrict__ in, TO *__restrict__ out, const int *skip) {
+    pdl_wait();
     if (skipped(skip)) return;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = (TO)in[i];
@@ -926,6 +934,7 @@ __device__ __forceinline__ void put_smooth0(const Smooth0Out &z0, int32_t i, dou
 // u = 0, r = f; the last block initialises the iteration state from |f|
 __global__ void k_cg_init(int32_t n, const double *__restrict__ f, double *__restrict__ u, double *__restrict__ r,
                           double *__restrict__ partial, CgState *cg, double tol, int maxiter, Smooth0Out z0) {
+    pdl_wait();
     double s = 0.0;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double fi = f[i];
@@ -955,6 +964,7 @@ __global__ void k_cg_init(int32_t n, const double *__restrict__ f, double *__res
 // target 2: r_new.z_old of the flexible variant)
 __global__ void k_dot(int32_t n, const double *__restrict__ x, const double *__restrict__ y,
                       double *__restrict__ partial, const int *skip, CgState *cg, int target) {
+    pdl_wait();
     if (skipped(skip)) return;
     double s = 0.0;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) s = fma(x[i], y[i], s);
@@ -972,6 +982,7 @@ __global__ void k_dot(int32_t n, const double *__restrict__ x, const double *__r
 
 // after the first preconditioner application: p = z, r.z becomes current
 __global__ void k_cg_set_rz_p(int32_t n, const double *__restrict__ z, double *__restrict__ p, CgState *cg) {
+    pdl_wait();
     if (cg->done) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) cg->rz = cg->rz_next;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = z[i];
@@ -981,6 +992,7 @@ __global__ void k_cg_set_rz_p(int32_t n, const double *__restrict__ z, double *_
 __global__ void k_spmv_dot(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                            const double *__restrict__ val, const double *__restrict__ p, double *__restrict__ q,
                            double *__restrict__ partial, CgState *cg) {
+    pdl_wait();
     if (cg->done) return;
     // r.z of the previous iteration becomes current (read only by the last block)
     if (blockIdx.x == 0 && threadIdx.x == 0) cg->rz = cg->rz_next;
@@ -1009,6 +1021,7 @@ __global__ void k_spmv_dot(int32_t n, const int32_t *__restrict__ ptr, const int
 __global__ void k_cg_update_ur(int32_t n, CgState *cg, const double *__restrict__ p, const double *__restrict__ q,
                                double *__restrict__ u, double *__restrict__ r, double *__restrict__ partial,
                                int use_h, cudaGraphConditionalHandle hb, Smooth0Out z0) {
+    pdl_wait();
     if (cg->done) {
         if (use_h && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(hb, 0u);
         return;
@@ -1043,6 +1056,7 @@ __global__ void k_true_residual(int32_t n, const int32_t *__restrict__ ptr, cons
                                 const double *__restrict__ val, const double *__restrict__ f,
                                 const double *__restrict__ u, double *__restrict__ t, double *__restrict__ partial,
                                 CgState *cg, int force) {
+    pdl_wait();
     if (!force && (cg->done || !cg->need_true)) return;
     double d = 0.0;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -1072,6 +1086,7 @@ __global__ void k_true_residual(int32_t n, const int32_t *__restrict__ ptr, cons
 
 __global__ void k_replace_r(int32_t n, const CgState *cg, const double *__restrict__ t, double *__restrict__ r,
                             Smooth0Out z0) {
+    pdl_wait();
     if (cg->done || !cg->copy_r) return;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double ti = t[i];
@@ -1087,6 +1102,7 @@ __global__ void k_replace_r(int32_t n, const CgState *cg, const double *__restri
 // cap of maxiter + 4 bodies.
 __global__ void k_cg_update_p(int32_t n, CgState *cg, const double *__restrict__ z, double *__restrict__ p,
                               int use_h, cudaGraphConditionalHandle h) {
+    pdl_wait();
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
     if (cg->done) {
         if (lead && use_h) cudaGraphSetConditional(h, 0u);
@@ -1164,6 +1180,7 @@ __device__ bool bi_reduce2(double a, double b, double *pa, double *pb, unsigned 
 __global__ void k_bi_init(int32_t n, const double *__restrict__ f, double *__restrict__ x, double *__restrict__ r,
                           double *__restrict__ rh, double *__restrict__ p, double *__restrict__ v,
                           double *__restrict__ partial, BiState *st, double tol, int maxiter) {
+    pdl_wait();
     double s = 0.0;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double fi = f[i];
@@ -1191,6 +1208,7 @@ __global__ void k_bi_init(int32_t n, const double *__restrict__ f, double *__res
 // rho = (r^, r); beta = (rho / rho_old)(alpha / omega)
 __global__ void k_bi_rho(int32_t n, const double *__restrict__ rh, const double *__restrict__ r,
                          double *__restrict__ partial, BiState *st) {
+    pdl_wait();
     if (st->done) return;
     double d = 0.0;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) d = fma(rh[i], r[i], d);
@@ -1210,6 +1228,7 @@ __global__ void k_bi_rho(int32_t n, const double *__restrict__ rh, const double 
 // p = r + beta (p - omega v)
 __global__ void k_bi_p(int32_t n, const double *__restrict__ r, const double *__restrict__ v, double *__restrict__ p,
                        const BiState *st) {
+    pdl_wait();
     if (st->done) return;
     const double beta = st->beta, omega = st->omega;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
@@ -1221,6 +1240,7 @@ template <int BS>
 __global__ void k_bi_spmv_rv(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                              const double *__restrict__ val, const double *__restrict__ ph, double *__restrict__ v,
                              const double *__restrict__ rh, double *__restrict__ partial, BiState *st) {
+    pdl_wait();
     if (st->done) return;
     double d = 0.0;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -1244,6 +1264,7 @@ __global__ void k_bi_spmv_rv(int32_t n, const int32_t *__restrict__ ptr, const i
 // s = r - alpha v and |s|: converged at the half step when |s|/|f| <= tol
 __global__ void k_bi_s(int32_t n, const double *__restrict__ r, const double *__restrict__ v, double *__restrict__ sv,
                        double *__restrict__ partial, BiState *st) {
+    pdl_wait();
     if (st->done) return;
     const double alpha = st->alpha;
     double d = 0.0;
@@ -1264,6 +1285,7 @@ __global__ void k_bi_s(int32_t n, const double *__restrict__ r, const double *__
 // half step: x += alpha p^, r = s
 __global__ void k_bi_half(int32_t n, const double *__restrict__ ph, const double *__restrict__ sv,
                           double *__restrict__ x, double *__restrict__ r, const BiState *st) {
+    pdl_wait();
     if (st->done || !st->half) return;
     const double alpha = st->alpha;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -1278,6 +1300,7 @@ __global__ void k_bi_spmv_t(int32_t n, const int32_t *__restrict__ ptr, const in
                             const double *__restrict__ val, const double *__restrict__ sh,
                             const double *__restrict__ sv, double *__restrict__ t, double *__restrict__ partial,
                             BiState *st) {
+    pdl_wait();
     if (st->skip) return;
     double a = 0.0, b = 0.0;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -1305,6 +1328,7 @@ __global__ void k_bi_spmv_t(int32_t n, const int32_t *__restrict__ ptr, const in
 __global__ void k_bi_xr(int32_t n, const double *__restrict__ ph, const double *__restrict__ sh,
                         const double *__restrict__ sv, const double *__restrict__ t, double *__restrict__ x,
                         double *__restrict__ r, double *__restrict__ partial, BiState *st) {
+    pdl_wait();
     if (st->skip) return;
     const double alpha = st->alpha, omega = st->omega;
     double d = 0.0;
@@ -1328,6 +1352,7 @@ template <int BS>
 __global__ void k_bi_true(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                           const double *__restrict__ val, const double *__restrict__ f, const double *__restrict__ x,
                           double *__restrict__ t, double *__restrict__ partial, BiState *st, int force) {
+    pdl_wait();
     if (!force && (st->done || !st->need_true)) return;
     double d = 0.0;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -1355,6 +1380,7 @@ __global__ void k_bi_true(int32_t n, const int32_t *__restrict__ ptr, const int3
 }
 
 __global__ void k_bi_replace(int32_t n, const double *__restrict__ t, double *__restrict__ r, const BiState *st) {
+    pdl_wait();
     if (st->done || !st->copy_r) return;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) r[i] = t[i];
 }
@@ -1363,6 +1389,7 @@ __global__ void k_bi_replace(int32_t n, const double *__restrict__ t, double *__
 // maxiter (and, in the graph, keep the while loop going; hard cap maxiter + 4
 // bodies)
 __global__ void k_bi_end(BiState *st, int use_h, cudaGraphConditionalHandle h) {
+    pdl_wait();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     st->pad += 1;  // bodies run (the graph's launch count)
     if (!st->done) {
@@ -1503,7 +1530,7 @@ void launch_smooth0_residual(const Level &L, const V *val, const V *m, const TF 
                              cudaStream_t s) {
     count_launch();
     const unsigned g = (unsigned)nblocks((int64_t)L.n * L.lpr);
-    LPR_DISPATCH(L.lpr, (k_smooth0_residual<V, TF, P_><<<g, kThreads, 0, s>>>(L.n, L.A_ptr, L.A_col, val, m, f, u,
+    LPR_DISPATCH(L.lpr, (launch_pdl(k_smooth0_residual<V, TF, P_>, g, kThreads, 0, s, L.n, L.A_ptr, L.A_col, val, m, f, u,
                                                                               r, skip)))
 }
 template <class V, class TF, class TO>
@@ -1511,7 +1538,7 @@ void launch_smooth_sweep(const Level &L, const V *val, const V *m, const TF *f, 
                          const int *skip, cudaStream_t s) {
     count_launch();
     const unsigned g = (unsigned)nblocks((int64_t)L.n * L.lpr);
-    LPR_DISPATCH(L.lpr, (k_smooth_sweep<V, TF, TO, P_><<<g, kThreads, 0, s>>>(L.n, L.A_ptr, L.A_col, val, m, f,
+    LPR_DISPATCH(L.lpr, (launch_pdl(k_smooth_sweep<V, TF, TO, P_>, g, kThreads, 0, s, L.n, L.A_ptr, L.A_col, val, m, f,
                                                                               u_in, u_out, skip)))
 }
 template <class V>
@@ -1519,7 +1546,7 @@ void launch_smooth_sweep_dot(const Level &L, const V *val, const V *m, const dou
                              double *partial, CgState *cg, const int *skip, cudaStream_t s) {
     count_launch();
     const unsigned g = (unsigned)cg_blocks(L.n);
-    LPR_DISPATCH(L.lpr, (k_smooth_sweep_dot<V, P_><<<g, kCgThreads, 0, s>>>(L.n, L.A_ptr, L.A_col, val, m, f, u_in,
+    LPR_DISPATCH(L.lpr, (launch_pdl(k_smooth_sweep_dot<V, P_>, g, kCgThreads, 0, s, L.n, L.A_ptr, L.A_col, val, m, f, u_in,
                                                                              z, partial, cg, skip)))
 }
 template void launch_smooth_sweep_dot<double>(const Level &, const double *, const double *, const double *,
@@ -1531,31 +1558,31 @@ template <class V, class TF>
 void launch_residual(const Level &L, const V *val, const TF *f, const V *u, V *r, const int *skip, cudaStream_t s) {
     count_launch();
     const unsigned g = (unsigned)nblocks((int64_t)L.n * L.lpr);
-    LPR_DISPATCH(L.lpr, (k_residual<V, TF, P_><<<g, kThreads, 0, s>>>(L.n, L.A_ptr, L.A_col, val, f, u, r, skip)))
+    LPR_DISPATCH(L.lpr, (launch_pdl(k_residual<V, TF, P_>, g, kThreads, 0, s, L.n, L.A_ptr, L.A_col, val, f, u, r, skip)))
 }
 template <class V>
 void launch_restrict(const Level &L, const V *Rval, const V *r, V *fc, const V *mc, V *uc, const int *skip,
                      cudaStream_t s) {
     count_launch();
     const unsigned g = (unsigned)nblocks((int64_t)L.nc * L.lpr_r);
-    LPR_DISPATCH(L.lpr_r, (k_restrict<V, P_><<<g, kThreads, 0, s>>>(L.nc, L.R_ptr, L.R_col, Rval, r, fc, mc, uc,
+    LPR_DISPATCH(L.lpr_r, (launch_pdl(k_restrict<V, P_>, g, kThreads, 0, s, L.nc, L.R_ptr, L.R_col, Rval, r, fc, mc, uc,
                                                                     skip)))
 }
 template <class V>
 void launch_prolong(const Level &L, const V *Pval, const V *uc, V *u, const int *skip, cudaStream_t s) {
     count_launch();
-    k_prolong<V><<<nblocks(L.n), kThreads, 0, s>>>(L.n, L.P_ptr, L.P_col, Pval, uc, u, skip);
+    launch_pdl(k_prolong<V>, nblocks(L.n), kThreads, 0, s, L.n, L.P_ptr, L.P_col, Pval, uc, u, skip);
 }
 template <class V, class TF, class TO>
 void launch_coarse_solve(int32_t n, const double *inv, const TF *f, TO *u, const int *skip, cudaStream_t s) {
     count_launch();
-    k_coarse_solve<TF, TO><<<nblocks((int64_t)n * 32, 128), 128, 0, s>>>(n, inv, f, u, skip);
+    launch_pdl(k_coarse_solve<TF, TO>, nblocks((int64_t)n * 32, 128), 128, 0, s, n, inv, f, u, skip);
 }
 template <class TI, class TO>
 void launch_copy_cast(int64_t n, const TI *in, TO *out, const int *skip, cudaStream_t s) {
     int64_t b = nblocks(n);
     count_launch();
-    k_copy_cast<TI, TO><<<(unsigned)(b > 8192 ? 8192 : b), kThreads, 0, s>>>(n, in, out, skip);
+    launch_pdl(k_copy_cast<TI, TO>, (unsigned)(b > 8192 ? 8192 : b), kThreads, 0, s, n, in, out, skip);
 }
 
 #define INST_V(V, TF, TO)                                                                                           \
@@ -1611,96 +1638,96 @@ int cg_blocks(int64_t n) {
 void launch_cg_init(int32_t n, const double *f, double *u, double *r, double *partial, CgState *cg, double tol,
                     int maxiter, const Smooth0Out &z0, cudaStream_t s) {
     count_launch();
-    k_cg_init<<<cg_blocks(n), kCgThreads, 0, s>>>(n, f, u, r, partial, cg, tol, maxiter, z0);
+    launch_pdl(k_cg_init, cg_blocks(n), kCgThreads, 0, s, n, f, u, r, partial, cg, tol, maxiter, z0);
 }
 void launch_dot(int32_t n, const double *x, const double *y, double *partial, const int *skip, CgState *cg, int target,
                 cudaStream_t s) {
     count_launch();
-    k_dot<<<cg_blocks(n), kCgThreads, 0, s>>>(n, x, y, partial, skip, cg, target);
+    launch_pdl(k_dot, cg_blocks(n), kCgThreads, 0, s, n, x, y, partial, skip, cg, target);
 }
 void launch_cg_set_rz_p(int32_t n, const double *z, double *p, CgState *cg, cudaStream_t s) {
     count_launch();
-    k_cg_set_rz_p<<<cg_blocks(n), kCgThreads, 0, s>>>(n, z, p, cg);
+    launch_pdl(k_cg_set_rz_p, cg_blocks(n), kCgThreads, 0, s, n, z, p, cg);
 }
 void launch_spmv_dot(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *p,
                      double *q, double *partial, CgState *cg, cudaStream_t s) {
     count_launch();
-    k_spmv_dot<<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, col, val, p, q, partial, cg);
+    launch_pdl(k_spmv_dot, cg_blocks(n), kCgThreads, 0, s, n, ptr, col, val, p, q, partial, cg);
 }
 void launch_cg_update_ur(int32_t n, CgState *cg, const double *p, const double *q, double *u, double *r,
                          double *partial, int use_h, cudaGraphConditionalHandle hb, const Smooth0Out &z0,
                          cudaStream_t s) {
     count_launch();
-    k_cg_update_ur<<<cg_blocks(n), kCgThreads, 0, s>>>(n, cg, p, q, u, r, partial, use_h, hb, z0);
+    launch_pdl(k_cg_update_ur, cg_blocks(n), kCgThreads, 0, s, n, cg, p, q, u, r, partial, use_h, hb, z0);
 }
 void launch_true_residual(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *f,
                           const double *u, double *t, double *partial, CgState *cg, int force, cudaStream_t s) {
     count_launch();
-    k_true_residual<<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, col, val, f, u, t, partial, cg, force);
+    launch_pdl(k_true_residual, cg_blocks(n), kCgThreads, 0, s, n, ptr, col, val, f, u, t, partial, cg, force);
 }
 void launch_replace_r(int32_t n, const CgState *cg, const double *t, double *r, const Smooth0Out &z0, cudaStream_t s) {
     count_launch();
-    k_replace_r<<<cg_blocks(n), kCgThreads, 0, s>>>(n, cg, t, r, z0);
+    launch_pdl(k_replace_r, cg_blocks(n), kCgThreads, 0, s, n, cg, t, r, z0);
 }
 void launch_cg_update_p(int32_t n, CgState *cg, const double *z, double *p, int use_h, cudaGraphConditionalHandle h,
                         cudaStream_t s) {
     count_launch();
-    k_cg_update_p<<<cg_blocks(n), kCgThreads, 0, s>>>(n, cg, z, p, use_h, h);
+    launch_pdl(k_cg_update_p, cg_blocks(n), kCgThreads, 0, s, n, cg, z, p, use_h, h);
 }
 
 
 void launch_bi_init(int32_t n, const double *f, double *x, double *r, double *rh, double *p, double *v,
                     double *partial, BiState *st, double tol, int maxiter, cudaStream_t s) {
     count_launch();
-    k_bi_init<<<cg_blocks(n), kCgThreads, 0, s>>>(n, f, x, r, rh, p, v, partial, st, tol, maxiter);
+    launch_pdl(k_bi_init, cg_blocks(n), kCgThreads, 0, s, n, f, x, r, rh, p, v, partial, st, tol, maxiter);
 }
 void launch_bi_rho(int32_t n, const double *rh, const double *r, double *partial, BiState *st, cudaStream_t s) {
     count_launch();
-    k_bi_rho<<<cg_blocks(n), kCgThreads, 0, s>>>(n, rh, r, partial, st);
+    launch_pdl(k_bi_rho, cg_blocks(n), kCgThreads, 0, s, n, rh, r, partial, st);
 }
 void launch_bi_p(int32_t n, const double *r, const double *v, double *p, BiState *st, cudaStream_t s) {
     count_launch();
-    k_bi_p<<<cg_blocks(n), kCgThreads, 0, s>>>(n, r, v, p, st);
+    launch_pdl(k_bi_p, cg_blocks(n), kCgThreads, 0, s, n, r, v, p, st);
 }
 void launch_bi_spmv_rv(int32_t n, int bs, const int32_t *ptr, const int32_t *col, const double *val,
                        const double *ph, double *v, const double *rh, double *partial, BiState *st, cudaStream_t s) {
     count_launch();
-    if (bs == 4) k_bi_spmv_rv<4><<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, col, val, ph, v, rh, partial, st);
-    else k_bi_spmv_rv<1><<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, col, val, ph, v, rh, partial, st);
+    if (bs == 4) launch_pdl(k_bi_spmv_rv<4>, cg_blocks(n), kCgThreads, 0, s, n, ptr, col, val, ph, v, rh, partial, st);
+    else launch_pdl(k_bi_spmv_rv<1>, cg_blocks(n), kCgThreads, 0, s, n, ptr, col, val, ph, v, rh, partial, st);
 }
 void launch_bi_s(int32_t n, const double *r, const double *v, double *sv, double *partial, BiState *st,
                  cudaStream_t s) {
     count_launch();
-    k_bi_s<<<cg_blocks(n), kCgThreads, 0, s>>>(n, r, v, sv, partial, st);
+    launch_pdl(k_bi_s, cg_blocks(n), kCgThreads, 0, s, n, r, v, sv, partial, st);
 }
 void launch_bi_half(int32_t n, const double *ph, const double *sv, double *x, double *r, BiState *st, cudaStream_t s) {
     count_launch();
-    k_bi_half<<<cg_blocks(n), kCgThreads, 0, s>>>(n, ph, sv, x, r, st);
+    launch_pdl(k_bi_half, cg_blocks(n), kCgThreads, 0, s, n, ph, sv, x, r, st);
 }
 void launch_bi_spmv_t(int32_t n, int bs, const int32_t *ptr, const int32_t *col, const double *val,
                       const double *sh, const double *sv, double *t, double *partial, BiState *st, cudaStream_t s) {
     count_launch();
-    if (bs == 4) k_bi_spmv_t<4><<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, col, val, sh, sv, t, partial, st);
-    else k_bi_spmv_t<1><<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, col, val, sh, sv, t, partial, st);
+    if (bs == 4) launch_pdl(k_bi_spmv_t<4>, cg_blocks(n), kCgThreads, 0, s, n, ptr, col, val, sh, sv, t, partial, st);
+    else launch_pdl(k_bi_spmv_t<1>, cg_blocks(n), kCgThreads, 0, s, n, ptr, col, val, sh, sv, t, partial, st);
 }
 void launch_bi_xr(int32_t n, const double *ph, const double *sh, const double *sv, const double *t, double *x,
                   double *r, double *partial, BiState *st, cudaStream_t s) {
     count_launch();
-    k_bi_xr<<<cg_blocks(n), kCgThreads, 0, s>>>(n, ph, sh, sv, t, x, r, partial, st);
+    launch_pdl(k_bi_xr, cg_blocks(n), kCgThreads, 0, s, n, ph, sh, sv, t, x, r, partial, st);
 }
 void launch_bi_true(int32_t n, int bs, const int32_t *ptr, const int32_t *col, const double *val, const double *f,
                     const double *x, double *t, double *partial, BiState *st, int force, cudaStream_t s) {
     count_launch();
-    if (bs == 4) k_bi_true<4><<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, col, val, f, x, t, partial, st, force);
-    else k_bi_true<1><<<cg_blocks(n), kCgThreads, 0, s>>>(n, ptr, col, val, f, x, t, partial, st, force);
+    if (bs == 4) launch_pdl(k_bi_true<4>, cg_blocks(n), kCgThreads, 0, s, n, ptr, col, val, f, x, t, partial, st, force);
+    else launch_pdl(k_bi_true<1>, cg_blocks(n), kCgThreads, 0, s, n, ptr, col, val, f, x, t, partial, st, force);
 }
 void launch_bi_replace(int32_t n, const double *t, double *r, BiState *st, cudaStream_t s) {
     count_launch();
-    k_bi_replace<<<cg_blocks(n), kCgThreads, 0, s>>>(n, t, r, st);
+    launch_pdl(k_bi_replace, cg_blocks(n), kCgThreads, 0, s, n, t, r, st);
 }
 void launch_bi_end(BiState *st, int use_h, cudaGraphConditionalHandle h, cudaStream_t s) {
     count_launch();
-    k_bi_end<<<1, 32, 0, s>>>(st, use_h, h);
+    launch_pdl(k_bi_end, 1, 32, 0, s, st, use_h, h);
 }
 
 }  // namespace amgpr
