@@ -235,6 +235,7 @@ __device__ __forceinline__ void apply_minv(const double *__restrict__ m, const d
 // first pre-smoothing step from u = 0: u = Minv f
 __global__ void k_block_smooth0(int32_t n, const double *__restrict__ minv, const double *__restrict__ f,
                                 double *__restrict__ u, const int *skip) {
+    pdl_wait();
     if (skip && *skip) return;
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -249,6 +250,7 @@ __global__ void k_block_sweep(int32_t n, const int32_t *__restrict__ ptr, const 
                               const double *__restrict__ bv, const double *__restrict__ minv,
                               const double *__restrict__ f, const double *__restrict__ uin, double *__restrict__ uout,
                               const int *skip) {
+    pdl_wait();
     if (skip && *skip) return;
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -266,6 +268,7 @@ __global__ void k_block_sweep(int32_t n, const int32_t *__restrict__ ptr, const 
 __global__ void k_block_residual(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                                  const double *__restrict__ bv, const double *__restrict__ f,
                                  const double *__restrict__ u, double *__restrict__ r, const int *skip) {
+    pdl_wait();
     if (skip && *skip) return;
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -281,6 +284,7 @@ __global__ void k_block_residual(int32_t n, const int32_t *__restrict__ ptr, con
 __global__ void k_block_restrict(int32_t nc, const int32_t *__restrict__ Rptr, const int32_t *__restrict__ Rcol,
                                  const double *__restrict__ Rval, const double *__restrict__ r,
                                  double *__restrict__ fc, const int *skip) {
+    pdl_wait();
     if (skip && *skip) return;
     const int32_t I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nc) return;
@@ -299,6 +303,7 @@ __global__ void k_block_restrict(int32_t nc, const int32_t *__restrict__ Rptr, c
 __global__ void k_block_prolong(int32_t n, const int32_t *__restrict__ Pptr, const int32_t *__restrict__ Pcol,
                                 const double *__restrict__ Pval, const double *__restrict__ uc,
                                 double *__restrict__ u, const int *skip) {
+    pdl_wait();
     if (skip && *skip) return;
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -345,27 +350,27 @@ void launch_block_to_dense(int32_t n, const int32_t *ptr, const int32_t *col, co
 void launch_block_smooth0(int32_t n, const double *minv, const double *f, double *u, const int *skip,
                           cudaStream_t s) {
     count_launch();
-    k_block_smooth0<<<bblocks(n), kBThreads, 0, s>>>(n, minv, f, u, skip);
+    launch_pdl(k_block_smooth0, bblocks(n), kBThreads, 0, s, n, minv, f, u, skip);
 }
 void launch_block_sweep(int32_t n, const int32_t *ptr, const int32_t *col, const double *bv, const double *minv,
                         const double *f, const double *uin, double *uout, const int *skip, cudaStream_t s) {
     count_launch();
-    k_block_sweep<<<bblocks(n), kBThreads, 0, s>>>(n, ptr, col, bv, minv, f, uin, uout, skip);
+    launch_pdl(k_block_sweep, bblocks(n), kBThreads, 0, s, n, ptr, col, bv, minv, f, uin, uout, skip);
 }
 void launch_block_residual(int32_t n, const int32_t *ptr, const int32_t *col, const double *bv, const double *f,
                            const double *u, double *r, const int *skip, cudaStream_t s) {
     count_launch();
-    k_block_residual<<<bblocks(n), kBThreads, 0, s>>>(n, ptr, col, bv, f, u, r, skip);
+    launch_pdl(k_block_residual, bblocks(n), kBThreads, 0, s, n, ptr, col, bv, f, u, r, skip);
 }
 void launch_block_restrict(int32_t nc, const int32_t *Rptr, const int32_t *Rcol, const double *Rval, const double *r,
                            double *fc, const int *skip, cudaStream_t s) {
     count_launch();
-    k_block_restrict<<<bblocks(nc), kBThreads, 0, s>>>(nc, Rptr, Rcol, Rval, r, fc, skip);
+    launch_pdl(k_block_restrict, bblocks(nc), kBThreads, 0, s, nc, Rptr, Rcol, Rval, r, fc, skip);
 }
 void launch_block_prolong(int32_t n, const int32_t *Pptr, const int32_t *Pcol, const double *Pval, const double *uc,
                           double *u, const int *skip, cudaStream_t s) {
     count_launch();
-    k_block_prolong<<<bblocks(n), kBThreads, 0, s>>>(n, Pptr, Pcol, Pval, uc, u, skip);
+    launch_pdl(k_block_prolong, bblocks(n), kBThreads, 0, s, n, Pptr, Pcol, Pval, uc, u, skip);
 }
 
 }  // namespace amgpr
