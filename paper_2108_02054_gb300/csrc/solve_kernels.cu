@@ -301,22 +301,33 @@ __global__ void k_smoother(int32_t n, const int32_t *__restrict__ ptr, const V *
 }
 
 // fine level: copy the new values into the hierarchy (optionally an FP32
-// copy as well), flag non-finite entries and build the smoother in one pass
+// copy as well), flag non-finite entries and build the smoother in one kernel
 __global__ void k_ingest_fine(int32_t n, const int32_t *__restrict__ ptr, const double *__restrict__ in,
                               const int32_t *__restrict__ dia, int type, double wj, double *__restrict__ out,
                               float *__restrict__ outf, double *__restrict__ m, float *__restrict__ mf, int *st) {
-    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double s = 0.0;
+    // one warp per 32 consecutive rows: their values are one contiguous range,
+    // copied, cast and checked with coalesced accesses; then each lane forms
+    // its row's smoother from the same values (now in L1/L2) in column order
+    const int lane = threadIdx.x & 31;
+    const int32_t r0 = (int32_t)((((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 5);
+    if (r0 >= n) return;  // warp-uniform
+    const int32_t r1 = min(r0 + 32, n);
+    const int32_t p0 = ptr[r0], p1 = ptr[r1];
     bool finite = true;
-    for (int32_t p = ptr[i]; p < ptr[i + 1]; ++p) {
+    for (int32_t p = p0 + lane; p < p1; p += 32) {
         const double v = in[p];
         finite = finite && isfinite(v);
-        s = fma(v, v, s);
         if (out) out[p] = v;
         if (outf) outf[p] = (float)v;
     }
-    if (!finite) atomicOr(st, DEV_ERR_NONFINITE);
+    if (__any_sync(0xffffffffu, !finite) && lane == 0) atomicOr(st, DEV_ERR_NONFINITE);
+    const int32_t i = r0 + lane;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int32_t p = ptr[i]; p < ptr[i + 1]; ++p) {
+        const double v = in[p];
+        s = fma(v, v, s);
+    }
     const double aii = in[dia[i]];
     double mi;
     if (type == AMG_SMOOTHER_SPAI0) mi = s != 0.0 ? aii / s : 0.0;
