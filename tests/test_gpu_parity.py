@@ -284,6 +284,15 @@ def test_error_statuses():
     with pytest.raises(B.AmgError) as e:
         G.partial_rebuild(nan)
     assert e.value.status == B.AMG_ERR_NONFINITE
+    # the check covers every group of 32 rows: a NaN in the last entry (the
+    # last group) and an infinity mid-matrix
+    for pos, bad_v in ((v.numel() - 1, float("nan")), (v.numel() // 2 + 3, float("inf"))):
+        G.full_setup(ptr, col, v)
+        w = v.clone()
+        w[pos] = bad_v
+        with pytest.raises(B.AmgError) as e:
+            G.partial_rebuild(w)
+        assert e.value.status == B.AMG_ERR_NONFINITE
     G.full_setup(ptr, col, v)
     f = torch.tensor(I.rhs(256), device="cuda")
     G1 = B.AMG(maxiter=1, coarse_enough=16)
