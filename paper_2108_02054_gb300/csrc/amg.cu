@@ -274,16 +274,17 @@ amg_status max_row(amg_ctx *ctx, int32_t n, const int32_t *ptr, int32_t *out) {
     return AMG_OK;
 }
 
-// Lanes per row for a level's matrix-vector kernels: about `per_lane`
-// entries per lane (eight for A's rows, sixteen for the restriction's R rows,
-// which measured faster with longer runs on large levels), then more lanes
-// until the level offers enough threads to fill the GPU (short fine-level
-// rows keep one lane and the plain sequential row sum).
-int choose_lpr(int64_t rows, int64_t nnz, double per_lane = 8.0) {
+// Lanes per row for a level's matrix-vector kernels (A rows, R rows): about
+// sixteen entries per lane, then more lanes until the level offers enough
+// threads to fill the GPU (short fine-level rows keep one lane and the plain
+// sequential row sum).  Measured against eight and thirty-two entries per
+// lane: sixteen is fastest on the large levels at 128^3 and 192^3, and the
+// occupancy rule leaves the 64^3 levels as they were.
+int choose_lpr(int64_t rows, int64_t nnz) {
     if (rows <= 0) return 1;
     const double avg = (double)nnz / (double)rows;
     int p = 1;
-    while (p < 32 && per_lane * p < avg) p *= 2;
+    while (p < 32 && 16.0 * p < avg) p *= 2;
     while (p < 32 && rows * p < 152LL * 1024) p *= 2;
     return p;
 }
@@ -492,7 +493,7 @@ amg_status full_setup_impl(amg_ctx *ctx, const double *d_val) {
         TRY(alloc(ctx, &L.R_val, (size_t)L.nnzR));
         launch_transpose_scatter(L.n, L.P_ptr, L.P_col, L.P_val, L.R_ptr, cursor, L.R_col, L.R_val, ctx->s);
         launch_sort_rows(nagg, L.R_ptr, L.R_col, L.R_val, ctx->s);
-        L.lpr_r = choose_lpr(nagg, L.nnzR, 16.0);
+        L.lpr_r = choose_lpr(nagg, L.nnzR);
         // symbolic Galerkin product: AP = A*P, A_c = R*AP (+ diagonal)
         TRY(symbolic_product(ctx, L.n, nagg, L.A_ptr, L.A_col, L.P_ptr, L.P_col, 0, &L.AP_ptr, &L.AP_col,
                              &L.nnzAP));
