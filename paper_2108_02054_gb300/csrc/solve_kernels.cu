@@ -885,8 +885,11 @@ __global__ void k_copy_cast(int64_t n, const TI *__restrict__ in, TO *__restrict
 // (a fenced atomic counter, reset by that block) sums the partials in index
 // order and takes the iteration's scalar step itself, so no separate
 // single-block kernel is needed and the sums stay deterministic.
-constexpr int kCgThreads = 256;
-constexpr int kCgMaxBlocks = 152 * 8;
+constexpr int kCgThreads = 256;       // vectors up to kCgLargeN entries
+constexpr int kCgThreadsLarge = 512;  // longer vectors
+constexpr int kCgMaxBlocks = 152 * 4;  // long vectors: four blocks of 512 per SM
+constexpr int64_t kCgLargeN = (int64_t)152 * 8 * 256 * 4;
+inline int cg_threads(int64_t n) { return n >= kCgLargeN ? kCgThreadsLarge : kCgThreads; }
 
 // deterministic block sum (fixed lane / warp order)
 __device__ double block_sum(double v) {
@@ -1557,7 +1560,7 @@ void launch_smooth_sweep_dot(const Level &L, const V *val, const V *m, const dou
                              double *partial, CgState *cg, const int *skip, cudaStream_t s) {
     count_launch();
     const unsigned g = (unsigned)cg_blocks(L.n);
-    LPR_DISPATCH(L.lpr, (launch_pdl(k_smooth_sweep_dot<V, P_>, g, kCgThreads, 0, s, L.n, L.A_ptr, L.A_col, val, m, f, u_in,
+    LPR_DISPATCH(L.lpr, (launch_pdl(k_smooth_sweep_dot<V, P_>, g, cg_threads(L.n), 0, s, L.n, L.A_ptr, L.A_col, val, m, f, u_in,
                                                                              z, partial, cg, skip)))
 }
 template void launch_smooth_sweep_dot<double>(const Level &, const double *, const double *, const double *,
@@ -1638,103 +1641,106 @@ template void launch_copy_cast<float, double>(int64_t, const float *, double *, 
 // Grid of the Krylov kernels (grid-stride loops, one partial per block).  The
 // last-block reduction costs grow with the number of blocks (each block's
 // partial, fence and counter update sit on the final block's critical path),
-// so vectors up to about 1.2 M entries run on two blocks per SM; longer ones
-// need the full occupancy of eight to keep enough loads in flight.
+// so vectors up to about 1.2 M entries run on two blocks of 256 per SM; longer
+// ones need full occupancy to keep enough loads in flight, reached with four
+// blocks of 512 per SM (half the partials of eight blocks of 256, measured
+// faster at 128^3 and 192^3).
 int cg_blocks(int64_t n) {
-    int64_t b = (n + kCgThreads - 1) / kCgThreads;
-    const int64_t cap = n >= (int64_t)kCgMaxBlocks * kCgThreads * 4 ? kCgMaxBlocks : 152 * 2;
+    const int t = cg_threads(n);
+    int64_t b = (n + t - 1) / t;
+    const int64_t cap = n >= kCgLargeN ? kCgMaxBlocks : 152 * 2;
     if (b > cap) b = cap;
     return (int)(b < 1 ? 1 : b);
 }
 void launch_cg_init(int32_t n, const double *f, double *u, double *r, double *partial, CgState *cg, double tol,
                     int maxiter, const Smooth0Out &z0, cudaStream_t s) {
     count_launch();
-    launch_pdl(k_cg_init, cg_blocks(n), kCgThreads, 0, s, n, f, u, r, partial, cg, tol, maxiter, z0);
+    launch_pdl(k_cg_init, cg_blocks(n), cg_threads(n), 0, s, n, f, u, r, partial, cg, tol, maxiter, z0);
 }
 void launch_dot(int32_t n, const double *x, const double *y, double *partial, const int *skip, CgState *cg, int target,
                 cudaStream_t s) {
     count_launch();
-    launch_pdl(k_dot, cg_blocks(n), kCgThreads, 0, s, n, x, y, partial, skip, cg, target);
+    launch_pdl(k_dot, cg_blocks(n), cg_threads(n), 0, s, n, x, y, partial, skip, cg, target);
 }
 void launch_cg_set_rz_p(int32_t n, const double *z, double *p, CgState *cg, cudaStream_t s) {
     count_launch();
-    launch_pdl(k_cg_set_rz_p, cg_blocks(n), kCgThreads, 0, s, n, z, p, cg);
+    launch_pdl(k_cg_set_rz_p, cg_blocks(n), cg_threads(n), 0, s, n, z, p, cg);
 }
 void launch_spmv_dot(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *p,
                      double *q, double *partial, CgState *cg, cudaStream_t s) {
     count_launch();
-    launch_pdl(k_spmv_dot, cg_blocks(n), kCgThreads, 0, s, n, ptr, col, val, p, q, partial, cg);
+    launch_pdl(k_spmv_dot, cg_blocks(n), cg_threads(n), 0, s, n, ptr, col, val, p, q, partial, cg);
 }
 void launch_cg_update_ur(int32_t n, CgState *cg, const double *p, const double *q, double *u, double *r,
                          double *partial, int use_h, cudaGraphConditionalHandle hb, const Smooth0Out &z0,
                          cudaStream_t s) {
     count_launch();
-    launch_pdl(k_cg_update_ur, cg_blocks(n), kCgThreads, 0, s, n, cg, p, q, u, r, partial, use_h, hb, z0);
+    launch_pdl(k_cg_update_ur, cg_blocks(n), cg_threads(n), 0, s, n, cg, p, q, u, r, partial, use_h, hb, z0);
 }
 void launch_true_residual(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *f,
                           const double *u, double *t, double *partial, CgState *cg, int force, cudaStream_t s) {
     count_launch();
-    launch_pdl(k_true_residual, cg_blocks(n), kCgThreads, 0, s, n, ptr, col, val, f, u, t, partial, cg, force);
+    launch_pdl(k_true_residual, cg_blocks(n), cg_threads(n), 0, s, n, ptr, col, val, f, u, t, partial, cg, force);
 }
 void launch_replace_r(int32_t n, const CgState *cg, const double *t, double *r, const Smooth0Out &z0, cudaStream_t s) {
     count_launch();
-    launch_pdl(k_replace_r, cg_blocks(n), kCgThreads, 0, s, n, cg, t, r, z0);
+    launch_pdl(k_replace_r, cg_blocks(n), cg_threads(n), 0, s, n, cg, t, r, z0);
 }
 void launch_cg_update_p(int32_t n, CgState *cg, const double *z, double *p, int use_h, cudaGraphConditionalHandle h,
                         cudaStream_t s) {
     count_launch();
-    launch_pdl(k_cg_update_p, cg_blocks(n), kCgThreads, 0, s, n, cg, z, p, use_h, h);
+    launch_pdl(k_cg_update_p, cg_blocks(n), cg_threads(n), 0, s, n, cg, z, p, use_h, h);
 }
 
 
 void launch_bi_init(int32_t n, const double *f, double *x, double *r, double *rh, double *p, double *v,
                     double *partial, BiState *st, double tol, int maxiter, cudaStream_t s) {
     count_launch();
-    launch_pdl(k_bi_init, cg_blocks(n), kCgThreads, 0, s, n, f, x, r, rh, p, v, partial, st, tol, maxiter);
+    launch_pdl(k_bi_init, cg_blocks(n), cg_threads(n), 0, s, n, f, x, r, rh, p, v, partial, st, tol, maxiter);
 }
 void launch_bi_rho(int32_t n, const double *rh, const double *r, double *partial, BiState *st, cudaStream_t s) {
     count_launch();
-    launch_pdl(k_bi_rho, cg_blocks(n), kCgThreads, 0, s, n, rh, r, partial, st);
+    launch_pdl(k_bi_rho, cg_blocks(n), cg_threads(n), 0, s, n, rh, r, partial, st);
 }
 void launch_bi_p(int32_t n, const double *r, const double *v, double *p, BiState *st, cudaStream_t s) {
     count_launch();
-    launch_pdl(k_bi_p, cg_blocks(n), kCgThreads, 0, s, n, r, v, p, st);
+    launch_pdl(k_bi_p, cg_blocks(n), cg_threads(n), 0, s, n, r, v, p, st);
 }
 void launch_bi_spmv_rv(int32_t n, int bs, const int32_t *ptr, const int32_t *col, const double *val,
                        const double *ph, double *v, const double *rh, double *partial, BiState *st, cudaStream_t s) {
     count_launch();
-    if (bs == 4) launch_pdl(k_bi_spmv_rv<4>, cg_blocks(n), kCgThreads, 0, s, n, ptr, col, val, ph, v, rh, partial, st);
-    else launch_pdl(k_bi_spmv_rv<1>, cg_blocks(n), kCgThreads, 0, s, n, ptr, col, val, ph, v, rh, partial, st);
+    if (bs == 4) launch_pdl(k_bi_spmv_rv<4>, cg_blocks(n), cg_threads(n), 0, s, n, ptr, col, val, ph, v, rh, partial, st);
+    else launch_pdl(k_bi_spmv_rv<1>, cg_blocks(n), cg_threads(n), 0, s, n, ptr, col, val, ph, v, rh, partial, st);
 }
 void launch_bi_s(int32_t n, const double *r, const double *v, double *sv, double *partial, BiState *st,
                  cudaStream_t s) {
     count_launch();
-    launch_pdl(k_bi_s, cg_blocks(n), kCgThreads, 0, s, n, r, v, sv, partial, st);
+    launch_pdl(k_bi_s, cg_blocks(n), cg_threads(n), 0, s, n, r, v, sv, partial, st);
 }
 void launch_bi_half(int32_t n, const double *ph, const double *sv, double *x, double *r, BiState *st, cudaStream_t s) {
     count_launch();
-    launch_pdl(k_bi_half, cg_blocks(n), kCgThreads, 0, s, n, ph, sv, x, r, st);
+    launch_pdl(k_bi_half, cg_blocks(n), cg_threads(n), 0, s, n, ph, sv, x, r, st);
 }
 void launch_bi_spmv_t(int32_t n, int bs, const int32_t *ptr, const int32_t *col, const double *val,
                       const double *sh, const double *sv, double *t, double *partial, BiState *st, cudaStream_t s) {
     count_launch();
-    if (bs == 4) launch_pdl(k_bi_spmv_t<4>, cg_blocks(n), kCgThreads, 0, s, n, ptr, col, val, sh, sv, t, partial, st);
-    else launch_pdl(k_bi_spmv_t<1>, cg_blocks(n), kCgThreads, 0, s, n, ptr, col, val, sh, sv, t, partial, st);
+    if (bs == 4) launch_pdl(k_bi_spmv_t<4>, cg_blocks(n), cg_threads(n), 0, s, n, ptr, col, val, sh, sv, t, partial, st);
+    else launch_pdl(k_bi_spmv_t<1>, cg_blocks(n), cg_threads(n), 0, s, n, ptr, col, val, sh, sv, t, partial, st);
 }
 void launch_bi_xr(int32_t n, const double *ph, const double *sh, const double *sv, const double *t, double *x,
                   double *r, double *partial, BiState *st, cudaStream_t s) {
     count_launch();
-    launch_pdl(k_bi_xr, cg_blocks(n), kCgThreads, 0, s, n, ph, sh, sv, t, x, r, partial, st);
+    launch_pdl(k_bi_xr, cg_blocks(n), cg_threads(n), 0, s, n, ph, sh, sv, t, x, r, partial, st);
 }
 void launch_bi_true(int32_t n, int bs, const int32_t *ptr, const int32_t *col, const double *val, const double *f,
                     const double *x, double *t, double *partial, BiState *st, int force, cudaStream_t s) {
     count_launch();
-    if (bs == 4) launch_pdl(k_bi_true<4>, cg_blocks(n), kCgThreads, 0, s, n, ptr, col, val, f, x, t, partial, st, force);
-    else launch_pdl(k_bi_true<1>, cg_blocks(n), kCgThreads, 0, s, n, ptr, col, val, f, x, t, partial, st, force);
+    if (bs == 4) launch_pdl(k_bi_true<4>, cg_blocks(n), cg_threads(n), 0, s, n, ptr, col, val, f, x, t, partial, st, force);
+    else launch_pdl(k_bi_true<1>, cg_blocks(n), cg_threads(n), 0, s, n, ptr, col, val, f, x, t, partial, st, force);
 }
 void launch_bi_replace(int32_t n, const double *t, double *r, BiState *st, cudaStream_t s) {
     count_launch();
-    launch_pdl(k_bi_replace, cg_blocks(n), kCgThreads, 0, s, n, t, r, st);
+    launch_pdl(k_bi_replace, cg_blocks(n), cg_threads(n), 0, s, n, t, r, st);
 }
 void launch_bi_end(BiState *st, int use_h, cudaGraphConditionalHandle h, cudaStream_t s) {
     count_launch();
