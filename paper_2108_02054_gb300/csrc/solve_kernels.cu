@@ -375,7 +375,8 @@ __device__ __forceinline__ KeyIdx better(KeyIdx a, KeyIdx b) {
 // Small matrices (n <= kLuSmemN) are factorised in shared memory by one block
 // with a lazy row permutation: rows are not moved during the elimination,
 // perm[i] names the physical row at position i, and the factors are written
-// out in position order at the end.  Larger ones use the global-memory kernel.
+// out in position order at the end.  Larger ones use the cluster kernel (up to
+// kLuClusterN rows) or the global-memory kernel.
 constexpr int kLuSmemN = 160;
 constexpr int kLuClusterN = 448;   // 8 CTAs x 56 rows x 448 columns fit in 227 KB each
 constexpr int kLuThreads = 512;
