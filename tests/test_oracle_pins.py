@@ -605,3 +605,84 @@ def test_levelset_partial_reuse_keeps_iterations():
     part = O.run_time_steps(ptr, col, vals, f, O.MODE_PARTIAL, prm, solver="bicgstab")
     assert all(r.status == O.OK for r in full + part)
     assert sum(r.iters for r in part) <= 1.5 * sum(r.iters for r in full)
+
+
+# ---------------------------------------------------------------- strength predicate
+def _strength_from_values(A, theta_l):
+    """The strength rule (Alg. 1's transfer-operator step, Vanek-Mandel-Brezina
+    smoothed aggregation) recomputed from the matrix values alone: entry (i, j),
+    j != i, is strong iff a_ij^2 > theta_l^2 |a_ii a_jj| in row i's direction
+    or, for the entry (j, i), in row j's (every product rounded on its own)."""
+    import scipy.sparse as sp
+    n = A.nrows
+    rows = np.repeat(np.arange(n), np.diff(A.ptr))
+    off = A.col != rows
+    diag = np.zeros(n)
+    diag[rows[~off]] = A.val[~off]
+    eps2 = theta_l * theta_l
+    one = (A.val * A.val > eps2 * np.abs(diag[rows] * diag[A.col])) & off
+    M = sp.csr_matrix((one.astype(np.int8), A.col, A.ptr), shape=(n, n))
+    MT = M.T.tocsr()
+    back = np.asarray(MT[rows, A.col]).ravel() != 0
+    return (one | (back & off)).astype(np.uint8), one, diag
+
+
+def _hierarchy_cases():
+    p2, c2, v2 = O.poisson_assemble(2, 24, I.density(2, 24, 3, 10))
+    p3, c3, v3 = O.poisson_assemble(3, 12, I.density(3, 12, 4, 10))
+    pl, cl, vl = O.levelset_assemble(3, 10, *I.levelset_faces(3, 10, 2, 10))
+    return {"2d": (p2, c2, v2), "3d": (p3, c3, v3), "levelset3d": (pl, cl, vl)}
+
+
+@pytest.mark.parametrize("case", ["2d", "3d", "levelset3d"])
+def test_strength_flags_match_the_predicate_on_every_level(case):
+    ptr, col, val = _hierarchy_cases()[case]
+    prm = O.Params(coarse_enough=16)
+    H = O.Hierarchy(ptr, col, val, prm)
+    assert H.nlevels >= 3
+    asym_seen = False
+    for l in range(H.nlevels):
+        lv = H.level(l)
+        if l == H.nlevels - 1:
+            assert not lv.strong.any()          # the coarsest level is not aggregated
+            continue
+        theta_l = 0.08 / 2 ** l
+        ref, one, diag = _strength_from_values(lv.A, theta_l)
+        assert np.array_equal(lv.strong, ref), f"level {l}"
+        # the readings this pins each change the flags on this data: theta not
+        # squared, theta not halved per level, ">=" for ">" (no tie here), and the
+        # one-sided test where A is not symmetric
+        rows = np.repeat(np.arange(lv.A.nrows), np.diff(lv.A.ptr))
+        offd = lv.A.col != rows
+        not_sq = (lv.A.val ** 2 > theta_l * np.abs(diag[rows] * diag[lv.A.col])) & offd
+        assert not np.array_equal(not_sq.astype(np.uint8), ref), f"theta vs theta^2 indistinct, level {l}"
+        if l > 0:
+            const = _strength_from_values(lv.A, 0.08)[0]
+            assert not np.array_equal(const, ref), f"halving indistinct, level {l}"
+        if not np.array_equal(one.astype(np.uint8), ref):
+            asym_seen = True
+    if case == "levelset3d":
+        assert asym_seen                       # the symmetrised reading matters here
+
+
+def test_strength_is_strict_at_an_exact_tie():
+    """a_ij^2 == theta^2 |a_ii a_jj| exactly (a_ii = a_jj = 1, a_ij = -0.08) is
+    weak under the strict '>'; -0.2 is strong."""
+    n = 12
+    ptr, col, val = [0], [], []
+    for i in range(n):
+        for j in (i - 1, i, i + 1):
+            if 0 <= j < n:
+                col.append(j)
+                if j == i:
+                    val.append(1.0)
+                else:
+                    val.append(-0.08 if min(i, j) % 2 == 0 else -0.2)
+        ptr.append(len(col))
+    ptr, col, val = np.array(ptr, np.int32), np.array(col, np.int32), np.array(val)
+    assert (-0.08) * (-0.08) == 0.08 * 0.08 * abs(1.0 * 1.0)
+    H = O.Hierarchy(ptr, col, val, O.Params(coarse_enough=2, max_levels=2))
+    lv = H.level(0)
+    rows = np.repeat(np.arange(n), np.diff(ptr))
+    expect = ((val == -0.2) & (col != rows)).astype(np.uint8)
+    assert np.array_equal(lv.strong, expect)
