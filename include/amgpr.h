@@ -201,7 +201,9 @@ enum {
     AMG_PROF_DOT = 12,         /* CG: r.z */
     AMG_PROF_COARSE = 13,      /* coarsest solve (dense inverse times vector) */
     AMG_PROF_EMPTY = 14,       /* an empty event pair in the same stream or graph: the timing overhead */
-    AMG_PROF_NSLOTS = 15
+    AMG_PROF_GALERKIN = 15,    /* numeric Galerkin product of every level (one pair per level) */
+    AMG_PROF_SMOOTHERS = 16,   /* smoother diagonals of the coarse levels (one pair per level) */
+    AMG_PROF_NSLOTS = 17
 };
 amg_status amg_profile(amg_ctx *ctx, int32_t enable);
 amg_status amg_profile_read(amg_ctx *ctx, int32_t slot, double *total_ms, int64_t *launches);
@@ -254,6 +256,19 @@ amg_status amg_stokes_values(int32_t N, const double *d_rho, const double *d_mu,
 amg_status amg_poisson_grad_theta(int32_t dim, int32_t N, int32_t dirichlet_top, const double *d_rho,
                                   const double *d_u, const double *d_lam, double *d_grad,
                                   void *cuda_stream);
+/* The same two calls with the per-cell log-density theta = log rho as input
+ * (device, n doubles): each kernel forms rho = exp(theta) itself, so a
+ * differentiable solve over theta does all of its arithmetic in the library.
+ * amg_poisson_values_log: the values of amg_poisson_values for rho = exp(theta).
+ * amg_poisson_grad_log: dL/dtheta per cell, as amg_poisson_grad_theta for
+ * rho = exp(theta), with the face terms -(lam_c - lam_j)(u_c - u_j) chained
+ * through dk_f/dtheta_c = -2 rho_c / (rho_c + rho_j)^2 and the Dirichlet term
+ * (-lam_c u_c)(-2 / rho_c).  Both asynchronous on cuda_stream; AMG_ERR_ARG on
+ * a bad size or a null pointer. */
+amg_status amg_poisson_values_log(int32_t dim, int32_t N, int32_t dirichlet_top, const double *d_theta,
+                                  const int32_t *d_ptr, double *d_val, void *cuda_stream);
+amg_status amg_poisson_grad_log(int32_t dim, int32_t N, int32_t dirichlet_top, const double *d_theta,
+                                const double *d_u, const double *d_lam, double *d_grad, void *cuda_stream);
 
 /* Allocation-free variant of amg_poisson_pattern (no counterpart in the
  * paper).  It exists for callers that must not allocate device memory at

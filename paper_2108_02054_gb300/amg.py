@@ -35,10 +35,11 @@ EXPORTS = [
     "amg_step", "amg_solve", "amg_apply_vcycle", "amg_step_solve_host", "amg_num_levels", "amg_level_sizes",
     "amg_export_csr", "amg_export_level_vec", "amg_export_coarse_lu", "amg_poisson_nnz", "amg_poisson_pattern",
     "amg_poisson_values", "amg_poisson_grad_theta", "amg_profile", "amg_profile_read", "amg_kernel_launches",
-    "amg_poisson_pattern_noalloc", "amg_levelset_values", "amg_stokes_values",
+    "amg_poisson_pattern_noalloc", "amg_levelset_values", "amg_stokes_values", "amg_poisson_values_log",
+    "amg_poisson_grad_log",
 ]
 PROF_SLOTS = ["cg_spmv", "smooth0_l0", "sweep_l0", "restrict_l0", "prolong_l0", "ap_l0", "rap_l0", "ingest", "lu",
-              "inv", "cg_update", "cg_p", "dot", "coarse", "empty"]
+              "inv", "cg_update", "cg_p", "dot", "coarse", "empty", "galerkin", "smoothers"]
 
 
 class amg_params(ctypes.Structure):
@@ -104,6 +105,8 @@ def lib():
                 "amg_poisson_pattern_noalloc": (_i32, [_i32, _i32, _vp, _vp, _vp]),
                 "amg_levelset_values": (_i32, [_i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp]),
                 "amg_stokes_values": (_i32, [_i32, _vp, _vp, _vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp]),
+                "amg_poisson_values_log": (_i32, [_i32, _i32, _i32, _vp, _vp, _vp, _vp]),
+                "amg_poisson_grad_log": (_i32, [_i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -316,6 +319,17 @@ def poisson_values(dim: int, N: int, rho, ptr, dirichlet_top: bool = True, out=N
     return val
 
 
+def poisson_values_log(dim: int, N: int, theta, ptr, dirichlet_top: bool = True, out=None, stream=None):
+    """poisson_values for rho = exp(theta), the exponential taken in the kernel."""
+    import torch
+    val = out if out is not None else torch.empty(poisson_nnz(dim, N), dtype=torch.float64, device="cuda")
+    st = lib().amg_poisson_values_log(dim, N, int(dirichlet_top), _dptr(theta), _dptr(ptr), _dptr(val),
+                                      _vp(_stream(stream)))
+    if st != AMG_OK:
+        raise AmgError(st, "amg_poisson_values_log failed")
+    return val
+
+
 def levelset_values(dim: int, N: int, fx, fy, fz, ptr, out=None, stream=None):
     """Device values of the upwind convection-diffusion (level-set) matrix on
     the pattern from poisson_pattern; fx, fy, fz are the face velocities (fz
@@ -358,4 +372,15 @@ def poisson_grad_theta(dim: int, N: int, rho, u, lam, dirichlet_top: bool = True
                                       _vp(_stream(stream)))
     if st != AMG_OK:
         raise AmgError(st, "amg_poisson_grad_theta failed")
+    return g
+
+
+def poisson_grad_log(dim: int, N: int, theta, u, lam, dirichlet_top: bool = True, stream=None):
+    """dL/dtheta per cell for rho = exp(theta) (the exponential taken in the kernel)."""
+    import torch
+    g = torch.empty_like(u)
+    st = lib().amg_poisson_grad_log(dim, N, int(dirichlet_top), _dptr(theta), _dptr(u), _dptr(lam), _dptr(g),
+                                    _vp(_stream(stream)))
+    if st != AMG_OK:
+        raise AmgError(st, "amg_poisson_grad_log failed")
     return g

@@ -128,12 +128,15 @@ struct ProfScope {
             prof_record(b, c->s);
         }
     }
-    ~ProfScope() {
+    // end the timed span now (the destructor then does nothing)
+    void close() {
         if (!b) return;
         cudaEvent_t e = prof_event(c);
         prof_record(e, c->s);
         c->prof.rec[slot].push_back({b, e});
+        b = nullptr;
     }
+    ~ProfScope() { close(); }
 };
 
 #define CK(call)                                                                            \
@@ -379,6 +382,7 @@ amg_status numeric_rebuild(amg_ctx *ctx, const double *d_val, bool galerkin) {
     for (int l = 0; l + 1 < ctx->nlev; ++l) {
         Level &L = ctx->lev[l];
         Level &C = ctx->lev[l + 1];
+        ProfScope pg_(ctx, AMG_PROF_GALERKIN, galerkin);
         if (galerkin && L.gather_ready) {
             if (mx) {
                 { ProfScope ps_(ctx, AMG_PROF_AP_L0, l == 0); launch_gather_apply<float>(L.nnzAP, L.g1_ptr, L.g1_idx, L.g1_wf, L.A_valf, L.AP_valf, ctx->s); }
@@ -396,7 +400,9 @@ amg_status numeric_rebuild(amg_ctx *ctx, const double *d_val, bool galerkin) {
                 { ProfScope ps_(ctx, AMG_PROF_RAP_L0, l == 0); launch_rap_numeric_f64(L, C.A_ptr, C.A_val, ctx->s); }
             }
         }
+        pg_.close();
         if (l + 1 < ctx->nlev - 1) {
+            ProfScope psm_(ctx, AMG_PROF_SMOOTHERS);
             if (mx) launch_smoother_f32(C.n, C.A_ptr, C.A_valf, C.dia, p.smoother, p.jacobi_omega, C.mf, ctx->s);
             else launch_smoother_f64(C.n, C.A_ptr, C.A_val, C.dia, p.smoother, p.jacobi_omega, C.m, ctx->s);
         }
@@ -1605,9 +1611,17 @@ amg_status amg_poisson_pattern(int32_t dim, int32_t N, int32_t *d_ptr, int32_t *
     int32_t *len = nullptr;
     int64_t *tmp = nullptr;
     int *st = nullptr;
+    // on a failed allocation the ones already made are released before returning
     if (cudaMallocAsync(&len, sizeof(int32_t) * (size_t)n, s) != cudaSuccess) return AMG_ERR_OOM;
-    if (cudaMallocAsync(&tmp, sizeof(int64_t) * (size_t)scan_tmp_elems(n), s) != cudaSuccess) return AMG_ERR_OOM;
-    if (cudaMallocAsync(&st, sizeof(int), s) != cudaSuccess) return AMG_ERR_OOM;
+    if (cudaMallocAsync(&tmp, sizeof(int64_t) * (size_t)scan_tmp_elems(n), s) != cudaSuccess) {
+        cudaFreeAsync(len, s);
+        return AMG_ERR_OOM;
+    }
+    if (cudaMallocAsync(&st, sizeof(int), s) != cudaSuccess) {
+        cudaFreeAsync(len, s);
+        cudaFreeAsync(tmp, s);
+        return AMG_ERR_OOM;
+    }
     cudaMemsetAsync(st, 0, sizeof(int), s);
     launch_poisson_rowlen(dim, N, len, s);
     scan_counts(len, d_ptr, n, st, tmp, s);
@@ -1623,7 +1637,15 @@ amg_status amg_poisson_values(int32_t dim, int32_t N, int32_t dirichlet_top, con
                               const int32_t *d_ptr, double *d_val, void *cuda_stream) {
     if ((dim != 2 && dim != 3) || N < 1 || !d_rho || !d_ptr || !d_val) return AMG_ERR_ARG;
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    launch_poisson_vals(dim, N, dirichlet_top, d_rho, d_ptr, d_val, s);
+    launch_poisson_vals(dim, N, dirichlet_top, d_rho, 0, d_ptr, d_val, s);
+    if (cudaGetLastError() != cudaSuccess) return AMG_ERR_CUDA;
+    return AMG_OK;
+}
+
+amg_status amg_poisson_values_log(int32_t dim, int32_t N, int32_t dirichlet_top, const double *d_theta,
+                                  const int32_t *d_ptr, double *d_val, void *cuda_stream) {
+    if ((dim != 2 && dim != 3) || N < 1 || !d_theta || !d_ptr || !d_val) return AMG_ERR_ARG;
+    launch_poisson_vals(dim, N, dirichlet_top, d_theta, 1, d_ptr, d_val, (cudaStream_t)cuda_stream);
     if (cudaGetLastError() != cudaSuccess) return AMG_ERR_CUDA;
     return AMG_OK;
 }
@@ -1652,7 +1674,15 @@ amg_status amg_stokes_values(int32_t N, const double *d_rho, const double *d_mu,
 amg_status amg_poisson_grad_theta(int32_t dim, int32_t N, int32_t dirichlet_top, const double *d_rho,
                                   const double *d_u, const double *d_lam, double *d_grad, void *cuda_stream) {
     if ((dim != 2 && dim != 3) || N < 1 || !d_rho || !d_u || !d_lam || !d_grad) return AMG_ERR_ARG;
-    launch_poisson_grad(dim, N, dirichlet_top, d_rho, d_u, d_lam, d_grad, (cudaStream_t)cuda_stream);
+    launch_poisson_grad(dim, N, dirichlet_top, d_rho, 0, d_u, d_lam, d_grad, (cudaStream_t)cuda_stream);
+    if (cudaGetLastError() != cudaSuccess) return AMG_ERR_CUDA;
+    return AMG_OK;
+}
+
+amg_status amg_poisson_grad_log(int32_t dim, int32_t N, int32_t dirichlet_top, const double *d_theta,
+                                const double *d_u, const double *d_lam, double *d_grad, void *cuda_stream) {
+    if ((dim != 2 && dim != 3) || N < 1 || !d_theta || !d_u || !d_lam || !d_grad) return AMG_ERR_ARG;
+    launch_poisson_grad(dim, N, dirichlet_top, d_theta, 1, d_u, d_lam, d_grad, (cudaStream_t)cuda_stream);
     if (cudaGetLastError() != cudaSuccess) return AMG_ERR_CUDA;
     return AMG_OK;
 }

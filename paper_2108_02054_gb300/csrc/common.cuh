@@ -129,9 +129,10 @@ int64_t scan_tmp_elems(int64_t n);
 
 void launch_poisson_rowlen(int dim, int N, int32_t *len, cudaStream_t s);
 void launch_poisson_cols(int dim, int N, const int32_t *ptr, int32_t *col, cudaStream_t s);
-void launch_poisson_vals(int dim, int N, int top, const double *rho, const int32_t *ptr, double *val,
+// logd != 0: rho holds the log-density theta and every density is exp(theta)
+void launch_poisson_vals(int dim, int N, int top, const double *rho, int logd, const int32_t *ptr, double *val,
                          cudaStream_t s);
-void launch_poisson_grad(int dim, int N, int top, const double *rho, const double *u, const double *lam,
+void launch_poisson_grad(int dim, int N, int top, const double *rho, int logd, const double *u, const double *lam,
                          double *grad, cudaStream_t s);
 void launch_levelset_vals(int dim, int N, const double *fx, const double *fy, const double *fz, const int32_t *ptr,
                           double *val, cudaStream_t s);

@@ -160,10 +160,17 @@ __global__ void k_poisson_cols(int dim, int N, int64_t n, const int32_t *__restr
     if (dim == 3 && z < N - 1) col[p++] = (int32_t)(c + s3);
 }
 
+// per-cell density: the input itself, or exp of it when the input is the
+// log-density theta = log rho
+__device__ __forceinline__ double cell_rho(const double *__restrict__ in, int64_t c, int logd) {
+    const double x = in[c];
+    return logd ? exp(x) : x;
+}
+
 // Row c: neighbours in ascending index order, off-diagonal -2/(rho_c + rho_nb),
 // diagonal = running sum of the face coefficients in that order, then the
 // ghost-cell Dirichlet term 2/rho_c on the top face.
-__global__ void k_poisson_vals(int dim, int N, int64_t n, int top, const double *__restrict__ rho,
+__global__ void k_poisson_vals(int dim, int N, int64_t n, int top, const double *__restrict__ rho, int logd,
                                const int32_t *__restrict__ ptr, double *__restrict__ val) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n) return;
@@ -179,12 +186,12 @@ __global__ void k_poisson_vals(int dim, int N, int64_t n, int top, const double 
     if (x < N - 1) nb[nnb++] = c + 1;
     if (y < N - 1) nb[nnb++] = c + s2;
     if (dim == 3 && z < N - 1) nb[nnb++] = c + s3;
-    const double rc = rho[c];
+    const double rc = cell_rho(rho, c, logd);
     double diag = 0.0;
     int32_t p = ptr[c], dpos = p;
     for (int t = 0; t < nnb; ++t, ++p) {
         if (nb[t] < 0) { dpos = p; continue; }
-        double k = 2.0 / (rc + rho[nb[t]]);
+        double k = 2.0 / (rc + cell_rho(rho, nb[t], logd));
         diag = diag + k;
         val[p] = -k;
     }
@@ -233,7 +240,7 @@ __global__ void k_levelset_vals(int dim, int N, int64_t n, const double *__restr
 // of cell c contributes dL/dk_f * dk_f/dtheta_c with
 // dL/dk_f = -(lam_c - lam_j)(u_c - u_j), dk_f/dtheta_c = -2 rho_c/(rho_c + rho_j)^2;
 // the Dirichlet term contributes (-lam_c u_c) * (-2/rho_c).
-__global__ void k_poisson_grad(int dim, int N, int64_t n, int top, const double *__restrict__ rho,
+__global__ void k_poisson_grad(int dim, int N, int64_t n, int top, const double *__restrict__ rho, int logd,
                                const double *__restrict__ u, const double *__restrict__ lam,
                                double *__restrict__ grad) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -249,12 +256,12 @@ __global__ void k_poisson_grad(int dim, int N, int64_t n, int top, const double 
     if (x < N - 1) nb[nnb++] = c + 1;
     if (y < N - 1) nb[nnb++] = c + s2;
     if (dim == 3 && z < N - 1) nb[nnb++] = c + s3;
-    const double rc = rho[c], lc = lam[c], uc = u[c];
+    const double rc = cell_rho(rho, c, logd), lc = lam[c], uc = u[c];
     double g = 0.0;
     for (int t = 0; t < nnb; ++t) {
         int64_t j = nb[t];
         double dLdk = -(lc - lam[j]) * (uc - u[j]);
-        double s = rc + rho[j];
+        double s = rc + cell_rho(rho, j, logd);
         g += dLdk * (-2.0 * rc / (s * s));
     }
     int is_top = dim == 2 ? (y == N - 1) : (z == N - 1);
@@ -823,17 +830,17 @@ void launch_poisson_cols(int dim, int N, const int32_t *ptr, int32_t *col, cudaS
     count_launch();
     k_poisson_cols<<<nblocks(n), kThreads, 0, s>>>(dim, N, n, ptr, col);
 }
-void launch_poisson_vals(int dim, int N, int top, const double *rho, const int32_t *ptr, double *val,
+void launch_poisson_vals(int dim, int N, int top, const double *rho, int logd, const int32_t *ptr, double *val,
                          cudaStream_t s) {
     int64_t n = dim == 2 ? (int64_t)N * N : (int64_t)N * N * N;
     count_launch();
-    k_poisson_vals<<<nblocks(n), kThreads, 0, s>>>(dim, N, n, top, rho, ptr, val);
+    k_poisson_vals<<<nblocks(n), kThreads, 0, s>>>(dim, N, n, top, rho, logd, ptr, val);
 }
-void launch_poisson_grad(int dim, int N, int top, const double *rho, const double *u, const double *lam,
+void launch_poisson_grad(int dim, int N, int top, const double *rho, int logd, const double *u, const double *lam,
                          double *grad, cudaStream_t s) {
     int64_t n = dim == 2 ? (int64_t)N * N : (int64_t)N * N * N;
     count_launch();
-    k_poisson_grad<<<nblocks(n), kThreads, 0, s>>>(dim, N, n, top, rho, u, lam, grad);
+    k_poisson_grad<<<nblocks(n), kThreads, 0, s>>>(dim, N, n, top, rho, logd, u, lam, grad);
 }
 
 void launch_levelset_vals(int dim, int N, const double *fx, const double *fy, const double *fz, const int32_t *ptr,

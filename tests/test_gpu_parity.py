@@ -125,12 +125,20 @@ def test_irregular_random_matrix():
 
 
 # ------------------------------------------------------------------ partial rebuild (Alg. 4)
+FLAVOURS = {"sa_spai0": {}, "plain_jacobi": {"smoothed": 0, "smoother": 1}}
+
+
+@pytest.mark.parametrize("flavour", sorted(FLAVOURS))
 @pytest.mark.parametrize("dim,N,T", [(2, 32, 10), (3, 40, 20)])
-def test_partial_rebuild_matches_oracle(dim, N, T):
+def test_partial_rebuild_matches_oracle(dim, N, T, flavour):
+    """Alg. 4 for smoothed aggregation + SPAI0 and for the paper's own flavour
+    (plain aggregation + damped Jacobi, Sec. 4): hierarchy structure, P/R and
+    every coarse value bit for bit, smoothers to rounding, LU pivots."""
+    kw = FLAVOURS[flavour]
     ptr, col, v0 = gpu_problem(dim, N, 0, T)
-    G = B.AMG()
+    G = B.AMG(**kw)
     G.full_setup(ptr, col, v0)
-    H = O.Hierarchy(*oracle_problem(dim, N, 0, T))
+    H = O.Hierarchy(*oracle_problem(dim, N, 0, T), O.Params(**kw))
     for k in (1, T // 2, T - 1):
         _, _, vk = gpu_problem(dim, N, k, T)
         G.partial_rebuild(vk)
@@ -156,8 +164,43 @@ def test_partial_rebuild_on_unchanged_values_equals_full_setup_bitwise():
 
 
 # ------------------------------------------------------------------ V-cycle and solve
+def vcycle_envelope(H, r, npre=1, npost=1):
+    """Alg. 2 with every operator and vector replaced by its absolute value
+    (|A_l|, |m_l|, |R_l|, |P_l|, |A_L^-1|): an entrywise upper envelope of every
+    term the V-cycle sums, so the rounding difference of two implementations
+    of the same V-cycle is at most a small multiple of eps times this."""
+    lv = [H.level(l) for l in range(H.nlevels)]
+    nL = lv[-1].A.nrows
+    invL = np.abs(np.linalg.inv(lv[-1].A.dense()))
+
+    def cycle(l, f):
+        if l == len(lv) - 1:
+            return invL @ f
+        L = lv[l]
+        A = abs(_sp(L.A.ptr, L.A.col, L.A.val, L.A.nrows))
+        m = np.abs(L.m)
+        u = m * f
+        for _ in range(npre - 1):
+            u = u + m * (f + A @ u)
+        fc = abs(_sp(L.R.ptr, L.R.col, L.R.val, L.A.nrows)) @ (f + A @ u)
+        u = u + abs(_sp(L.P.ptr, L.P.col, L.P.val, L.nagg)) @ cycle(l + 1, fc)
+        for _ in range(npost):
+            u = u + m * (f + A @ u)
+        return u
+
+    assert nL == lv[-1].A.ncols
+    return cycle(0, np.abs(r))
+
+
 @pytest.mark.parametrize("dim,N", [(2, 32), (3, 48), (3, 64)])
 def test_vcycle_matches_oracle(dim, N):
+    """Entry by entry.  Every level's operators are bit-identical to the
+    oracle's and every sweep keeps its order; the one difference is the
+    coarsest solve (the GPU multiplies by the explicit inverse, the oracle
+    substitutes through the LU factors).  Each entry must agree within 1e-9 of
+    the V-cycle's absolute-term envelope, about 1e7 eps: room for the
+    conditioning of the coarsest solve, far below what a wrong sweep on any
+    row would leave."""
     ptr, col, v = gpu_problem(dim, N, 1, 5)
     G = B.AMG()
     G.full_setup(ptr, col, v)
@@ -165,7 +208,11 @@ def test_vcycle_matches_oracle(dim, N):
     r = np.random.default_rng(5).normal(size=N ** dim)
     z = G.vcycle(torch.tensor(r, device="cuda")).cpu().numpy()
     zo = H.vcycle(r)
-    assert np.linalg.norm(z - zo) <= 1e-10 * np.linalg.norm(zo)
+    env = vcycle_envelope(H, r)
+    ratio = np.abs(z - zo) / env
+    print(f"V-cycle {dim}D N={N}: max |z - z_o| / envelope = {ratio.max():.2e}, "
+          f"envelope / |z_o| median {np.median(env / np.maximum(np.abs(zo), 1e-300)):.1f}")
+    assert np.all(np.abs(z - zo) <= 1e-9 * env), ratio.max()
 
 
 @pytest.mark.parametrize("dim,N,T", [(2, 32, 10), (3, 64, 50)])
@@ -199,15 +246,17 @@ def test_single_level_and_zero_rhs():
 
 
 # ------------------------------------------------------------------ time-step modes
+@pytest.mark.parametrize("flavour", sorted(FLAVOURS))
 @pytest.mark.parametrize("mode", [B.MODE_PARTIAL, B.MODE_FULL_REBUILD, B.MODE_FULL_REUSE] if torch.cuda.is_available() else [0])
-def test_time_series_modes_match_oracle(mode):
+def test_time_series_modes_match_oracle(mode, flavour):
+    kw = FLAVOURS[flavour]
     dim, N, T = 2, 32, 10
     ptr, col, _ = gpu_problem(dim, N, 0, T)
     f = I.rhs(N * N)
     ft = torch.tensor(f, device="cuda")
-    G = B.AMG(mode=mode)
+    G = B.AMG(mode=mode, **kw)
     vals = [oracle_problem(dim, N, k, T)[2] for k in range(T)]
-    recs = O.run_time_steps(*oracle_problem(dim, N, 0, T)[:2], vals, f, mode)
+    recs = O.run_time_steps(*oracle_problem(dim, N, 0, T)[:2], vals, f, mode, params=O.Params(**kw))
     for k in range(T):
         _, _, vk = gpu_problem(dim, N, k, T)
         si = G.step(vk, ptr, col)
@@ -249,13 +298,22 @@ def test_mixed_precision_reaches_fp64_tolerance(dim, N, T):
             _, _, vk = gpu_problem(dim, N, k, T)
             G.partial_rebuild(vk)
             H.rebuild(oracle_problem(dim, N, k, T)[2])
-        # structure identical to the FP64 oracle; values within FP32 accuracy
+        # structure identical to the FP64 oracle; every coarse value within FP32
+        # accuracy of the oracle's, entry by entry, against the nested
+        # absolute-term bound B_0 = |A|, B_{l+1} = |P_l|^T B_l |P_l|
         compare_hierarchy(G, H, values_bitwise=False, check_values=False)
+        optr, ocol, ovk = oracle_problem(dim, N, k, T)
+        Bd = abs(_sp(optr, ocol, ovk, N ** dim))
+        worst = 0.0
         for l in range(1, G.nlevels):
+            lo, o = H.level(l - 1), H.level(l)
+            Pa = abs(_sp(lo.P.ptr, lo.P.col, lo.P.val, lo.nagg))
+            Bd = (Pa.T @ Bd @ Pa).tocsr()
+            bd = np.asarray(Bd[np.repeat(np.arange(o.A.nrows), np.diff(o.A.ptr)), o.A.col]).ravel()
             gv = G.export_level(l)["A"][2]
-            ov = H.level(l).A.val
-            scale = np.abs(ov).max()
-            assert np.max(np.abs(gv - ov)) <= 1e-5 * scale
+            assert np.all(np.abs(gv - o.A.val) <= 1e-6 * bd), l
+            worst = max(worst, float(np.max(np.abs(gv - o.A.val) / bd)))
+        print(f"mixed {dim}D N={N} step {k}: max coarse |a - a_o| / bound = {worst:.2e}")
         u, info = G.solve(ft, 1e-8)
         uo, it, rr, st = H.pcg(f, 1e-8)
         assert info.status == 0 and info.rel_resid <= 1e-8
