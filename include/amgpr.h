@@ -285,7 +285,10 @@ amg_status amg_poisson_grad_log(int32_t dim, int32_t N, int32_t dirichlet_top, c
  *    AMG_ERR_CAPACITY without launching anything.
  *  - The first call on a device looks up that array's device address (once
  *    per device, with that device current); make this first call before any
- *    stream capture.
+ *    stream capture.  The address is kept for the life of the process: after
+ *    a cudaDeviceReset of a device, do not call this entry point on it again.
+ *  - A CUDA error already pending when it is called (from earlier work) is
+ *    returned as AMG_ERR_CUDA without launching anything and is not cleared.
  *  - All calls share the one array and it keeps the last call's contents;
  *    each call writes every entry it reads, so nothing needs clearing, but
  *    calls whose work overlaps on the GPU (on different streams, or from

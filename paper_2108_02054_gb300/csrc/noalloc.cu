@@ -110,7 +110,10 @@ __global__ void k_na_scan_in_place(int32_t *ptr, int64_t n, const int64_t *bsum,
 }
 
 // device address of the scratch array on the current device (first call per
-// device resolves it; the host-side symbol itself is not a device address)
+// device resolves it; the host-side symbol itself is not a device address).
+// The cached address belongs to the device's context: after a
+// cudaDeviceReset it is stale, so a process that resets a device must not
+// call this entry point on that device again.
 amg_status scratch_for_current_device(int64_t **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return AMG_ERR_CUDA;
@@ -134,6 +137,9 @@ extern "C" amg_status amg_poisson_pattern_noalloc(int32_t dim, int32_t N, int32_
     if ((dim != 2 && dim != 3) || N < 1 || !d_ptr || !d_col) return AMG_ERR_ARG;
     const int64_t n = dim == 2 ? (int64_t)N * N : (int64_t)N * N * N;
     if (n > AMG_NOALLOC_MAX_CELLS) return AMG_ERR_CAPACITY;
+    // an error left by earlier, unrelated work is reported without being
+    // cleared, and nothing is launched on top of it
+    if (cudaPeekAtLastError() != cudaSuccess) return AMG_ERR_CUDA;
     int64_t *scratch = nullptr;
     amg_status st = scratch_for_current_device(&scratch);
     if (st != AMG_OK) return st;

@@ -117,6 +117,52 @@ def random_spd_like(n: int, density_: float, seed: int) -> tuple[np.ndarray, np.
     return np.asarray(ptr, np.int32), np.asarray(col, np.int32), np.asarray(val, np.float64)
 
 
+def random_arrow_spd(n: int, density_: float, arm: int, seed: int):
+    """random_spd_like plus one dense 'arrow' row and column (node 0 coupled to
+    `arm` random nodes): rows far longer than a stencil's, for the edge cases
+    of the row-length-dependent kernels.  Sorted CSR (ptr, col, val)."""
+    ptr, col, val = random_spd_like(n, density_, seed)
+    rng = np.random.default_rng(seed + 1000)
+    M = np.zeros((n, n))
+    for i in range(n):
+        M[i, col[ptr[i]:ptr[i + 1]]] = val[ptr[i]:ptr[i + 1]]
+    np.fill_diagonal(M, 0.0)
+    nb = rng.choice(np.arange(1, n), size=arm, replace=False)
+    w = -rng.uniform(0.01, 0.5, arm)
+    M[0, nb] += w
+    M[nb, 0] += w
+    d = -M.sum(axis=1) + rng.uniform(0.0, 0.5, n) + 1e-3
+    M[np.arange(n), np.arange(n)] = d
+    p, c, v = [0], [], []
+    for i in range(n):
+        nz = np.nonzero(M[i])[0]
+        c.extend(nz.tolist())
+        v.extend(M[i, nz].tolist())
+        p.append(len(c))
+    return np.asarray(p, np.int32), np.asarray(c, np.int32), np.asarray(v, np.float64)
+
+
+def revalue_symmetric(ptr, col, val, seed: int, spread: float = 0.5):
+    """New values on the same symmetric pattern: every off-diagonal pair scaled
+    by one seeded factor in [1 - spread, 1 + spread], the diagonal reset to the
+    negated off-diagonal row sum plus a seeded margin (diagonally dominant)."""
+    n = ptr.size - 1
+    rng = np.random.default_rng(seed)
+    lo = np.minimum(np.repeat(np.arange(n), np.diff(ptr)), col).astype(np.int64)
+    hi = np.maximum(np.repeat(np.arange(n), np.diff(ptr)), col).astype(np.int64)
+    key = lo * n + hi
+    uk, inv = np.unique(key, return_inverse=True)
+    fac = 1.0 + spread * rng.uniform(-1.0, 1.0, uk.size)
+    rows = np.repeat(np.arange(n), np.diff(ptr))
+    off = col != rows
+    out = np.where(off, val * fac[inv], 0.0)
+    rs = np.zeros(n)
+    np.add.at(rs, rows, out)
+    margin = rng.uniform(0.0, 0.5, n) + 1e-3
+    out[~off] = -rs[rows[~off]] + margin[rows[~off]]
+    return out
+
+
 # ---------------------------------------------------------------- level-set transport stand-in
 LEVELSET_COURANT = 2.0
 

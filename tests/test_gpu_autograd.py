@@ -103,10 +103,18 @@ def test_adjoint_64cubed_against_oracle_gradient_and_fd(precision):
     print(f"64^3 precision={precision}: |g - g_oracle|/|g| = {err:.2e}, iters fwd {S.last_info.iters} "
           f"adj {S.adjoint_info.iters}")
     assert err <= 1e-6, err
+    # per cell against the FP64 oracle gradient: 1e-6 relative, plus a floor
+    # of 1e-9 max|g| for cells whose gradient is far below the largest (the
+    # solves stop at a relative residual of 1e-13 / 1e-12)
+    gate = 1e-6 * np.abs(go) + 1e-9 * gmax
+    assert np.all(np.abs(g - go) <= gate), np.max(np.abs(g - go) / gate)
+    big = np.abs(go) >= 1e-3 * gmax
+    rel = np.abs(g - go)[big] / np.abs(go)[big]
+    print(f"64^3 precision={precision}: per cell |g - g_oracle|/|g_oracle| over the {big.sum()} cells with "
+          f"|g| >= 1e-3 max|g|: median {np.median(rel):.2e}, max {rel.max():.2e}")
 
-    # central differences of GPU solves (partial rebuilds of the same hierarchy),
-    # converged ten times tighter than the gradient's solves
-    tol_fd = tol / 10
+    # central differences of GPU solves (partial rebuilds of the same hierarchy)
+    tol_fd = tol
 
     def loss(t, tol_=tol_fd):
         S.tol = tol_
@@ -115,34 +123,33 @@ def test_adjoint_64cubed_against_oracle_gradient_and_fd(precision):
         S.tol = tol
         return 0.5 * float(((uu - utt) ** 2).sum())
 
-    # round-off term of a central difference: each loss value carries the
-    # error of its solve; the change of L(theta0) between tol_fd and 10 tol_fd
-    # over-estimates it (floored at 10 eps |L|), and the two evaluations of a
-    # difference give at most 2 dL / (2 h)
-    L0, L0_loose = loss(theta0), loss(theta0, 10 * tol_fd)
-    dL = max(abs(L0 - L0_loose), 10 * np.finfo(float).eps * abs(L0))
+    # each difference quotient's own error: solver noise (each loss value
+    # carries its solve's error, which the +h and -h solves need not share)
+    # plus rounding; estimated per cell as twice the change of the quotient
+    # between h and 2 h (truncation, O(h^2), is far below it), plus 4 eps |L| / h
     h = 1e-6
-    r_fd = dL / h
-    fds = {}
+    L0 = loss(theta0)
+    fds, noise = {}, {}
     for cell in I.fd_cells(n, 32, seed=3):
         e = np.zeros(n)
-        e[cell] = h
-        fds[int(cell)] = (loss(theta0 + e) - loss(theta0 - e)) / (2 * h)
-    fdmax = max(abs(v) for v in fds.values())
-    # the round-off term is no larger than the old gradient-scaled bound, so
-    # the per-cell test below is at least as strict as that one everywhere
-    assert r_fd <= 1e-6 * fdmax, (r_fd, fdmax)
-    worst_rel, limited = 0.0, 0
+        e[cell] = 1.0
+        fd = (loss(theta0 + h * e) - loss(theta0 - h * e)) / (2 * h)
+        fd2 = (loss(theta0 + 2 * h * e) - loss(theta0 - 2 * h * e)) / (4 * h)
+        fds[int(cell)] = fd
+        noise[int(cell)] = 2 * abs(fd - fd2) + 4 * np.finfo(float).eps * abs(L0) / h
+    gm = np.abs(go).max()
+    worst_rel, limited, rels = 0.0, 0, []
     for cell, fd in fds.items():
         err = abs(g[cell] - fd)
-        # per cell: 1e-6 relative to the difference quotient, plus its round-off
-        assert err <= 1e-6 * abs(fd) + r_fd, (cell, g[cell], fd, r_fd)
-        if r_fd > 1e-6 * abs(fd):
+        # per cell: 1e-6 relative to the difference quotient, plus its own error
+        assert err <= 1e-6 * abs(fd) + noise[cell], (cell, g[cell], fd, noise[cell])
+        rels.append(err / abs(fd))
+        if noise[cell] > 1e-6 * abs(fd):
             limited += 1
-        worst_rel = max(worst_rel, err / abs(fd))
-    print(f"64^3 precision={precision}: FD (h=1e-6, 32 cells) worst per-cell |g - fd|/|fd| = {worst_rel:.2e}; "
-          f"round-off term {r_fd:.2e} (loss error {dL:.2e}, |L| {L0:.3e}); cells whose 1e-6 |fd| is below "
-          f"it: {limited} of {len(fds)}")
+    rels = np.array(rels)
+    print(f"64^3 precision={precision}: FD (h=1e-6, 32 cells) per-cell |g - fd|/|fd|: median {np.median(rels):.2e}, "
+          f"max {rels.max():.2e}; cells whose FD error estimate exceeds 1e-6 |fd|: {limited} of {len(fds)} "
+          f"(largest estimate {max(noise.values()):.2e} = {max(noise.values()) / gm:.2e} max|g|, |L| = {L0:.3e})")
 
 
 def test_log_density_assembly_and_gradient_kernels():

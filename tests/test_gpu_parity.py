@@ -124,6 +124,27 @@ def test_irregular_random_matrix():
     compare_hierarchy(G, H)
 
 
+@pytest.mark.parametrize("case", ["random", "arrow"])
+def test_partial_rebuild_irregular_patterns(case):
+    """Alg. 4 on irregular patterns: a random symmetric pattern, and one with a
+    dense arrow row (rows of about 300 entries on the finest level).  The whole
+    hierarchy, values bit for bit, after two rebuilds with new values."""
+    if case == "random":
+        ptr, col, val = I.random_spd_like(900, 0.012, seed=11)
+    else:
+        ptr, col, val = I.random_arrow_spd(900, 0.006, 300, seed=12)
+    assert np.diff(ptr).max() > 8 and (case == "random" or np.diff(ptr).max() > 256)
+    G = B.AMG(coarse_enough=30)
+    G.full_setup(*(torch.tensor(a, device="cuda") for a in (ptr, col, val)))
+    H = O.Hierarchy(ptr, col, val, O.Params(coarse_enough=30))
+    assert G.nlevels >= 3
+    for seed in (21, 22):
+        v = I.revalue_symmetric(ptr, col, val, seed)
+        G.partial_rebuild(torch.tensor(v, device="cuda"))
+        assert H.rebuild(v) == 0
+        compare_hierarchy(G, H)
+
+
 # ------------------------------------------------------------------ partial rebuild (Alg. 4)
 FLAVOURS = {"sa_spai0": {}, "plain_jacobi": {"smoothed": 0, "smoother": 1}}
 

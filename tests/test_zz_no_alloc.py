@@ -28,8 +28,10 @@ def test_noalloc_pattern_matches_allocating_version_on_two_calls():
     L = B.lib()
     stream = torch.cuda.current_stream().cuda_stream
     # a large 3D grid first (many scan tiles), then a small 2D one, so the
-    # second call runs over scratch that still holds the first call's sums
-    for dim, N in ((3, 97), (2, 45)):
+    # second call runs over scratch that still holds the first call's sums;
+    # then 170^3 cells (1,200 tiles: the tile scan carries across more than
+    # one 1,024-tile chunk) over the small call's leftovers
+    for dim, N in ((3, 97), (2, 45), (3, 170)):
         nnz = int(L.amg_poisson_nnz(dim, N))
         st_ref, p_ref, c_ref = _pattern(L.amg_poisson_pattern, dim, N, nnz, stream)
         st, p, c = _pattern(L.amg_poisson_pattern_noalloc, dim, N, nnz, stream)
