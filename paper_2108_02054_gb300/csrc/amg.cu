@@ -873,7 +873,10 @@ void enqueue_cg_iter_a(amg_ctx *ctx, double *u, int use_h, cudaGraphConditionalH
     }
     {
         ProfScope ps_(ctx, AMG_PROF_CG_UPDATE, true);
-        launch_cg_update_ur(n, cg, ctx->cg_p, ctx->cg_q, u, ctx->cg_r, ctx->part_rr, use_h, hb, cg_smooth0(ctx), ctx->s);
+        // flexible variant: r_new.z_old in the same pass (z still holds the last z)
+        const bool flex = mixed(ctx);
+        launch_cg_update_ur(n, cg, ctx->cg_p, ctx->cg_q, u, ctx->cg_r, ctx->part_rr, flex ? ctx->cg_z : nullptr,
+                            ctx->part_rzo, use_h, hb, cg_smooth0(ctx), ctx->s);
     }
 }
 
@@ -884,15 +887,15 @@ void enqueue_cg_iter_b(amg_ctx *ctx, const double *f, double *u) {
     CgState *cg = ctx->cg;
     launch_true_residual(n, ctx->fine_ptr, ctx->fine_col, ctx->A_sys, f, u, ctx->cg_t, ctx->part_tt,
                          cg, 0, ctx->s);
-    launch_replace_r(n, cg, ctx->cg_t, ctx->cg_r, cg_smooth0(ctx), ctx->s);
+    launch_replace_r(n, cg, ctx->cg_t, ctx->cg_r, mixed(ctx) ? ctx->cg_z : nullptr, ctx->part_rzo, cg_smooth0(ctx),
+                     ctx->s);
 }
 
 // C: z = B r with the partials of r.z, beta and p (and the loop condition)
 void enqueue_cg_iter_c(amg_ctx *ctx, int use_h, cudaGraphConditionalHandle h) {
     const int32_t n = ctx->n;
-    const bool flex = mixed(ctx);
     CgState *cg = ctx->cg;
-    if (flex) launch_dot(n, ctx->cg_r, ctx->cg_z, ctx->part_rzo, &cg->done, cg, 2, ctx->s);
+    // (the flexible variant's r_new.z_old was formed by the u / r update)
     vcycle(ctx, ctx->cg_r, ctx->cg_z, &cg->done, ctx->part_rz, cg_u0(ctx));
     {
         ProfScope ps_(ctx, AMG_PROF_CG_P, true);

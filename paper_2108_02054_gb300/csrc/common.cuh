@@ -255,12 +255,15 @@ void launch_dot(int32_t n, const double *x, const double *y, double *partial, co
 void launch_cg_set_rz_p(int32_t n, const double *z, double *p, CgState *cg, cudaStream_t s);
 void launch_spmv_dot(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *p,
                      double *q, double *partial, CgState *cg, cudaStream_t s);
+// zo (flexible variant, else null): the previous z; r_new.z_old goes to cg->rzo
+// through the partials part_zo
 void launch_cg_update_ur(int32_t n, CgState *cg, const double *p, const double *q, double *u, double *r,
-                         double *partial, int use_h, cudaGraphConditionalHandle hb, const Smooth0Out &z0,
-                         cudaStream_t s);
+                         double *partial, const double *zo, double *part_zo, int use_h, cudaGraphConditionalHandle hb,
+                         const Smooth0Out &z0, cudaStream_t s);
 void launch_true_residual(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *f,
                           const double *u, double *t, double *partial, CgState *cg, int force, cudaStream_t s);
-void launch_replace_r(int32_t n, const CgState *cg, const double *t, double *r, const Smooth0Out &z0, cudaStream_t s);
+void launch_replace_r(int32_t n, CgState *cg, const double *t, double *r, const double *zo, double *part_zo,
+                      const Smooth0Out &z0, cudaStream_t s);
 void launch_cg_update_p(int32_t n, CgState *cg, const double *z, double *p, int use_h, cudaGraphConditionalHandle h,
                         cudaStream_t s);
 

@@ -941,6 +941,26 @@ __device__ bool cg_reduce(double d, double *partial, unsigned *counter, double *
     return true;
 }
 
+// two sums at once, each with the arithmetic (and so the result) of cg_reduce
+__device__ bool cg_reduce2(double d1, double d2, double *part1, double *part2, unsigned *counter, double *t1,
+                           double *t2) {
+    d1 = block_sum(d1);
+    d2 = block_sum(d2);
+    if (threadIdx.x == 0) {
+        part1[blockIdx.x] = d1;
+        part2[blockIdx.x] = d2;
+    }
+    if (!cg_last_block(counter)) return false;
+    const double a = cg_sum_partials(part1, gridDim.x);
+    const double b = cg_sum_partials(part2, gridDim.x);
+    if (threadIdx.x == 0) {
+        *t1 = a;
+        *t2 = b;
+        *counter = 0u;
+    }
+    return true;
+}
+
 __device__ __forceinline__ void put_smooth0(const Smooth0Out &z0, int32_t i, double ri) {
     if (z0.u) z0.u[i] = z0.m[i] * ri;
     if (z0.uf) z0.uf[i] = z0.mf[i] * (float)ri;
@@ -1032,26 +1052,33 @@ __global__ void k_spmv_dot(int32_t n, const int32_t *__restrict__ ptr, const int
 }
 
 // u += alpha p, r -= alpha q; the last block checks the recurrence residual
-// (graph: opens the IF branch hb of the true-residual check when it meets tol)
+// (graph: opens the IF branch hb of the true-residual check when it meets tol).
+// With zo (the flexible variant), also r_new.z_old into cg->rzo, summed as the
+// separate dot kernel would sum it (same grid, same order).
 __global__ void k_cg_update_ur(int32_t n, CgState *cg, const double *__restrict__ p, const double *__restrict__ q,
                                double *__restrict__ u, double *__restrict__ r, double *__restrict__ partial,
-                               int use_h, cudaGraphConditionalHandle hb, Smooth0Out z0) {
+                               const double *__restrict__ zo, double *__restrict__ part_zo, int use_h,
+                               cudaGraphConditionalHandle hb, Smooth0Out z0) {
     pdl_wait();
     if (cg->done) {
         if (use_h && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(hb, 0u);
         return;
     }
     const double alpha = cg->alpha;
-    double s = 0.0;
+    double s = 0.0, so = 0.0;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         u[i] = fma(alpha, p[i], u[i]);
         const double ri = fma(-alpha, q[i], r[i]);
         r[i] = ri;
         put_smooth0(z0, i, ri);
         s = fma(ri, ri, s);
+        if (zo) so = fma(ri, zo[i], so);
     }
-    double rr = 0.0;
-    if (cg_reduce(s, partial, &cg->ctr[CG_CTR_RR], &rr) && threadIdx.x == 0) {
+    double rr = 0.0, rzo = 0.0;
+    const bool last = zo ? cg_reduce2(s, so, partial, part_zo, &cg->ctr[CG_CTR_RR], &rr, &rzo)
+                         : cg_reduce(s, partial, &cg->ctr[CG_CTR_RR], &rr);
+    if (last && threadIdx.x == 0) {
+        if (zo) cg->rzo = rzo;
         cg->iter += 1;
         cg->rr = rr;
         cg->res = sqrt(rr) / cg->nf;
@@ -1099,15 +1126,22 @@ __global__ void k_true_residual(int32_t n, const int32_t *__restrict__ ptr, cons
     }
 }
 
-__global__ void k_replace_r(int32_t n, const CgState *cg, const double *__restrict__ t, double *__restrict__ r,
-                            Smooth0Out z0) {
+// r = t when the true residual replaces the recurrence residual; with zo (the
+// flexible variant), r_new.z_old is formed again from the new r
+__global__ void k_replace_r(int32_t n, CgState *cg, const double *__restrict__ t, double *__restrict__ r,
+                            const double *__restrict__ zo, double *__restrict__ part_zo, Smooth0Out z0) {
     pdl_wait();
     if (cg->done || !cg->copy_r) return;
+    double so = 0.0;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double ti = t[i];
         r[i] = ti;
         put_smooth0(z0, i, ti);
+        if (zo) so = fma(ti, zo[i], so);
     }
+    if (!zo) return;
+    double rzo = 0.0;
+    if (cg_reduce(so, part_zo, &cg->ctr[CG_CTR_RZO], &rzo) && threadIdx.x == 0) cg->rzo = rzo;
 }
 
 // beta = (r.z_new - r.z_old) / (r.z)_old, the flexible form (r.z_old = 0 for
@@ -1673,19 +1707,21 @@ void launch_spmv_dot(int32_t n, const int32_t *ptr, const int32_t *col, const do
     launch_pdl(k_spmv_dot, cg_blocks(n), cg_threads(n), 0, s, n, ptr, col, val, p, q, partial, cg);
 }
 void launch_cg_update_ur(int32_t n, CgState *cg, const double *p, const double *q, double *u, double *r,
-                         double *partial, int use_h, cudaGraphConditionalHandle hb, const Smooth0Out &z0,
-                         cudaStream_t s) {
+                         double *partial, const double *zo, double *part_zo, int use_h, cudaGraphConditionalHandle hb,
+                         const Smooth0Out &z0, cudaStream_t s) {
     count_launch();
-    launch_pdl(k_cg_update_ur, cg_blocks(n), cg_threads(n), 0, s, n, cg, p, q, u, r, partial, use_h, hb, z0);
+    launch_pdl(k_cg_update_ur, cg_blocks(n), cg_threads(n), 0, s, n, cg, p, q, u, r, partial, zo, part_zo, use_h, hb,
+               z0);
 }
 void launch_true_residual(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *f,
                           const double *u, double *t, double *partial, CgState *cg, int force, cudaStream_t s) {
     count_launch();
     launch_pdl(k_true_residual, cg_blocks(n), cg_threads(n), 0, s, n, ptr, col, val, f, u, t, partial, cg, force);
 }
-void launch_replace_r(int32_t n, const CgState *cg, const double *t, double *r, const Smooth0Out &z0, cudaStream_t s) {
+void launch_replace_r(int32_t n, CgState *cg, const double *t, double *r, const double *zo, double *part_zo,
+                      const Smooth0Out &z0, cudaStream_t s) {
     count_launch();
-    launch_pdl(k_replace_r, cg_blocks(n), cg_threads(n), 0, s, n, cg, t, r, z0);
+    launch_pdl(k_replace_r, cg_blocks(n), cg_threads(n), 0, s, n, cg, t, r, zo, part_zo, z0);
 }
 void launch_cg_update_p(int32_t n, CgState *cg, const double *z, double *p, int use_h, cudaGraphConditionalHandle h,
                         cudaStream_t s) {
