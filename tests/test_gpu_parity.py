@@ -526,3 +526,22 @@ def test_cluster_lu_for_mid_size_coarsest_level(N, ce, nL):
     u, info = G.solve(torch.tensor(f, device="cuda"), 1e-8)
     _, it, _, st = H.pcg(f, 1e-8)
     assert info.status == 0 and st == O.OK and abs(info.iters - it) <= 1
+
+
+@pytest.mark.parametrize("n", [1, 5, 33, 87, 150, 151, 161, 300])
+def test_coarse_inverse_every_size_class(n):
+    """On a one-level hierarchy the V-cycle is the coarsest solve, the explicit
+    inverse (from the LU factors) times r: against a dense solve of the same
+    diagonally dominant matrix, for the register kernel (n <= 150), the
+    shared-memory kernel (n <= 160) and the column-major kernel above."""
+    rng = np.random.default_rng(2000 + n)
+    M = rng.uniform(-1.0, 1.0, (n, n))
+    M[np.arange(n), np.arange(n)] = np.abs(M).sum(axis=1) + 1.0
+    ptr, col, val = (torch.tensor(a, device="cuda") for a in _dense_csr(M))
+    G = B.AMG(coarse_enough=n)
+    G.full_setup(ptr, col, val)
+    assert G.nlevels == 1
+    r = rng.normal(size=n)
+    z = G.vcycle(torch.tensor(r, device="cuda")).cpu().numpy()
+    ref = np.linalg.solve(M, r)
+    assert np.linalg.norm(z - ref) <= 1e-12 * np.linalg.norm(ref) * np.linalg.cond(M)
