@@ -185,19 +185,21 @@ def level_sizes(G):
     return out
 
 
-def algorithmic_bytes(slot, lv, s):
-    """Bytes one launch must move at minimum (int32 indices, s-byte values of
-    the hierarchy; CG vectors are FP64).  lv: level sizes list."""
+def algorithmic_bytes(slot, lv, s, cb=4):
+    """Bytes one launch must move at minimum (s-byte values of the hierarchy,
+    CG vectors FP64, int32 row pointers and P / R indices; the finest
+    matrix's column index takes cb bytes an entry: 4 as int32, 1 when the
+    pattern is stored as one-byte offsets).  lv: level sizes list."""
     L0 = lv[0]
     n, nnz = L0["n"], L0["nnz"]
     nc, nnzP = L0["nagg"], L0["nnzP"]
     nnzc = lv[1]["nnz"] if len(lv) > 1 else 0
     if slot == "cg_spmv":      # q = A p, p.q: ptr, col, val(f64), p, q
-        return 4 * (n + 1) + 12 * nnz + 16 * n
+        return 4 * (n + 1) + (cb + 8) * nnz + 16 * n
     if slot == "smooth0_l0":   # r = f - A u0 (u0 = m o f, written with f): ptr, col, val, u0, f(f64), r
-        return 4 * (n + 1) + nnz * (4 + s) + n * s + 8 * n + n * s
+        return 4 * (n + 1) + nnz * (cb + s) + n * s + 8 * n + n * s
     if slot == "sweep_l0":     # z = u + m (f - A u): ptr, col, val, m, f(f64), u, z(f64)
-        return 4 * (n + 1) + nnz * (4 + s) + n * s + 8 * n + n * s + 8 * n
+        return 4 * (n + 1) + nnz * (cb + s) + n * s + 8 * n + n * s + 8 * n
     if slot == "restrict_l0":  # f_c = R r
         return 4 * (nc + 1) + nnzP * (4 + s) + n * s + nc * s
     if slot == "prolong_l0":   # u += P u_c
@@ -283,7 +285,7 @@ def run_mode(B, torch, w, mode, ptr, col, vals, f, warm_idx, timed_idx, flush, p
         "max_rel_resid": max(i.rel_resid for _, i in infos),
         "rebuilds": sum(s.rebuilt for s, _ in infos),
         "all_converged": all(i.status == 0 for _, i in infos),
-        "wall_s": wall, "launches": launches, "levels": level_sizes(G),
+        "wall_s": wall, "launches": launches, "levels": level_sizes(G), "col_bytes": G.pattern_info()[0],
     }
     return G, res, prof, u
 
@@ -547,7 +549,7 @@ def run_ours(args):
         per_raw = ms / cnt
         # solve kernels are timed inside a graph: the empty pair's time is the timing overhead
         per = per_raw - overhead_ms if name in GRAPH_TIMED and per_raw > 2 * overhead_ms else per_raw
-        by = algorithmic_bytes(name, part["levels"], s)
+        by = algorithmic_bytes(name, part["levels"], s, part["col_bytes"])
         fl = algorithmic_flops(name, part["levels"]) if s == 8 else None
         kernels[name] = {"ms_total_per_step": per * cnt / len(timed_idx), "launches_per_step": cnt / len(timed_idx),
                          "us_per_launch": per * 1e3, "us_per_launch_timed": per_raw * 1e3,
@@ -561,6 +563,7 @@ def run_ours(args):
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(ach / peak, 4), "peak_source": peak_kind, "traffic": traffic,
                 "algorithmic_bytes_per_launch": kernels[dom]["algorithmic_bytes"],
+                "column_index_bytes": part["col_bytes"],
                 "event_pair_overhead_us": round(overhead_ms * 1e3, 3)}
     if kernels[dom]["achieved_fp64_tflops"]:
         # FP64 hierarchy: the same kernel against the FP64 pipe (derived peak); the

@@ -169,6 +169,15 @@ amg_status amg_export_csr(amg_ctx *ctx, int32_t level, int32_t which, int32_t *d
  * diagonal (FP64); any pointer may be NULL. */
 amg_status amg_export_level_vec(amg_ctx *ctx, int32_t level, int32_t *d_agg, uint8_t *d_strong,
                                 double *d_m);
+/* How the finest level's matrix kernels read column indices (no counterpart
+ * in the paper; an implementation detail reported for the roofline).  When
+ * the pattern's rows use at most 256 distinct column offsets (column - row,
+ * as a stencil's do), each entry's column is stored as one byte naming its
+ * offset in a table: *col_bytes = 1 and *noffsets = the table's size.
+ * Otherwise the int32 columns are read: *col_bytes = 4, *noffsets = 0.
+ * Values and arithmetic are the same either way.  AMG_ERR_STATE before a
+ * pattern is set. */
+amg_status amg_pattern_info(const amg_ctx *ctx, int32_t *col_bytes, int32_t *noffsets);
 /* Coarsest LU factors (n_L x n_L row-major, FP64) and pivots. */
 amg_status amg_export_coarse_lu(amg_ctx *ctx, double *d_lu, int32_t *d_piv);
 

@@ -36,7 +36,7 @@ EXPORTS = [
     "amg_export_csr", "amg_export_level_vec", "amg_export_coarse_lu", "amg_poisson_nnz", "amg_poisson_pattern",
     "amg_poisson_values", "amg_poisson_grad_theta", "amg_profile", "amg_profile_read", "amg_kernel_launches",
     "amg_poisson_pattern_noalloc", "amg_levelset_values", "amg_stokes_values", "amg_poisson_values_log",
-    "amg_poisson_grad_log",
+    "amg_poisson_grad_log", "amg_pattern_info",
 ]
 PROF_SLOTS = ["cg_spmv", "smooth0_l0", "sweep_l0", "restrict_l0", "prolong_l0", "ap_l0", "rap_l0", "ingest", "lu",
               "inv", "cg_update", "cg_p", "dot", "coarse", "empty", "galerkin", "smoothers"]
@@ -235,6 +235,12 @@ class AMG:
         s = (ctypes.c_int64 * 6)()
         self._check(lib().amg_level_sizes(self._h, level, s))
         return [int(x) for x in s]
+
+    def pattern_info(self):
+        """(column bytes per entry the finest level's kernels read, offset-table size)."""
+        cb, no = _i32(), _i32()
+        self._check(lib().amg_pattern_info(self._h, ctypes.byref(cb), ctypes.byref(no)))
+        return cb.value, no.value
 
     def export_level(self, level: int) -> dict:
         """Copies of A, P, R (CSR), aggregates, strong flags and smoother on the host."""

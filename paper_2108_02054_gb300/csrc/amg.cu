@@ -45,6 +45,11 @@ struct amg_ctx {
     // fine pattern (persistent)
     int32_t n = 0, nnz = 0;
     int32_t *fine_ptr = nullptr, *fine_col = nullptr;
+    // its compressed columns, when its rows use at most kMaxColOffsets offsets
+    uint8_t *fine_cidx = nullptr;
+    int32_t *fine_coff = nullptr, *coff_table = nullptr;
+    int *coff_count = nullptr;
+    int fine_ncoff = 0;
     // hierarchy
     int nlev = 0;
     Level lev[kMaxLevels];
@@ -420,6 +425,11 @@ amg_status full_setup_impl(amg_ctx *ctx, const double *d_val) {
     F.nnz = nnz;
     F.A_ptr = ctx->fine_ptr;
     F.A_col = ctx->fine_col;
+    if (ctx->fine_ncoff) {
+        F.A_cidx = ctx->fine_cidx;
+        F.A_coff = ctx->fine_coff;
+        F.A_ncoff = ctx->fine_ncoff;
+    }
     TRY(alloc(ctx, &F.A_val, (size_t)nnz));
     TRY(alloc(ctx, &F.dia, (size_t)n));
     launch_check_pattern(n, F.A_ptr, F.A_col, F.dia, ctx->d_st, ctx->s);
@@ -583,6 +593,10 @@ amg_status ensure_persistent(amg_ctx *ctx, int32_t n, int32_t nnz) {
     if (ctx->fine_ptr && ctx->n == n && ctx->nnz == nnz) return AMG_OK;
     for (void *q : ctx->persist) cudaFreeAsync(q, ctx->s);
     ctx->persist.clear();
+    ctx->fine_cidx = nullptr;
+    ctx->fine_coff = ctx->coff_table = nullptr;
+    ctx->coff_count = nullptr;
+    ctx->fine_ncoff = 0;
     ctx->n = n;
     ctx->nnz = nnz;
     TRY(alloc(ctx, &ctx->fine_ptr, (size_t)n + 1, true));
@@ -623,13 +637,55 @@ amg_status ensure_persistent(amg_ctx *ctx, int32_t n, int32_t nnz) {
     return AMG_OK;
 }
 
+// The fine pattern's compressed columns: one byte per entry naming its offset
+// column - row in a table of at most kMaxColOffsets, when the rows use no
+// more (a stencil's handful); otherwise fine_ncoff = 0 and the kernels read
+// the int32 columns.  The values and every operation stay the same; the
+// finest level's matrix kernels then move 3 bytes less per entry.
+amg_status compress_pattern(amg_ctx *ctx) {
+    ctx->fine_ncoff = 0;
+    if (blockmode(ctx) || ctx->n >= (1 << 30)) return AMG_OK;
+    if (!ctx->fine_cidx) {
+        TRY(alloc(ctx, &ctx->fine_cidx, (size_t)ctx->nnz, true));
+        TRY(alloc(ctx, &ctx->fine_coff, (size_t)kMaxColOffsets, true));
+        TRY(alloc(ctx, &ctx->coff_table, (size_t)kColOffsetSlots, true));
+        TRY(alloc(ctx, &ctx->coff_count, 1, true));
+    }
+    CK(cudaMemsetAsync(ctx->coff_table, 0x80, sizeof(int32_t) * kColOffsetSlots, ctx->s));
+    CK(cudaMemsetAsync(ctx->coff_count, 0, sizeof(int), ctx->s));
+    launch_col_offsets_collect(ctx->n, ctx->fine_ptr, ctx->fine_col, ctx->coff_table, ctx->coff_count, ctx->s);
+    std::vector<int32_t> tab(kColOffsetSlots);
+    int cnt = 0;
+    CK(cudaMemcpyAsync(tab.data(), ctx->coff_table, sizeof(int32_t) * kColOffsetSlots, cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaMemcpyAsync(&cnt, ctx->coff_count, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    if (cnt < 1 || cnt > kMaxColOffsets) return AMG_OK;
+    std::vector<int32_t> off;
+    for (int32_t v : tab)
+        if (v != kColOffsetEmpty) off.push_back(v);
+    if ((int)off.size() != cnt) return AMG_OK;
+    std::sort(off.begin(), off.end());
+    CK(cudaMemcpyAsync(ctx->fine_coff, off.data(), sizeof(int32_t) * off.size(), cudaMemcpyHostToDevice, ctx->s));
+    TRY(reset_status(ctx));
+    launch_col_offsets_encode(ctx->n, ctx->fine_ptr, ctx->fine_col, ctx->fine_coff, cnt, ctx->fine_cidx, ctx->d_st,
+                              ctx->s);
+    TRY(check_device(ctx, "column compression"));
+    ctx->fine_ncoff = cnt;
+    return AMG_OK;
+}
+
 amg_status set_pattern(amg_ctx *ctx, int32_t n, int32_t nnz, const int32_t *d_ptr, const int32_t *d_col) {
     if (n <= 0 || nnz < n || !d_ptr || !d_col) return set_err(ctx, AMG_ERR_ARG, "bad matrix size or null pattern");
     TRY(ensure_persistent(ctx, n, nnz));
     if (d_ptr == ctx->fine_ptr && d_col == ctx->fine_col) return AMG_OK;
     CK(cudaMemcpyAsync(ctx->fine_ptr, d_ptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToDevice, ctx->s));
     CK(cudaMemcpyAsync(ctx->fine_col, d_col, sizeof(int32_t) * (size_t)nnz, cudaMemcpyDeviceToDevice, ctx->s));
-    return AMG_OK;
+    return compress_pattern(ctx);
+}
+
+// the finest level's column indices as the matrix kernels read them
+ColIdx fine_cols(const amg_ctx *ctx) {
+    return ColIdx{ctx->fine_col, ctx->fine_ncoff ? ctx->fine_cidx : nullptr, ctx->fine_coff, ctx->fine_ncoff};
 }
 
 void update_sys(amg_ctx *ctx) {
@@ -868,7 +924,7 @@ void enqueue_cg_iter_a(amg_ctx *ctx, double *u, int use_h, cudaGraphConditionalH
     CgState *cg = ctx->cg;
     {
         ProfScope ps_(ctx, AMG_PROF_CG_SPMV, true);
-        launch_spmv_dot(n, ctx->fine_ptr, ctx->fine_col, ctx->A_sys, ctx->cg_p, ctx->cg_q, ctx->part_pq, cg,
+        launch_spmv_dot(n, ctx->fine_ptr, fine_cols(ctx), ctx->A_sys, ctx->cg_p, ctx->cg_q, ctx->part_pq, cg,
                         ctx->s);
     }
     {
@@ -885,7 +941,7 @@ void enqueue_cg_iter_a(amg_ctx *ctx, double *u, int use_h, cudaGraphConditionalH
 void enqueue_cg_iter_b(amg_ctx *ctx, const double *f, double *u) {
     const int32_t n = ctx->n;
     CgState *cg = ctx->cg;
-    launch_true_residual(n, ctx->fine_ptr, ctx->fine_col, ctx->A_sys, f, u, ctx->cg_t, ctx->part_tt,
+    launch_true_residual(n, ctx->fine_ptr, fine_cols(ctx), ctx->A_sys, f, u, ctx->cg_t, ctx->part_tt,
                          cg, 0, ctx->s);
     launch_replace_r(n, cg, ctx->cg_t, ctx->cg_r, mixed(ctx) ? ctx->cg_z : nullptr, ctx->part_rzo, cg_smooth0(ctx),
                      ctx->s);
@@ -906,7 +962,7 @@ void enqueue_cg_iter_c(amg_ctx *ctx, int use_h, cudaGraphConditionalHandle h) {
 // the true relative residual of the returned iterate
 void enqueue_cg_epilogue(amg_ctx *ctx, const double *f, double *u) {
     const int32_t n = ctx->n;
-    launch_true_residual(n, ctx->fine_ptr, ctx->fine_col, ctx->A_sys, f, u, ctx->cg_t, ctx->part_tt,
+    launch_true_residual(n, ctx->fine_ptr, fine_cols(ctx), ctx->A_sys, f, u, ctx->cg_t, ctx->part_tt,
                          ctx->cg, 1,
                          ctx->s);
 }
@@ -1553,6 +1609,14 @@ amg_status amg_export_level_vec(amg_ctx *ctx, int32_t level, int32_t *d_agg, uin
         else CK(cudaMemcpyAsync(d_m, L.m, sizeof(double) * (size_t)L.n, cudaMemcpyDeviceToDevice, ctx->s));
     }
     CK(cudaStreamSynchronize(ctx->s));
+    return AMG_OK;
+}
+
+amg_status amg_pattern_info(const amg_ctx *ctx, int32_t *col_bytes, int32_t *noffsets) {
+    if (!ctx || !col_bytes || !noffsets) return AMG_ERR_ARG;
+    if (!ctx->fine_ptr) return AMG_ERR_STATE;
+    *col_bytes = ctx->fine_ncoff ? 1 : 4;
+    *noffsets = ctx->fine_ncoff;
     return AMG_OK;
 }
 

@@ -47,6 +47,18 @@ struct BiState {
     int iter, maxiter, done, status, replacements, half, need_true, copy_r, skip, pad;
 };
 
+// Column indices of a matrix: plain int32 (col), or, for a pattern whose
+// rows use at most kMaxColOffsets distinct column offsets (column - row, as
+// in a stencil), one byte per entry (cidx) naming its offset in a table
+// (off, noff entries): column = row + off[cidx[p]].
+constexpr int kMaxColOffsets = 256;
+struct ColIdx {
+    const int32_t *col = nullptr;
+    const uint8_t *cidx = nullptr;
+    const int32_t *off = nullptr;
+    int noff = 0;
+};
+
 template <class V>
 struct VecSet {
     V *u = nullptr, *f = nullptr, *r = nullptr, *t = nullptr;
@@ -55,6 +67,11 @@ struct VecSet {
 struct Level {
     int32_t n = 0, nnz = 0;
     int32_t *A_ptr = nullptr, *A_col = nullptr, *dia = nullptr;
+    // the finest level's compressed columns (when its pattern allows them)
+    const uint8_t *A_cidx = nullptr;
+    const int32_t *A_coff = nullptr;
+    int A_ncoff = 0;
+    ColIdx cols() const { return ColIdx{A_col, A_cidx, A_coff, A_ncoff}; }
     double *A_val = nullptr;   // FP64 values (level 0: the hierarchy's copy of the fine matrix)
     float *A_valf = nullptr;   // FP32 values (mixed precision)
     // transfer operators (absent on the coarsest level)
@@ -253,14 +270,25 @@ void launch_cg_init(int32_t n, const double *f, double *u, double *r, double *pa
 void launch_dot(int32_t n, const double *x, const double *y, double *partial, const int *skip, CgState *cg, int target,
                 cudaStream_t s);
 void launch_cg_set_rz_p(int32_t n, const double *z, double *p, CgState *cg, cudaStream_t s);
-void launch_spmv_dot(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *p,
+void launch_spmv_dot(int32_t n, const int32_t *ptr, const ColIdx &col, const double *val, const double *p,
                      double *q, double *partial, CgState *cg, cudaStream_t s);
+// the compressed form of a pattern: collect the distinct offsets column - row
+// into an open-addressed table of kColOffsetSlots ints (empty:
+// kColOffsetEmpty, the int of four 0x80 bytes; *count the distinct keys,
+// capped), then encode every entry's offset index against the sorted table
+// off (noff entries)
+constexpr int kColOffsetSlots = 1024;
+constexpr int32_t kColOffsetEmpty = (int32_t)0x80808080u;
+void launch_col_offsets_collect(int32_t n, const int32_t *ptr, const int32_t *col, int32_t *table, int *count,
+                                cudaStream_t s);
+void launch_col_offsets_encode(int32_t n, const int32_t *ptr, const int32_t *col, const int32_t *off, int noff,
+                               uint8_t *cidx, int *st, cudaStream_t s);
 // zo (flexible variant, else null): the previous z; r_new.z_old goes to cg->rzo
 // through the partials part_zo
 void launch_cg_update_ur(int32_t n, CgState *cg, const double *p, const double *q, double *u, double *r,
                          double *partial, const double *zo, double *part_zo, int use_h, cudaGraphConditionalHandle hb,
                          const Smooth0Out &z0, cudaStream_t s);
-void launch_true_residual(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *f,
+void launch_true_residual(int32_t n, const int32_t *ptr, const ColIdx &col, const double *val, const double *f,
                           const double *u, double *t, double *partial, CgState *cg, int force, cudaStream_t s);
 void launch_replace_r(int32_t n, CgState *cg, const double *t, double *r, const double *zo, double *part_zo,
                       const Smooth0Out &z0, cudaStream_t s);

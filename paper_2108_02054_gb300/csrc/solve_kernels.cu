@@ -27,6 +27,15 @@ inline int nblocks(int64_t n, int t = kThreads) {
 
 __device__ __forceinline__ bool skipped(const int *skip) { return skip != nullptr && *skip != 0; }
 
+// A compressed column pattern (ColIdx with cidx set) names entry p's column
+// as row + off[cidx[p]].  Its offset table goes to shared memory once per
+// block; every thread of the block must call this.
+__device__ __forceinline__ void stage_col_offsets(const ColIdx &ci, int32_t *s_off) {
+    if (!ci.cidx) return;
+    for (int t = threadIdx.x; t < ci.noff; t += blockDim.x) s_off[t] = ci.off[t];
+    __syncthreads();
+}
+
 // ------------------------------------------------------------------ Galerkin, FP64
 constexpr int kApThreads = 128;
 constexpr int kApSlots = 32;
@@ -721,6 +730,69 @@ k_lu_inverse_t(int32_t n, const double *__restrict__ luT, const int32_t *__restr
     for (int32_t r = lane; r < n; r += 32) inv[(int64_t)r * n + j] = x[r];
 }
 
+// ---- compressed columns of a pattern (built once per pattern)
+// The distinct offsets column - row go into an open-addressed table; the
+// lanes of a warp that share an offset insert it once (match), and a key is
+// probed before any compare-and-swap, so almost every entry costs one read.
+// Empty slots hold kColOffsetEmpty (the host fills the table with bytes 0x80;
+// no offset of a pattern with fewer than 2^30 rows equals it).  *count counts
+// the distinct keys; past kMaxColOffsets the pattern stays uncompressed and
+// inserting stops.
+__global__ void k_col_offsets_collect(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                                      int32_t *table, int *count) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = i < n;
+    const int32_t b = active ? ptr[i] : 0, len = active ? ptr[i + 1] - b : 0;
+    const int32_t lmax = (int32_t)__reduce_max_sync(0xffffffffu, (unsigned)len);
+    for (int32_t k = 0; k < lmax; ++k) {
+        const bool has = k < len;
+        const int32_t d = has ? col[b + k] - i : 0;
+        const unsigned grp = __match_any_sync(0xffffffffu, has ? d : kColOffsetEmpty);
+        const bool leader = has && (__ffs(grp) - 1) == (int)(threadIdx.x & 31);
+        if (leader && *(volatile int *)count <= kMaxColOffsets) {
+            unsigned h = ((unsigned)d * 2654435761u) & (kColOffsetSlots - 1);
+            for (int probe = 0; probe < kColOffsetSlots; ++probe) {
+                const int32_t cur = ((volatile int32_t *)table)[h];
+                if (cur == d) break;
+                if (cur == kColOffsetEmpty) {
+                    const int32_t old = atomicCAS(table + h, kColOffsetEmpty, d);
+                    if (old == kColOffsetEmpty) {
+                        atomicAdd(count, 1);
+                        break;
+                    }
+                    if (old == d) break;
+                }
+                h = (h + 1) & (kColOffsetSlots - 1);
+            }
+        }
+    }
+}
+
+// cidx[p] = position of column - row in the sorted table off (binary search
+// in shared memory); an offset missing from the table flags the status word
+__global__ void k_col_offsets_encode(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                                     const int32_t *__restrict__ off, int noff, uint8_t *__restrict__ cidx, int *st) {
+    __shared__ int32_t s_off[kMaxColOffsets];
+    for (int t = threadIdx.x; t < noff; t += blockDim.x) s_off[t] = off[t];
+    __syncthreads();
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int32_t p = ptr[i]; p < ptr[i + 1]; ++p) {
+        const int32_t d = col[p] - i;
+        int lo = 0, hi = noff - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (s_off[mid] < d) lo = mid + 1;
+            else hi = mid;
+        }
+        if (noff == 0 || s_off[lo] != d) {
+            atomicOr(st, DEV_ERR_STATE);
+            lo = 0;
+        }
+        cidx[p] = (uint8_t)lo;
+    }
+}
+
 // u = A_L^-1 f, one warp per row
 template <class TF, class TO>
 __global__ void k_coarse_solve(int32_t n, const double *__restrict__ inv, const TF *__restrict__ f,
@@ -749,18 +821,20 @@ __device__ __forceinline__ V group_sum(V s) {
 
 // zero-guess pre-smoothing fused with the residual: u = m o f, r = f - A u
 template <class V, class TF, int LPR>
-__global__ void k_smooth0_residual(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
+__global__ void k_smooth0_residual(int32_t n, const int32_t *__restrict__ ptr, ColIdx ci,
                                    const V *__restrict__ val, const V *__restrict__ m, const TF *__restrict__ f,
                                    V *__restrict__ u, V *__restrict__ r, const int *skip) {
+    __shared__ int32_t s_off[kMaxColOffsets];
     pdl_wait();
     if (skipped(skip)) return;
+    stage_col_offsets(ci, s_off);
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int32_t i = (int32_t)(gt / LPR);
     const int sub = (int)(gt % LPR);
     V s = 0;
     if (i < n)
         for (int32_t p = ptr[i] + sub; p < ptr[i + 1]; p += LPR) {
-            const int32_t j = col[p];
+            const int32_t j = ci.cidx ? i + s_off[ci.cidx[p]] : ci.col[p];
             s = fma(val[p], m[j] * (V)f[j], s);
         }
     s = group_sum<LPR>(s);
@@ -773,17 +847,20 @@ __global__ void k_smooth0_residual(int32_t n, const int32_t *__restrict__ ptr, c
 
 // u_out = u_in + m o (f - A u_in)
 template <class V, class TF, class TO, int LPR>
-__global__ void k_smooth_sweep(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
+__global__ void k_smooth_sweep(int32_t n, const int32_t *__restrict__ ptr, ColIdx ci,
                                const V *__restrict__ val, const V *__restrict__ m, const TF *__restrict__ f,
                                const V *__restrict__ u_in, TO *__restrict__ u_out, const int *skip) {
+    __shared__ int32_t s_off[kMaxColOffsets];
     pdl_wait();
     if (skipped(skip)) return;
+    stage_col_offsets(ci, s_off);
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int32_t i = (int32_t)(gt / LPR);
     const int sub = (int)(gt % LPR);
     V s = 0;
     if (i < n)
-        for (int32_t p = ptr[i] + sub; p < ptr[i + 1]; p += LPR) s = fma(val[p], u_in[col[p]], s);
+        for (int32_t p = ptr[i] + sub; p < ptr[i + 1]; p += LPR)
+            s = fma(val[p], u_in[ci.cidx ? i + s_off[ci.cidx[p]] : ci.col[p]], s);
     s = group_sum<LPR>(s);
     if (i < n && sub == 0) u_out[i] = (TO)fma(m[i], (V)f[i] - s, u_in[i]);
 }
@@ -793,12 +870,14 @@ __global__ void k_smooth_sweep(int32_t n, const int32_t *__restrict__ ptr, const
 __device__ double block_sum(double v);
 __device__ bool cg_reduce(double d, double *partial, unsigned *counter, double *total);
 template <class V, int LPR>
-__global__ void k_smooth_sweep_dot(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
+__global__ void k_smooth_sweep_dot(int32_t n, const int32_t *__restrict__ ptr, ColIdx ci,
                                    const V *__restrict__ val, const V *__restrict__ m, const double *__restrict__ f,
                                    const V *__restrict__ u_in, double *__restrict__ z, double *__restrict__ partial,
                                    CgState *cg, const int *skip) {
+    __shared__ int32_t s_off[kMaxColOffsets];
     pdl_wait();
     if (skipped(skip)) return;
+    stage_col_offsets(ci, s_off);
     const int64_t total = (int64_t)n * LPR;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     double d = 0.0;
@@ -808,7 +887,8 @@ __global__ void k_smooth_sweep_dot(int32_t n, const int32_t *__restrict__ ptr, c
         const int sub = (int)(gt % LPR);
         V s = 0;
         if (gt < total)
-            for (int32_t p = ptr[i] + sub; p < ptr[i + 1]; p += LPR) s = fma(val[p], u_in[col[p]], s);
+            for (int32_t p = ptr[i] + sub; p < ptr[i + 1]; p += LPR)
+                s = fma(val[p], u_in[ci.cidx ? i + s_off[ci.cidx[p]] : ci.col[p]], s);
         s = group_sum<LPR>(s);
         if (gt < total && sub == 0) {
             const double fi = f[i];
@@ -823,17 +903,20 @@ __global__ void k_smooth_sweep_dot(int32_t n, const int32_t *__restrict__ ptr, c
 }
 
 template <class V, class TF, int LPR>
-__global__ void k_residual(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
+__global__ void k_residual(int32_t n, const int32_t *__restrict__ ptr, ColIdx ci,
                            const V *__restrict__ val, const TF *__restrict__ f, const V *__restrict__ u,
                            V *__restrict__ r, const int *skip) {
+    __shared__ int32_t s_off[kMaxColOffsets];
     pdl_wait();
     if (skipped(skip)) return;
+    stage_col_offsets(ci, s_off);
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int32_t i = (int32_t)(gt / LPR);
     const int sub = (int)(gt % LPR);
     V s = 0;
     if (i < n)
-        for (int32_t p = ptr[i] + sub; p < ptr[i + 1]; p += LPR) s = fma(val[p], u[col[p]], s);
+        for (int32_t p = ptr[i] + sub; p < ptr[i + 1]; p += LPR)
+            s = fma(val[p], u[ci.cidx ? i + s_off[ci.cidx[p]] : ci.col[p]], s);
     s = group_sum<LPR>(s);
     if (i < n && sub == 0) r[i] = (V)f[i] - s;
 }
@@ -1024,17 +1107,22 @@ __global__ void k_cg_set_rz_p(int32_t n, const double *__restrict__ z, double *_
 }
 
 // q = A p; the last block forms p.q and alpha = r.z / p.q (breakdown: p.q <= 0)
-__global__ void k_spmv_dot(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
+__global__ void k_spmv_dot(int32_t n, const int32_t *__restrict__ ptr, ColIdx ci,
                            const double *__restrict__ val, const double *__restrict__ p, double *__restrict__ q,
                            double *__restrict__ partial, CgState *cg) {
+    __shared__ int32_t s_off[kMaxColOffsets];
     pdl_wait();
     if (cg->done) return;
+    stage_col_offsets(ci, s_off);
     // r.z of the previous iteration becomes current (read only by the last block)
     if (blockIdx.x == 0 && threadIdx.x == 0) cg->rz = cg->rz_next;
     double d = 0.0;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double s = 0.0;
-        for (int32_t e = ptr[i]; e < ptr[i + 1]; ++e) s = fma(val[e], p[col[e]], s);
+        if (ci.cidx)
+            for (int32_t e = ptr[i]; e < ptr[i + 1]; ++e) s = fma(val[e], p[i + s_off[ci.cidx[e]]], s);
+        else
+            for (int32_t e = ptr[i]; e < ptr[i + 1]; ++e) s = fma(val[e], p[ci.col[e]], s);
         q[i] = s;
         d = fma(p[i], s, d);
     }
@@ -1094,16 +1182,19 @@ __global__ void k_cg_update_ur(int32_t n, CgState *cg, const double *__restrict_
 // t = f - A u, the true residual, when the recurrence reports convergence; the
 // last block accepts convergence or schedules the replacement of r (twice at
 // most).  With force: unconditionally, the final relative residual.
-__global__ void k_true_residual(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
+__global__ void k_true_residual(int32_t n, const int32_t *__restrict__ ptr, ColIdx ci,
                                 const double *__restrict__ val, const double *__restrict__ f,
                                 const double *__restrict__ u, double *__restrict__ t, double *__restrict__ partial,
                                 CgState *cg, int force) {
+    __shared__ int32_t s_off[kMaxColOffsets];
     pdl_wait();
     if (!force && (cg->done || !cg->need_true)) return;
+    stage_col_offsets(ci, s_off);
     double d = 0.0;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double s = 0.0;
-        for (int32_t e = ptr[i]; e < ptr[i + 1]; ++e) s = fma(val[e], u[col[e]], s);
+        for (int32_t e = ptr[i]; e < ptr[i + 1]; ++e)
+            s = fma(val[e], u[ci.cidx ? i + s_off[ci.cidx[e]] : ci.col[e]], s);
         const double ti = f[i] - s;
         t[i] = ti;
         d = fma(ti, ti, d);
@@ -1579,7 +1670,7 @@ void launch_smooth0_residual(const Level &L, const V *val, const V *m, const TF 
                              cudaStream_t s) {
     count_launch();
     const unsigned g = (unsigned)nblocks((int64_t)L.n * L.lpr);
-    LPR_DISPATCH(L.lpr, (launch_pdl(k_smooth0_residual<V, TF, P_>, g, kThreads, 0, s, L.n, L.A_ptr, L.A_col, val, m, f, u,
+    LPR_DISPATCH(L.lpr, (launch_pdl(k_smooth0_residual<V, TF, P_>, g, kThreads, 0, s, L.n, L.A_ptr, L.cols(), val, m, f, u,
                                                                               r, skip)))
 }
 template <class V, class TF, class TO>
@@ -1587,7 +1678,7 @@ void launch_smooth_sweep(const Level &L, const V *val, const V *m, const TF *f, 
                          const int *skip, cudaStream_t s) {
     count_launch();
     const unsigned g = (unsigned)nblocks((int64_t)L.n * L.lpr);
-    LPR_DISPATCH(L.lpr, (launch_pdl(k_smooth_sweep<V, TF, TO, P_>, g, kThreads, 0, s, L.n, L.A_ptr, L.A_col, val, m, f,
+    LPR_DISPATCH(L.lpr, (launch_pdl(k_smooth_sweep<V, TF, TO, P_>, g, kThreads, 0, s, L.n, L.A_ptr, L.cols(), val, m, f,
                                                                               u_in, u_out, skip)))
 }
 template <class V>
@@ -1595,7 +1686,7 @@ void launch_smooth_sweep_dot(const Level &L, const V *val, const V *m, const dou
                              double *partial, CgState *cg, const int *skip, cudaStream_t s) {
     count_launch();
     const unsigned g = (unsigned)cg_blocks(L.n);
-    LPR_DISPATCH(L.lpr, (launch_pdl(k_smooth_sweep_dot<V, P_>, g, cg_threads(L.n), 0, s, L.n, L.A_ptr, L.A_col, val, m, f, u_in,
+    LPR_DISPATCH(L.lpr, (launch_pdl(k_smooth_sweep_dot<V, P_>, g, cg_threads(L.n), 0, s, L.n, L.A_ptr, L.cols(), val, m, f, u_in,
                                                                              z, partial, cg, skip)))
 }
 template void launch_smooth_sweep_dot<double>(const Level &, const double *, const double *, const double *,
@@ -1607,7 +1698,7 @@ template <class V, class TF>
 void launch_residual(const Level &L, const V *val, const TF *f, const V *u, V *r, const int *skip, cudaStream_t s) {
     count_launch();
     const unsigned g = (unsigned)nblocks((int64_t)L.n * L.lpr);
-    LPR_DISPATCH(L.lpr, (launch_pdl(k_residual<V, TF, P_>, g, kThreads, 0, s, L.n, L.A_ptr, L.A_col, val, f, u, r, skip)))
+    LPR_DISPATCH(L.lpr, (launch_pdl(k_residual<V, TF, P_>, g, kThreads, 0, s, L.n, L.A_ptr, L.cols(), val, f, u, r, skip)))
 }
 template <class V>
 void launch_restrict(const Level &L, const V *Rval, const V *r, V *fc, const V *mc, V *uc, const int *skip,
@@ -1701,7 +1792,7 @@ void launch_cg_set_rz_p(int32_t n, const double *z, double *p, CgState *cg, cuda
     count_launch();
     launch_pdl(k_cg_set_rz_p, cg_blocks(n), cg_threads(n), 0, s, n, z, p, cg);
 }
-void launch_spmv_dot(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *p,
+void launch_spmv_dot(int32_t n, const int32_t *ptr, const ColIdx &col, const double *val, const double *p,
                      double *q, double *partial, CgState *cg, cudaStream_t s) {
     count_launch();
     launch_pdl(k_spmv_dot, cg_blocks(n), cg_threads(n), 0, s, n, ptr, col, val, p, q, partial, cg);
@@ -1713,7 +1804,17 @@ void launch_cg_update_ur(int32_t n, CgState *cg, const double *p, const double *
     launch_pdl(k_cg_update_ur, cg_blocks(n), cg_threads(n), 0, s, n, cg, p, q, u, r, partial, zo, part_zo, use_h, hb,
                z0);
 }
-void launch_true_residual(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *f,
+void launch_col_offsets_collect(int32_t n, const int32_t *ptr, const int32_t *col, int32_t *table, int *count,
+                                cudaStream_t s) {
+    count_launch();
+    k_col_offsets_collect<<<nblocks(n), kThreads, 0, s>>>(n, ptr, col, table, count);
+}
+void launch_col_offsets_encode(int32_t n, const int32_t *ptr, const int32_t *col, const int32_t *off, int noff,
+                               uint8_t *cidx, int *st, cudaStream_t s) {
+    count_launch();
+    k_col_offsets_encode<<<nblocks(n), kThreads, 0, s>>>(n, ptr, col, off, noff, cidx, st);
+}
+void launch_true_residual(int32_t n, const int32_t *ptr, const ColIdx &col, const double *val, const double *f,
                           const double *u, double *t, double *partial, CgState *cg, int force, cudaStream_t s) {
     count_launch();
     launch_pdl(k_true_residual, cg_blocks(n), cg_threads(n), 0, s, n, ptr, col, val, f, u, t, partial, cg, force);

@@ -142,6 +142,27 @@ def random_arrow_spd(n: int, density_: float, arm: int, seed: int):
     return np.asarray(p, np.int32), np.asarray(c, np.int32), np.asarray(v, np.float64)
 
 
+def random_banded_spd(n: int, band: int, density_: float, seed: int):
+    """A random symmetric, diagonally dominant matrix whose entries lie within
+    `band` of the diagonal (so its rows use at most 2 band + 1 distinct column
+    offsets), in sorted CSR form."""
+    rng = np.random.default_rng(seed)
+    i, j = np.triu_indices(n, 1)
+    keep = (j - i <= band) & (rng.random(i.size) < density_)
+    M = np.zeros((n, n))
+    w = -rng.uniform(0.01, 1.0, keep.sum())
+    M[i[keep], j[keep]] = w
+    M = M + M.T
+    M[np.arange(n), np.arange(n)] = -M.sum(axis=1) + rng.uniform(0.0, 0.5, n) + 1e-3
+    p, c, v = [0], [], []
+    for r in range(n):
+        nz = np.nonzero(M[r])[0]
+        c.extend(nz.tolist())
+        v.extend(M[r, nz].tolist())
+        p.append(len(c))
+    return np.asarray(p, np.int32), np.asarray(c, np.int32), np.asarray(v, np.float64)
+
+
 def revalue_symmetric(ptr, col, val, seed: int, spread: float = 0.5):
     """New values on the same symmetric pattern: every off-diagonal pair scaled
     by one seeded factor in [1 - spread, 1 + spread], the diagonal reset to the

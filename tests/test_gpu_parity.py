@@ -545,3 +545,29 @@ def test_coarse_inverse_every_size_class(n):
     z = G.vcycle(torch.tensor(r, device="cuda")).cpu().numpy()
     ref = np.linalg.solve(M, r)
     assert np.linalg.norm(z - ref) <= 1e-12 * np.linalg.norm(ref) * np.linalg.cond(M)
+
+
+@pytest.mark.parametrize("band", [120, 140])
+def test_banded_patterns_through_both_column_forms(band):
+    """The finest level's matrix kernels read one byte per entry when the rows
+    use at most 256 distinct column offsets (band 120: up to 241 offsets) and
+    the int32 columns otherwise (band 140: up to 281): hierarchy, V-cycle and
+    solve against the oracle either way."""
+    n = 1500
+    ptr, col, val = I.random_banded_spd(n, band, 0.04, seed=band)
+    offs = np.unique(col - np.repeat(np.arange(n), np.diff(ptr)))
+    assert (offs.size <= 256) == (band == 120)
+    G = B.AMG(coarse_enough=40)
+    G.full_setup(*(torch.tensor(a, device="cuda") for a in (ptr, col, val)))
+    H = O.Hierarchy(ptr, col, val, O.Params(coarse_enough=40))
+    compare_hierarchy(G, H)
+    r = np.random.default_rng(9).normal(size=n)
+    z = G.vcycle(torch.tensor(r, device="cuda")).cpu().numpy()
+    zo = H.vcycle(r)
+    assert np.all(np.abs(z - zo) <= 1e-9 * vcycle_envelope(H, r))
+    f = I.rhs(n)
+    u, info = G.solve(torch.tensor(f, device="cuda"), 1e-8)
+    uo, it, rr, st = H.pcg(f, 1e-8)
+    assert info.status == 0 and st == 0 and abs(info.iters - it) <= 1
+    A = _sp(ptr, col, val, n)
+    assert np.linalg.norm(f - A @ u.cpu().numpy()) <= 1e-8 * np.linalg.norm(f)
