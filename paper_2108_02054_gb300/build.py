@@ -12,7 +12,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB_PATH = os.path.join(HERE, "libamgpr.so")
 SOURCES = ["setup_kernels.cu", "solve_kernels.cu", "amg.cu", "noalloc.cu", "block.cu"]
-HEADERS = [os.path.join(CSRC, "common.cuh"), os.path.join(ROOT, "include", "amgpr.h")]
+HEADERS = [os.path.join(CSRC, "common.cuh"), os.path.join(CSRC, "fdiv.cuh"), os.path.join(ROOT, "include", "amgpr.h")]
 
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",

@@ -198,6 +198,8 @@ amg_status check_device(amg_ctx *ctx, const char *where) {
     if (st & DEV_ERR_CAPACITY)
         return set_err(ctx, AMG_ERR_CAPACITY, w + ": a row of a Galerkin product exceeds the kernel capacity");
     if (st & DEV_ERR_OVERFLOW) return set_err(ctx, AMG_ERR_CAPACITY, w + ": an index count exceeds int32");
+    if (st & DEV_ERR_TIMEOUT)
+        return set_err(ctx, AMG_ERR_CUDA, w + ": a message between the CTAs of the coarsest LU did not arrive");
     return set_err(ctx, AMG_ERR_STATE, w + ": inconsistent hierarchy state");
 }
 

@@ -22,6 +22,7 @@ enum : int {
     DEV_ERR_STATE = 8,
     DEV_ERR_SINGULAR = 16,
     DEV_ERR_OVERFLOW = 32,
+    DEV_ERR_TIMEOUT = 64,  // a bounded wait between the CTAs of a cluster ran out
 };
 
 constexpr int kMaxLevels = 32;

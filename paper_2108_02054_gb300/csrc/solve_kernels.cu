@@ -13,6 +13,7 @@
 #include <cooperative_groups.h>
 
 #include "common.cuh"
+#include "fdiv.cuh"
 
 namespace amgpr {
 
@@ -571,6 +572,429 @@ k_dense_lu_cluster(int32_t n, double *__restrict__ g, double *__restrict__ gT, i
     cluster.sync();
 }
 
+// ---- the coarsest LU for n <= kLuPipeN: a pipelined cluster factorisation
+//
+// On this part an FP64 instruction holds its SM sub-partition for about 64
+// cycles whatever the number of active lanes, an FP64 division takes about
+// 565 cycles and a cluster barrier about 400.  So the elimination keeps one
+// pivot search, one division and one fma per step on its critical path, does
+// the division in integer arithmetic (div_rn: the same IEEE quotient), and
+// has no cluster-wide barrier between steps.
+//
+// Column j belongs to CTA (j / B) % C of a C-CTA cluster (blocks of B
+// consecutive columns dealt round-robin), stored column-major in that CTA's
+// shared memory, one row per lane of four compute warps; the columns of the
+// block being factorised live in registers.  Step k is taken by the owner of
+// column k alone (its column is already updated through step k-1): the
+// pivot search (each warp's candidate carries the row's remaining block
+// values and the reciprocal of its value, so one barrier serves the search),
+// the multipliers l_r = a_rk / a_kk, and one message per step: a row of the
+// multipliers and a header (pivot position, pivot row, singular flag) that a
+// fifth warp copies into every other CTA's slot for step k with one bulk
+// copy each; the copy's byte count completes that slot's mbarrier.  Every
+// CTA applies the steps to its own columns in order, the next owner's block
+// first, so a message's latency is paid once per block of B steps.
+//
+// Rows never move: every lane tracks the position of its row and the step at
+// which the row became a pivot (the lazy form of the row swaps), and writes
+// its row at its final position at the end.  Each entry sees the operations
+// of the textbook row-swapping elimination in the same order (one division
+// per multiplier, then a_rc = fma(-l_r, a_kc, a_rc) step by step), so the
+// factors and pivots are identical to it.
+//
+// Every wait is bounded by a clock budget; on expiry the CTA sets
+// DEV_ERR_TIMEOUT, waits no more and goes to the final cluster barrier, which
+// every CTA then reaches.
+constexpr int kLuPipeN = 128;
+constexpr int kLuPipeMinN = 48;  // below: the one-CTA kernel is faster (fewer steps to pipeline)
+constexpr int kLuPipeWarps = 4;                           // compute warps, one row per lane
+constexpr int kLuPipeThreads = (kLuPipeWarps + 1) * 32;   // and the sender warp
+constexpr int kLuPipeC = 8;                               // CTAs of the cluster
+constexpr int kLuPipeB = 4;                               // columns per ownership block
+constexpr bool kLuPipeIntDiv = true;                      // multipliers by div_rn
+constexpr long long kLuPipeWaitClocks = 2000000000ll;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint32_t peer_addr(uint32_t a, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_done(uint32_t bar) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], 0;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait for phase 0 of an mbarrier; false when the budget ran out
+__device__ __forceinline__ bool mbar_wait(uint32_t bar) {
+    if (mbar_done(bar)) return true;
+    const long long t0 = clock64();
+    while (!mbar_done(bar))
+        if (clock64() - t0 > kLuPipeWaitClocks) return false;
+    return true;
+}
+__device__ __forceinline__ void bulk_to_peer(uint32_t dst, uint32_t src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     dst),
+                 "r"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+// barrier of the compute warps only (named barrier 1)
+__device__ __forceinline__ void lu_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kLuPipeWarps * 32) : "memory"); }
+__device__ __forceinline__ int lu_sync_or(int pred) {
+    int r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.s32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.s32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"(pred), "n"(kLuPipeWarps * 32)
+        : "memory");
+    return r;
+}
+
+template <int B>
+struct PivCand {
+    unsigned long long key;
+    int32_t pos, row;
+    double val;
+    double vals[B];  // the row's values in the block's columns
+    DivRecip rc;     // reciprocal of val
+};
+// header of step k: pivot position, pivot row, singular flag
+__device__ __forceinline__ unsigned long long piv_header(int32_t p, int32_t row, bool sing) {
+    return (unsigned long long)(uint32_t)p | ((unsigned long long)(uint32_t)row << 16) |
+           ((unsigned long long)(sing ? 1u : 0u) << 32);
+}
+
+template <int C, int B>
+struct LuPipeMap {
+    int32_t n, nblk;
+    __device__ int32_t owner(int32_t k) const { return (k / B) % C; }
+    __device__ int32_t last_col(int32_t q) const {
+        if (q >= nblk) return -1;
+        const int32_t b = q + C * ((nblk - 1 - q) / C);
+        return min(n, (b + 1) * B) - 1;
+    }
+    __device__ int32_t local(int32_t j) const { return ((j / B) / C) * B + j % B; }
+    __device__ int32_t global(int32_t q, int32_t lc) const { return (q + C * (lc / B)) * B + lc % B; }
+    __device__ int32_t ncols(int32_t q) const { return q < nblk ? local(last_col(q)) + 1 : 0; }
+};
+
+// shared memory: n_even mbarriers, n - 1 message rows of lu_pipe_row(n)
+// doubles (multipliers, then the header at n_even), the own columns
+__host__ __device__ inline int32_t lu_pipe_even(int32_t n) { return (n + 1) & ~1; }
+__host__ __device__ inline int32_t lu_pipe_row(int32_t n) { return lu_pipe_even(n) + 2; }
+size_t lu_pipe_smem(int32_t n, int C, int B) {
+    const size_t nblk = (size_t)(n + B - 1) / B, per = (nblk + C - 1) / C * B;
+    return ((size_t)lu_pipe_even(n) + (size_t)(n > 0 ? n - 1 : 0) * lu_pipe_row(n) + per * n) * 8;
+}
+
+template <int C, int B, bool IntDiv>
+__global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kLuPipeThreads)
+k_dense_lu_pipe(int32_t n, double *__restrict__ g, double *__restrict__ gT, int32_t *__restrict__ piv, int *st) {
+    extern __shared__ __align__(16) unsigned long long sm_pipe[];
+    __shared__ PivCand<B> cand_buf[2][kLuPipeWarps];  // by step parity: a fast warp may write step k+1's
+    __shared__ int s_quit;
+    cgr::cluster_group cluster = cgr::this_cluster();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int32_t rank = (int32_t)cluster.block_rank();
+    const LuPipeMap<C, B> M{n, (n + B - 1) / B};
+    const int32_t nmine = M.ncols(rank), ne = lu_pipe_even(n), row = lu_pipe_row(n);
+    unsigned long long *bar = sm_pipe;                       // one mbarrier per step
+    double *msg = (double *)(sm_pipe + ne);                  // message rows, [step][row]
+    double *col = msg + (size_t)(n > 0 ? n - 1 : 0) * row;   // own columns, [local column][row]
+    const uint32_t off_msg = 8u * (uint32_t)ne, row_bytes = 8u * (uint32_t)row;
+
+    // setup: barriers (own steps: the compute warps arrive; others: one
+    // arrival with the message's byte count), the own columns
+    for (int32_t s = tid; s < n; s += kLuPipeThreads)
+        mbar_init(smem_addr(bar + s), M.owner(s) == rank ? (uint32_t)kLuPipeWarps : 1u);
+    if (tid == 0) s_quit = 0;
+    __syncthreads();
+    if (tid == 0) asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int32_t s = tid; s < n - 1; s += kLuPipeThreads)
+        if (M.owner(s) != rank) mbar_arrive_expect(smem_addr(bar + s), row_bytes);
+    for (int32_t e = tid; e < nmine * n; e += kLuPipeThreads) {
+        const int32_t lc = e / n, r = e % n;
+        col[e] = g[(int64_t)r * n + M.global(rank, lc)];
+    }
+    cluster.sync();
+
+    if (warp == kLuPipeWarps) {
+        // the sender: each own step's message row to every other CTA
+        const uint32_t base = smem_addr(sm_pipe);
+        bool stop = false;
+        for (int32_t bk = rank; bk < M.nblk && !stop; bk += C)
+            for (int32_t k = bk * B; k < min(n - 1, bk * B + B) && !stop; ++k) {
+                const uint32_t b = smem_addr(bar + k);
+                bool ready = mbar_done(b);
+                const long long t0 = clock64();
+                while (!ready) {
+                    if (*(volatile int *)&s_quit) {
+                        __threadfence_block();
+                        ready = mbar_done(b);
+                        if (!ready) stop = true;
+                        break;
+                    }
+                    if (clock64() - t0 > kLuPipeWaitClocks) {
+                        if (lane == 0) atomicOr(st, DEV_ERR_TIMEOUT);
+                        stop = true;
+                        break;
+                    }
+                    ready = mbar_done(b);
+                }
+                if (!ready) break;
+                if (lane == 0) {
+#pragma unroll 1
+                    for (int q = 0; q < C; ++q)
+                        if (q != rank) {
+                            const uint32_t pb = peer_addr(base, (uint32_t)q);
+                            bulk_to_peer(pb + off_msg + row_bytes * (uint32_t)k, smem_addr(msg + (size_t)k * row),
+                                         row_bytes, pb + 8u * (uint32_t)k);
+                        }
+                }
+                const unsigned long long h = (unsigned long long)__double_as_longlong(msg[(size_t)k * row + ne]);
+                if ((h >> 32) & 1ull) stop = true;
+            }
+    } else {
+        const int32_t r = tid;
+        const bool valid = r < n;
+        int32_t pos = r, pstep = n;  // position of this lane's row; step at which it became a pivot
+        bool abort = false;
+        int32_t kstop = n;  // step at which the elimination met a zero column
+
+        // read the header of a received step: wait, then update the row bookkeeping
+        auto consume = [&](int32_t s) -> bool {
+            const int late = mbar_wait(smem_addr(bar + s)) ? 0 : 1;
+            if (lu_sync_or(late)) {
+                if (tid == 0) atomicOr(st, DEV_ERR_TIMEOUT);
+                abort = true;
+                return false;
+            }
+            const unsigned long long h = (unsigned long long)__double_as_longlong(msg[(size_t)s * row + ne]);
+            if ((h >> 32) & 1ull) {
+                kstop = s;
+                return false;
+            }
+            const int32_t p = (int32_t)(h & 0xffffu), pr = (int32_t)((h >> 16) & 0xffffu);
+            if (r == pr) { pos = s; pstep = s; }
+            else if (pos == s) pos = p;
+            return true;
+        };
+        // apply step s to the local columns [lo, hi) in shared memory
+        auto apply = [&](int32_t s, int32_t lo, int32_t hi) {
+            if (lo >= hi) return;
+            const bool act = valid && pstep > s;
+            if (!__any_sync(0xffffffffu, act)) return;
+            const double *m = msg + (size_t)s * row;
+            const int32_t pr = (int32_t)(((unsigned long long)__double_as_longlong(m[ne]) >> 16) & 0xffffu);
+            const double l = act ? m[r] : 0.0;
+            int32_t lc = lo;
+            for (; lc + 4 <= hi; lc += 4) {
+                double u[4], x[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    u[q] = col[(size_t)(lc + q) * n + pr];
+                    x[q] = act ? col[(size_t)(lc + q) * n + r] : 0.0;
+                }
+                if (act)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) col[(size_t)(lc + q) * n + r] = fma(-l, u[q], x[q]);
+            }
+            for (; lc < hi; ++lc) {
+                const double u = col[(size_t)lc * n + pr];
+                if (act) col[(size_t)lc * n + r] = fma(-l, u, col[(size_t)lc * n + r]);
+            }
+        };
+
+        int32_t s_all = 0;  // steps applied to every own column beyond the current block
+        for (int32_t bk = rank; bk < M.nblk && kstop == n && !abort; bk += C) {
+            const int32_t k0 = bk * B, k1 = min(n, k0 + B), nb = k1 - k0;
+            const int32_t lb = M.local(k0), lb1 = lb + nb;  // the block's local columns
+            // steps of the other CTAs since this CTA's previous block, the
+            // block's columns first; the last one (which the block waits for)
+            // on the block's columns only, in registers
+            bool deferred = false;
+            for (int32_t s = s_all; s + 1 < k0; ++s) {
+                if (!consume(s)) break;
+                apply(s, lb, nmine);  // the block's columns come first
+            }
+            if (kstop != n || abort) break;
+            double vb[B];
+            bool have_last = false;
+            if (k0 > s_all && k0 >= 1) {
+                if (!consume(k0 - 1)) break;
+                have_last = true;
+                deferred = true;
+            }
+#pragma unroll
+            for (int t = 0; t < B; ++t) vb[t] = valid && t < nb ? col[(size_t)(lb + t) * n + r] : 0.0;
+            if (have_last) {
+                const double *m = msg + (size_t)(k0 - 1) * row;
+                const int32_t pr = (int32_t)(((unsigned long long)__double_as_longlong(m[ne]) >> 16) & 0xffffu);
+                const bool act = valid && pstep > k0 - 1;
+                const double l = act ? m[r] : 0.0;
+#pragma unroll
+                for (int t = 0; t < B; ++t)
+                    if (t < nb) {
+                        const double u = col[(size_t)(lb + t) * n + pr];
+                        if (act) vb[t] = fma(-l, u, vb[t]);
+                    }
+            }
+            // the block's steps
+            DivRecip rc;  // reciprocal of this lane's value in the step's column
+            if (IntDiv) rc = div_recip(vb[0]);
+            int32_t pk[B];  // the block's pivots, stored at the end of the block
+#pragma unroll
+            for (int t = 0; t < B; ++t) {
+                if (t >= nb) break;
+                const int32_t k = k0 + t;
+                const double v = vb[t];
+                const bool cand_ok = valid && pstep >= k;
+                const unsigned long long key = cand_ok ? mag_key(v) : 0ull;
+                const unsigned hi = (unsigned)(key >> 32), lo = (unsigned)key;
+                const unsigned mh = __reduce_max_sync(0xffffffffu, hi);
+                const unsigned ml = __reduce_max_sync(0xffffffffu, hi == mh ? lo : 0u);
+                const bool top = cand_ok && hi == mh && lo == ml;
+                const unsigned bp = __reduce_min_sync(0xffffffffu, top ? (unsigned)pos : 0xffffffffu);
+                const unsigned wmask = __ballot_sync(0xffffffffu, top && (unsigned)pos == bp);
+                PivCand<B> *cand = cand_buf[k & 1];
+                if (wmask == 0u) {
+                    if (lane == 0) {
+                        cand[warp].key = 0ull;
+                        cand[warp].pos = n;
+                        cand[warp].row = -1;
+                    }
+                } else if (lane == __ffs(wmask) - 1) {
+                    PivCand<B> &c = cand[warp];
+                    c.key = key;
+                    c.pos = pos;
+                    c.row = r;
+                    c.val = v;
+#pragma unroll
+                    for (int q = 0; q < B; ++q) c.vals[q] = vb[q];
+                    if (IntDiv) c.rc = rc;
+                }
+                lu_sync();
+                int bw = 0;
+                {
+                    unsigned long long bk_ = cand[0].key;
+                    int32_t bpos = cand[0].pos;
+#pragma unroll
+                    for (int w = 1; w < kLuPipeWarps; ++w) {
+                        const unsigned long long kw = cand[w].key;
+                        const int32_t pw = cand[w].pos;
+                        if (kw > bk_ || (kw == bk_ && pw < bpos)) { bk_ = kw; bpos = pw; bw = w; }
+                    }
+                }
+                const PivCand<B> &best = cand[bw];
+                const int32_t brow = best.row, bpos = best.pos;
+                const bool sing = best.key == 0ull || brow < 0;
+                double *m = msg + (size_t)k * row;
+                if (sing) {
+                    // the receivers see the flag in the header; no multipliers
+                    // follow (the last step has no message row)
+                    kstop = k;
+                    if (tid == 0) {
+                        if (k < n - 1) m[ne] = __longlong_as_double((long long)piv_header(k, 0, true));
+                        atomicOr(st, DEV_ERR_SINGULAR);
+                        for (int32_t q = k; q < n; ++q) piv[q] = q;
+                    }
+                    if (k < n - 1) {
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(smem_addr(bar + k));
+                    }
+                    break;
+                }
+                if (r == brow) { pos = k; pstep = k; }
+                else if (pos == k) pos = bpos;
+                const bool act = valid && pstep > k;
+                double l = 0.0;
+                if (IntDiv) {
+                    const DivRecip brc = best.rc;
+                    if (act) l = div_rn(v, brc);
+                } else {
+                    const double akk = best.val;
+                    if (act) l = v / akk;
+                }
+                double u[B];
+#pragma unroll
+                for (int q = 0; q < B; ++q) u[q] = best.vals[q];
+                // the block's next column first: the next step waits for it
+                if (t + 1 < nb) {
+                    if (act) vb[t + 1] = fma(-l, u[t + 1], vb[t + 1]);
+                    if (IntDiv) rc = div_recip(vb[t + 1]);
+                }
+                if (act) {
+                    vb[t] = l;
+                    if (k < n - 1) m[r] = l;
+                }
+                pk[t] = bpos;
+                if (tid == 0 && k < n - 1) m[ne] = __longlong_as_double((long long)piv_header(bpos, brow, false));
+                if (k < n - 1) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_addr(bar + k));
+                }
+#pragma unroll
+                for (int q = 0; q < B; ++q)
+                    if (q > t + 1 && q < nb && act) vb[q] = fma(-l, u[q], vb[q]);
+            }
+            // the block's pivots, then the block back to shared memory, then
+            // this CTA's later columns: the deferred step and the block's
+            // steps (up to a zero column)
+            if (tid == 0)
+#pragma unroll
+                for (int t = 0; t < B; ++t)
+                    if (t < nb && k0 + t < kstop) piv[k0 + t] = pk[t];
+            if (valid)
+#pragma unroll
+                for (int t = 0; t < B; ++t)
+                    if (t < nb) col[(size_t)(lb + t) * n + r] = vb[t];
+            const int32_t kend = kstop != n ? kstop : k1;
+            lu_sync();
+            for (int32_t s = deferred ? k0 - 1 : k0; s < kend; ++s) {
+                apply(s, lb1, nmine);
+                lu_sync();
+            }
+            s_all = k1;
+        }
+        // the headers after this CTA's last block (final positions)
+        if (kstop == n && !abort)
+            for (int32_t s = s_all; s < n - 1; ++s)
+                if (!consume(s)) break;
+        if (!abort && valid)
+            for (int32_t lc = 0; lc < nmine; ++lc) {
+                const int32_t j = M.global(rank, lc);
+                const double v = col[(size_t)lc * n + r];
+                g[(int64_t)pos * n + j] = v;
+                if (gT) gT[(int64_t)j * n + pos] = v;
+            }
+        // every arrival is made: let the sender stop waiting
+        lu_sync();
+        if (tid == 0) {
+            __threadfence_block();
+            *(volatile int *)&s_quit = 1;
+        }
+    }
+    // no CTA leaves while a message to or from it may be in flight
+    cluster.sync();
+}
+
 __global__ void __launch_bounds__(1024) k_dense_lu(int32_t n, double *__restrict__ a, int32_t *__restrict__ piv,
                                                    int *st) {
     __shared__ KeyIdx wbest[32];
@@ -683,6 +1107,50 @@ k_lu_inverse(int32_t n, const double *__restrict__ lu_g, const int32_t *__restri
     }
     if (staged)
         for (int32_t r = lane; r < n; r += 32) inv[(int64_t)r * n + j] = x[r];
+}
+
+// explicit inverse from the LU factors (n <= kLuSmemN): one block per column
+// j of A^-1 with one row per thread (so each substitution step costs one fma
+// and one block barrier, not a warp's serial chunks), the factors staged in
+// shared memory.  The arithmetic per entry is that of k_lu_inverse: L y =
+// P e_j, then U x = y with x_k = y_k * (1 / u_kk), each in step order.
+__global__ void __launch_bounds__((kLuSmemN + 31) / 32 * 32)
+k_lu_inverse_rows(int32_t n, const double *__restrict__ lu_g, const int32_t *__restrict__ piv,
+                  double *__restrict__ inv) {
+    extern __shared__ double sm_iv[];
+    double *lu = sm_iv;                       // n x n, row-major
+    double *xs = lu + (int64_t)n * n;          // x_k as each step finalises it
+    const int32_t j = blockIdx.x, r = threadIdx.x;
+    const int64_t nn = (int64_t)n * n;
+    for (int64_t e = threadIdx.x; e < nn; e += blockDim.x) lu[e] = lu_g[e];
+    // P e_j is the unit vector at the position that the row swaps move j to
+    int32_t pos = j;
+    for (int32_t k = 0; k < n; ++k) {
+        const int32_t p = piv[k];
+        if (p < 0 || p >= n || p == k) continue;
+        if (pos == k) pos = p;
+        else if (pos == p) pos = k;
+    }
+    const bool valid = r < n;
+    const double rd = valid ? 1.0 / lu_g[(int64_t)r * n + r] : 0.0;
+    double x = valid && r == pos ? 1.0 : 0.0;
+    __syncthreads();
+    // L y = P e_j (unit lower triangular); entries before pos stay zero
+    for (int32_t k = pos; k < n - 1; ++k) {
+        if (r == k) xs[k] = x;
+        __syncthreads();
+        if (valid && r > k) x = fma(-lu[(int64_t)r * n + k], xs[k], x);
+    }
+    // U x = y
+    for (int32_t k = n - 1; k >= 0; --k) {
+        if (r == k) {
+            x = x * rd;
+            xs[k] = x;
+        }
+        __syncthreads();
+        if (valid && r < k) x = fma(-lu[(int64_t)r * n + k], xs[k], x);
+    }
+    if (valid) inv[(int64_t)r * n + j] = x;
 }
 
 // explicit inverse from column-major factors (n > kLuSmemN): the factors stay
@@ -1617,6 +2085,11 @@ void launch_dense_lu(int32_t n, double *a, int32_t *piv, int *st, cudaStream_t s
     static bool attr = false;
     const int max_bytes = kLuSmemN * kLuSmemN * (int)sizeof(double);
     if (!attr) {
+        cudaFuncSetAttribute(k_dense_lu_pipe<kLuPipeC, kLuPipeB, kLuPipeIntDiv>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lu_pipe_smem(kLuPipeN, kLuPipeC, kLuPipeB));
+        if (kLuPipeC > 8)
+            cudaFuncSetAttribute(k_dense_lu_pipe<kLuPipeC, kLuPipeB, kLuPipeIntDiv>,
+                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         cudaFuncSetAttribute(k_dense_lu_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         cudaFuncSetAttribute(k_dense_lu_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)lu_cluster_smem(kLuClusterN));
@@ -1626,7 +2099,10 @@ void launch_dense_lu(int32_t n, double *a, int32_t *piv, int *st, cudaStream_t s
         attr = true;
     }
     count_launch();
-    if (n <= kLuSmemN)
+    if (n > kLuPipeMinN && n <= kLuPipeN)
+        k_dense_lu_pipe<kLuPipeC, kLuPipeB, kLuPipeIntDiv>
+            <<<kLuPipeC, kLuPipeThreads, lu_pipe_smem(n, kLuPipeC, kLuPipeB), s>>>(n, a, aT, piv, st);
+    else if (n <= kLuSmemN)
         k_dense_lu_smem<<<1, kLuThreads, (size_t)n * n * sizeof(double), s>>>(n, a, piv, st);
     else if (n <= kLuClusterN)
         k_dense_lu_cluster<<<kLuClusterCtas, kLuClusterThreads, lu_cluster_smem(n), s>>>(n, a, aT, piv, st);
@@ -1646,13 +2122,17 @@ void launch_lu_inverse(int32_t n, const double *lu, const int32_t *piv, double *
                           kLuSmemN * (int)sizeof(int32_t);
     if (!attr) {
         cudaFuncSetAttribute(k_lu_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(k_lu_inverse_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (kLuSmemN * kLuSmemN + kLuSmemN) * (int)sizeof(double));
         attr = true;
     }
-    const size_t bytes = n <= kLuSmemN ? ((size_t)n * n + (size_t)(kInvWarps + 1) * n) * sizeof(double) +
-                                             (size_t)n * sizeof(int32_t)
-                                       : 0;
     count_launch();
-    k_lu_inverse<<<(unsigned)((n + kInvWarps - 1) / kInvWarps), kInvWarps * 32, bytes, s>>>(n, lu, piv, inv);
+    if (n <= kLuSmemN) {
+        const unsigned threads = (unsigned)((n + 31) / 32 * 32);
+        k_lu_inverse_rows<<<(unsigned)n, threads, ((size_t)n * n + (size_t)n) * sizeof(double), s>>>(n, lu, piv, inv);
+        return;
+    }
+    k_lu_inverse<<<(unsigned)((n + kInvWarps - 1) / kInvWarps), kInvWarps * 32, 0, s>>>(n, lu, piv, inv);
 }
 
 #define LPR_DISPATCH(lpr, KCALL)                   \

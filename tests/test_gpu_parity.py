@@ -472,11 +472,13 @@ def _dense_csr(M):
     return ptr, col, np.ascontiguousarray(M, np.float64).ravel()
 
 
-@pytest.mark.parametrize("n", [1, 2, 5, 31, 32, 33, 87, 128, 129, 160, 161, 250, 448, 449, 500])
+@pytest.mark.parametrize("n", [1, 2, 5, 31, 32, 33, 48, 49, 87, 100, 127, 128, 129, 160, 161, 250, 448, 449, 500])
 @pytest.mark.parametrize("dup", [False, True])
 def test_coarsest_lu_with_tied_pivots_and_singular_input(n, dup):
-    """The coarsest dense LU of every kernel size class (one block up to 160
-    rows, the eight-CTA cluster up to 448, the global-memory kernel above) on
+    """The coarsest dense LU of every kernel size class (one block up to 48
+    rows, the pipelined eight-CTA cluster up to 128 with whole and partial
+    last column blocks, one block again up to 160, the eight-CTA cluster up to
+    448, the global-memory kernel above) on
     a one-level hierarchy whose matrix is dense with small-integer entries, so
     that many candidates tie in magnitude: the pivots (first position of the
     largest magnitude) and the factors equal the oracle's bit for bit.  With a
@@ -528,12 +530,12 @@ def test_cluster_lu_for_mid_size_coarsest_level(N, ce, nL):
     assert info.status == 0 and st == O.OK and abs(info.iters - it) <= 1
 
 
-@pytest.mark.parametrize("n", [1, 5, 33, 87, 150, 151, 161, 300])
+@pytest.mark.parametrize("n", [1, 5, 33, 87, 150, 160, 161, 300])
 def test_coarse_inverse_every_size_class(n):
     """On a one-level hierarchy the V-cycle is the coarsest solve, the explicit
     inverse (from the LU factors) times r: against a dense solve of the same
-    diagonally dominant matrix, for the register kernel (n <= 150), the
-    shared-memory kernel (n <= 160) and the column-major kernel above."""
+    diagonally dominant matrix, for the one-row-per-thread kernel (n <= 160)
+    and the column-major kernel above."""
     rng = np.random.default_rng(2000 + n)
     M = rng.uniform(-1.0, 1.0, (n, n))
     M[np.arange(n), np.arange(n)] = np.abs(M).sum(axis=1) + 1.0
