@@ -87,7 +87,8 @@ def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         d = json.load(open(p))
-        return d.get("hbm_gbs", 6672.5), "measured"
+        if "hbm_gbs" in d:
+            return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
 
 
