@@ -1117,24 +1117,37 @@ k_lu_inverse(int32_t n, const double *__restrict__ lu_g, const int32_t *__restri
 __global__ void __launch_bounds__((kLuSmemN + 31) / 32 * 32)
 k_lu_inverse_rows(int32_t n, const double *__restrict__ lu_g, const int32_t *__restrict__ piv,
                   double *__restrict__ inv) {
-    extern __shared__ double sm_iv[];
+    extern __shared__ __align__(16) double sm_iv[];
     double *lu = sm_iv;                       // n x n, row-major
     double *xs = lu + (int64_t)n * n;          // x_k as each step finalises it
+    int32_t *pv = (int32_t *)(xs + n);         // the pivots
     const int32_t j = blockIdx.x, r = threadIdx.x;
     const int64_t nn = (int64_t)n * n;
-    for (int64_t e = threadIdx.x; e < nn; e += blockDim.x) lu[e] = lu_g[e];
+    // the factors by 16-byte asynchronous copies, all in flight at once; an
+    // odd tail element (or an unaligned source) by plain copies
+    if (((uintptr_t)lu_g & 15u) == 0u) {
+        for (int64_t e = 2 * (int64_t)threadIdx.x; e + 1 < nn; e += 2 * (int64_t)blockDim.x)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(lu + e)), "l"(lu_g + e)
+                         : "memory");
+        if ((nn & 1) && threadIdx.x == 0) lu[nn - 1] = lu_g[nn - 1];
+    } else {
+        for (int64_t e = threadIdx.x; e < nn; e += blockDim.x) lu[e] = lu_g[e];
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    const bool valid = r < n;
+    if (valid) pv[r] = piv[r];
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    const double rd = valid ? 1.0 / lu_g[(int64_t)r * n + r] : 0.0;
+    __syncthreads();
     // P e_j is the unit vector at the position that the row swaps move j to
     int32_t pos = j;
     for (int32_t k = 0; k < n; ++k) {
-        const int32_t p = piv[k];
+        const int32_t p = pv[k];
         if (p < 0 || p >= n || p == k) continue;
         if (pos == k) pos = p;
         else if (pos == p) pos = k;
     }
-    const bool valid = r < n;
-    const double rd = valid ? 1.0 / lu_g[(int64_t)r * n + r] : 0.0;
     double x = valid && r == pos ? 1.0 : 0.0;
-    __syncthreads();
     // L y = P e_j (unit lower triangular); entries before pos stay zero
     for (int32_t k = pos; k < n - 1; ++k) {
         if (r == k) xs[k] = x;
@@ -2123,13 +2136,15 @@ void launch_lu_inverse(int32_t n, const double *lu, const int32_t *piv, double *
     if (!attr) {
         cudaFuncSetAttribute(k_lu_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         cudaFuncSetAttribute(k_lu_inverse_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (kLuSmemN * kLuSmemN + kLuSmemN) * (int)sizeof(double));
+                             (kLuSmemN * kLuSmemN + kLuSmemN) * (int)sizeof(double) + kLuSmemN * (int)sizeof(int32_t));
         attr = true;
     }
     count_launch();
     if (n <= kLuSmemN) {
         const unsigned threads = (unsigned)((n + 31) / 32 * 32);
-        k_lu_inverse_rows<<<(unsigned)n, threads, ((size_t)n * n + (size_t)n) * sizeof(double), s>>>(n, lu, piv, inv);
+        k_lu_inverse_rows<<<(unsigned)n, threads,
+                            ((size_t)n * n + (size_t)n) * sizeof(double) + (size_t)n * sizeof(int32_t), s>>>(n, lu, piv,
+                                                                                                         inv);
         return;
     }
     k_lu_inverse<<<(unsigned)((n + kInvWarps - 1) / kInvWarps), kInvWarps * 32, 0, s>>>(n, lu, piv, inv);
