@@ -174,9 +174,11 @@ amg_status amg_export_level_vec(amg_ctx *ctx, int32_t level, int32_t *d_agg, uin
  * the pattern's rows use at most 256 distinct column offsets (column - row,
  * as a stencil's do), each entry's column is stored as one byte naming its
  * offset in a table: *col_bytes = 1 and *noffsets = the table's size.
- * Otherwise the int32 columns are read: *col_bytes = 4, *noffsets = 0.
- * Values and arithmetic are the same either way.  AMG_ERR_STATE before a
- * pattern is set. */
+ * Otherwise, after a full setup, when every offset fits in 16 bits, the
+ * offsets themselves are read: *col_bytes = 2 (the coarser levels use the
+ * same rule).  Otherwise the int32 columns: *col_bytes = 4; *noffsets = 0 in
+ * both cases.  Values and arithmetic are the same either way.
+ * AMG_ERR_STATE before a pattern is set. */
 amg_status amg_pattern_info(const amg_ctx *ctx, int32_t *col_bytes, int32_t *noffsets);
 /* Coarsest LU factors (n_L x n_L row-major, FP64) and pivots. */
 amg_status amg_export_coarse_lu(amg_ctx *ctx, double *d_lu, int32_t *d_piv);

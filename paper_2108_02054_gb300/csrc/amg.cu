@@ -417,6 +417,31 @@ amg_status numeric_rebuild(amg_ctx *ctx, const double *d_val, bool galerkin) {
     return coarse_factor(ctx);
 }
 
+// Two-byte column offsets (column - row) for every level without the
+// one-byte form, kept where all of a level's offsets fit in 16 bits (a
+// coarse level of a grid hierarchy: up to about 24,000 at 192^3); the matrix
+// kernels of those levels then move 2 bytes less per entry.  Built once per
+// full setup: the patterns stay fixed across partial rebuilds.
+amg_status build_delta16(amg_ctx *ctx) {
+    if (blockmode(ctx)) return AMG_OK;
+    int *flags = nullptr;
+    TRY(alloc(ctx, &flags, (size_t)kMaxLevels));
+    CK(cudaMemsetAsync(flags, 0, sizeof(int) * kMaxLevels, ctx->s));
+    int16_t *buf[kMaxLevels] = {};
+    for (int l = 0; l < ctx->nlev; ++l) {
+        Level &L = ctx->lev[l];
+        if (L.A_cidx || L.n <= 0 || L.nnz <= 0) continue;
+        TRY(alloc(ctx, &buf[l], (size_t)L.nnz));
+        launch_col_delta16(L.n, L.A_ptr, L.A_col, buf[l], flags + l, ctx->s);
+    }
+    int h[kMaxLevels] = {};
+    CK(cudaMemcpyAsync(h, flags, sizeof(h), cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    for (int l = 0; l < ctx->nlev; ++l)
+        if (buf[l] && h[l] == 0) ctx->lev[l].A_c16 = buf[l];
+    return AMG_OK;
+}
+
 amg_status full_setup_impl(amg_ctx *ctx, const double *d_val) {
     const amg_params &p = ctx->prm;
     free_hierarchy(ctx);
@@ -585,6 +610,7 @@ amg_status full_setup_impl(amg_ctx *ctx, const double *d_val) {
     if (lu_wants_transpose((int32_t)nL)) TRY(alloc(ctx, &ctx->luT, (size_t)(nL * nL)));
     if (mixed(ctx))
         for (int l = 1; l < ctx->nlev; ++l) launch_cast_f32(ctx->lev[l].nnz, ctx->lev[l].A_val, ctx->lev[l].A_valf, ctx->s);
+    TRY(build_delta16(ctx));
     TRY(numeric_rebuild(ctx, blockmode(ctx) ? ctx->lev[0].Ab : ctx->lev[0].A_val, false));
     TRY(check_device(ctx, "full setup"));
     ctx->have_setup = true;
@@ -687,7 +713,8 @@ amg_status set_pattern(amg_ctx *ctx, int32_t n, int32_t nnz, const int32_t *d_pt
 
 // the finest level's column indices as the matrix kernels read them
 ColIdx fine_cols(const amg_ctx *ctx) {
-    return ColIdx{ctx->fine_col, ctx->fine_ncoff ? ctx->fine_cidx : nullptr, ctx->fine_coff, ctx->fine_ncoff};
+    return ColIdx{ctx->fine_col, ctx->fine_ncoff ? ctx->fine_cidx : nullptr, ctx->fine_coff, ctx->fine_ncoff,
+                  ctx->nlev > 0 ? ctx->lev[0].A_c16 : nullptr};
 }
 
 void update_sys(amg_ctx *ctx) {
@@ -1617,7 +1644,7 @@ amg_status amg_export_level_vec(amg_ctx *ctx, int32_t level, int32_t *d_agg, uin
 amg_status amg_pattern_info(const amg_ctx *ctx, int32_t *col_bytes, int32_t *noffsets) {
     if (!ctx || !col_bytes || !noffsets) return AMG_ERR_ARG;
     if (!ctx->fine_ptr) return AMG_ERR_STATE;
-    *col_bytes = ctx->fine_ncoff ? 1 : 4;
+    *col_bytes = ctx->fine_ncoff ? 1 : (ctx->nlev > 0 && ctx->lev[0].A_c16 ? 2 : 4);
     *noffsets = ctx->fine_ncoff;
     return AMG_OK;
 }

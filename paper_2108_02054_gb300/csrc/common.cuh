@@ -48,16 +48,19 @@ struct BiState {
     int iter, maxiter, done, status, replacements, half, need_true, copy_r, skip, pad;
 };
 
-// Column indices of a matrix: plain int32 (col), or, for a pattern whose
+// Column indices of a matrix: plain int32 (col); or, for a pattern whose
 // rows use at most kMaxColOffsets distinct column offsets (column - row, as
 // in a stencil), one byte per entry (cidx) naming its offset in a table
-// (off, noff entries): column = row + off[cidx[p]].
+// (off, noff entries): column = row + off[cidx[p]]; or, when every offset
+// column - row fits in 16 bits, two bytes per entry (c16): column = row +
+// c16[p].  The kernels read the first form that is set.
 constexpr int kMaxColOffsets = 256;
 struct ColIdx {
     const int32_t *col = nullptr;
     const uint8_t *cidx = nullptr;
     const int32_t *off = nullptr;
     int noff = 0;
+    const int16_t *c16 = nullptr;
 };
 
 template <class V>
@@ -68,11 +71,13 @@ struct VecSet {
 struct Level {
     int32_t n = 0, nnz = 0;
     int32_t *A_ptr = nullptr, *A_col = nullptr, *dia = nullptr;
-    // the finest level's compressed columns (when its pattern allows them)
+    // the finest level's one-byte columns (when its pattern allows them);
+    // otherwise the two-byte offsets of any level whose offsets fit
     const uint8_t *A_cidx = nullptr;
     const int32_t *A_coff = nullptr;
     int A_ncoff = 0;
-    ColIdx cols() const { return ColIdx{A_col, A_cidx, A_coff, A_ncoff}; }
+    int16_t *A_c16 = nullptr;
+    ColIdx cols() const { return ColIdx{A_col, A_cidx, A_coff, A_ncoff, A_c16}; }
     double *A_val = nullptr;   // FP64 values (level 0: the hierarchy's copy of the fine matrix)
     float *A_valf = nullptr;   // FP32 values (mixed precision)
     // transfer operators (absent on the coarsest level)
@@ -280,6 +285,8 @@ void launch_spmv_dot(int32_t n, const int32_t *ptr, const ColIdx &col, const dou
 // off (noff entries)
 constexpr int kColOffsetSlots = 1024;
 constexpr int32_t kColOffsetEmpty = (int32_t)0x80808080u;
+// c16[p] = col[p] - row for every entry; *flag = 1 if an offset does not fit
+void launch_col_delta16(int32_t n, const int32_t *ptr, const int32_t *col, int16_t *c16, int *flag, cudaStream_t s);
 void launch_col_offsets_collect(int32_t n, const int32_t *ptr, const int32_t *col, int32_t *table, int *count,
                                 cudaStream_t s);
 void launch_col_offsets_encode(int32_t n, const int32_t *ptr, const int32_t *col, const int32_t *off, int noff,

@@ -36,6 +36,10 @@ __device__ __forceinline__ void stage_col_offsets(const ColIdx &ci, int32_t *s_o
     for (int t = threadIdx.x; t < ci.noff; t += blockDim.x) s_off[t] = ci.off[t];
     __syncthreads();
 }
+// the column of entry p of row i, in whichever form the pattern is held
+__device__ __forceinline__ int32_t col_at(const ColIdx &ci, const int32_t *s_off, int32_t i, int32_t p) {
+    return ci.cidx ? i + s_off[ci.cidx[p]] : (ci.c16 ? i + (int32_t)ci.c16[p] : ci.col[p]);
+}
 
 // ------------------------------------------------------------------ Galerkin, FP64
 constexpr int kApThreads = 128;
@@ -1211,6 +1215,20 @@ k_lu_inverse_t(int32_t n, const double *__restrict__ luT, const int32_t *__restr
     for (int32_t r = lane; r < n; r += 32) inv[(int64_t)r * n + j] = x[r];
 }
 
+// ---- two-byte column offsets (built once per pattern)
+__global__ void k_col_delta16(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                              int16_t *__restrict__ c16, int *flag) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    bool wide = false;
+    for (int32_t p = ptr[i]; p < ptr[i + 1]; ++p) {
+        const int32_t d = col[p] - i;
+        wide |= d < -32768 || d > 32767;
+        c16[p] = (int16_t)d;
+    }
+    if (wide) atomicOr(flag, 1);
+}
+
 // ---- compressed columns of a pattern (built once per pattern)
 // The distinct offsets column - row go into an open-addressed table; the
 // lanes of a warp that share an offset insert it once (match), and a key is
@@ -1315,7 +1333,7 @@ __global__ void k_smooth0_residual(int32_t n, const int32_t *__restrict__ ptr, C
     V s = 0;
     if (i < n)
         for (int32_t p = ptr[i] + sub; p < ptr[i + 1]; p += LPR) {
-            const int32_t j = ci.cidx ? i + s_off[ci.cidx[p]] : ci.col[p];
+            const int32_t j = col_at(ci, s_off, i, p);
             s = fma(val[p], m[j] * (V)f[j], s);
         }
     s = group_sum<LPR>(s);
@@ -1341,7 +1359,7 @@ __global__ void k_smooth_sweep(int32_t n, const int32_t *__restrict__ ptr, ColId
     V s = 0;
     if (i < n)
         for (int32_t p = ptr[i] + sub; p < ptr[i + 1]; p += LPR)
-            s = fma(val[p], u_in[ci.cidx ? i + s_off[ci.cidx[p]] : ci.col[p]], s);
+            s = fma(val[p], u_in[col_at(ci, s_off, i, p)], s);
     s = group_sum<LPR>(s);
     if (i < n && sub == 0) u_out[i] = (TO)fma(m[i], (V)f[i] - s, u_in[i]);
 }
@@ -1369,7 +1387,7 @@ __global__ void k_smooth_sweep_dot(int32_t n, const int32_t *__restrict__ ptr, C
         V s = 0;
         if (gt < total)
             for (int32_t p = ptr[i] + sub; p < ptr[i + 1]; p += LPR)
-                s = fma(val[p], u_in[ci.cidx ? i + s_off[ci.cidx[p]] : ci.col[p]], s);
+                s = fma(val[p], u_in[col_at(ci, s_off, i, p)], s);
         s = group_sum<LPR>(s);
         if (gt < total && sub == 0) {
             const double fi = f[i];
@@ -1397,7 +1415,7 @@ __global__ void k_residual(int32_t n, const int32_t *__restrict__ ptr, ColIdx ci
     V s = 0;
     if (i < n)
         for (int32_t p = ptr[i] + sub; p < ptr[i + 1]; p += LPR)
-            s = fma(val[p], u[ci.cidx ? i + s_off[ci.cidx[p]] : ci.col[p]], s);
+            s = fma(val[p], u[col_at(ci, s_off, i, p)], s);
     s = group_sum<LPR>(s);
     if (i < n && sub == 0) r[i] = (V)f[i] - s;
 }
@@ -1602,6 +1620,8 @@ __global__ void k_spmv_dot(int32_t n, const int32_t *__restrict__ ptr, ColIdx ci
         double s = 0.0;
         if (ci.cidx)
             for (int32_t e = ptr[i]; e < ptr[i + 1]; ++e) s = fma(val[e], p[i + s_off[ci.cidx[e]]], s);
+        else if (ci.c16)
+            for (int32_t e = ptr[i]; e < ptr[i + 1]; ++e) s = fma(val[e], p[i + (int32_t)ci.c16[e]], s);
         else
             for (int32_t e = ptr[i]; e < ptr[i + 1]; ++e) s = fma(val[e], p[ci.col[e]], s);
         q[i] = s;
@@ -1675,7 +1695,7 @@ __global__ void k_true_residual(int32_t n, const int32_t *__restrict__ ptr, ColI
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double s = 0.0;
         for (int32_t e = ptr[i]; e < ptr[i + 1]; ++e)
-            s = fma(val[e], u[ci.cidx ? i + s_off[ci.cidx[e]] : ci.col[e]], s);
+            s = fma(val[e], u[col_at(ci, s_off, i, e)], s);
         const double ti = f[i] - s;
         t[i] = ti;
         d = fma(ti, ti, d);
@@ -2298,6 +2318,10 @@ void launch_cg_update_ur(int32_t n, CgState *cg, const double *p, const double *
     count_launch();
     launch_pdl(k_cg_update_ur, cg_blocks(n), cg_threads(n), 0, s, n, cg, p, q, u, r, partial, zo, part_zo, use_h, hb,
                z0);
+}
+void launch_col_delta16(int32_t n, const int32_t *ptr, const int32_t *col, int16_t *c16, int *flag, cudaStream_t s) {
+    count_launch();
+    k_col_delta16<<<nblocks(n), kThreads, 0, s>>>(n, ptr, col, c16, flag);
 }
 void launch_col_offsets_collect(int32_t n, const int32_t *ptr, const int32_t *col, int32_t *table, int *count,
                                 cudaStream_t s) {

@@ -163,6 +163,28 @@ def random_banded_spd(n: int, band: int, density_: float, seed: int):
     return np.asarray(p, np.int32), np.asarray(c, np.int32), np.asarray(v, np.float64)
 
 
+def random_wide_spd(n: int, far: int, npairs: int, seed: int):
+    """A random symmetric, diagonally dominant sparse matrix: a random
+    tridiagonal band plus `npairs` symmetric couplings between rows at least
+    `far` apart (so that column offsets exceed 16 bits when far > 32767), in
+    sorted CSR form."""
+    import scipy.sparse as sps
+    rng = np.random.default_rng(seed)
+    r = np.arange(n - 1)
+    i = rng.integers(0, n - far, npairs)
+    j = np.minimum(i + far + rng.integers(0, n, npairs) % np.maximum(n - far - i, 1), n - 1)
+    rows = np.concatenate([r, i])
+    cols = np.concatenate([r + 1, j])
+    w = -rng.uniform(0.01, 1.0, rows.size)
+    U = sps.coo_matrix((w, (rows, cols)), shape=(n, n))
+    M = (U + U.T).tocsr()
+    M.sum_duplicates()
+    d = -np.asarray(M.sum(axis=1)).ravel() + rng.uniform(0.0, 0.5, n) + 1e-3
+    M = (M + sps.diags(d)).tocsr()
+    M.sort_indices()
+    return M.indptr.astype(np.int32), M.indices.astype(np.int32), M.data.astype(np.float64)
+
+
 def revalue_symmetric(ptr, col, val, seed: int, spread: float = 0.5):
     """New values on the same symmetric pattern: every off-diagonal pair scaled
     by one seeded factor in [1 - spread, 1 + spread], the diagonal reset to the

@@ -549,18 +549,27 @@ def test_coarse_inverse_every_size_class(n):
     assert np.linalg.norm(z - ref) <= 1e-12 * np.linalg.norm(ref) * np.linalg.cond(M)
 
 
-@pytest.mark.parametrize("band", [120, 140])
-def test_banded_patterns_through_both_column_forms(band):
+@pytest.mark.parametrize("form", ["one_byte", "two_byte", "int32"])
+def test_patterns_through_every_column_form(form):
     """The finest level's matrix kernels read one byte per entry when the rows
-    use at most 256 distinct column offsets (band 120: up to 241 offsets) and
-    the int32 columns otherwise (band 140: up to 281): hierarchy, V-cycle and
-    solve against the oracle either way."""
-    n = 1500
-    ptr, col, val = I.random_banded_spd(n, band, 0.04, seed=band)
+    use at most 256 distinct column offsets (band 120: up to 241 offsets),
+    two-byte offsets when they all fit in 16 bits (band 140: up to 281
+    distinct ones), and the int32 columns otherwise (couplings 40,000 rows
+    apart): the form reported, then hierarchy, V-cycle and solve against the
+    oracle in each."""
+    if form == "int32":
+        n = 48000
+        ptr, col, val = I.random_wide_spd(n, 40000, 300, seed=5)
+    else:
+        n = 1500
+        band = 120 if form == "one_byte" else 140
+        ptr, col, val = I.random_banded_spd(n, band, 0.04, seed=band)
     offs = np.unique(col - np.repeat(np.arange(n), np.diff(ptr)))
-    assert (offs.size <= 256) == (band == 120)
+    assert (offs.size <= 256) == (form == "one_byte")
+    assert (np.abs(offs).max() > 32767) == (form == "int32")
     G = B.AMG(coarse_enough=40)
     G.full_setup(*(torch.tensor(a, device="cuda") for a in (ptr, col, val)))
+    assert G.pattern_info()[0] == {"one_byte": 1, "two_byte": 2, "int32": 4}[form]
     H = O.Hierarchy(ptr, col, val, O.Params(coarse_enough=40))
     compare_hierarchy(G, H)
     r = np.random.default_rng(9).normal(size=n)
