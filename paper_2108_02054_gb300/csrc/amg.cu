@@ -417,28 +417,44 @@ amg_status numeric_rebuild(amg_ctx *ctx, const double *d_val, bool galerkin) {
     return coarse_factor(ctx);
 }
 
-// Two-byte column offsets (column - row) for every level without the
-// one-byte form, kept where all of a level's offsets fit in 16 bits (a
-// coarse level of a grid hierarchy: up to about 24,000 at 192^3); the matrix
-// kernels of those levels then move 2 bytes less per entry.  Built once per
-// full setup: the patterns stay fixed across partial rebuilds.
+// Two-byte column offsets for every level without the one-byte form: A's
+// columns as column - row, P's as column - (int)(row * n_c / n); each kept
+// where all of a level's offsets fit in 16 bits (a coarse level of a grid
+// hierarchy: up to about 24,000 at 192^3; the finest level's P: about
+// 11,000), so the matrix kernels and the prolongation move 2 bytes less per
+// entry.  Built once per full setup: the patterns stay fixed across partial
+// rebuilds.
 amg_status build_delta16(amg_ctx *ctx) {
     if (blockmode(ctx)) return AMG_OK;
     int *flags = nullptr;
-    TRY(alloc(ctx, &flags, (size_t)kMaxLevels));
-    CK(cudaMemsetAsync(flags, 0, sizeof(int) * kMaxLevels, ctx->s));
-    int16_t *buf[kMaxLevels] = {};
+    TRY(alloc(ctx, &flags, (size_t)(2 * kMaxLevels)));
+    CK(cudaMemsetAsync(flags, 0, sizeof(int) * 2 * kMaxLevels, ctx->s));
+    int16_t *buf[kMaxLevels] = {}, *pbuf[kMaxLevels] = {};
+    float ratio[kMaxLevels] = {};
     for (int l = 0; l < ctx->nlev; ++l) {
         Level &L = ctx->lev[l];
-        if (L.A_cidx || L.n <= 0 || L.nnz <= 0) continue;
-        TRY(alloc(ctx, &buf[l], (size_t)L.nnz));
-        launch_col_delta16(L.n, L.A_ptr, L.A_col, buf[l], flags + l, ctx->s);
+        if (!L.A_cidx && L.n > 0 && L.nnz > 0) {
+            TRY(alloc(ctx, &buf[l], (size_t)L.nnz));
+            launch_col_delta16(L.n, L.A_ptr, L.A_col, 0.0f, buf[l], flags + l, ctx->s);
+        }
+        // P (fine rows, coarse columns): offsets from the row's linear image
+        // in the coarse numbering
+        if (l + 1 < ctx->nlev && L.P_col && L.nnzP > 0 && L.nc > 0) {
+            ratio[l] = (float)L.nc / (float)L.n;
+            TRY(alloc(ctx, &pbuf[l], (size_t)L.nnzP));
+            launch_col_delta16(L.n, L.P_ptr, L.P_col, ratio[l], pbuf[l], flags + kMaxLevels + l, ctx->s);
+        }
     }
-    int h[kMaxLevels] = {};
+    int h[2 * kMaxLevels] = {};
     CK(cudaMemcpyAsync(h, flags, sizeof(h), cudaMemcpyDeviceToHost, ctx->s));
     CK(cudaStreamSynchronize(ctx->s));
-    for (int l = 0; l < ctx->nlev; ++l)
+    for (int l = 0; l < ctx->nlev; ++l) {
         if (buf[l] && h[l] == 0) ctx->lev[l].A_c16 = buf[l];
+        if (pbuf[l] && h[kMaxLevels + l] == 0) {
+            ctx->lev[l].P_c16 = pbuf[l];
+            ctx->lev[l].P_ratio = ratio[l];
+        }
+    }
     return AMG_OK;
 }
 

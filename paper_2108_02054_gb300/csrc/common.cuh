@@ -83,6 +83,9 @@ struct Level {
     // transfer operators (absent on the coarsest level)
     int32_t nc = 0, nnzP = 0, nnzR = 0, nnzAP = 0;
     int32_t *P_ptr = nullptr, *P_col = nullptr;
+    // P's columns as two-byte offsets from (int)(row * P_ratio), when they fit
+    int16_t *P_c16 = nullptr;
+    float P_ratio = 0.0f;
     double *P_val = nullptr;
     float *P_valf = nullptr;
     int32_t *R_ptr = nullptr, *R_col = nullptr;
@@ -285,8 +288,10 @@ void launch_spmv_dot(int32_t n, const int32_t *ptr, const ColIdx &col, const dou
 // off (noff entries)
 constexpr int kColOffsetSlots = 1024;
 constexpr int32_t kColOffsetEmpty = (int32_t)0x80808080u;
-// c16[p] = col[p] - row for every entry; *flag = 1 if an offset does not fit
-void launch_col_delta16(int32_t n, const int32_t *ptr, const int32_t *col, int16_t *c16, int *flag, cudaStream_t s);
+// c16[p] = col[p] - base(row) for every entry, base(i) = i (ratio == 0) or
+// (int)((float)i * ratio); *flag = 1 if an offset does not fit in 16 bits
+void launch_col_delta16(int32_t n, const int32_t *ptr, const int32_t *col, float ratio, int16_t *c16, int *flag,
+                        cudaStream_t s);
 void launch_col_offsets_collect(int32_t n, const int32_t *ptr, const int32_t *col, int32_t *table, int *count,
                                 cudaStream_t s);
 void launch_col_offsets_encode(int32_t n, const int32_t *ptr, const int32_t *col, const int32_t *off, int noff,

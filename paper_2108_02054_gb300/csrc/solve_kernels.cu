@@ -1216,13 +1216,17 @@ k_lu_inverse_t(int32_t n, const double *__restrict__ luT, const int32_t *__restr
 }
 
 // ---- two-byte column offsets (built once per pattern)
+__device__ __forceinline__ int32_t delta16_base(int32_t i, float ratio) {
+    return ratio == 0.0f ? i : __float2int_rz((float)i * ratio);
+}
 __global__ void k_col_delta16(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
-                              int16_t *__restrict__ c16, int *flag) {
+                              float ratio, int16_t *__restrict__ c16, int *flag) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const int32_t b = delta16_base(i, ratio);
     bool wide = false;
     for (int32_t p = ptr[i]; p < ptr[i + 1]; ++p) {
-        const int32_t d = col[p] - i;
+        const int32_t d = col[p] - b;
         wide |= d < -32768 || d > 32767;
         c16[p] = (int16_t)d;
     }
@@ -1441,17 +1445,23 @@ __global__ void k_restrict(int32_t nc, const int32_t *__restrict__ R_ptr, const 
     }
 }
 
-// u += P u_c
+// u += P u_c (P's columns as int32, or as two-byte offsets from
+// (int)(row * ratio) when they fit)
 template <class V>
 __global__ void k_prolong(int32_t n, const int32_t *__restrict__ P_ptr, const int32_t *__restrict__ P_col,
-                          const V *__restrict__ P_val, const V *__restrict__ uc, V *__restrict__ u,
-                          const int *skip) {
+                          const int16_t *__restrict__ P_c16, float ratio, const V *__restrict__ P_val,
+                          const V *__restrict__ uc, V *__restrict__ u, const int *skip) {
     pdl_wait();
     if (skipped(skip)) return;
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     V s = u[i];
-    for (int32_t p = P_ptr[i]; p < P_ptr[i + 1]; ++p) s = fma(P_val[p], uc[P_col[p]], s);
+    if (P_c16) {
+        const int32_t b = delta16_base(i, ratio);
+        for (int32_t p = P_ptr[i]; p < P_ptr[i + 1]; ++p) s = fma(P_val[p], uc[b + (int32_t)P_c16[p]], s);
+    } else {
+        for (int32_t p = P_ptr[i]; p < P_ptr[i + 1]; ++p) s = fma(P_val[p], uc[P_col[p]], s);
+    }
     u[i] = s;
 }
 
@@ -2226,7 +2236,8 @@ void launch_restrict(const Level &L, const V *Rval, const V *r, V *fc, const V *
 template <class V>
 void launch_prolong(const Level &L, const V *Pval, const V *uc, V *u, const int *skip, cudaStream_t s) {
     count_launch();
-    launch_pdl(k_prolong<V>, nblocks(L.n), kThreads, 0, s, L.n, L.P_ptr, L.P_col, Pval, uc, u, skip);
+    launch_pdl(k_prolong<V>, nblocks(L.n), kThreads, 0, s, L.n, L.P_ptr, L.P_col, (const int16_t *)L.P_c16, L.P_ratio,
+               Pval, uc, u, skip);
 }
 template <class V, class TF, class TO>
 void launch_coarse_solve(int32_t n, const double *inv, const TF *f, TO *u, const int *skip, cudaStream_t s) {
@@ -2319,9 +2330,10 @@ void launch_cg_update_ur(int32_t n, CgState *cg, const double *p, const double *
     launch_pdl(k_cg_update_ur, cg_blocks(n), cg_threads(n), 0, s, n, cg, p, q, u, r, partial, zo, part_zo, use_h, hb,
                z0);
 }
-void launch_col_delta16(int32_t n, const int32_t *ptr, const int32_t *col, int16_t *c16, int *flag, cudaStream_t s) {
+void launch_col_delta16(int32_t n, const int32_t *ptr, const int32_t *col, float ratio, int16_t *c16, int *flag,
+                        cudaStream_t s) {
     count_launch();
-    k_col_delta16<<<nblocks(n), kThreads, 0, s>>>(n, ptr, col, c16, flag);
+    k_col_delta16<<<nblocks(n), kThreads, 0, s>>>(n, ptr, col, ratio, c16, flag);
 }
 void launch_col_offsets_collect(int32_t n, const int32_t *ptr, const int32_t *col, int32_t *table, int *count,
                                 cudaStream_t s) {
