@@ -615,7 +615,6 @@ constexpr int kLuPipeWarps = 4;                           // compute warps, one 
 constexpr int kLuPipeThreads = (kLuPipeWarps + 1) * 32;   // and the sender warp
 constexpr int kLuPipeC = 8;                               // CTAs of the cluster
 constexpr int kLuPipeB = 4;                               // columns per ownership block
-constexpr bool kLuPipeIntDiv = true;                      // multipliers by div_rn
 constexpr long long kLuPipeWaitClocks = 2000000000ll;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -673,9 +672,8 @@ template <int B>
 struct PivCand {
     unsigned long long key;
     int32_t pos, row;
-    double val;
     double vals[B];  // the row's values in the block's columns
-    DivRecip rc;     // reciprocal of val
+    DivRecip rc;     // reciprocal of its value in the step's column
 };
 // header of step k: pivot position, pivot row, singular flag
 __device__ __forceinline__ unsigned long long piv_header(int32_t p, int32_t row, bool sing) {
@@ -706,7 +704,7 @@ size_t lu_pipe_smem(int32_t n, int C, int B) {
     return ((size_t)lu_pipe_even(n) + (size_t)(n > 0 ? n - 1 : 0) * lu_pipe_row(n) + per * n) * 8;
 }
 
-template <int C, int B, bool IntDiv>
+template <int C, int B>
 __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kLuPipeThreads)
 k_dense_lu_pipe(int32_t n, double *__restrict__ g, double *__restrict__ gT, int32_t *__restrict__ piv, int *st) {
     extern __shared__ __align__(16) unsigned long long sm_pipe[];
@@ -859,8 +857,7 @@ k_dense_lu_pipe(int32_t n, double *__restrict__ g, double *__restrict__ gT, int3
                     }
             }
             // the block's steps
-            DivRecip rc;  // reciprocal of this lane's value in the step's column
-            if (IntDiv) rc = div_recip(vb[0]);
+            DivRecip rc = div_recip(vb[0]);  // reciprocal of this lane's value in the step's column
             int32_t pk[B];  // the block's pivots, stored at the end of the block
 #pragma unroll
             for (int t = 0; t < B; ++t) {
@@ -887,10 +884,9 @@ k_dense_lu_pipe(int32_t n, double *__restrict__ g, double *__restrict__ gT, int3
                     c.key = key;
                     c.pos = pos;
                     c.row = r;
-                    c.val = v;
 #pragma unroll
                     for (int q = 0; q < B; ++q) c.vals[q] = vb[q];
-                    if (IntDiv) c.rc = rc;
+                    c.rc = rc;
                 }
                 lu_sync();
                 int bw = 0;
@@ -928,12 +924,9 @@ k_dense_lu_pipe(int32_t n, double *__restrict__ g, double *__restrict__ gT, int3
                 else if (pos == k) pos = bpos;
                 const bool act = valid && pstep > k;
                 double l = 0.0;
-                if (IntDiv) {
+                {
                     const DivRecip brc = best.rc;
                     if (act) l = div_rn(v, brc);
-                } else {
-                    const double akk = best.val;
-                    if (act) l = v / akk;
                 }
                 double u[B];
 #pragma unroll
@@ -941,7 +934,7 @@ k_dense_lu_pipe(int32_t n, double *__restrict__ g, double *__restrict__ gT, int3
                 // the block's next column first: the next step waits for it
                 if (t + 1 < nb) {
                     if (act) vb[t + 1] = fma(-l, u[t + 1], vb[t + 1]);
-                    if (IntDiv) rc = div_recip(vb[t + 1]);
+                    rc = div_recip(vb[t + 1]);
                 }
                 if (act) {
                     vb[t] = l;
@@ -2128,10 +2121,10 @@ void launch_dense_lu(int32_t n, double *a, int32_t *piv, int *st, cudaStream_t s
     static bool attr = false;
     const int max_bytes = kLuSmemN * kLuSmemN * (int)sizeof(double);
     if (!attr) {
-        cudaFuncSetAttribute(k_dense_lu_pipe<kLuPipeC, kLuPipeB, kLuPipeIntDiv>,
+        cudaFuncSetAttribute(k_dense_lu_pipe<kLuPipeC, kLuPipeB>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lu_pipe_smem(kLuPipeN, kLuPipeC, kLuPipeB));
         if (kLuPipeC > 8)
-            cudaFuncSetAttribute(k_dense_lu_pipe<kLuPipeC, kLuPipeB, kLuPipeIntDiv>,
+            cudaFuncSetAttribute(k_dense_lu_pipe<kLuPipeC, kLuPipeB>,
                                  cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         cudaFuncSetAttribute(k_dense_lu_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         cudaFuncSetAttribute(k_dense_lu_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2143,7 +2136,7 @@ void launch_dense_lu(int32_t n, double *a, int32_t *piv, int *st, cudaStream_t s
     }
     count_launch();
     if (n > kLuPipeMinN && n <= kLuPipeN)
-        k_dense_lu_pipe<kLuPipeC, kLuPipeB, kLuPipeIntDiv>
+        k_dense_lu_pipe<kLuPipeC, kLuPipeB>
             <<<kLuPipeC, kLuPipeThreads, lu_pipe_smem(n, kLuPipeC, kLuPipeB), s>>>(n, a, aT, piv, st);
     else if (n <= kLuSmemN)
         k_dense_lu_smem<<<1, kLuThreads, (size_t)n * n * sizeof(double), s>>>(n, a, piv, st);
