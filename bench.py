@@ -561,6 +561,7 @@ def run_ours(args):
                          "us_per_launch": per * 1e3, "us_per_launch_timed": per_raw * 1e3,
                          "algorithmic_bytes": by,
                          "achieved_gbs": (by / (per * 1e-3) / 1e9) if by else None,
+                         "frac_of_copy": round(by / (per * 1e-3) / 1e9 / peak, 4) if by else None,
                          "algorithmic_flops": fl,
                          "achieved_fp64_tflops": (fl / (per * 1e-3) / 1e12) if fl else None}
     dom = max((k for k in kernels if kernels[k]["achieved_gbs"]), key=lambda k: kernels[k]["ms_total_per_step"])
