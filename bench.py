@@ -68,8 +68,10 @@ def parse():
                     help="timed steps of the full-rebuild and full-reuse comparison runs")
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the oracle leg (the CPU baseline and the per-step error against the oracle)")
-    ap.add_argument("--oracle-samples", type=int, default=5,
-                    help="sampled time steps (0, 1, 2, then every 10th) run by the oracle leg")
+    ap.add_argument("--oracle-samples", type=int, default=-1,
+                    help="time steps run by the oracle leg: the first N of 0, 1, 2, then every 10th; "
+                         "default: every step up to the last timed one on the grids that fit L2 "
+                         "(2d32, 3d64), the first 5 of that set on the larger ones")
     ap.add_argument("--eager-profile", action="store_true",
                     help="time the per-kernel run on the host-driven launch loop (every kernel a separate "
                          "launch; for ncu launch lists, which do not see some kernel nodes of a graph)")
@@ -319,6 +321,15 @@ def sampled_steps(T, count, upto):
     return seq[:max(count, 0)]
 
 
+def oracle_steps(w, count, upto):
+    """The oracle leg's steps: `count` < 0 picks the default, every step up to
+    `upto` on the small grids (2d32, 3d64: well under a second each), the
+    first 5 sampled steps on the larger ones (seconds each)."""
+    if count < 0:
+        return list(range(0, upto + 1)) if w.n <= 262144 else sampled_steps(w.T, 5, upto)
+    return sampled_steps(w.T, count, upto)
+
+
 def cpu_cores():
     """(os.cpu_count(), the cores this process may run on)."""
     try:
@@ -496,7 +507,7 @@ def run_ours(args):
     pool = async_res = tmpdir = None
     samples = []
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        samples = sampled_steps(w.T, args.oracle_samples, max([0] + warm_idx + timed_idx))
+        samples = oracle_steps(w, args.oracle_samples, max([0] + warm_idx + timed_idx))
         if samples:
             tmpdir = tf.mkdtemp(prefix="amg_oracle_")
             nwork = oracle_workers(len(samples), w.n)

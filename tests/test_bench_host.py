@@ -72,6 +72,11 @@ def test_reference_arm_config_matches_ours():
     assert warm == [1, 2, 3] and timed == list(range(4, 24))
     assert bench.sampled_steps(w.T, 5, max(timed)) == [0, 1, 2, 10, 20]
     assert bench.sampled_steps(10, 9, 9) == [0, 1, 2]
+    # the default oracle leg: sampled steps on the large grids, every step on the small ones
+    assert bench.oracle_steps(w, -1, max(timed)) == [0, 1, 2, 10, 20]
+    w64 = I.WORKLOADS["3d64"]
+    assert bench.oracle_steps(w64, -1, 23) == list(range(24))
+    assert bench.oracle_steps(w64, 3, 23) == [0, 1, 2]
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "2d32",
                           "--steps", "3", "--warmup", "1"], capture_output=True, text=True, timeout=300, cwd=ROOT)
     assert out.returncode == 0, out.stderr
