@@ -152,8 +152,11 @@ amg_status amg_apply_vcycle(amg_ctx *ctx, const double *d_r, double *d_z);
 
 /* End to end with host buffers: copies h_val (nnz doubles) and h_f (n doubles)
  * to the device, runs amg_step and amg_solve, copies u back to h_u (n
- * doubles) and synchronises.  The pattern must already be known (a previous
- * amg_full_setup or amg_step). */
+ * doubles) and synchronises.  h_f's copy runs on the context's own copy
+ * stream while the step's rebuild runs; every copy has ended when the call
+ * returns, whatever its status.  Pinned host buffers give the full copy
+ * rate.  The pattern must already be known (a previous amg_full_setup or
+ * amg_step). */
 amg_status amg_step_solve_host(amg_ctx *ctx, const double *h_val, const double *h_f, double *h_u,
                                double tol, amg_info *info);
 

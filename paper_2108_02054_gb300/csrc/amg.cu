@@ -79,6 +79,9 @@ struct amg_ctx {
     ProfData prof;
     // whole-solve CUDA graph (rebuilt after a full setup or a new tolerance)
     cudaStream_t s_cap = nullptr, s_cap_main = nullptr, s_cap_if = nullptr;
+    // host-buffer entry point: the right-hand side's copy runs beside the rebuild
+    cudaStream_t s_copy = nullptr;
+    cudaEvent_t ev_vals = nullptr, ev_f = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     bool use_graph = true;
@@ -1435,6 +1438,9 @@ amg_status amg_create(amg_ctx **out, const amg_params *prm, void *cuda_stream) {
     if (cudaStreamCreateWithFlags(&ctx->s_cap, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&ctx->s_cap_main, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&ctx->s_cap_if, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->s_copy, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_vals, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_f, cudaEventDisableTiming) != cudaSuccess ||
         cudaMallocHost(&ctx->h_cg, sizeof(CgState)) != cudaSuccess ||
         cudaMallocHost(&ctx->h_bi, sizeof(BiState)) != cudaSuccess ||
         cudaMallocHost(&ctx->h_st, sizeof(int)) != cudaSuccess ||
@@ -1456,6 +1462,12 @@ void amg_destroy(amg_ctx *ctx) {
     if (ctx->s_cap) cudaStreamDestroy(ctx->s_cap);
     if (ctx->s_cap_main) cudaStreamDestroy(ctx->s_cap_main);
     if (ctx->s_cap_if) cudaStreamDestroy(ctx->s_cap_if);
+    if (ctx->s_copy) {
+        cudaStreamSynchronize(ctx->s_copy);
+        cudaStreamDestroy(ctx->s_copy);
+    }
+    if (ctx->ev_vals) cudaEventDestroy(ctx->ev_vals);
+    if (ctx->ev_f) cudaEventDestroy(ctx->ev_f);
     for (auto &v : ctx->prof.rec)
         for (auto &pr : v) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
@@ -1590,11 +1602,25 @@ amg_status amg_step_solve_host(amg_ctx *ctx, const double *h_val, const double *
     if (!ctx->fine_ptr) return set_err(ctx, AMG_ERR_STATE, "no pattern: call amg_full_setup or amg_step first");
     if (!h_val || !h_f || !h_u) return set_err(ctx, AMG_ERR_ARG, "null host buffer");
     CK(cudaMemcpyAsync(ctx->stage_val, h_val, sizeof(double) * nvals(ctx), cudaMemcpyHostToDevice, ctx->s));
-    CK(cudaMemcpyAsync(ctx->stage_f, h_f, sizeof(double) * (size_t)nvec(ctx), cudaMemcpyHostToDevice, ctx->s));
+    // the right-hand side is needed only by the solve: copied on a side stream
+    // while the step's rebuild runs, after the values (so the two copies do
+    // not share the link)
+    CK(cudaEventRecord(ctx->ev_vals, ctx->s));
+    CK(cudaStreamWaitEvent(ctx->s_copy, ctx->ev_vals, 0));
+    CK(cudaMemcpyAsync(ctx->stage_f, h_f, sizeof(double) * (size_t)nvec(ctx), cudaMemcpyHostToDevice, ctx->s_copy));
+    CK(cudaEventRecord(ctx->ev_f, ctx->s_copy));
+    // the caller's buffers stay in use until their copies end: an early
+    // return waits for both streams
+    auto drain = [ctx](amg_status r) {
+        cudaStreamSynchronize(ctx->s);
+        cudaStreamSynchronize(ctx->s_copy);
+        return r;
+    };
     amg_status st = amg_step(ctx, ctx->n, ctx->nnz, ctx->fine_ptr, ctx->fine_col, ctx->stage_val, info);
-    if (st != AMG_OK) return st;
+    if (st != AMG_OK) return drain(st);
+    if (cudaStreamWaitEvent(ctx->s, ctx->ev_f, 0) != cudaSuccess) return drain(AMG_ERR_CUDA);
     st = amg_solve(ctx, ctx->stage_f, ctx->stage_u, tol, info);
-    if (st != AMG_OK && st != AMG_NOT_CONVERGED) return st;
+    if (st != AMG_OK && st != AMG_NOT_CONVERGED) return drain(st);
     CK(cudaMemcpyAsync(h_u, ctx->stage_u, sizeof(double) * (size_t)nvec(ctx), cudaMemcpyDeviceToHost, ctx->s));
     CK(cudaStreamSynchronize(ctx->s));
     return st;

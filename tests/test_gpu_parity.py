@@ -289,20 +289,32 @@ def test_time_series_modes_match_oracle(mode, flavour):
             assert info.rel_resid <= 1e-8
 
 
-def test_host_buffer_entry_point():
+@pytest.mark.parametrize("pinned", [False, True])
+def test_host_buffer_entry_point(pinned):
+    """amg_step_solve_host against the oracle's rebuild + PCG, from pageable
+    and from pinned host buffers (where the right-hand side's copy runs
+    asynchronously beside the rebuild); two calls in a row with different
+    values and right-hand sides, so a solve that started before its new
+    right-hand side landed would fail the second comparison."""
     dim, N = 3, 24
     ptr, col, v0 = gpu_problem(dim, N, 0, 4)
     G = B.AMG()
     G.step(v0, ptr, col)
-    f = I.rhs(N ** 3)
-    hv = np.ascontiguousarray(oracle_problem(dim, N, 2, 4)[2])
-    hu = np.zeros(N ** 3)
-    info = G.step_solve_host(hv, f, hu, 1e-8)
     H = O.Hierarchy(*oracle_problem(dim, N, 0, 4))
-    H.rebuild(hv)
-    uo, it, rr, st = H.pcg(f, 1e-8)
-    assert info.status == 0 and abs(info.iters - it) <= 1
-    assert np.linalg.norm(hu - uo) <= 1e-5 * np.linalg.norm(uo)
+
+    def host(a):
+        t = torch.tensor(np.ascontiguousarray(a))
+        return (t.pin_memory() if pinned else t).numpy()
+
+    for k, seed in ((2, 0), (3, 11)):
+        f = host(I.rhs(N ** 3, seed=seed))
+        hv = host(oracle_problem(dim, N, k, 4)[2])
+        hu = host(np.zeros(N ** 3))
+        info = G.step_solve_host(hv, f, hu, 1e-8)
+        H.rebuild(np.array(hv))
+        uo, it, rr, st = H.pcg(np.array(f), 1e-8)
+        assert info.status == 0 and abs(info.iters - it) <= 1
+        assert np.linalg.norm(hu - uo) <= 1e-5 * np.linalg.norm(uo)
 
 
 # ------------------------------------------------------------------ mixed precision
