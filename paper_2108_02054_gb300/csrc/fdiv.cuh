@@ -1,4 +1,5 @@
-// Correctly rounded FP64 division in integer arithmetic.
+// Correctly rounded FP64 division, and FP64 -> FP32 conversion, in integer
+// arithmetic.
 //
 // On this part an FP64 division takes about 565 cycles (its refinement steps
 // run on the FP64 pipe, 64 cycles per warp instruction), while 32-bit integer
@@ -166,6 +167,48 @@ __device__ __forceinline__ double div_rn(double num, const DivRecip &R) {
         (long long)(((xb ^ R.sgn) & 0x8000000000000000ull) | ((unsigned long long)be << 52) | (m & 0x000fffffffffffffull)));
 }
 
+
+
+// Whether x is finite, from its exponent bits (the FP64 compare would run on
+// the FP64 pipe).
+__device__ __forceinline__ bool finite_bits(double x) {
+    return ((unsigned long long)__double_as_longlong(x) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
+}
+
+// (float)x rounded to nearest, ties to even, from the IEEE 754 formats: on
+// this part the conversion instruction runs on the FP64 pipe (about as slow
+// as an FP64 add), these integer steps do not.  Worth it where the FP64 pipe
+// bounds a kernel (the finest level's copy-and-cast), not elsewhere (measured
+// slower in the V-cycle kernels).  The 52-bit significand drops
+// 29 bits (normal results) or more (subnormal results, shift 52 - (e + 149)
+// for an unbiased exponent e), rounded from the dropped bits; a carry out of
+// the significand moves to the next exponent (up to infinity).  Infinities
+// and NaNs use the conversion instruction.
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;
+    const int eb = (int)((b >> 52) & 0x7ff);
+    if (eb == 0x7ff) return (float)x;
+    const int e = eb - 1023;
+    if (e > 127) return __uint_as_float(sgn | 0x7f800000u);
+    const unsigned long long full = (b & 0x000fffffffffffffull) | (eb ? 0x0010000000000000ull : 0ull);
+    // result = round(full * 2^(e - 52)) in units of the float's last place:
+    // 2^(e - 23) for normal results, 2^-149 for subnormal ones
+    const int sh = e >= -126 ? 29 : 52 - (e + 149);
+    if (eb == 0 || sh > 63) return __uint_as_float(sgn);
+    unsigned long long q = full >> sh;
+    const unsigned long long rem = full & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (q & 1ull))) q += 1ull;
+    unsigned bits;
+    if (e >= -126) {
+        // q in [2^23, 2^24]: the hidden bit and 23 fraction bits (2^24: a carry)
+        bits = (unsigned)((unsigned long long)(e + 127) << 23) + (unsigned)(q - (1ull << 23));
+        if (bits >= 0x7f800000u) bits = 0x7f800000u;
+    } else {
+        bits = (unsigned)q;  // subnormal (2^23: the smallest normal)
+    }
+    return __uint_as_float(sgn | bits);
+}
 
 
 }  // namespace amgpr

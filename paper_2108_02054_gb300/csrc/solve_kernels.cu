@@ -327,12 +327,15 @@ __global__ void k_ingest_fine(int32_t n, const int32_t *__restrict__ ptr, const 
     if (r0 >= n) return;  // warp-uniform
     const int32_t r1 = min(r0 + 32, n);
     const int32_t p0 = ptr[r0], p1 = ptr[r1];
+    // (the finiteness test, the FP32 cast and the division below are done in
+    // integer arithmetic with the same results: on this part their FP64
+    // instructions bound the kernel)
     bool finite = true;
     for (int32_t p = p0 + lane; p < p1; p += 32) {
         const double v = in[p];
-        finite = finite && isfinite(v);
+        finite = finite && finite_bits(v);
         if (out) out[p] = v;
-        if (outf) outf[p] = (float)v;
+        if (outf) outf[p] = f64_to_f32_rn(v);
     }
     if (__any_sync(0xffffffffu, !finite) && lane == 0) atomicOr(st, DEV_ERR_NONFINITE);
     const int32_t i = r0 + lane;
@@ -344,10 +347,10 @@ __global__ void k_ingest_fine(int32_t n, const int32_t *__restrict__ ptr, const 
     }
     const double aii = in[dia[i]];
     double mi;
-    if (type == AMG_SMOOTHER_SPAI0) mi = s != 0.0 ? aii / s : 0.0;
-    else mi = aii != 0.0 ? wj / aii : 0.0;
+    if (type == AMG_SMOOTHER_SPAI0) mi = s != 0.0 ? div_rn(aii, div_recip(s)) : 0.0;
+    else mi = aii != 0.0 ? div_rn(wj, div_recip(aii)) : 0.0;
     if (m) m[i] = mi;
-    if (mf) mf[i] = (float)mi;
+    if (mf) mf[i] = f64_to_f32_rn(mi);
 }
 
 __global__ void k_cast_f32(int64_t n, const double *__restrict__ in, float *__restrict__ out) {

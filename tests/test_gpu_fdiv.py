@@ -1,5 +1,7 @@
-"""The integer FP64 division used for the coarsest LU's multipliers
-(csrc/fdiv.cuh) against IEEE division: a small CUDA program built here runs
+"""The integer FP64 division used for the coarsest LU's multipliers and the
+finest smoother (csrc/fdiv.cuh) against IEEE division, and its FP64 -> FP32
+conversion against the conversion instruction: a small CUDA program built
+here runs
 div_rn on classes of inputs chosen to hit its edges (random operands across
 the normal range, raw 64-bit patterns with zeros, subnormals, infinities and
 NaNs, significands near all-ones and near one, every pair of small integers,
@@ -70,6 +72,19 @@ __global__ void k_check(int cls, long long n, unsigned long long *bad, long long
         if (i < ns) { sx[i] = x; sd[i] = d; sq[i] = q; }
     }
 }
+__global__ void k_cvt(int cls, long long n, unsigned long long *bad, long long ns, double *sx, float *sq) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long a = mix(0x9E3779B97F4A7C15ull * (unsigned long long)(i + 1) + 77 + cls);
+        unsigned long long b = a;
+        if (cls == 1) b = (a & 0x800fffffffffffffull) | ((unsigned long long)(1023 - 160 + (a >> 56) %% 320) << 52);
+        if (cls == 2) b = (a & 0x800000001fffffffull) | ((unsigned long long)(1023 - 150 + (a >> 58) %% 30) << 52) |
+                          (((a >> 20) & 1ull) << 28);
+        const double x = __longlong_as_double((long long)b);
+        const float q = f64_to_f32_rn(x), h = (float)x;
+        if (!((q != q && h != h) || __float_as_uint(q) == __float_as_uint(h))) atomicAdd(bad, 1ull);
+        if (i < ns) { sx[i] = x; sq[i] = q; }
+    }
+}
 int main(int argc, char **argv) {
     const long long n = atoll(argv[1]), ns = atoll(argv[2]);
     unsigned long long *bad; double *s;
@@ -91,6 +106,22 @@ int main(int argc, char **argv) {
         fwrite(&k, 8, 1, f);
         fwrite(buf, 8, 3 * k, f);
     }
+    // FP64 -> FP32: three classes (random bits, around the float range, near ties in the subnormal range)
+    for (int cls = 0; cls < 3; ++cls) {
+        cudaMemset(bad, 0, 8);
+        k_cvt<<<1216, 256>>>(cls, n, bad, ns, s, (float *)(s + ns));
+        if (cudaDeviceSynchronize() != cudaSuccess) return 2;
+        unsigned long long h;
+        cudaMemcpy(&h, bad, 8, cudaMemcpyDeviceToHost);
+        printf("cvt%%d %%lld %%llu\n", cls, n, h);
+        static double bx[2000000];
+        static float bq[2000000];
+        cudaMemcpy(bx, s, 8 * ns, cudaMemcpyDeviceToHost);
+        cudaMemcpy(bq, s + ns, 4 * ns, cudaMemcpyDeviceToHost);
+        fwrite(&ns, 8, 1, f);
+        fwrite(bx, 8, ns, f);
+        fwrite(bq, 4, ns, f);
+    }
     fclose(f);
     return 0;
 }
@@ -98,17 +129,17 @@ int main(int argc, char **argv) {
 
 
 @pytest.mark.gpu
-def test_integer_division_is_ieee_division(tmp_path):
+def test_integer_fp64_arithmetic_is_ieee(tmp_path):
     src = tmp_path / "fdiv_check.cu"
     src.write_text(SRC % {"header": HEADER})
     exe = tmp_path / "fdiv_check"
     subprocess.check_call([PB._nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", str(exe), str(src)])
     samples = tmp_path / "samples.bin"
     out = subprocess.run([str(exe), "20000000", "400000", str(samples)], capture_output=True, text=True, check=True)
-    rows = [tuple(int(v) for v in line.split()) for line in out.stdout.split("\n") if line.strip()]
-    assert len(rows) == 5
+    rows = [line.split() for line in out.stdout.split("\n") if line.strip()]
+    assert len(rows) == 8
     for cls, n, bad in rows:
-        assert bad == 0, (cls, n, bad)
+        assert int(bad) == 0, (cls, n, bad)
     raw = np.fromfile(samples, dtype=np.uint8)
     off = 0
     for _ in range(5):
@@ -121,3 +152,14 @@ def test_integer_division_is_ieee_division(tmp_path):
             ref = x / d
         same = (q.view(np.int64) == ref.view(np.int64)) | (np.isnan(q) & np.isnan(ref))
         assert same.all(), (x[~same][:3], d[~same][:3], q[~same][:3], ref[~same][:3])
+    for _ in range(3):
+        k = int(raw[off:off + 8].view(np.int64)[0])
+        off += 8
+        x = raw[off:off + 8 * k].view(np.float64)
+        off += 8 * k
+        q = raw[off:off + 4 * k].view(np.float32)
+        off += 4 * k
+        with np.errstate(all="ignore"):
+            ref = x.astype(np.float32)
+        same = (q.view(np.int32) == ref.view(np.int32)) | (np.isnan(q) & np.isnan(ref))
+        assert same.all(), (x[~same][:3], q[~same][:3], ref[~same][:3])
