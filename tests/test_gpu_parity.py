@@ -516,6 +516,35 @@ def test_coarsest_lu_with_tied_pivots_and_singular_input(n, dup):
     assert np.array_equal(lu, olu)
 
 
+@pytest.mark.parametrize("j", [0, 3, 4, 31, 32, 50, 85, 86])
+def test_pipelined_lu_zero_column_at_every_position(j):
+    """A zero column j makes the elimination meet an all-zero candidate column
+    exactly at step j (earlier steps subtract multiples of zeros from it). In
+    the pipelined cluster kernel (n = 87, four-column blocks dealt to eight
+    CTAs) j = 0, 3, 4, 31, 32, 50, 85, 86 put that step first or last in an
+    owner's block, at an owner change, and at the final step (which sends no
+    message): the setup reports ERR_SINGULAR as the oracle does, and a
+    regular matrix factorised next by the same context matches the oracle
+    bit for bit (the kernel left nothing behind)."""
+    n = 87
+    rng = np.random.default_rng(300 + j)
+    M = rng.integers(-3, 4, (n, n)).astype(np.float64) + np.eye(n) * 20.0
+    Z = M.copy()
+    Z[:, j] = 0.0
+    _, _, ost = O.dense_lu(Z)
+    assert ost == O.ERR_SINGULAR
+    G = B.AMG(coarse_enough=n)
+    ptr, col, val = (torch.tensor(a, device="cuda") for a in _dense_csr(Z))
+    with pytest.raises(B.AmgError) as e:
+        G.full_setup(ptr, col, val)
+    assert e.value.status == B.AMG_ERR_SINGULAR
+    olu, opiv, ost = O.dense_lu(M)
+    assert ost == O.OK
+    G.full_setup(*(torch.tensor(a, device="cuda") for a in _dense_csr(M)))
+    lu, piv = G.coarse_lu()
+    assert np.array_equal(piv, opiv) and np.array_equal(lu, olu)
+
+
 @pytest.mark.parametrize("N,ce,nL", [(32, 250, 191), (40, 400, 369)])
 def test_cluster_lu_for_mid_size_coarsest_level(N, ce, nL):
     """A coarsest level between 160 and 448 rows is factorised by the
