@@ -1474,11 +1474,12 @@ __global__ void k_copy_cast(int64_t n, const TI *__restrict__ in, TO *__restrict
 // (a fenced atomic counter, reset by that block) sums the partials in index
 // order and takes the iteration's scalar step itself, so no separate
 // single-block kernel is needed and the sums stay deterministic.
-constexpr int kCgThreads = 256;       // vectors up to kCgLargeN entries
-constexpr int kCgThreadsLarge = 512;  // longer vectors
+// 512 threads a block at every size (256 below kCgLargeN measured 1% slower
+// per CG iteration at 64^3: 16 warps per SM hid less latency than 32)
+constexpr int kCgThreads = 512;
 constexpr int kCgMaxBlocks = 152 * 4;  // long vectors: four blocks of 512 per SM
 constexpr int64_t kCgLargeN = (int64_t)152 * 8 * 256 * 4;
-inline int cg_threads(int64_t n) { return n >= kCgLargeN ? kCgThreadsLarge : kCgThreads; }
+inline int cg_threads(int64_t) { return kCgThreads; }
 
 // deterministic block sum (fixed lane / warp order)
 __device__ double block_sum(double v) {
@@ -2289,7 +2290,7 @@ template void launch_copy_cast<float, double>(int64_t, const float *, double *, 
 // Grid of the Krylov kernels (grid-stride loops, one partial per block).  The
 // last-block reduction costs grow with the number of blocks (each block's
 // partial, fence and counter update sit on the final block's critical path),
-// so vectors up to about 1.2 M entries run on two blocks of 256 per SM; longer
+// so vectors up to about 1.2 M entries run on two blocks of 512 per SM; longer
 // ones need full occupancy to keep enough loads in flight, reached with four
 // blocks of 512 per SM (half the partials of eight blocks of 256, measured
 // faster at 128^3 and 192^3).
