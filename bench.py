@@ -305,18 +305,25 @@ def run_mode(B, torch, w, mode, ptr, col, vals, f, warm_idx, timed_idx, flush, p
     return G, res, prof, u
 
 
-def e2e_leg(B, G, w, vals_host, f_host, idx):
+def e2e_leg(B, G, w, vals, f_host, idx, warm=()):
     """Same steps through the host-buffer entry point: the H2D copy of the step's
-    values and right-hand side and the D2H copy of u are inside the timing."""
+    values and right-hand side and the D2H copy of u are inside the timing.  The
+    `warm` steps go through the same call untimed first (the first partial
+    rebuild builds the gather operators and the solve graph is captured once),
+    as the device-resident timing has its warm-up steps.  Each step's values are
+    staged into one pinned host buffer before its call, outside the timing."""
     import torch
     hu = torch.empty(w.n, dtype=torch.float64).pin_memory()
     hf = torch.tensor(f_host).pin_memory()
-    hv = {k: torch.tensor(v).pin_memory() for k, v in vals_host.items()}
+    hv = torch.empty(vals[idx[0]].numel(), dtype=torch.float64).pin_memory()
     times = []
-    for k in idx:
+    for j, k in enumerate(list(warm) + list(idx)):
+        hv.copy_(vals[k])
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
-        G.step_solve_host(hv[k].numpy(), hf.numpy(), hu.numpy(), TOL)
-        times.append(time.perf_counter() - t0)
+        G.step_solve_host(hv.numpy(), hf.numpy(), hu.numpy(), TOL)
+        if j >= len(warm):
+            times.append(time.perf_counter() - t0)
     return statistics.mean(times), 8 * (w.nnz + w.n), 8 * w.n
 
 
@@ -626,10 +633,8 @@ def run_ours(args):
     # end to end through the host-buffer entry point (rank-local)
     Ge = B.AMG(precision=B.PREC_MIXED if w.precision == "mixed" else B.PREC_FP64, mode=B.MODE_PARTIAL)
     Ge.step(vals[0], ptr, col)
-    vals_host = {k: vals[k].cpu().numpy() for k in timed_idx[:min(len(timed_idx), 10)]}
-    e2e_s, h2d, d2h = e2e_leg(B, Ge, w, vals_host, I.rhs(w.n), timed_idx[:min(len(timed_idx), 10)])
+    e2e_s, h2d, d2h = e2e_leg(B, Ge, w, vals, I.rhs(w.n), timed_idx, warm_idx[-3:])
     Ge.close()
-    del vals_host
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": len(timed_idx),
