@@ -35,6 +35,17 @@ struct ProfData {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> rec[AMG_PROF_NSLOTS];
 };
 
+// The host-buffer entry point copies a partial step's fine values in row
+// chunks; chunk c (rows row[c] .. row[c + 1] - 1, boundaries multiples of 32)
+// is on the device once ev[c] has completed, and its ingest and its rows of
+// the finest A P (whose terms read only those rows' values) wait only for it.
+constexpr int kHostChunks = 8;
+struct FineChunks {
+    const int32_t *row;     // kHostChunks + 1 row boundaries
+    const int32_t *ap;      // the finest A P's entry offsets at those rows
+    const cudaEvent_t *ev;  // kHostChunks events on the copy stream
+};
+
 struct amg_ctx {
     amg_params prm{};
     cudaStream_t s = nullptr;
@@ -82,6 +93,11 @@ struct amg_ctx {
     // host-buffer entry point: the right-hand side's copy runs beside the rebuild
     cudaStream_t s_copy = nullptr;
     cudaEvent_t ev_vals = nullptr, ev_f = nullptr;
+    // ... and, for a partial step, the values arrive in row chunks (one event
+    // each); the chunk boundaries are read once per hierarchy
+    cudaEvent_t ev_chunk[kHostChunks] = {};
+    int32_t ck_row[kHostChunks + 1] = {}, ck_e[kHostChunks + 1] = {}, ck_ap[kHostChunks + 1] = {};
+    int64_t setup_gen = 0, ck_gen = -1;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     bool use_graph = true;
@@ -378,27 +394,43 @@ amg_status block_numeric_rebuild(amg_ctx *ctx, const double *d_val, bool galerki
 }
 
 // numeric part shared by the full setup and the partial rebuild (Alg. 4 body)
-amg_status numeric_rebuild(amg_ctx *ctx, const double *d_val, bool galerkin) {
+amg_status numeric_rebuild(amg_ctx *ctx, const double *d_val, bool galerkin, const FineChunks *ck = nullptr) {
     if (blockmode(ctx)) return block_numeric_rebuild(ctx, d_val, galerkin);
     const amg_params &p = ctx->prm;
     Level &F = ctx->lev[0];
     const bool mx = mixed(ctx);
-    {
-        ProfScope ps_(ctx, AMG_PROF_INGEST);
-        launch_ingest_fine(F.n, F.A_ptr, d_val, F.dia, p.smoother, p.jacobi_omega,
+    auto ingest = [&](int32_t r0, int32_t r1) {
+        launch_ingest_fine(r0, r1, F.A_ptr, d_val, F.dia, p.smoother, p.jacobi_omega,
                            d_val == F.A_val ? nullptr : F.A_val, mx ? F.A_valf : nullptr, mx ? nullptr : F.m,
                            mx ? F.mf : nullptr, ctx->d_st, ctx->s);
+    };
+    // with chunks (the caller checked that the gather operators exist), each
+    // chunk's ingest and its rows of the finest stage 1 run once it has arrived
+    const bool ck_ap = ck && galerkin && ctx->nlev > 1;
+    if (ck) {
+        for (int c = 0; c < kHostChunks; ++c) {
+            CK(cudaStreamWaitEvent(ctx->s, ck->ev[c], 0));
+            ingest(ck->row[c], ck->row[c + 1]);
+            if (!ck_ap) continue;
+            const int64_t e0 = ck->ap[c], ne = (int64_t)ck->ap[c + 1] - e0;
+            if (mx) launch_gather_apply<float>(ne, F.g1_ptr + e0, F.g1_idx, F.g1_wf, F.A_valf, F.AP_valf + e0, ctx->s);
+            else launch_gather_apply<double>(ne, F.g1_ptr + e0, F.g1_idx, F.g1_w, F.A_val, F.AP_val + e0, ctx->s);
+        }
+    } else {
+        ProfScope ps_(ctx, AMG_PROF_INGEST);
+        ingest(0, F.n);
     }
     for (int l = 0; l + 1 < ctx->nlev; ++l) {
         Level &L = ctx->lev[l];
         Level &C = ctx->lev[l + 1];
         ProfScope pg_(ctx, AMG_PROF_GALERKIN, galerkin);
         if (galerkin && L.gather_ready) {
+            const bool s1 = !(ck_ap && l == 0);  // stage 1 of the finest level not yet applied
             if (mx) {
-                { ProfScope ps_(ctx, AMG_PROF_AP_L0, l == 0); launch_gather_apply<float>(L.nnzAP, L.g1_ptr, L.g1_idx, L.g1_wf, L.A_valf, L.AP_valf, ctx->s); }
+                if (s1) { ProfScope ps_(ctx, AMG_PROF_AP_L0, l == 0); launch_gather_apply<float>(L.nnzAP, L.g1_ptr, L.g1_idx, L.g1_wf, L.A_valf, L.AP_valf, ctx->s); }
                 { ProfScope ps_(ctx, AMG_PROF_RAP_L0, l == 0); launch_gather_apply<float>(C.nnz, L.g2_ptr, L.g2_idx, L.g2_wf, L.AP_valf, C.A_valf, ctx->s); }
             } else {
-                { ProfScope ps_(ctx, AMG_PROF_AP_L0, l == 0); launch_gather_apply<double>(L.nnzAP, L.g1_ptr, L.g1_idx, L.g1_w, L.A_val, L.AP_val, ctx->s); }
+                if (s1) { ProfScope ps_(ctx, AMG_PROF_AP_L0, l == 0); launch_gather_apply<double>(L.nnzAP, L.g1_ptr, L.g1_idx, L.g1_w, L.A_val, L.AP_val, ctx->s); }
                 { ProfScope ps_(ctx, AMG_PROF_RAP_L0, l == 0); launch_gather_apply<double>(C.nnz, L.g2_ptr, L.g2_idx, L.g2_w, L.AP_val, C.A_val, ctx->s); }
             }
         } else if (galerkin) {
@@ -633,6 +665,7 @@ amg_status full_setup_impl(amg_ctx *ctx, const double *d_val) {
     TRY(numeric_rebuild(ctx, blockmode(ctx) ? ctx->lev[0].Ab : ctx->lev[0].A_val, false));
     TRY(check_device(ctx, "full setup"));
     ctx->have_setup = true;
+    ctx->setup_gen += 1;
     return AMG_OK;
 }
 
@@ -1448,6 +1481,11 @@ amg_status amg_create(amg_ctx **out, const amg_params *prm, void *cuda_stream) {
         amg_destroy(ctx);
         return AMG_ERR_CUDA;
     }
+    for (cudaEvent_t &e : ctx->ev_chunk)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            amg_destroy(ctx);
+            return AMG_ERR_CUDA;
+        }
     *out = ctx;
     return AMG_OK;
 }
@@ -1468,6 +1506,8 @@ void amg_destroy(amg_ctx *ctx) {
     }
     if (ctx->ev_vals) cudaEventDestroy(ctx->ev_vals);
     if (ctx->ev_f) cudaEventDestroy(ctx->ev_f);
+    for (cudaEvent_t e : ctx->ev_chunk)
+        if (e) cudaEventDestroy(e);
     for (auto &v : ctx->prof.rec)
         for (auto &pr : v) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
@@ -1500,15 +1540,24 @@ amg_status amg_full_setup(amg_ctx *ctx, int32_t n, int32_t nnz, const int32_t *d
     return AMG_OK;
 }
 
-amg_status amg_partial_rebuild(amg_ctx *ctx, const double *d_val) {
-    if (!ctx) return AMG_ERR_ARG;
-    if (!ctx->have_setup) return set_err(ctx, AMG_ERR_STATE, "partial rebuild before a full setup");
-    if (!d_val) return set_err(ctx, AMG_ERR_ARG, "null values");
+namespace {
+// the partial-mode step takes a preventive full setup (every rebuild_every
+// steps, or when the last solve took rebuild_iter_growth times the iterations
+// of the first solve after the last full setup)
+bool preventive_rebuild_due(const amg_ctx *ctx) {
+    const amg_params &p = ctx->prm;
+    const bool regular = p.rebuild_every > 0 && ctx->steps_since_full + 1 >= p.rebuild_every;
+    const bool growth = p.rebuild_iter_growth > 0.0 && ctx->iters_after_full > 0 &&
+                        ctx->last_iters > p.rebuild_iter_growth * ctx->iters_after_full;
+    return regular || growth;
+}
+
+amg_status partial_rebuild_impl(amg_ctx *ctx, const double *d_val, const FineChunks *ck) {
     TRY(reset_status(ctx));
     if (ctx->use_gather)
         for (int l = 0; l + 1 < ctx->nlev; ++l)
             if (!ctx->lev[l].gather_ready) TRY(build_gather(ctx, l));
-    TRY(numeric_rebuild(ctx, d_val, true));
+    TRY(numeric_rebuild(ctx, d_val, true, ck));
     if (ctx->A_sys_own)
         CK(cudaMemcpyAsync(ctx->A_sys_own, d_val, sizeof(double) * nvals(ctx), cudaMemcpyDeviceToDevice,
                            ctx->s));
@@ -1517,6 +1566,46 @@ amg_status amg_partial_rebuild(amg_ctx *ctx, const double *d_val) {
     ctx->last_rebuilt = 0;
     ctx->steps_since_full += 1;
     return AMG_OK;
+}
+
+// whether the host-buffer step can take its values in chunks: a partial
+// rebuild (no preventive full setup due) of a scalar hierarchy whose gather
+// operators exist, with per-kernel timing off
+bool host_chunks_ok(const amg_ctx *ctx) {
+    if (!ctx->have_setup || blockmode(ctx) || ctx->prof.on || ctx->prm.mode != AMG_MODE_PARTIAL || !ctx->use_gather ||
+        preventive_rebuild_due(ctx))
+        return false;
+    for (int l = 0; l + 1 < ctx->nlev; ++l)
+        if (!ctx->lev[l].gather_ready) return false;
+    return true;
+}
+
+// chunk boundaries: rows (multiples of 32), their first value and their first
+// entry of the finest A P, read once per hierarchy
+amg_status prepare_chunks(amg_ctx *ctx) {
+    if (ctx->ck_gen == ctx->setup_gen) return AMG_OK;
+    const int32_t n = ctx->n;
+    for (int c = 0; c < kHostChunks; ++c) ctx->ck_row[c] = (int32_t)(((int64_t)n * c / kHostChunks) & ~(int64_t)31);
+    ctx->ck_row[kHostChunks] = n;
+    const bool ap = ctx->nlev > 1 && ctx->lev[0].AP_ptr;
+    for (int c = 0; c <= kHostChunks; ++c) {
+        CK(cudaMemcpyAsync(&ctx->ck_e[c], ctx->fine_ptr + ctx->ck_row[c], sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->s));
+        if (ap)
+            CK(cudaMemcpyAsync(&ctx->ck_ap[c], ctx->lev[0].AP_ptr + ctx->ck_row[c], sizeof(int32_t),
+                               cudaMemcpyDeviceToHost, ctx->s));
+        else ctx->ck_ap[c] = 0;
+    }
+    CK(cudaStreamSynchronize(ctx->s));
+    ctx->ck_gen = ctx->setup_gen;
+    return AMG_OK;
+}
+}  // namespace
+
+amg_status amg_partial_rebuild(amg_ctx *ctx, const double *d_val) {
+    if (!ctx) return AMG_ERR_ARG;
+    if (!ctx->have_setup) return set_err(ctx, AMG_ERR_STATE, "partial rebuild before a full setup");
+    if (!d_val) return set_err(ctx, AMG_ERR_ARG, "null values");
+    return partial_rebuild_impl(ctx, d_val, nullptr);
 }
 
 amg_status amg_step(amg_ctx *ctx, int32_t n, int32_t nnz, const int32_t *d_ptr, const int32_t *d_col,
@@ -1530,11 +1619,7 @@ amg_status amg_step(amg_ctx *ctx, int32_t n, int32_t nnz, const int32_t *d_ptr, 
     if (!ctx->have_setup) {
         st = amg_full_setup(ctx, n, nnz, d_ptr, d_col, d_val);
     } else if (mode == AMG_MODE_PARTIAL) {
-        const amg_params &p = ctx->prm;
-        const bool regular = p.rebuild_every > 0 && ctx->steps_since_full + 1 >= p.rebuild_every;
-        const bool growth = p.rebuild_iter_growth > 0.0 && ctx->iters_after_full > 0 &&
-                            ctx->last_iters > p.rebuild_iter_growth * ctx->iters_after_full;
-        if (regular || growth) {
+        if (preventive_rebuild_due(ctx)) {
             st = full_setup_impl(ctx, d_val);
             if (st == AMG_OK) {
                 update_sys(ctx);
@@ -1601,14 +1686,6 @@ amg_status amg_step_solve_host(amg_ctx *ctx, const double *h_val, const double *
     if (!ctx) return AMG_ERR_ARG;
     if (!ctx->fine_ptr) return set_err(ctx, AMG_ERR_STATE, "no pattern: call amg_full_setup or amg_step first");
     if (!h_val || !h_f || !h_u) return set_err(ctx, AMG_ERR_ARG, "null host buffer");
-    CK(cudaMemcpyAsync(ctx->stage_val, h_val, sizeof(double) * nvals(ctx), cudaMemcpyHostToDevice, ctx->s));
-    // the right-hand side is needed only by the solve: copied on a side stream
-    // while the step's rebuild runs, after the values (so the two copies do
-    // not share the link)
-    CK(cudaEventRecord(ctx->ev_vals, ctx->s));
-    CK(cudaStreamWaitEvent(ctx->s_copy, ctx->ev_vals, 0));
-    CK(cudaMemcpyAsync(ctx->stage_f, h_f, sizeof(double) * (size_t)nvec(ctx), cudaMemcpyHostToDevice, ctx->s_copy));
-    CK(cudaEventRecord(ctx->ev_f, ctx->s_copy));
     // the caller's buffers stay in use until their copies end: an early
     // return waits for both streams
     auto drain = [ctx](amg_status r) {
@@ -1616,7 +1693,51 @@ amg_status amg_step_solve_host(amg_ctx *ctx, const double *h_val, const double *
         cudaStreamSynchronize(ctx->s_copy);
         return r;
     };
-    amg_status st = amg_step(ctx, ctx->n, ctx->nnz, ctx->fine_ptr, ctx->fine_col, ctx->stage_val, info);
+    auto ok = [ctx](cudaError_t e, const char *what) {
+        if (e == cudaSuccess) return AMG_OK;
+        return set_err(ctx, AMG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    };
+    amg_status st = AMG_OK;
+    const size_t vbytes = sizeof(double) * nvals(ctx), fbytes = sizeof(double) * (size_t)nvec(ctx);
+    if (host_chunks_ok(ctx)) {
+        // a partial step: the values go over the link in row chunks on the
+        // copy stream, each chunk's ingest and finest A P rows start as soon as
+        // it has arrived, and the right-hand side follows the values
+        TRY(prepare_chunks(ctx));
+        if ((st = ok(cudaEventRecord(ctx->ev_vals, ctx->s), "event")) != AMG_OK) return drain(st);
+        if ((st = ok(cudaStreamWaitEvent(ctx->s_copy, ctx->ev_vals, 0), "event wait")) != AMG_OK) return drain(st);
+        for (int c = 0; c < kHostChunks; ++c) {
+            const size_t e0 = (size_t)ctx->ck_e[c], e1 = (size_t)ctx->ck_e[c + 1];
+            if (e1 > e0 && (st = ok(cudaMemcpyAsync(ctx->stage_val + e0, h_val + e0, sizeof(double) * (e1 - e0),
+                                                    cudaMemcpyHostToDevice, ctx->s_copy), "values copy")) != AMG_OK)
+                return drain(st);
+            if ((st = ok(cudaEventRecord(ctx->ev_chunk[c], ctx->s_copy), "event")) != AMG_OK) return drain(st);
+        }
+        if ((st = ok(cudaMemcpyAsync(ctx->stage_f, h_f, fbytes, cudaMemcpyHostToDevice, ctx->s_copy), "rhs copy")) !=
+                AMG_OK ||
+            (st = ok(cudaEventRecord(ctx->ev_f, ctx->s_copy), "event")) != AMG_OK)
+            return drain(st);
+        const FineChunks ck{ctx->ck_row, ctx->ck_ap, ctx->ev_chunk};
+        st = partial_rebuild_impl(ctx, ctx->stage_val, &ck);
+        if (info) {
+            info->rebuilt = ctx->last_rebuilt;
+            info->nlevels = ctx->nlev;
+        }
+    } else {
+        if ((st = ok(cudaMemcpyAsync(ctx->stage_val, h_val, vbytes, cudaMemcpyHostToDevice, ctx->s), "values copy")) !=
+            AMG_OK)
+            return drain(st);
+        // the right-hand side is needed only by the solve: copied on a side
+        // stream while the step's rebuild runs, after the values (so the two
+        // copies do not share the link)
+        if ((st = ok(cudaEventRecord(ctx->ev_vals, ctx->s), "event")) != AMG_OK ||
+            (st = ok(cudaStreamWaitEvent(ctx->s_copy, ctx->ev_vals, 0), "event wait")) != AMG_OK ||
+            (st = ok(cudaMemcpyAsync(ctx->stage_f, h_f, fbytes, cudaMemcpyHostToDevice, ctx->s_copy), "rhs copy")) !=
+                AMG_OK ||
+            (st = ok(cudaEventRecord(ctx->ev_f, ctx->s_copy), "event")) != AMG_OK)
+            return drain(st);
+        st = amg_step(ctx, ctx->n, ctx->nnz, ctx->fine_ptr, ctx->fine_col, ctx->stage_val, info);
+    }
     if (st != AMG_OK) return drain(st);
     if (cudaStreamWaitEvent(ctx->s, ctx->ev_f, 0) != cudaSuccess) return drain(AMG_ERR_CUDA);
     st = amg_solve(ctx, ctx->stage_f, ctx->stage_u, tol, info);

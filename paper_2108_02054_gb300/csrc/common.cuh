@@ -223,9 +223,11 @@ void launch_smoother_f64(int32_t n, const int32_t *ptr, const double *val, const
                          double *m, cudaStream_t s);
 void launch_smoother_f32(int32_t n, const int32_t *ptr, const float *val, const int32_t *dia, int type, double wj,
                          float *m, cudaStream_t s);
-// level-0 ingest: copy new values to the hierarchy (and the FP32 copy), check them, build the smoother
-void launch_ingest_fine(int32_t n, const int32_t *ptr, const double *val_in, const int32_t *dia, int type,
-                        double wj, double *val_out, float *valf_out, double *m, float *mf, int *st, cudaStream_t s);
+// level-0 ingest of rows row0 .. row1 - 1 (row0 a multiple of 32): copy new
+// values to the hierarchy (and the FP32 copy), check them, build the smoother
+void launch_ingest_fine(int32_t row0, int32_t row1, const int32_t *ptr, const double *val_in, const int32_t *dia,
+                        int type, double wj, double *val_out, float *valf_out, double *m, float *mf, int *st,
+                        cudaStream_t s);
 void launch_cast_f32(int64_t n, const double *in, float *out, cudaStream_t s);
 
 // coarsest level: dense LU and explicit inverse

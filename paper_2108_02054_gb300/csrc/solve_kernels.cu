@@ -316,14 +316,15 @@ __global__ void k_smoother(int32_t n, const int32_t *__restrict__ ptr, const V *
 
 // fine level: copy the new values into the hierarchy (optionally an FP32
 // copy as well), flag non-finite entries and build the smoother in one kernel
-__global__ void k_ingest_fine(int32_t n, const int32_t *__restrict__ ptr, const double *__restrict__ in,
+__global__ void k_ingest_fine(int32_t row0, int32_t n, const int32_t *__restrict__ ptr, const double *__restrict__ in,
                               const int32_t *__restrict__ dia, int type, double wj, double *__restrict__ out,
                               float *__restrict__ outf, double *__restrict__ m, float *__restrict__ mf, int *st) {
-    // one warp per 32 consecutive rows: their values are one contiguous range,
-    // copied, cast and checked with coalesced accesses; then each lane forms
-    // its row's smoother from the same values (now in L1/L2) in column order
+    // rows row0 .. n - 1 (row0 a multiple of 32); one warp per 32 consecutive
+    // rows: their values are one contiguous range, copied, cast and checked
+    // with coalesced accesses; then each lane forms its row's smoother from
+    // the same values (now in L1/L2) in column order
     const int lane = threadIdx.x & 31;
-    const int32_t r0 = (int32_t)((((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 5);
+    const int32_t r0 = row0 + (int32_t)((((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 5);
     if (r0 >= n) return;  // warp-uniform
     const int32_t r1 = min(r0 + 32, n);
     const int32_t p0 = ptr[r0], p1 = ptr[r1];
@@ -2099,10 +2100,13 @@ void launch_smoother_f32(int32_t n, const int32_t *ptr, const float *val, const 
     count_launch();
     k_smoother<float><<<nblocks(n), kThreads, 0, s>>>(n, ptr, val, dia, type, (float)wj, m);
 }
-void launch_ingest_fine(int32_t n, const int32_t *ptr, const double *val_in, const int32_t *dia, int type,
-                        double wj, double *val_out, float *valf_out, double *m, float *mf, int *st, cudaStream_t s) {
+void launch_ingest_fine(int32_t row0, int32_t row1, const int32_t *ptr, const double *val_in, const int32_t *dia,
+                        int type, double wj, double *val_out, float *valf_out, double *m, float *mf, int *st,
+                        cudaStream_t s) {
+    if (row1 <= row0) return;
     count_launch();
-    k_ingest_fine<<<nblocks(n), kThreads, 0, s>>>(n, ptr, val_in, dia, type, wj, val_out, valf_out, m, mf, st);
+    k_ingest_fine<<<nblocks(row1 - row0), kThreads, 0, s>>>(row0, row1, ptr, val_in, dia, type, wj, val_out, valf_out,
+                                                            m, mf, st);
 }
 void launch_cast_f32(int64_t n, const double *in, float *out, cudaStream_t s) {
     int64_t b = nblocks(n);

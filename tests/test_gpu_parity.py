@@ -317,6 +317,43 @@ def test_host_buffer_entry_point(pinned):
         assert np.linalg.norm(hu - uo) <= 1e-5 * np.linalg.norm(uo)
 
 
+@pytest.mark.parametrize("precision,dim,N", [("fp64", 3, 37), ("mixed", 3, 40), ("fp64", 2, 9)])
+def test_host_entry_point_chunked_equals_device_path(precision, dim, N):
+    """From the second partial step on, amg_step_solve_host sends the values in
+    row chunks and starts each chunk's ingest and its rows of the finest A P as
+    soon as the chunk has landed.  Over consecutive steps its solutions,
+    iteration counts and coarse operators are those of the device-buffer path
+    bit for bit: on a grid whose row count the chunk boundaries do not divide
+    (37^3), in mixed precision (40^3), and on a one-level hierarchy whose
+    chunks are mostly empty (9^2 = 81 rows)."""
+    T = 6
+    prec = B.PREC_MIXED if precision == "mixed" else B.PREC_FP64
+    n = N ** dim
+    ptr, col, v0 = gpu_problem(dim, N, 0, T)
+    Gh, Gd = B.AMG(precision=prec), B.AMG(precision=prec)
+    Gh.step(v0, ptr, col)
+    Gd.step(v0, ptr, col)
+    hu = torch.empty(n, dtype=torch.float64).pin_memory()
+    for k in range(1, T):
+        vk = gpu_problem(dim, N, k, T)[2]
+        f = I.rhs(n, seed=k)
+        hv, hf = vk.cpu().pin_memory(), torch.tensor(f).pin_memory()
+        ih = Gh.step_solve_host(hv.numpy(), hf.numpy(), hu.numpy(), 1e-8)
+        info = Gd.step(vk)
+        ud, idd = Gd.solve(torch.tensor(f, device="cuda"), 1e-8)
+        assert ih.status == idd.status == 0 and ih.rebuilt == info.rebuilt == 0
+        assert ih.iters == idd.iters, (k, ih.iters, idd.iters)
+        assert np.array_equal(hu.numpy(), ud.cpu().numpy()), f"solution, step {k}"
+        assert Gh.nlevels == Gd.nlevels
+        for l in range(Gd.nlevels):
+            gh, gd = Gh.export_level(l), Gd.export_level(l)
+            assert np.array_equal(gh["A"][2], gd["A"][2]), f"A values level {l}, step {k}"
+            if l < Gd.nlevels - 1:
+                assert np.array_equal(gh["m"], gd["m"]), f"smoother level {l}, step {k}"
+    Gh.close()
+    Gd.close()
+
+
 # ------------------------------------------------------------------ mixed precision
 @pytest.mark.parametrize("dim,N,T", [(2, 32, 10), (3, 64, 50)])
 def test_mixed_precision_reaches_fp64_tolerance(dim, N, T):
