@@ -155,9 +155,10 @@ amg_status amg_apply_vcycle(amg_ctx *ctx, const double *d_r, double *d_z);
  * doubles) and synchronises.  h_f's copy runs on the context's own copy
  * stream while the step's rebuild runs.  When the step is a partial rebuild
  * whose gather operators already exist (from the second partial step on),
- * h_val goes over in eight row chunks on that stream, and each chunk's
- * ingest and its rows of the finest A P start as soon as it has arrived;
- * the results are the same bit for bit.  Every copy has ended when the call
+ * h_val goes over in eight row chunks on that stream. As soon as a chunk
+ * has arrived, its ingest and its rows of the finest A P start, followed by
+ * the finest Galerkin rows of the coarse rows whose R rows end within the
+ * chunks that have arrived; the results are the same bit for bit.  Every copy has ended when the call
  * returns, whatever its status.  Pinned host buffers give the full copy
  * rate.  The pattern must already be known (a previous amg_full_setup or
  * amg_step). */

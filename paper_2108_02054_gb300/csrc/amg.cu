@@ -40,9 +40,13 @@ struct ProfData {
 // is on the device once ev[c] has completed, and its ingest and its rows of
 // the finest A P (whose terms read only those rows' values) wait only for it.
 constexpr int kHostChunks = 8;
+// Stage 2 follows in coarse-row ranges: once chunks 0 .. c have landed, the
+// coarse rows before crow[c + 1] (the leading rows whose R rows reach no fine
+// row of a later chunk) have every A P row they read.
 struct FineChunks {
     const int32_t *row;     // kHostChunks + 1 row boundaries
     const int32_t *ap;      // the finest A P's entry offsets at those rows
+    const int32_t *ac;      // the next level's entry offsets at the coarse boundaries crow
     const cudaEvent_t *ev;  // kHostChunks events on the copy stream
 };
 
@@ -97,6 +101,7 @@ struct amg_ctx {
     // each); the chunk boundaries are read once per hierarchy
     cudaEvent_t ev_chunk[kHostChunks] = {};
     int32_t ck_row[kHostChunks + 1] = {}, ck_e[kHostChunks + 1] = {}, ck_ap[kHostChunks + 1] = {};
+    int32_t ck_crow[kHostChunks + 1] = {}, ck_ac[kHostChunks + 1] = {};
     int64_t setup_gen = 0, ck_gen = -1;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
@@ -415,6 +420,11 @@ amg_status numeric_rebuild(amg_ctx *ctx, const double *d_val, bool galerkin, con
             const int64_t e0 = ck->ap[c], ne = (int64_t)ck->ap[c + 1] - e0;
             if (mx) launch_gather_apply<float>(ne, F.g1_ptr + e0, F.g1_idx, F.g1_wf, F.A_valf, F.AP_valf + e0, ctx->s);
             else launch_gather_apply<double>(ne, F.g1_ptr + e0, F.g1_idx, F.g1_w, F.A_val, F.AP_val + e0, ctx->s);
+            // the coarse rows whose A P rows are now all there
+            Level &C1 = ctx->lev[1];
+            const int64_t o0 = ck->ac[c], no = (int64_t)ck->ac[c + 1] - o0;
+            if (mx) launch_gather_apply<float>(no, F.g2_ptr + o0, F.g2_idx, F.g2_wf, F.AP_valf, C1.A_valf + o0, ctx->s);
+            else launch_gather_apply<double>(no, F.g2_ptr + o0, F.g2_idx, F.g2_w, F.AP_val, C1.A_val + o0, ctx->s);
         }
     } else {
         ProfScope ps_(ctx, AMG_PROF_INGEST);
@@ -425,13 +435,13 @@ amg_status numeric_rebuild(amg_ctx *ctx, const double *d_val, bool galerkin, con
         Level &C = ctx->lev[l + 1];
         ProfScope pg_(ctx, AMG_PROF_GALERKIN, galerkin);
         if (galerkin && L.gather_ready) {
-            const bool s1 = !(ck_ap && l == 0);  // stage 1 of the finest level not yet applied
+            const bool s1 = !(ck_ap && l == 0);  // the finest level's stages not yet applied
             if (mx) {
                 if (s1) { ProfScope ps_(ctx, AMG_PROF_AP_L0, l == 0); launch_gather_apply<float>(L.nnzAP, L.g1_ptr, L.g1_idx, L.g1_wf, L.A_valf, L.AP_valf, ctx->s); }
-                { ProfScope ps_(ctx, AMG_PROF_RAP_L0, l == 0); launch_gather_apply<float>(C.nnz, L.g2_ptr, L.g2_idx, L.g2_wf, L.AP_valf, C.A_valf, ctx->s); }
+                if (s1) { ProfScope ps_(ctx, AMG_PROF_RAP_L0, l == 0); launch_gather_apply<float>(C.nnz, L.g2_ptr, L.g2_idx, L.g2_wf, L.AP_valf, C.A_valf, ctx->s); }
             } else {
                 if (s1) { ProfScope ps_(ctx, AMG_PROF_AP_L0, l == 0); launch_gather_apply<double>(L.nnzAP, L.g1_ptr, L.g1_idx, L.g1_w, L.A_val, L.AP_val, ctx->s); }
-                { ProfScope ps_(ctx, AMG_PROF_RAP_L0, l == 0); launch_gather_apply<double>(C.nnz, L.g2_ptr, L.g2_idx, L.g2_w, L.AP_val, C.A_val, ctx->s); }
+                if (s1) { ProfScope ps_(ctx, AMG_PROF_RAP_L0, l == 0); launch_gather_apply<double>(C.nnz, L.g2_ptr, L.g2_idx, L.g2_w, L.AP_val, C.A_val, ctx->s); }
             }
         } else if (galerkin) {
             if (mx) {
@@ -1596,6 +1606,30 @@ amg_status prepare_chunks(amg_ctx *ctx) {
         else ctx->ck_ap[c] = 0;
     }
     CK(cudaStreamSynchronize(ctx->s));
+    // coarse boundaries: the leading coarse rows whose R rows (sorted by fine
+    // row) end before the chunk's last row, from the prefix maximum of each R
+    // row's last column
+    for (int c = 0; c <= kHostChunks; ++c) ctx->ck_crow[c] = ctx->ck_ac[c] = 0;
+    if (ap) {
+        const Level &L = ctx->lev[0];
+        const int32_t nc = L.nc;
+        std::vector<int32_t> last((size_t)nc, -1);
+        int32_t *d_last = nullptr;
+        TRY(alloc(ctx, &d_last, (size_t)nc));
+        launch_row_last(nc, L.R_ptr, L.R_col, d_last, ctx->s);
+        CK(cudaMemcpyAsync(last.data(), d_last, sizeof(int32_t) * (size_t)nc, cudaMemcpyDeviceToHost, ctx->s));
+        CK(cudaStreamSynchronize(ctx->s));
+        int32_t I = 0, pmax = -1;
+        for (int c = 1; c <= kHostChunks; ++c) {
+            const int32_t lim = ctx->ck_row[c];  // rows before this have landed with chunks 0 .. c - 1
+            while (I < nc && std::max(pmax, last[I]) < lim) pmax = std::max(pmax, last[(size_t)I++]);
+            ctx->ck_crow[c] = c == kHostChunks ? nc : I;
+        }
+        for (int c = 0; c <= kHostChunks; ++c)
+            CK(cudaMemcpyAsync(&ctx->ck_ac[c], ctx->lev[1].A_ptr + ctx->ck_crow[c], sizeof(int32_t),
+                               cudaMemcpyDeviceToHost, ctx->s));
+        CK(cudaStreamSynchronize(ctx->s));
+    }
     ctx->ck_gen = ctx->setup_gen;
     return AMG_OK;
 }
@@ -1717,7 +1751,7 @@ amg_status amg_step_solve_host(amg_ctx *ctx, const double *h_val, const double *
                 AMG_OK ||
             (st = ok(cudaEventRecord(ctx->ev_f, ctx->s_copy), "event")) != AMG_OK)
             return drain(st);
-        const FineChunks ck{ctx->ck_row, ctx->ck_ap, ctx->ev_chunk};
+        const FineChunks ck{ctx->ck_row, ctx->ck_ap, ctx->ck_ac, ctx->ev_chunk};
         st = partial_rebuild_impl(ctx, ctx->stage_val, &ck);
         if (info) {
             info->rebuilt = ctx->last_rebuilt;

@@ -198,6 +198,7 @@ void launch_t2_fill(int32_t nc, const int32_t *R_ptr, const int32_t *R_col, cons
                     const int32_t *AP_col, const int32_t *Ac_ptr, const int32_t *Ac_col, const int32_t *t2ptr,
                     uint16_t *slot2, int *st, cudaStream_t s);
 void launch_row_maxlen(int32_t n, const int32_t *ptr, int *out, cudaStream_t s);
+void launch_row_last(int32_t n, const int32_t *ptr, const int32_t *col, int32_t *last, cudaStream_t s);
 // gather operators of the numeric Galerkin product (AP = N a, A_c = M AP)
 void launch_group_terms(int32_t nrows, const int32_t *tptr, const uint16_t *slot, const int32_t *out_ptr,
                         int32_t *eptr, int32_t *perm, int *st, cudaStream_t s);

@@ -793,6 +793,15 @@ __global__ void k_permute_terms(int64_t nt, const int32_t *__restrict__ perm, co
     }
 }
 
+// last[i]: the last column of row i (rows sorted), -1 for an empty row
+__global__ void k_row_last(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                           int32_t *__restrict__ last) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t e = ptr[i + 1];
+    last[i] = e > ptr[i] ? col[e - 1] : -1;
+}
+
 __global__ void k_row_maxlen(int32_t n, const int32_t *__restrict__ ptr, int *out) {
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     int l = i < n ? ptr[i + 1] - ptr[i] : 0;
@@ -993,6 +1002,11 @@ void launch_permute_terms(int64_t nt, const int32_t *perm, const int32_t *idx_in
     count_launch();
     k_permute_terms<<<(unsigned)(b > 8192 ? 8192 : b), kThreads, 0, s>>>(nt, perm, idx_in, w_in, idx_out, w_out,
                                                                          wf_out);
+}
+void launch_row_last(int32_t n, const int32_t *ptr, const int32_t *col, int32_t *last, cudaStream_t s) {
+    if (n <= 0) return;
+    count_launch();
+    k_row_last<<<nblocks(n), kThreads, 0, s>>>(n, ptr, col, last);
 }
 void launch_row_maxlen(int32_t n, const int32_t *ptr, int *out, cudaStream_t s) {
     count_launch();
