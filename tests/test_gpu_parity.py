@@ -354,6 +354,40 @@ def test_host_entry_point_chunked_equals_device_path(precision, dim, N):
     Gd.close()
 
 
+def test_host_entry_point_chunked_reports_nonfinite_values():
+    """A non-finite value in any chunk of a chunked host-buffer step (first,
+    middle, last entry) is reported as AMG_ERR_NONFINITE, every copy has ended
+    when the call returns, and the next step with finite values gives the
+    device path's solution bit for bit."""
+    dim, N, T = 3, 24, 6
+    n = N ** dim
+    ptr, col, v0 = gpu_problem(dim, N, 0, T)
+    Gh, Gd = B.AMG(), B.AMG()
+    Gh.step(v0, ptr, col)
+    Gd.step(v0, ptr, col)
+    hu = torch.empty(n, dtype=torch.float64).pin_memory()
+    hf = torch.tensor(I.rhs(n)).pin_memory()
+    v1 = gpu_problem(dim, N, 1, T)[2]
+    Gh.step_solve_host(v1.cpu().pin_memory().numpy(), hf.numpy(), hu.numpy(), 1e-8)  # builds the gather operators
+    Gd.step(v1)
+    Gd.solve(torch.tensor(hf.numpy(), device="cuda"), 1e-8)
+    for k, (pos, bad) in enumerate(((0, float("nan")), (v0.numel() // 2 + 5, float("inf")),
+                                    (v0.numel() - 1, float("nan"))), start=2):
+        w = gpu_problem(dim, N, k, T)[2].cpu()
+        w[pos] = bad
+        with pytest.raises(B.AmgError) as e:
+            Gh.step_solve_host(w.pin_memory().numpy(), hf.numpy(), hu.numpy(), 1e-8)
+        assert e.value.status == B.AMG_ERR_NONFINITE
+    vk = gpu_problem(dim, N, 5, T)[2]
+    ih = Gh.step_solve_host(vk.cpu().pin_memory().numpy(), hf.numpy(), hu.numpy(), 1e-8)
+    Gd.step(vk)
+    ud, idd = Gd.solve(torch.tensor(hf.numpy(), device="cuda"), 1e-8)
+    assert ih.status == idd.status == 0 and ih.iters == idd.iters
+    assert np.array_equal(hu.numpy(), ud.cpu().numpy())
+    Gh.close()
+    Gd.close()
+
+
 # ------------------------------------------------------------------ mixed precision
 @pytest.mark.parametrize("dim,N,T", [(2, 32, 10), (3, 64, 50)])
 def test_mixed_precision_reaches_fp64_tolerance(dim, N, T):
