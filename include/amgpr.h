@@ -114,7 +114,10 @@ const char *amg_last_error(const amg_ctx *ctx);
 /* Alg. 1: full setup from A (n rows, nnz entries; device CSR).  Copies the
  * pattern and values; builds strength, aggregates, tentative and smoothed P,
  * R = P^T, the Galerkin patterns with their gather metadata, every A_{l+1},
- * the smoothers and the coarsest LU.  Replaces any previous hierarchy. */
+ * the smoothers and the coarsest LU.  Replaces any previous hierarchy.
+ * AMG_ERR_PATTERN: row pointers not starting at 0, decreasing or not ending
+ * at nnz (checked before any column is read), or unsorted / out-of-range
+ * columns or a missing diagonal; the context then holds no hierarchy. */
 amg_status amg_full_setup(amg_ctx *ctx, int32_t n, int32_t nnz, const int32_t *d_ptr,
                           const int32_t *d_col, const double *d_val);
 

@@ -60,6 +60,7 @@ struct amg_ctx {
     // fine pattern (persistent)
     int32_t n = 0, nnz = 0;
     int32_t *fine_ptr = nullptr, *fine_col = nullptr;
+    bool pattern_ok = false;  // the stored pattern passed the row-pointer check
     // its compressed columns, when its rows use at most kMaxColOffsets offsets
     uint8_t *fine_cidx = nullptr;
     int32_t *fine_coff = nullptr, *coff_table = nullptr;
@@ -767,10 +768,19 @@ amg_status compress_pattern(amg_ctx *ctx) {
 amg_status set_pattern(amg_ctx *ctx, int32_t n, int32_t nnz, const int32_t *d_ptr, const int32_t *d_col) {
     if (n <= 0 || nnz < n || !d_ptr || !d_col) return set_err(ctx, AMG_ERR_ARG, "bad matrix size or null pattern");
     TRY(ensure_persistent(ctx, n, nnz));
-    if (d_ptr == ctx->fine_ptr && d_col == ctx->fine_col) return AMG_OK;
+    if (d_ptr == ctx->fine_ptr && d_col == ctx->fine_col)
+        return ctx->pattern_ok ? AMG_OK : set_err(ctx, AMG_ERR_PATTERN, "the stored pattern did not pass its checks");
+    ctx->pattern_ok = false;
     CK(cudaMemcpyAsync(ctx->fine_ptr, d_ptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToDevice, ctx->s));
     CK(cudaMemcpyAsync(ctx->fine_col, d_col, sizeof(int32_t) * (size_t)nnz, cudaMemcpyDeviceToDevice, ctx->s));
-    return compress_pattern(ctx);
+    // the row pointers first: every later kernel reads the columns they delimit
+    TRY(reset_status(ctx));
+    launch_check_rowptr(n, nnz, ctx->fine_ptr, ctx->d_st, ctx->s);
+    if (check_device(ctx, "row pointers") != AMG_OK)
+        return set_err(ctx, AMG_ERR_PATTERN, "row pointers: not 0 at row 0, decreasing, or not ending at nnz");
+    TRY(compress_pattern(ctx));
+    ctx->pattern_ok = true;
+    return AMG_OK;
 }
 
 // the finest level's column indices as the matrix kernels read them
@@ -1535,8 +1545,13 @@ amg_status amg_full_setup(amg_ctx *ctx, int32_t n, int32_t nnz, const int32_t *d
                           const double *d_val) {
     if (!ctx) return AMG_ERR_ARG;
     if (!d_val) return set_err(ctx, AMG_ERR_ARG, "null values");
-    TRY(set_pattern(ctx, n, nnz, d_ptr, d_col));
-    amg_status st = full_setup_impl(ctx, d_val);
+    amg_status st = set_pattern(ctx, n, nnz, d_ptr, d_col);
+    if (st != AMG_OK) {
+        // the stored pattern was replaced: no hierarchy refers to it any more
+        free_hierarchy(ctx);
+        return st;
+    }
+    st = full_setup_impl(ctx, d_val);
     if (st != AMG_OK) {
         free_hierarchy(ctx);
         return st;

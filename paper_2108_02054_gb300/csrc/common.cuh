@@ -163,6 +163,8 @@ void launch_poisson_grad(int dim, int N, int top, const double *rho, int logd, c
 void launch_levelset_vals(int dim, int N, const double *fx, const double *fy, const double *fz, const int32_t *ptr,
                           double *val, cudaStream_t s);
 
+// a caller's row pointers (ptr[0] = 0, non-decreasing, ptr[n] = nnz): DEV_ERR_PATTERN otherwise
+void launch_check_rowptr(int32_t n, int32_t nnz, const int32_t *ptr, int *st, cudaStream_t s);
 void launch_check_pattern(int32_t n, const int32_t *ptr, const int32_t *col, int32_t *dia, int *st,
                           cudaStream_t s);
 void launch_check_finite(int64_t nnz, const double *val, int *st, cudaStream_t s);

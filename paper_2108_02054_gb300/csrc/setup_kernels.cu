@@ -270,6 +270,19 @@ __global__ void k_poisson_grad(int dim, int N, int64_t n, int top, const double 
 }
 
 // ------------------------------------------------------------------ checks
+// a caller's row pointers: ptr[0] = 0, non-decreasing, ptr[n] = nnz, checked
+// before any kernel reads the columns they delimit
+__global__ void k_check_rowptr(int32_t n, int32_t nnz, const int32_t *__restrict__ ptr, int *st) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = ptr[i];
+        bool bad = v < 0 || v > nnz;
+        if (i == 0) bad = bad || v != 0;
+        if (i == n) bad = bad || v != nnz;
+        else bad = bad || ptr[i + 1] < v;
+        if (bad) atomicOr(st, DEV_ERR_PATTERN);
+    }
+}
+
 __global__ void k_check_pattern(int32_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                                 int32_t *__restrict__ dia, int *st) {
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -859,6 +872,11 @@ void launch_levelset_vals(int dim, int N, const double *fx, const double *fy, co
     k_levelset_vals<<<nblocks(n), kThreads, 0, s>>>(dim, N, n, fx, fy, fz, ptr, val);
 }
 
+void launch_check_rowptr(int32_t n, int32_t nnz, const int32_t *ptr, int *st, cudaStream_t s) {
+    const int64_t b = nblocks((int64_t)n + 1);
+    count_launch();
+    k_check_rowptr<<<(unsigned)(b > 4096 ? 4096 : b), kThreads, 0, s>>>(n, nnz, ptr, st);
+}
 void launch_check_pattern(int32_t n, const int32_t *ptr, const int32_t *col, int32_t *dia, int *st,
                           cudaStream_t s) {
     count_launch();

@@ -455,6 +455,25 @@ def test_error_statuses():
         with pytest.raises(B.AmgError) as e:
             G.partial_rebuild(w)
         assert e.value.status == B.AMG_ERR_NONFINITE
+    # row pointers inconsistent with nnz (a truncated column array), decreasing
+    # or not starting at 0: reported before any kernel reads the columns they
+    # delimit, and the context then takes a good pattern
+    G3 = B.AMG()
+    cases = [(ptr, col[:-5].clone(), v[:-5].clone())]
+    for pos, val in ((4, None), (0, 1)):
+        bp = ptr.clone()
+        bp[pos] = bp[pos + 1] + 1 if val is None else val
+        cases.append((bp, col, v))
+    for bp, bc, bv in cases:
+        with pytest.raises(B.AmgError) as e:
+            G3.full_setup(bp, bc, bv)
+        assert e.value.status == B.AMG_ERR_PATTERN
+        with pytest.raises(B.AmgError) as e:
+            G3.step_solve_host(bv.cpu().numpy(), np.zeros(256), np.zeros(256), 1e-8)
+        assert e.value.status in (B.AMG_ERR_PATTERN, B.AMG_ERR_STATE)
+    G3.full_setup(ptr, col, v)
+    u3, i3 = G3.solve(torch.tensor(I.rhs(256), device="cuda"), 1e-8)
+    assert i3.status == 0
     G.full_setup(ptr, col, v)
     f = torch.tensor(I.rhs(256), device="cuda")
     G1 = B.AMG(maxiter=1, coarse_enough=16)
