@@ -122,11 +122,28 @@ def _stream(stream=None) -> int:
     return int(s.cuda_stream)
 
 
-def _dptr(t) -> int:
+def _dptr(t, dtype=None, numel=None) -> int:
+    """The device address of a contiguous CUDA tensor, checked against the
+    element type and the least element count the call reads or writes (the
+    kernels cannot check a buffer's extent)."""
     import torch
     if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
         raise ValueError("expected a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"expected a {dtype} tensor, got {t.dtype}")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"expected at least {numel} elements, got {t.numel()}")
     return t.data_ptr()
+
+
+def _f64(t, numel=None) -> int:
+    import torch
+    return _dptr(t, torch.float64, numel)
+
+
+def _i32p(t, numel=None) -> int:
+    import torch
+    return _dptr(t, torch.int32, numel)
 
 
 def default_params(**overrides) -> amg_params:
@@ -183,19 +200,32 @@ class AMG:
         return st
 
     # ------------------------------------------------------------ Alg. 1 / 3 / 4
+    # values per matrix entry and per unknown of the vectors (4 x 4 blocks: 16, 4)
+    def _vpe(self) -> int:
+        return self.params.block_size * self.params.block_size
+
+    def _vec(self) -> int:
+        return self.n * self.params.block_size
+
     def full_setup(self, ptr, col, val):
-        self.n, self.nnz = ptr.numel() - 1, col.numel()
-        self._check(lib().amg_full_setup(self._h, self.n, self.nnz, _dptr(ptr), _dptr(col), _dptr(val)))
+        n, nnz = ptr.numel() - 1, col.numel()
+        args = (_i32p(ptr), _i32p(col), _f64(val, nnz * self._vpe()))
+        self.n, self.nnz = n, nnz
+        self._check(lib().amg_full_setup(self._h, n, nnz, *args))
 
     def partial_rebuild(self, val):
-        self._check(lib().amg_partial_rebuild(self._h, _dptr(val)))
+        self._check(lib().amg_partial_rebuild(self._h, _f64(val, self.nnz * self._vpe())))
 
     def step(self, val, ptr=None, col=None) -> Info:
         info = amg_info()
-        if ptr is not None:
-            self.n, self.nnz = ptr.numel() - 1, col.numel()
-        self._check(lib().amg_step(self._h, self.n, self.nnz, _dptr(ptr) if ptr is not None else None,
-                                   _dptr(col) if col is not None else None, _dptr(val), ctypes.byref(info)))
+        if (ptr is None) != (col is None):
+            raise ValueError("give both ptr and col, or neither")
+        n, nnz = (ptr.numel() - 1, col.numel()) if ptr is not None else (self.n, self.nnz)
+        dp = _i32p(ptr) if ptr is not None else None
+        dc = _i32p(col) if col is not None else None
+        dv = _f64(val, nnz * self._vpe())
+        self.n, self.nnz = n, nnz
+        self._check(lib().amg_step(self._h, n, nnz, dp, dc, dv, ctypes.byref(info)))
         return _info(info)
 
     def solve(self, f, tol: float = 1e-8, u=None, allow_not_converged: bool = True):
@@ -204,22 +234,25 @@ class AMG:
             u = torch.empty_like(f)
         info = amg_info()
         ok = (AMG_OK, AMG_NOT_CONVERGED) if allow_not_converged else (AMG_OK,)
-        self._check(lib().amg_solve(self._h, _dptr(f), _dptr(u), float(tol), ctypes.byref(info)), ok)
+        self._check(lib().amg_solve(self._h, _f64(f, self._vec()), _f64(u, self._vec()), float(tol),
+                                    ctypes.byref(info)), ok)
         return u, _info(info)
 
     def vcycle(self, r, z=None):
         import torch
         if z is None:
             z = torch.empty_like(r)
-        self._check(lib().amg_apply_vcycle(self._h, _dptr(r), _dptr(z)))
+        self._check(lib().amg_apply_vcycle(self._h, _f64(r, self._vec()), _f64(z, self._vec())))
         return z
 
     def step_solve_host(self, h_val: np.ndarray, h_f: np.ndarray, h_u: np.ndarray, tol: float = 1e-8) -> Info:
         """Host buffers in and out (copies inside the call)."""
         info = amg_info()
-        for a in (h_val, h_f, h_u):
+        for a, need in ((h_val, self.nnz * self._vpe()), (h_f, self._vec()), (h_u, self._vec())):
             if a.dtype != np.float64 or not a.flags.c_contiguous:
                 raise ValueError("host buffers must be contiguous float64")
+            if a.size < need:
+                raise ValueError(f"host buffer of {a.size} elements, the call copies {need}")
         self._check(lib().amg_step_solve_host(self._h, h_val.ctypes.data, h_f.ctypes.data, h_u.ctypes.data,
                                               float(tol), ctypes.byref(info)), (AMG_OK, AMG_NOT_CONVERGED))
         return _info(info)
@@ -317,8 +350,9 @@ def poisson_pattern(dim: int, N: int, stream=None):
 def poisson_values(dim: int, N: int, rho, ptr, dirichlet_top: bool = True, out=None, stream=None):
     """Device values of -div((1/rho) grad p) on the pattern from poisson_pattern."""
     import torch
-    val = out if out is not None else torch.empty(poisson_nnz(dim, N), dtype=torch.float64, device="cuda")
-    st = lib().amg_poisson_values(dim, N, int(dirichlet_top), _dptr(rho), _dptr(ptr), _dptr(val),
+    nnz, n = poisson_nnz(dim, N), N ** dim
+    val = out if out is not None else torch.empty(nnz, dtype=torch.float64, device="cuda")
+    st = lib().amg_poisson_values(dim, N, int(dirichlet_top), _f64(rho, n), _i32p(ptr, n + 1), _f64(val, nnz),
                                   _vp(_stream(stream)))
     if st != AMG_OK:
         raise AmgError(st, "amg_poisson_values failed")
@@ -328,9 +362,10 @@ def poisson_values(dim: int, N: int, rho, ptr, dirichlet_top: bool = True, out=N
 def poisson_values_log(dim: int, N: int, theta, ptr, dirichlet_top: bool = True, out=None, stream=None):
     """poisson_values for rho = exp(theta), the exponential taken in the kernel."""
     import torch
-    val = out if out is not None else torch.empty(poisson_nnz(dim, N), dtype=torch.float64, device="cuda")
-    st = lib().amg_poisson_values_log(dim, N, int(dirichlet_top), _dptr(theta), _dptr(ptr), _dptr(val),
-                                      _vp(_stream(stream)))
+    nnz, n = poisson_nnz(dim, N), N ** dim
+    val = out if out is not None else torch.empty(nnz, dtype=torch.float64, device="cuda")
+    st = lib().amg_poisson_values_log(dim, N, int(dirichlet_top), _f64(theta, n), _i32p(ptr, n + 1),
+                                      _f64(val, nnz), _vp(_stream(stream)))
     if st != AMG_OK:
         raise AmgError(st, "amg_poisson_values_log failed")
     return val
@@ -341,10 +376,12 @@ def levelset_values(dim: int, N: int, fx, fy, fz, ptr, out=None, stream=None):
     the pattern from poisson_pattern; fx, fy, fz are the face velocities (fz
     is ignored in 2D)."""
     import torch
-    val = out if out is not None else torch.empty(poisson_nnz(dim, N), dtype=torch.float64, device="cuda")
-    fz_p = _dptr(fz) if (dim == 3 or (fz is not None and fz.numel() > 0)) else 0
-    st = lib().amg_levelset_values(dim, N, _dptr(fx), _dptr(fy), fz_p, _dptr(ptr), _dptr(val),
-                                   _vp(_stream(stream)))
+    nnz, n = poisson_nnz(dim, N), N ** dim
+    val = out if out is not None else torch.empty(nnz, dtype=torch.float64, device="cuda")
+    faces = n // N * (N + 1)  # face values per direction: (N + 1) N^(dim - 1)
+    fz_p = _f64(fz, faces) if dim == 3 else (_dptr(fz) if fz is not None and fz.numel() > 0 else 0)
+    st = lib().amg_levelset_values(dim, N, _f64(fx, faces), _f64(fy, faces), fz_p, _i32p(ptr, n + 1),
+                                   _f64(val, nnz), _vp(_stream(stream)))
     if st != AMG_OK:
         raise AmgError(st, "amg_levelset_values failed")
     return val
@@ -354,10 +391,11 @@ def stokes_values(N: int, rho, mu, fx, fy, fz, mass: float, ptr, out=None, strea
     """Device block values (nnz x 16) of the 4 x 4 monolithic Navier-Stokes
     stand-in on the pattern from poisson_pattern(3, N)."""
     import torch
-    nnz = poisson_nnz(3, N)
+    nnz, n = poisson_nnz(3, N), N ** 3
+    faces = N * N * (N + 1)
     val = out if out is not None else torch.empty((nnz, 16), dtype=torch.float64, device="cuda")
-    st = lib().amg_stokes_values(N, _dptr(rho), _dptr(mu), _dptr(fx), _dptr(fy), _dptr(fz), float(mass),
-                                 _dptr(ptr), _dptr(val), _vp(_stream(stream)))
+    st = lib().amg_stokes_values(N, _f64(rho, n), _f64(mu, n), _f64(fx, faces), _f64(fy, faces), _f64(fz, faces),
+                                 float(mass), _i32p(ptr, n + 1), _f64(val, 16 * nnz), _vp(_stream(stream)))
     if st != AMG_OK:
         raise AmgError(st, "amg_stokes_values failed")
     return val
@@ -373,9 +411,10 @@ def block_params(**overrides) -> amg_params:
 
 def poisson_grad_theta(dim: int, N: int, rho, u, lam, dirichlet_top: bool = True, stream=None):
     import torch
+    n = N ** dim
     g = torch.empty_like(u)
-    st = lib().amg_poisson_grad_theta(dim, N, int(dirichlet_top), _dptr(rho), _dptr(u), _dptr(lam), _dptr(g),
-                                      _vp(_stream(stream)))
+    st = lib().amg_poisson_grad_theta(dim, N, int(dirichlet_top), _f64(rho, n), _f64(u, n), _f64(lam, n),
+                                      _f64(g, n), _vp(_stream(stream)))
     if st != AMG_OK:
         raise AmgError(st, "amg_poisson_grad_theta failed")
     return g
@@ -384,9 +423,10 @@ def poisson_grad_theta(dim: int, N: int, rho, u, lam, dirichlet_top: bool = True
 def poisson_grad_log(dim: int, N: int, theta, u, lam, dirichlet_top: bool = True, stream=None):
     """dL/dtheta per cell for rho = exp(theta) (the exponential taken in the kernel)."""
     import torch
+    n = N ** dim
     g = torch.empty_like(u)
-    st = lib().amg_poisson_grad_log(dim, N, int(dirichlet_top), _dptr(theta), _dptr(u), _dptr(lam), _dptr(g),
-                                    _vp(_stream(stream)))
+    st = lib().amg_poisson_grad_log(dim, N, int(dirichlet_top), _f64(theta, n), _f64(u, n), _f64(lam, n),
+                                    _f64(g, n), _vp(_stream(stream)))
     if st != AMG_OK:
         raise AmgError(st, "amg_poisson_grad_log failed")
     return g

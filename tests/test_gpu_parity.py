@@ -426,6 +426,41 @@ def test_mixed_precision_reaches_fp64_tolerance(dim, N, T):
 
 
 # ------------------------------------------------------------------ errors (all detected without faults)
+def test_binding_rejects_wrong_types_and_extents():
+    """The Python binding checks every tensor's element type and extent against
+    what the call reads or writes (the kernels cannot), and raises before
+    anything is launched."""
+    N = 8
+    n = N ** 3
+    ptr, col = B.poisson_pattern(3, N)
+    rho = torch.ones(n, dtype=torch.float64, device="cuda")
+    for bad_rho, bad_ptr in ((rho.float(), ptr), (rho[:-1], ptr), (rho, ptr.long()), (rho, ptr[:-1])):
+        with pytest.raises(ValueError):
+            B.poisson_values(3, N, bad_rho, bad_ptr)
+    with pytest.raises(ValueError):
+        B.poisson_values(3, N, rho, ptr, out=torch.empty(col.numel() - 1, dtype=torch.float64, device="cuda"))
+    v = B.poisson_values(3, N, rho, ptr)
+    G = B.AMG(coarse_enough=64)
+    for bad in (v.float(), v[:-3]):
+        with pytest.raises(ValueError):
+            G.full_setup(ptr, col, bad)
+    with pytest.raises(ValueError):
+        G.full_setup(ptr.long(), col, v)
+    G.full_setup(ptr, col, v)
+    with pytest.raises(ValueError):
+        G.partial_rebuild(v[:-1])
+    f = torch.ones(n, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        G.solve(f[:-1])
+    with pytest.raises(ValueError):
+        G.solve(f, u=torch.empty(n, dtype=torch.float32, device="cuda"))
+    with pytest.raises(ValueError):
+        G.step_solve_host(v.cpu().numpy(), np.zeros(n - 1), np.zeros(n), 1e-8)
+    u, info = G.solve(f, 1e-8)
+    assert info.status == 0
+    G.close()
+
+
 def test_error_statuses():
     ptr, col, v = gpu_problem(2, 16, 0, 2)
     G = B.AMG()
