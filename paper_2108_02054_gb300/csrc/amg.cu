@@ -287,13 +287,21 @@ amg_status symbolic_product(amg_ctx *ctx, int32_t nrows, int32_t ncols, const in
     int32_t *len = nullptr;
     TRY(alloc(ctx, &len, (size_t)nrows));
     TRY(alloc(ctx, C_ptr, (size_t)nrows + 1));
-    launch_spgemm_symbolic(nrows, ncols, X_ptr, X_col, Y_ptr, Y_col, add_diag, len, nullptr, nullptr, ctx->d_st,
+    // the hash tables are sized for the longest row of terms
+    int *d_max = nullptr;
+    TRY(alloc(ctx, &d_max, 1));
+    CK(cudaMemsetAsync(d_max, 0, sizeof(int), ctx->s));
+    launch_row_terms_max(nrows, X_ptr, X_col, Y_ptr, add_diag, d_max, ctx->s);
+    int32_t max_terms = 0;
+    TRY(read_scalar(ctx, d_max, &max_terms));
+    const int cap = spgemm_symbolic_cap(max_terms);
+    launch_spgemm_symbolic(nrows, ncols, X_ptr, X_col, Y_ptr, Y_col, add_diag, cap, len, nullptr, nullptr, ctx->d_st,
                            ctx->s);
     TRY(scan(ctx, len, *C_ptr, nrows));
     TRY(check_device(ctx, "symbolic product"));
     TRY(read_scalar(ctx, *C_ptr + nrows, C_nnz));
     TRY(alloc(ctx, C_col, (size_t)*C_nnz));
-    launch_spgemm_symbolic(nrows, ncols, X_ptr, X_col, Y_ptr, Y_col, add_diag, len, *C_ptr, *C_col, ctx->d_st,
+    launch_spgemm_symbolic(nrows, ncols, X_ptr, X_col, Y_ptr, Y_col, add_diag, cap, len, *C_ptr, *C_col, ctx->d_st,
                            ctx->s);
     return AMG_OK;
 }

@@ -26,9 +26,9 @@ enum : int {
 };
 
 constexpr int kMaxLevels = 32;
-// symbolic product: per-warp open-addressing hash of at most this many keys
+// symbolic product: per-warp open-addressing hash of at most this many slots
+// (a row of a Galerkin pattern may hold half as many distinct columns)
 constexpr int kHashCap = 4096;
-constexpr int kMaxRowUnique = kHashCap / 2;
 
 // Device-resident state of the CG iteration; every CG kernel reads and writes
 // it so that the loop needs no host round trip between its kernels.
@@ -186,8 +186,13 @@ void launch_transpose_scatter(int32_t n, const int32_t *P_ptr, const int32_t *P_
 void launch_sort_rows(int32_t nrows, const int32_t *ptr, int32_t *col, double *val, cudaStream_t s);
 // symbolic C = X*Y pattern: pass 1 (C_ptr == nullptr) writes row lengths into len,
 // pass 2 writes sorted columns into C_col at C_ptr
+// the most terms of any row of C = X * Y (a bound on its distinct columns),
+// into *out (atomic maximum; zero it first), and the hash-table capacity for it
+void launch_row_terms_max(int32_t nrows, const int32_t *X_ptr, const int32_t *X_col, const int32_t *Y_ptr,
+                          int add_diag, int *out, cudaStream_t s);
+int spgemm_symbolic_cap(int32_t max_terms);
 void launch_spgemm_symbolic(int32_t nrows, int32_t ncols, const int32_t *X_ptr, const int32_t *X_col,
-                            const int32_t *Y_ptr, const int32_t *Y_col, int add_diag, int32_t *len,
+                            const int32_t *Y_ptr, const int32_t *Y_col, int add_diag, int cap, int32_t *len,
                             const int32_t *C_ptr, int32_t *C_col, int *st, cudaStream_t s);
 void launch_t1_count(int32_t n, const int32_t *A_ptr, const int32_t *A_col, const int32_t *P_ptr, int32_t *cnt,
                      cudaStream_t s);

@@ -562,45 +562,67 @@ __global__ void k_sort_rows(int32_t nrows, const int32_t *__restrict__ ptr, int3
 }
 
 // ------------------------------------------------------------------ symbolic product
-constexpr int kSymWarps = 4;
-constexpr int kSymSmem = kSymWarps * (kHashCap + kMaxRowUnique + 2) * (int)sizeof(int32_t);
+// Each row's distinct columns go through a shared-memory hash table of `cap`
+// slots (a power of two, at least twice the product's longest row of terms,
+// so that a row's distinct columns always fit and probes stay short; at most
+// kHashCap), then are ranked into sorted order.
+constexpr int kSymSmemMax = 112 * 1024;
 
-__device__ __forceinline__ bool hash_insert(int32_t *keys, int32_t *count, int32_t c) {
-    uint32_t h = ((uint32_t)c * 2654435761u) >> (32 - 12);  // kHashCap = 4096 = 2^12
-    for (int probe = 0; probe < kHashCap; ++probe) {
+__device__ __forceinline__ bool hash_insert(int32_t *keys, int32_t *count, int32_t c, int cap, int shift) {
+    uint32_t h = ((uint32_t)c * 2654435761u) >> shift;
+    for (int probe = 0; probe < cap; ++probe) {
         int32_t old = atomicCAS(&keys[h], -1, c);
         if (old == -1) { atomicAdd(count, 1); return true; }
         if (old == c) return true;
-        h = (h + 1) & (kHashCap - 1);
+        h = (h + 1) & (uint32_t)(cap - 1);
     }
     return false;
 }
 
+// the most terms (entries of the selected Y rows, plus the diagonal) of any
+// row of C = X * Y: a bound on its distinct columns
+__global__ void k_row_terms_max(int32_t nrows, const int32_t *__restrict__ X_ptr, const int32_t *__restrict__ X_col,
+                                const int32_t *__restrict__ Y_ptr, int add_diag, int *out) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    int32_t c = 0;
+    if (i < nrows) {
+        c = add_diag ? 1 : 0;
+        for (int32_t p = X_ptr[i]; p < X_ptr[i + 1]; ++p) {
+            const int32_t k = X_col[p];
+            c += Y_ptr[k + 1] - Y_ptr[k];
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c = max(c, __shfl_xor_sync(0xffffffffu, c, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, c);
+}
+
 // one warp per row of C = X * Y: union of the Y-rows selected by X's row
-__global__ void __launch_bounds__(kSymWarps * 32)
-k_spgemm_symbolic(int32_t nrows, int32_t ncols, const int32_t *__restrict__ X_ptr, const int32_t *__restrict__ X_col,
-                  const int32_t *__restrict__ Y_ptr, const int32_t *__restrict__ Y_col, int add_diag,
-                  int32_t *__restrict__ len, const int32_t *__restrict__ C_ptr, int32_t *__restrict__ C_col,
-                  int *st) {
+__global__ void k_spgemm_symbolic(int32_t nrows, int32_t ncols, const int32_t *__restrict__ X_ptr,
+                                  const int32_t *__restrict__ X_col, const int32_t *__restrict__ Y_ptr,
+                                  const int32_t *__restrict__ Y_col, int add_diag, int cap, int shift,
+                                  int32_t *__restrict__ len, const int32_t *__restrict__ C_ptr,
+                                  int32_t *__restrict__ C_col, int *st) {
     extern __shared__ int32_t smem[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int32_t *keys = smem + w * (kHashCap + kMaxRowUnique + 2);
-    int32_t *list = keys + kHashCap;
-    int32_t *cnt = list + kMaxRowUnique;
-    const int32_t row = blockIdx.x * kSymWarps + w;
+    const int lcap = cap / 2;  // distinct columns a row may hold
+    int32_t *keys = smem + w * (cap + lcap + 2);
+    int32_t *list = keys + cap;
+    int32_t *cnt = list + lcap;
+    const int32_t row = blockIdx.x * (blockDim.x >> 5) + w;
     if (row >= nrows) return;  // warp-uniform
-    for (int h = lane; h < kHashCap; h += 32) keys[h] = -1;
+    for (int h = lane; h < cap; h += 32) keys[h] = -1;
     if (lane == 0) { cnt[0] = 0; cnt[1] = 0; }
     __syncwarp();
     bool ok = true;
-    if (add_diag && row < ncols && lane == 0) ok = hash_insert(keys, &cnt[0], row);
+    if (add_diag && row < ncols && lane == 0) ok = hash_insert(keys, &cnt[0], row, cap, shift);
     for (int32_t p = X_ptr[row] + lane; p < X_ptr[row + 1]; p += 32) {
         int32_t k = X_col[p];
-        for (int32_t q = Y_ptr[k]; q < Y_ptr[k + 1] && ok; ++q) ok = hash_insert(keys, &cnt[0], Y_col[q]);
+        for (int32_t q = Y_ptr[k]; q < Y_ptr[k + 1] && ok; ++q) ok = hash_insert(keys, &cnt[0], Y_col[q], cap, shift);
     }
     __syncwarp();
     const int32_t L = cnt[0];
-    if (!__all_sync(0xffffffffu, ok) || L > kMaxRowUnique) {
+    if (!__all_sync(0xffffffffu, ok) || L > lcap) {
         if (lane == 0) atomicOr(st, DEV_ERR_CAPACITY);
         return;
     }
@@ -608,7 +630,7 @@ k_spgemm_symbolic(int32_t nrows, int32_t ncols, const int32_t *__restrict__ X_pt
         if (lane == 0) len[row] = L;
         return;
     }
-    for (int h = lane; h < kHashCap; h += 32) {
+    for (int h = lane; h < cap; h += 32) {
         int32_t c = keys[h];
         if (c >= 0) list[atomicAdd(&cnt[1], 1)] = c;
     }
@@ -959,19 +981,35 @@ void launch_sort_rows(int32_t nrows, const int32_t *ptr, int32_t *col, double *v
     k_sort_rows<<<nblocks(nrows, 128), 128, 0, s>>>(nrows, ptr, col, val);
 }
 
+void launch_row_terms_max(int32_t nrows, const int32_t *X_ptr, const int32_t *X_col, const int32_t *Y_ptr,
+                          int add_diag, int *out, cudaStream_t s) {
+    if (nrows <= 0) return;
+    count_launch();
+    k_row_terms_max<<<nblocks(nrows), kThreads, 0, s>>>(nrows, X_ptr, X_col, Y_ptr, add_diag, out);
+}
+int spgemm_symbolic_cap(int32_t max_terms) {
+    int cap = 64;
+    while (cap < kHashCap && cap < 2 * max_terms) cap *= 2;
+    return cap;
+}
 void launch_spgemm_symbolic(int32_t nrows, int32_t ncols, const int32_t *X_ptr, const int32_t *X_col,
-                            const int32_t *Y_ptr, const int32_t *Y_col, int add_diag, int32_t *len,
+                            const int32_t *Y_ptr, const int32_t *Y_col, int add_diag, int cap, int32_t *len,
                             const int32_t *C_ptr, int32_t *C_col, int *st, cudaStream_t s) {
+    if (nrows <= 0) return;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_spgemm_symbolic, cudaFuncAttributeMaxDynamicSharedMemorySize, kSymSmem);
+        cudaFuncSetAttribute(k_spgemm_symbolic, cudaFuncAttributeMaxDynamicSharedMemorySize, kSymSmemMax);
         attr_set = true;
     }
-    if (nrows <= 0) return;
-    unsigned grid = (unsigned)((nrows + kSymWarps - 1) / kSymWarps);
+    int shift = 32;
+    for (int c = cap; c > 1; c >>= 1) --shift;  // cap = 2^(32 - shift)
+    const size_t per_warp = (size_t)(cap + cap / 2 + 2) * sizeof(int32_t);
+    int warps = 8;
+    while (warps > 1 && per_warp * (size_t)warps > (size_t)kSymSmemMax) warps >>= 1;
+    const unsigned grid = (unsigned)((nrows + warps - 1) / warps);
     count_launch();
-    k_spgemm_symbolic<<<grid, kSymWarps * 32, kSymSmem, s>>>(nrows, ncols, X_ptr, X_col, Y_ptr, Y_col, add_diag,
-                                                              len, C_ptr, C_col, st);
+    k_spgemm_symbolic<<<grid, warps * 32, per_warp * (size_t)warps, s>>>(nrows, ncols, X_ptr, X_col, Y_ptr, Y_col,
+                                                                        add_diag, cap, shift, len, C_ptr, C_col, st);
 }
 
 void launch_t1_count(int32_t n, const int32_t *A_ptr, const int32_t *A_col, const int32_t *P_ptr, int32_t *cnt,
