@@ -9,7 +9,10 @@
 // values feeding coarser levels) is written as separately rounded IEEE
 // operations in a fixed order; the library is built with --fmad=false so no
 // multiply-add is contracted behind our back.
+#include <climits>
+
 #include "common.cuh"
+#include "fdiv.cuh"
 
 namespace amgpr {
 
@@ -513,6 +516,9 @@ __global__ void k_p_fill(int32_t n, const int32_t *__restrict__ ptr, const int32
     double d = val[dia[i]];
     for (int32_t p = b; p < e; ++p)
         if (col[p] != i && !strong[p]) d = __dadd_rn(d, val[p]);
+    // every term divides by d: its reciprocal once, then correctly rounded
+    // quotients in integer arithmetic (the FP64 division bounds this kernel)
+    const DivRecip rd = div_recip(d);
     for (int32_t s = 0; s < nc; ++s) {
         const int32_t c = P_col[base + s];
         double v = (c == ai) ? 1.0 : 0.0;
@@ -521,7 +527,7 @@ __global__ void k_p_fill(int32_t n, const int32_t *__restrict__ ptr, const int32
             if (j != i && !strong[p]) continue;
             if (agg[j] != c) continue;
             double w = (j == i) ? d : val[p];
-            v = __dsub_rn(v, __ddiv_rn(__dmul_rn(omega, w), d));
+            v = __dsub_rn(v, div_rn(__dmul_rn(omega, w), rd));
         }
         P_val[base + s] = v;
     }
@@ -546,19 +552,88 @@ __global__ void k_transpose_scatter(int32_t n, const int32_t *__restrict__ P_ptr
     }
 }
 
-__global__ void k_sort_rows(int32_t nrows, const int32_t *__restrict__ ptr, int32_t *__restrict__ col,
-                            double *__restrict__ val) {
-    int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nrows) return;
-    const int32_t b = ptr[r], e = ptr[r + 1];
-    for (int32_t a = b + 1; a < e; ++a) {
-        int32_t c = col[a];
-        double v = val[a];
-        int32_t t = a;
-        while (t > b && col[t - 1] > c) { col[t] = col[t - 1]; val[t] = val[t - 1]; --t; }
-        col[t] = c;
-        val[t] = v;
+// Sort each row of a CSR matrix by column (columns distinct within a row),
+// one warp per row.  Rows of up to 128 entries are sorted in registers by a
+// bitonic network over the warp (entry e = 32 j + lane in slot j; padding
+// sorts last); longer rows by an insertion sort in place.
+template <int E>
+__device__ __forceinline__ void warp_bitonic(int32_t (&key)[E], double (&val)[E], int lane) {
+#pragma unroll
+    for (int k = 2; k <= 32 * E; k <<= 1) {
+#pragma unroll
+        for (int s = k >> 1; s > 0; s >>= 1) {
+            if (s >= 32) {
+#pragma unroll
+                for (int j = 0; j < E; ++j) {
+                    const int jp = j ^ (s >> 5);
+                    if (jp > j) {
+                        const bool up = ((j * 32 + lane) & k) == 0;
+                        if ((key[j] > key[jp]) == up) {
+                            const int32_t tk = key[j];
+                            key[j] = key[jp];
+                            key[jp] = tk;
+                            const double tv = val[j];
+                            val[j] = val[jp];
+                            val[jp] = tv;
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < E; ++j) {
+                    const int e = j * 32 + lane;
+                    const int32_t pk = __shfl_xor_sync(0xffffffffu, key[j], s);
+                    const double pv = __shfl_xor_sync(0xffffffffu, val[j], s);
+                    const bool up = (e & k) == 0, lower = (e & s) == 0;
+                    if (lower == up ? pk < key[j] : pk > key[j]) {
+                        key[j] = pk;
+                        val[j] = pv;
+                    }
+                }
+            }
+        }
     }
+}
+template <int E>
+__device__ __forceinline__ void warp_sort_row(int32_t b, int32_t len, int32_t *__restrict__ col,
+                                              double *__restrict__ val, int lane) {
+    int32_t key[E];
+    double v[E];
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+        const int e = j * 32 + lane;
+        key[j] = e < len ? col[b + e] : INT_MAX;
+        v[j] = e < len ? val[b + e] : 0.0;
+    }
+    warp_bitonic<E>(key, v, lane);
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+        const int e = j * 32 + lane;
+        if (e < len) {
+            col[b + e] = key[j];
+            val[b + e] = v[j];
+        }
+    }
+}
+constexpr int kSortWarps = 4;
+__global__ void __launch_bounds__(kSortWarps * 32)
+k_sort_rows(int32_t nrows, const int32_t *__restrict__ ptr, int32_t *__restrict__ col, double *__restrict__ val) {
+    const int lane = threadIdx.x & 31;
+    const int32_t r = blockIdx.x * kSortWarps + (threadIdx.x >> 5);
+    if (r >= nrows) return;  // warp-uniform
+    const int32_t b = ptr[r], e = ptr[r + 1], len = e - b;
+    if (len <= 1) return;
+    if (len <= 64) warp_sort_row<2>(b, len, col, val, lane);
+    else if (len <= 128) warp_sort_row<4>(b, len, col, val, lane);
+    else if (lane == 0)
+        for (int32_t a = b + 1; a < e; ++a) {
+            int32_t c = col[a];
+            double v = val[a];
+            int32_t t = a;
+            while (t > b && col[t - 1] > c) { col[t] = col[t - 1]; val[t] = val[t - 1]; --t; }
+            col[t] = c;
+            val[t] = v;
+        }
 }
 
 // ------------------------------------------------------------------ symbolic product
@@ -694,23 +769,53 @@ __global__ void k_t2_count(int32_t nc, const int32_t *__restrict__ R_ptr, const 
 }
 
 // slot2[t]: position within coarse row I of the column of the t-th term
-// (R entry (I,i) in column order, then row i of A*P in column order)
-__global__ void k_t2_fill(int32_t nc, const int32_t *__restrict__ R_ptr, const int32_t *__restrict__ R_col,
-                          const int32_t *__restrict__ AP_ptr, const int32_t *__restrict__ AP_col,
-                          const int32_t *__restrict__ Ac_ptr, const int32_t *__restrict__ Ac_col,
-                          const int32_t *__restrict__ t2ptr, uint16_t *__restrict__ slot2, int *st) {
-    int32_t I = blockIdx.x * blockDim.x + threadIdx.x;
-    if (I >= nc) return;
-    int64_t t = t2ptr[I];
-    const int32_t b = Ac_ptr[I], e = Ac_ptr[I + 1];
-    for (int32_t r = R_ptr[I]; r < R_ptr[I + 1]; ++r) {
-        int32_t i = R_col[r];
-        for (int32_t q = AP_ptr[i]; q < AP_ptr[i + 1]; ++q) {
-            int32_t c = AP_col[q];
-            int32_t pos = find_in_row(Ac_col, b, e, c);
-            if (pos >= e || Ac_col[pos] != c) { atomicOr(st, DEV_ERR_STATE); pos = b; }
-            slot2[t++] = (uint16_t)(pos - b);
+// (R entry (I,i) in column order, then row i of A*P in column order).  One
+// warp per coarse row: the row's columns of A_c staged in shared memory (rows
+// of up to kT2Cols entries; longer ones are searched in place), the lanes over
+// the R entries, the prefix of their A P row lengths giving each term's index
+constexpr int kT2Warps = 4;
+constexpr int kT2Cols = 1024;
+__global__ void __launch_bounds__(kT2Warps * 32)
+k_t2_fill(int32_t nc, const int32_t *__restrict__ R_ptr, const int32_t *__restrict__ R_col,
+               const int32_t *__restrict__ AP_ptr, const int32_t *__restrict__ AP_col,
+               const int32_t *__restrict__ Ac_ptr, const int32_t *__restrict__ Ac_col,
+               const int32_t *__restrict__ t2ptr, uint16_t *__restrict__ slot2, int *st) {
+    __shared__ int32_t s_cols[kT2Warps][kT2Cols];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int32_t I = blockIdx.x * kT2Warps + w;
+    if (I >= nc) return;  // warp-uniform
+    const int32_t b = Ac_ptr[I], L = Ac_ptr[I + 1] - b;
+    const int32_t *cols = Ac_col + b;
+    if (L <= kT2Cols) {
+        for (int32_t x = lane; x < L; x += 32) s_cols[w][x] = cols[x];
+        __syncwarp();
+        cols = s_cols[w];
+    }
+    const int64_t t0 = t2ptr[I];
+    const int32_t r1 = R_ptr[I + 1];
+    int64_t carry = 0;
+    for (int32_t rc = R_ptr[I]; rc < r1; rc += 32) {
+        const int32_t r = rc + lane;
+        int32_t q0 = 0, len = 0;
+        if (r < r1) {
+            const int32_t i = R_col[r];
+            q0 = AP_ptr[i];
+            len = AP_ptr[i + 1] - q0;
         }
+        int32_t inc = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const int64_t t = t0 + carry + (inc - len);
+        for (int32_t q = 0; q < len; ++q) {
+            const int32_t c = AP_col[q0 + q];
+            int32_t pos = find_in_row(cols, 0, L, c);
+            if (pos >= L || cols[pos] != c) { atomicOr(st, DEV_ERR_STATE); pos = 0; }
+            slot2[t + q] = (uint16_t)pos;
+        }
+        carry += __shfl_sync(0xffffffffu, inc, 31);
     }
 }
 
@@ -978,7 +1083,8 @@ void launch_transpose_scatter(int32_t n, const int32_t *P_ptr, const int32_t *P_
 }
 void launch_sort_rows(int32_t nrows, const int32_t *ptr, int32_t *col, double *val, cudaStream_t s) {
     count_launch();
-    k_sort_rows<<<nblocks(nrows, 128), 128, 0, s>>>(nrows, ptr, col, val);
+    if (nrows <= 0) return;
+    k_sort_rows<<<(unsigned)((nrows + kSortWarps - 1) / kSortWarps), kSortWarps * 32, 0, s>>>(nrows, ptr, col, val);
 }
 
 void launch_row_terms_max(int32_t nrows, const int32_t *X_ptr, const int32_t *X_col, const int32_t *Y_ptr,
@@ -1032,7 +1138,10 @@ void launch_t2_fill(int32_t nc, const int32_t *R_ptr, const int32_t *R_col, cons
                     const int32_t *AP_col, const int32_t *Ac_ptr, const int32_t *Ac_col, const int32_t *t2ptr,
                     uint16_t *slot2, int *st, cudaStream_t s) {
     count_launch();
-    k_t2_fill<<<nblocks(nc, 128), 128, 0, s>>>(nc, R_ptr, R_col, AP_ptr, AP_col, Ac_ptr, Ac_col, t2ptr, slot2, st);
+    if (nc <= 0) return;
+    k_t2_fill<<<(unsigned)((nc + kT2Warps - 1) / kT2Warps), kT2Warps * 32, 0, s>>>(nc, R_ptr, R_col, AP_ptr,
+                                                                                     AP_col, Ac_ptr, Ac_col, t2ptr,
+                                                                                     slot2, st);
 }
 void launch_group_terms(int32_t nrows, const int32_t *tptr, const uint16_t *slot, const int32_t *out_ptr,
                         int32_t *eptr, int32_t *perm, int *st, cudaStream_t s) {
