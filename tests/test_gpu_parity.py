@@ -213,7 +213,7 @@ def vcycle_envelope(H, r, npre=1, npost=1):
     return cycle(0, np.abs(r))
 
 
-@pytest.mark.parametrize("dim,N", [(2, 32), (3, 48), (3, 64)])
+@pytest.mark.parametrize("dim,N", [(2, 32), (3, 40), (3, 48), (3, 64)])
 def test_vcycle_matches_oracle(dim, N):
     """Entry by entry.  Every level's operators are bit-identical to the
     oracle's and every sweep keeps its order; the one difference is the
