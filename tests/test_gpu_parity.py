@@ -317,20 +317,23 @@ def test_host_buffer_entry_point(pinned):
         assert np.linalg.norm(hu - uo) <= 1e-5 * np.linalg.norm(uo)
 
 
-@pytest.mark.parametrize("precision,dim,N", [("fp64", 3, 37), ("mixed", 3, 40), ("fp64", 2, 9)])
-def test_host_entry_point_chunked_equals_device_path(precision, dim, N):
+@pytest.mark.parametrize("precision,dim,N,every", [("fp64", 3, 37, 0), ("mixed", 3, 40, 0), ("fp64", 2, 9, 0),
+                                                   ("mixed", 3, 33, 3)])
+def test_host_entry_point_chunked_equals_device_path(precision, dim, N, every):
     """From the second partial step on, amg_step_solve_host sends the values in
     row chunks and starts each chunk's ingest and its rows of the finest A P as
     soon as the chunk has landed.  Over consecutive steps its solutions,
     iteration counts and coarse operators are those of the device-buffer path
     bit for bit: on a grid whose row count the chunk boundaries do not divide
     (37^3), in mixed precision (40^3), and on a one-level hierarchy whose
-    chunks are mostly empty (9^2 = 81 rows)."""
+    chunks are mostly empty (9^2 = 81 rows).  With a preventive full setup
+    every third step (steps 2 and 5 chunked, step 3 a full setup), the chunk
+    boundaries must follow the new hierarchy."""
     T = 6
     prec = B.PREC_MIXED if precision == "mixed" else B.PREC_FP64
     n = N ** dim
     ptr, col, v0 = gpu_problem(dim, N, 0, T)
-    Gh, Gd = B.AMG(precision=prec), B.AMG(precision=prec)
+    Gh, Gd = B.AMG(precision=prec, rebuild_every=every), B.AMG(precision=prec, rebuild_every=every)
     Gh.step(v0, ptr, col)
     Gd.step(v0, ptr, col)
     hu = torch.empty(n, dtype=torch.float64).pin_memory()
@@ -341,7 +344,7 @@ def test_host_entry_point_chunked_equals_device_path(precision, dim, N):
         ih = Gh.step_solve_host(hv.numpy(), hf.numpy(), hu.numpy(), 1e-8)
         info = Gd.step(vk)
         ud, idd = Gd.solve(torch.tensor(f, device="cuda"), 1e-8)
-        assert ih.status == idd.status == 0 and ih.rebuilt == info.rebuilt == 0
+        assert ih.status == idd.status == 0 and ih.rebuilt == info.rebuilt == (1 if every and k % every == 0 else 0)
         assert ih.iters == idd.iters, (k, ih.iters, idd.iters)
         assert np.array_equal(hu.numpy(), ud.cpu().numpy()), f"solution, step {k}"
         assert Gh.nlevels == Gd.nlevels
