@@ -295,14 +295,19 @@ amg_status symbolic_product(amg_ctx *ctx, int32_t nrows, int32_t ncols, const in
     int32_t max_terms = 0;
     TRY(read_scalar(ctx, d_max, &max_terms));
     const int cap = spgemm_symbolic_cap(max_terms);
-    launch_spgemm_symbolic(nrows, ncols, X_ptr, X_col, Y_ptr, Y_col, add_diag, cap, len, nullptr, nullptr, ctx->d_st,
-                           ctx->s);
+    // lanes per row from X's average row length (its entries are spread over the lanes)
+    int32_t xnnz = 0;
+    TRY(read_scalar(ctx, X_ptr + nrows, &xnnz));
+    const double avg = nrows > 0 ? (double)xnnz / (double)nrows : 0.0;
+    const int lanes = avg <= 8.0 ? 8 : avg <= 16.0 ? 16 : 32;
+    launch_spgemm_symbolic(nrows, ncols, X_ptr, X_col, Y_ptr, Y_col, add_diag, cap, lanes, len, nullptr, nullptr,
+                           ctx->d_st, ctx->s);
     TRY(scan(ctx, len, *C_ptr, nrows));
     TRY(check_device(ctx, "symbolic product"));
     TRY(read_scalar(ctx, *C_ptr + nrows, C_nnz));
     TRY(alloc(ctx, C_col, (size_t)*C_nnz));
-    launch_spgemm_symbolic(nrows, ncols, X_ptr, X_col, Y_ptr, Y_col, add_diag, cap, len, *C_ptr, *C_col, ctx->d_st,
-                           ctx->s);
+    launch_spgemm_symbolic(nrows, ncols, X_ptr, X_col, Y_ptr, Y_col, add_diag, cap, lanes, len, *C_ptr, *C_col,
+                           ctx->d_st, ctx->s);
     return AMG_OK;
 }
 

@@ -191,9 +191,10 @@ void launch_sort_rows(int32_t nrows, const int32_t *ptr, int32_t *col, double *v
 void launch_row_terms_max(int32_t nrows, const int32_t *X_ptr, const int32_t *X_col, const int32_t *Y_ptr,
                           int add_diag, int *out, cudaStream_t s);
 int spgemm_symbolic_cap(int32_t max_terms);
+// (lanes per row: 8, 16 or 32, from X's average row length)
 void launch_spgemm_symbolic(int32_t nrows, int32_t ncols, const int32_t *X_ptr, const int32_t *X_col,
-                            const int32_t *Y_ptr, const int32_t *Y_col, int add_diag, int cap, int32_t *len,
-                            const int32_t *C_ptr, int32_t *C_col, int *st, cudaStream_t s);
+                            const int32_t *Y_ptr, const int32_t *Y_col, int add_diag, int cap, int lanes,
+                            int32_t *len, const int32_t *C_ptr, int32_t *C_col, int *st, cudaStream_t s);
 void launch_t1_count(int32_t n, const int32_t *A_ptr, const int32_t *A_col, const int32_t *P_ptr, int32_t *cnt,
                      cudaStream_t s);
 void launch_t1_fill(int32_t n, const int32_t *A_ptr, const int32_t *A_col, const int32_t *P_ptr,

@@ -672,50 +672,58 @@ __global__ void k_row_terms_max(int32_t nrows, const int32_t *__restrict__ X_ptr
     if ((threadIdx.x & 31) == 0) atomicMax(out, c);
 }
 
-// one warp per row of C = X * Y: union of the Y-rows selected by X's row
+// G lanes per row of C = X * Y (32 / G rows per warp, each with its own hash
+// table): the union of the Y-rows selected by X's row.  The warp's rows run
+// the same code with warp-wide syncs; a row past the end takes part with no
+// entries.
+template <int G>
 __global__ void k_spgemm_symbolic(int32_t nrows, int32_t ncols, const int32_t *__restrict__ X_ptr,
                                   const int32_t *__restrict__ X_col, const int32_t *__restrict__ Y_ptr,
                                   const int32_t *__restrict__ Y_col, int add_diag, int cap, int shift,
                                   int32_t *__restrict__ len, const int32_t *__restrict__ C_ptr,
                                   int32_t *__restrict__ C_col, int *st) {
     extern __shared__ int32_t smem[];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int lcap = cap / 2;  // distinct columns a row may hold
-    int32_t *keys = smem + w * (cap + lcap + 2);
+    const int lane = threadIdx.x & 31, sub = lane % G;
+    const int g = threadIdx.x / G;  // the row's group within the block
+    const int lcap = cap / 2;       // distinct columns a row may hold
+    int32_t *keys = smem + g * (cap + lcap + 2);
     int32_t *list = keys + cap;
     int32_t *cnt = list + lcap;
-    const int32_t row = blockIdx.x * (blockDim.x >> 5) + w;
-    if (row >= nrows) return;  // warp-uniform
-    for (int h = lane; h < cap; h += 32) keys[h] = -1;
-    if (lane == 0) { cnt[0] = 0; cnt[1] = 0; }
+    const int32_t row = blockIdx.x * (blockDim.x / G) + g;
+    const bool live = row < nrows;
+    for (int h = sub; h < cap; h += G) keys[h] = -1;
+    if (sub == 0) { cnt[0] = 0; cnt[1] = 0; }
     __syncwarp();
     bool ok = true;
-    if (add_diag && row < ncols && lane == 0) ok = hash_insert(keys, &cnt[0], row, cap, shift);
-    for (int32_t p = X_ptr[row] + lane; p < X_ptr[row + 1]; p += 32) {
-        int32_t k = X_col[p];
-        for (int32_t q = Y_ptr[k]; q < Y_ptr[k + 1] && ok; ++q) ok = hash_insert(keys, &cnt[0], Y_col[q], cap, shift);
-    }
+    if (live && add_diag && row < ncols && sub == 0) ok = hash_insert(keys, &cnt[0], row, cap, shift);
+    if (live)
+        for (int32_t p = X_ptr[row] + sub; p < X_ptr[row + 1]; p += G) {
+            int32_t k = X_col[p];
+            for (int32_t q = Y_ptr[k]; q < Y_ptr[k + 1] && ok; ++q) ok = hash_insert(keys, &cnt[0], Y_col[q], cap, shift);
+        }
     __syncwarp();
     const int32_t L = cnt[0];
-    if (!__all_sync(0xffffffffu, ok) || L > lcap) {
+    const bool bad = !__all_sync(0xffffffffu, ok) || __any_sync(0xffffffffu, live && L > lcap);
+    if (bad) {
         if (lane == 0) atomicOr(st, DEV_ERR_CAPACITY);
         return;
     }
     if (C_ptr == nullptr) {
-        if (lane == 0) len[row] = L;
+        if (live && sub == 0) len[row] = L;
         return;
     }
-    for (int h = lane; h < cap; h += 32) {
+    for (int h = sub; h < cap; h += G) {
         int32_t c = keys[h];
         if (c >= 0) list[atomicAdd(&cnt[1], 1)] = c;
     }
     __syncwarp();
+    if (!live) return;
     const int32_t base = C_ptr[row];
     if (C_ptr[row + 1] - base != L) {
-        if (lane == 0) atomicOr(st, DEV_ERR_STATE);
+        if (sub == 0) atomicOr(st, DEV_ERR_STATE);
         return;
     }
-    for (int32_t e = lane; e < L; e += 32) {
+    for (int32_t e = sub; e < L; e += G) {
         int32_t v = list[e], rank = 0;
         for (int32_t x = 0; x < L; ++x) rank += list[x] < v;
         C_col[base + rank] = v;
@@ -1098,24 +1106,41 @@ int spgemm_symbolic_cap(int32_t max_terms) {
     while (cap < kHashCap && cap < 2 * max_terms) cap *= 2;
     return cap;
 }
-void launch_spgemm_symbolic(int32_t nrows, int32_t ncols, const int32_t *X_ptr, const int32_t *X_col,
-                            const int32_t *Y_ptr, const int32_t *Y_col, int add_diag, int cap, int32_t *len,
-                            const int32_t *C_ptr, int32_t *C_col, int *st, cudaStream_t s) {
-    if (nrows <= 0) return;
+namespace {
+template <int G>
+void launch_symbolic_g(int32_t nrows, int32_t ncols, const int32_t *X_ptr, const int32_t *X_col,
+                       const int32_t *Y_ptr, const int32_t *Y_col, int add_diag, int cap, int shift, int32_t *len,
+                       const int32_t *C_ptr, int32_t *C_col, int *st, cudaStream_t s) {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_spgemm_symbolic, cudaFuncAttributeMaxDynamicSharedMemorySize, kSymSmemMax);
+        cudaFuncSetAttribute(k_spgemm_symbolic<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSymSmemMax);
         attr_set = true;
     }
+    const size_t per_row = (size_t)(cap + cap / 2 + 2) * sizeof(int32_t);
+    int warps = 8;
+    while (warps > 1 && per_row * (size_t)(warps * 32 / G) > (size_t)kSymSmemMax) warps >>= 1;
+    const int rows = warps * 32 / G;
+    const unsigned grid = (unsigned)((nrows + rows - 1) / rows);
+    count_launch();
+    k_spgemm_symbolic<G><<<grid, warps * 32, per_row * (size_t)rows, s>>>(nrows, ncols, X_ptr, X_col, Y_ptr, Y_col,
+                                                                         add_diag, cap, shift, len, C_ptr, C_col, st);
+}
+}  // namespace
+
+void launch_spgemm_symbolic(int32_t nrows, int32_t ncols, const int32_t *X_ptr, const int32_t *X_col,
+                            const int32_t *Y_ptr, const int32_t *Y_col, int add_diag, int cap, int lanes,
+                            int32_t *len, const int32_t *C_ptr, int32_t *C_col, int *st, cudaStream_t s) {
+    if (nrows <= 0) return;
     int shift = 32;
     for (int c = cap; c > 1; c >>= 1) --shift;  // cap = 2^(32 - shift)
-    const size_t per_warp = (size_t)(cap + cap / 2 + 2) * sizeof(int32_t);
-    int warps = 8;
-    while (warps > 1 && per_warp * (size_t)warps > (size_t)kSymSmemMax) warps >>= 1;
-    const unsigned grid = (unsigned)((nrows + warps - 1) / warps);
-    count_launch();
-    k_spgemm_symbolic<<<grid, warps * 32, per_warp * (size_t)warps, s>>>(nrows, ncols, X_ptr, X_col, Y_ptr, Y_col,
-                                                                        add_diag, cap, shift, len, C_ptr, C_col, st);
+    if (lanes <= 8)
+        launch_symbolic_g<8>(nrows, ncols, X_ptr, X_col, Y_ptr, Y_col, add_diag, cap, shift, len, C_ptr, C_col, st, s);
+    else if (lanes <= 16)
+        launch_symbolic_g<16>(nrows, ncols, X_ptr, X_col, Y_ptr, Y_col, add_diag, cap, shift, len, C_ptr, C_col, st,
+                              s);
+    else
+        launch_symbolic_g<32>(nrows, ncols, X_ptr, X_col, Y_ptr, Y_col, add_diag, cap, shift, len, C_ptr, C_col, st,
+                              s);
 }
 
 void launch_t1_count(int32_t n, const int32_t *A_ptr, const int32_t *A_col, const int32_t *P_ptr, int32_t *cnt,
